@@ -1,0 +1,282 @@
+"""Plain FP64 CPU oracle for the EIFMM evaluation path (arXiv:1408.0210).
+
+TEST INFRASTRUCTURE ONLY.  This package is the slow, obviously-correct CPU
+reference the GPU library is checked against.  Only the test suite, the smoke
+check and the CPU-baseline leg of the benchmark may import it; the GPU library
+never imports, links or calls it, and the two share no code.
+
+The arithmetic lives in ``eifmm_oracle.c`` (plain C, FP64, no fused
+multiply-add); this module only compiles it and marshals numpy arrays.
+
+  * ``direct_sum``  -- O1, Eq. (1), the exact definition.
+  * ``eim``         -- Algorithm 1 with the Gamma recursion of Section 2.
+  * ``eifmm``       -- O2, Algorithm 3 plus the near field, step by step.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "eifmm_oracle.c")
+_LIB = os.path.join(_HERE, "liborc.so")
+
+KERNELS = {
+    "inv_r": 0,
+    "config3": 1,
+    "quad": 2,
+    "one": 3,
+    "exp_r2": 4,
+    "cos20r_r": 5,
+    "sqrt_r2p1": 6,
+}
+MAX_LEVEL = 10
+TRAIN_NJ = 9
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library in place (gcc, OpenMP if present)."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC),
+                                             os.path.getmtime(os.path.join(_HERE, "eifmm_oracle.h")))):
+        return _LIB
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
+            "-fno-fast-math", "-o", _LIB + ".tmp", _SRC, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class _Dump(C.Structure):
+    _fields_ = [
+        ("W", C.c_void_p * (MAX_LEVEL + 1)),
+        ("What", C.c_void_p * (MAX_LEVEL + 1)),
+        ("g", C.c_void_p * (MAX_LEVEL + 1)),
+        ("l", C.c_void_p * (MAX_LEVEL + 1)),
+        ("lhat", C.c_void_p),
+        ("f_far", C.c_void_p),
+        ("f_near", C.c_void_p),
+        ("domain_violations", C.c_int64),
+        ("m2l_pairs", C.c_int64),
+        ("p2p_pairs", C.c_int64),
+    ]
+
+
+class _Level(C.Structure):
+    _fields_ = [("d", C.c_int), ("X", C.c_void_p), ("Y", C.c_void_p),
+                ("Gamma", C.c_void_p), ("B", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+        L.orc_kernel.restype = dbl
+        L.orc_kernel.argtypes = [i32, dbl, dbl, dbl]
+        for fn in (L.orc_direct_sum, L.orc_direct_sum_ld):
+            fn.restype = None
+            fn.argtypes = [i32, vp, i64, vp, i64, vp, i64, i32, i32, vp, i64, vp]
+        L.orc_morton_keys.restype = i64
+        L.orc_morton_keys.argtypes = [vp, i64, vp, dbl, i32, vp]
+        L.orc_sort_leaves.restype = None
+        L.orc_sort_leaves.argtypes = [vp, i64, i32, vp, vp]
+        L.orc_train_x.restype = i64
+        L.orc_train_x.argtypes = [i32, dbl, vp]
+        L.orc_train_y.restype = i64
+        L.orc_train_y.argtypes = [i32, dbl, i32, vp]
+        L.orc_eim.restype = i32
+        L.orc_eim.argtypes = [i32, vp, i64, vp, i64, dbl, i32, vp, vp, vp, vp, vp, vp]
+        L.orc_apply_delta.restype = None
+        L.orc_apply_delta.argtypes = [i32, vp, vp, vp]
+        L.orc_apply_delta_t.restype = None
+        L.orc_apply_delta_t.argtypes = [i32, vp, vp, vp]
+        L.orc_eifmm.restype = i32
+        L.orc_eifmm.argtypes = [i32, dbl, vp, i32, vp, vp, i64, vp, i64, vp, i64,
+                                i32, i32, vp, i64, vp]
+        L.orc_interaction_list.restype = i32
+        L.orc_interaction_list.argtypes = [i32, i64, vp]
+        L.orc_neighbours.restype = i32
+        L.orc_neighbours.argtypes = [i32, i64, vp]
+        L.orc_num_threads.restype = i32
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _kid(kern) -> int:
+    return KERNELS[kern] if isinstance(kern, str) else int(kern)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def kernel(kern, z) -> np.ndarray:
+    """k(z) for an array of displacements z (..., 3)."""
+    z = np.asarray(z, dtype=np.float64)
+    flat = z.reshape(-1, 3)
+    out = np.array([lib().orc_kernel(_kid(kern), *row) for row in flat])
+    return out.reshape(z.shape[:-1])
+
+
+def _col_major(sigma: np.ndarray) -> np.ndarray:
+    s = np.asarray(sigma, dtype=np.float64)
+    if s.ndim == 1:
+        s = s[:, None]
+    return np.asfortranarray(s)
+
+
+def direct_sum(kern, tgt, src, sigma, exclude_self=True, tgt_idx=None,
+               long_double=False) -> np.ndarray:
+    """O1, Eq. (1).  Returns f with shape (n_eval, nrhs)."""
+    tgt = np.ascontiguousarray(tgt, dtype=np.float64)
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    s = _col_major(sigma)
+    nrhs = s.shape[1]
+    idx = None if tgt_idx is None else np.ascontiguousarray(tgt_idx, dtype=np.int64)
+    n_eval = len(tgt) if idx is None else len(idx)
+    f = np.zeros((n_eval, nrhs), dtype=np.float64, order="F")
+    fn = lib().orc_direct_sum_ld if long_double else lib().orc_direct_sum
+    fn(_kid(kern), _p(tgt), len(tgt), _p(src), len(src), _p(s), s.shape[0], nrhs,
+       int(bool(exclude_self)), None if idx is None else _p(idx), n_eval, _p(f))
+    return np.ascontiguousarray(f)
+
+
+def morton_keys(xyz, lo, L, depth):
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    keys = np.zeros(len(xyz), dtype=np.uint32)
+    outside = lib().orc_morton_keys(_p(xyz), len(xyz), _p(lo), float(L), depth, _p(keys))
+    return keys, int(outside)
+
+
+def sort_leaves(keys, depth):
+    keys = np.ascontiguousarray(keys, dtype=np.uint32)
+    perm = np.zeros(len(keys), dtype=np.int32)
+    off = np.zeros((1 << (3 * depth)) + 1, dtype=np.int64)
+    lib().orc_sort_leaves(_p(keys), len(keys), depth, _p(perm), _p(off))
+    return perm, off
+
+
+def train_x(level, L=1.0):
+    n = lib().orc_train_x(level, float(L), None)
+    X = np.zeros((n, 3))
+    lib().orc_train_x(level, float(L), _p(X))
+    return X
+
+
+def train_y(level, L=1.0, nJ=TRAIN_NJ):
+    n = lib().orc_train_y(level, float(L), nJ, None)
+    Y = np.zeros((n, 3))
+    lib().orc_train_y(level, float(L), nJ, _p(Y))
+    return Y
+
+
+def eim(kern, X, Y, eps, d_max=512) -> dict:
+    """Algorithm 1 on the training grids X (D_x) and Y (D_y)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    ia = np.zeros(d_max, dtype=np.int64)
+    ib = np.zeros(d_max, dtype=np.int64)
+    G = np.zeros((d_max, d_max))
+    B = np.zeros((d_max, d_max))
+    piv = np.zeros(d_max + 1)
+    est = np.zeros(1)
+    d = lib().orc_eim(_kid(kern), _p(X), len(X), _p(Y), len(Y), float(eps), d_max,
+                      _p(ia), _p(ib), _p(G), _p(B), _p(piv), _p(est))
+    return dict(d=d, ia=ia[:d].copy(), ib=ib[:d].copy(),
+                Gamma=np.ascontiguousarray(G[:d, :d]),
+                B=np.ascontiguousarray(B[:d, :d]), piv=piv[:d + 1].copy(),
+                eps_est=float(est[0]), X=X[ia[:d]].copy(), Y=Y[ib[:d]].copy())
+
+
+def build_levels(kern, L, depth, eps, d_max=512) -> dict:
+    """EIM of every level k = 2..depth on the default training sets."""
+    return {k: eim(kern, train_x(k, L), train_y(k, L), eps, d_max)
+            for k in range(2, depth + 1)}
+
+
+def apply_delta(Gamma, B, v, transpose=False):
+    v = np.array(v, dtype=np.float64, copy=True)
+    G = np.ascontiguousarray(Gamma, dtype=np.float64)
+    Bm = np.ascontiguousarray(B, dtype=np.float64)
+    fn = lib().orc_apply_delta_t if transpose else lib().orc_apply_delta
+    fn(len(v), _p(G), _p(Bm), _p(v))
+    return v
+
+
+def eifmm(kern, L, lo, depth, levels, tgt, src, sigma, exclude_self=True,
+          dump=False):
+    """O2: Algorithm 3 plus the near field.  Returns f (n_tgt, nrhs), and the
+    intermediate arrays when dump=True (layout [box][rhs][m], Morton order)."""
+    tgt = np.ascontiguousarray(tgt, dtype=np.float64)
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    s = _col_major(sigma)
+    R = s.shape[1]
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    lv = (_Level * (MAX_LEVEL + 1))()
+    keep = []
+    for k in range(2, depth + 1):
+        e = levels[k]
+        arrs = [np.ascontiguousarray(e[n], dtype=np.float64) for n in ("X", "Y", "Gamma", "B")]
+        keep += arrs
+        lv[k] = _Level(e["d"], *[a.ctypes.data for a in arrs])
+    f = np.zeros((len(tgt), R), order="F")
+    dm = None
+    out = {}
+    if dump:
+        dm = _Dump()
+        for k in range(2, depth + 1):
+            d = levels[k]["d"]
+            for name in ("W", "What", "g", "l"):
+                a = np.zeros((8 ** k, R, d))
+                out.setdefault(name, {})[k] = a
+                getattr(dm, name)[k] = a.ctypes.data
+        d = levels[depth]["d"]
+        out["lhat"] = np.zeros((8 ** depth, R, d))
+        dm.lhat = out["lhat"].ctypes.data
+        out["f_far"] = np.zeros((len(tgt), R), order="F")
+        out["f_near"] = np.zeros((len(tgt), R), order="F")
+        dm.f_far = out["f_far"].ctypes.data
+        dm.f_near = out["f_near"].ctypes.data
+    rc = lib().orc_eifmm(_kid(kern), float(L), _p(lo), depth, C.cast(lv, C.c_void_p),
+                         _p(tgt), len(tgt), _p(src), len(src), _p(s), s.shape[0], R,
+                         int(bool(exclude_self)), _p(f), len(tgt),
+                         C.cast(C.pointer(dm), C.c_void_p) if dm is not None else None)
+    if rc != 0:
+        raise ValueError(f"orc_eifmm rejected its arguments (code {rc})")
+    f = np.ascontiguousarray(f)
+    if dump:
+        out["f_far"] = np.ascontiguousarray(out["f_far"])
+        out["f_near"] = np.ascontiguousarray(out["f_near"])
+        out["domain_violations"] = dm.domain_violations
+        out["m2l_pairs"] = dm.m2l_pairs
+        out["p2p_pairs"] = dm.p2p_pairs
+        return f, out
+    return f
+
+
+def interaction_list(level, box):
+    out = np.zeros(189, dtype=np.int64)
+    n = lib().orc_interaction_list(level, box, _p(out))
+    return out[:n].copy()
+
+
+def neighbours(level, box):
+    out = np.zeros(27, dtype=np.int64)
+    n = lib().orc_neighbours(level, box, _p(out))
+    return out[:n].copy()

@@ -1,0 +1,389 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Each check ties an oracle function to something independent of it: values
+computed by hand, closed forms, brute force on tiny inputs, the interpolation
+property of Section 2 (Property 2.1), exactness on separable low-rank kernels,
+the structural facts of the tree and lists (Sections 3.2-3.3) and the
+convergence of the method as the EIM tolerance shrinks.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1408_0210_gb300 import workloads as wl
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# O1, Eq. (1)
+# --------------------------------------------------------------------------
+def test_direct_sum_hand_example(orc):
+    g = json.load(open(os.path.join(GOLD, "direct_sum_hand.json")))
+    x = np.array(g["points"])
+    f = orc.direct_sum("inv_r", x, x, np.array(g["sigma"]))[:, 0]
+    np.testing.assert_allclose(f, g["f"], rtol=1e-15, atol=0)
+
+
+def test_direct_sum_closed_forms(orc):
+    x = wl.uniform_cube(700, 11)
+    y = wl.uniform_cube(500, 12)
+    s = wl.sigma_uniform(500, 2, 13)
+    # K = 1: f_i = sum_j sigma_j
+    f = orc.direct_sum("one", x, y, s, exclude_self=False)
+    np.testing.assert_allclose(f, np.tile(s.sum(0), (700, 1)), rtol=1e-12)
+    # K = |x - y|^2 = |x|^2 S0 - 2 x.S1 + S2 with moments of the sources
+    f = orc.direct_sum("quad", x, y, s, exclude_self=False)
+    S0, S1, S2 = s.sum(0), y.T @ s, ((y * y).sum(1)) @ s
+    ref = (x * x).sum(1)[:, None] * S0 - 2 * x @ S1 + S2
+    np.testing.assert_allclose(f, ref, rtol=1e-11)
+    # self exclusion: sets coincide, K = 1 gives S - sigma_i
+    f = orc.direct_sum("one", y, y, s, exclude_self=True)
+    np.testing.assert_allclose(f, s.sum(0) - s, rtol=1e-12, atol=1e-12)
+
+
+def test_direct_sum_shell_potential(orc):
+    # every point of a sphere of radius a is at distance a from its centre
+    n = 2000
+    i = np.arange(n) + 0.5
+    phi = np.arccos(1 - 2 * i / n)
+    th = math.pi * (1 + 5 ** 0.5) * i
+    a = 0.37
+    c = np.array([0.5, 0.5, 0.5])
+    pts = c + a * np.stack([np.cos(th) * np.sin(phi), np.sin(th) * np.sin(phi), np.cos(phi)], 1)
+    s = wl.sigma_uniform(n, 1, 5)
+    f = orc.direct_sum("inv_r", c[None], pts, s, exclude_self=False)
+    assert abs(f[0, 0] - s.sum() / a) <= 1e-12 * np.abs(s).sum() / a
+
+
+def test_direct_sum_summation_accuracy_and_subset(orc):
+    x = wl.uniform_cube(4096, 1)
+    s = wl.sigma_uniform(4096, 1, 101)
+    f = orc.direct_sum("inv_r", x, x, s)
+    fl = orc.direct_sum("inv_r", x, x, s, long_double=True)
+    assert np.linalg.norm(f - fl) / np.linalg.norm(fl) < 1e-13
+    idx = wl.sample_targets(4096, 100, 7)
+    fs = orc.direct_sum("inv_r", x, x, s, tgt_idx=idx)
+    np.testing.assert_array_equal(fs, f[idx])
+
+
+# --------------------------------------------------------------------------
+# Tree (Section 3.3)
+# --------------------------------------------------------------------------
+def _morton_py(ix, iy, iz, depth):
+    key = 0
+    for b in range(depth):
+        key |= ((ix >> b) & 1) << (3 * b)
+        key |= ((iy >> b) & 1) << (3 * b + 1)
+        key |= ((iz >> b) & 1) << (3 * b + 2)
+    return key
+
+
+@pytest.mark.parametrize("depth", [1, 3, 5])
+def test_morton_keys_exact(orc, depth):
+    x = wl.uniform_cube(3000, 21 + depth)
+    x[0] = [1.0, 0.0, 1.0]          # upper faces clamp into the last box
+    x[1] = [0.5, 0.25, 0.125]       # exactly on box boundaries
+    keys, outside = orc.morton_keys(x, [0.0, 0.0, 0.0], 1.0, depth)
+    assert outside == 0
+    n = 1 << depth
+    for i in range(len(x)):
+        c = [min(n - 1, int(math.floor(Fraction(v) * n))) for v in x[i]]
+        assert keys[i] == _morton_py(*c, depth)
+
+
+def test_morton_keys_general_box_and_outside(orc):
+    lo = np.array([-0.5, 2.0, 10.0])
+    L = 2.0
+    x = lo + L * wl.uniform_cube(500, 3)
+    x[0, 0] = lo[0] - 1e-9
+    x[1, 2] = lo[2] + L + 1e-9
+    keys, outside = orc.morton_keys(x, lo, L, 4)
+    assert outside == 2
+    for i in range(2, len(x)):
+        t = [(Fraction(x[i, a]) - Fraction(lo[a])) * Fraction(16) / Fraction(L) for a in range(3)]
+        c = [min(15, int(math.floor(v))) for v in t]
+        # FP64 rounding of (x - lo) * 2^k / L can cross an integer only when
+        # the exact value lies within a few ulps of it
+        near_int = any(abs(float(v - round(v))) < 1e-12 for v in t)
+        assert keys[i] == _morton_py(*c, 4) or near_int
+
+
+def test_sort_is_stable_and_offsets(orc):
+    x = wl.gaussian_mixture(5000, 3)
+    keys, _ = orc.morton_keys(x, [0, 0, 0], 1.0, 4)
+    perm, off = orc.sort_leaves(keys, 4)
+    order = np.lexsort((np.arange(len(keys)), keys))
+    np.testing.assert_array_equal(perm, order)
+    counts = np.bincount(keys, minlength=8 ** 4)
+    np.testing.assert_array_equal(np.diff(off), counts)
+    assert off[0] == 0 and off[-1] == len(x)
+
+
+# --------------------------------------------------------------------------
+# Neighbourhood and interaction lists (Sections 3.2, 3.3.2)
+# --------------------------------------------------------------------------
+def _coords(level):
+    n = 1 << level
+    c = np.array([[i, j, k] for k in range(n) for j in range(n) for i in range(n)])
+    keys = np.array([_morton_py(*t, level) for t in c])
+    out = np.zeros_like(c)
+    out[keys] = c
+    return out
+
+
+@pytest.mark.parametrize("level", [2, 3])
+def test_interaction_list_brute_force(orc, level):
+    c = _coords(level)
+    nbox = len(c)
+    total = 0
+    for I in range(nbox):
+        got = sorted(orc.interaction_list(level, I))
+        par = c[I] >> 1
+        exp = [J for J in range(nbox)
+               if np.abs((c[J] >> 1) - par).max() <= 1 and np.abs(c[J] - c[I]).max() > 1]
+        assert got == exp
+        total += len(got)
+    assert total == {2: 3096, 3: 53352}[level]
+
+
+def test_lists_tile_every_leaf_exactly_once(orc):
+    kap = 3
+    nleaf = 8 ** kap
+    for I in [0, 77, 300, 511, 146]:
+        hits = np.zeros(nleaf, dtype=int)
+        for J in orc.neighbours(kap, I):
+            hits[J] += 1
+        for k in range(2, kap + 1):
+            A = I >> (3 * (kap - k))
+            for J in orc.interaction_list(k, A):
+                leaves = np.arange(J << (3 * (kap - k)), (J + 1) << (3 * (kap - k)))
+                hits[leaves] += 1
+        assert (hits == 1).all()
+
+
+def test_interaction_offsets_are_the_316(orc):
+    c = _coords(3)
+    seen = set()
+    for I in range(512):
+        for J in orc.interaction_list(3, I):
+            seen.add(tuple(c[J] - c[I]))
+    assert len(seen) == 7 ** 3 - 3 ** 3
+
+
+# --------------------------------------------------------------------------
+# Training sets and EIM (Section 2, Algorithm 1)
+# --------------------------------------------------------------------------
+def test_training_sets_shape_and_domains(orc):
+    for k, nx in [(2, 15 ** 3 - 5 ** 3), (3, 21 ** 3 - 5 ** 3)]:
+        X, Y = orc.train_x(k), orc.train_y(k)
+        l = 2.0 ** -(k + 1)
+        assert len(X) == nx and len(Y) == 9 ** 3
+        m = np.abs(X).max(1)
+        assert (m >= 3 * l).all() and (m <= 1 - l + 1e-15).all()
+        assert np.abs(Y).max() == l and (np.abs(Y) <= l).all()
+        assert len(np.unique(X, axis=0)) == len(X)
+
+
+def _K(z, kern):
+    r2 = (z * z).sum(-1)
+    return {"inv_r": lambda: 1 / np.sqrt(r2), "quad": lambda: r2, "one": lambda: np.ones_like(r2),
+            "exp_r2": lambda: np.exp(-r2)}[kern]()
+
+
+def _interp(e, x, y, kern, orc):
+    """I_d K(x, y) = sum_{l,m} Delta_lm K(x, y_l) K(x_m, y), Eq. (approx2)."""
+    kx = _K(x[:, None, :] - e["Y"][None], kern)              # K(x, y_l)
+    ky = _K(e["X"][:, None, :] - y[None], kern)              # K(x_m, y)
+    dk = np.stack([orc.apply_delta(e["Gamma"], e["B"], ky[:, j]) for j in range(ky.shape[1])], 1)
+    return kx @ dk
+
+
+@pytest.fixture(scope="module")
+def eim3(orc):
+    X, Y = orc.train_x(3), orc.train_y(3)
+    return X, Y, orc.eim("inv_r", X, Y, 1e-6)
+
+
+def test_eim_structure_and_factorisation(orc, eim3):
+    X, Y, e = eim3
+    d = e["d"]
+    B, G = e["B"], e["Gamma"]
+    assert 100 < d < 300
+    np.testing.assert_array_equal(np.diag(B), np.ones(d))
+    assert np.all(np.triu(B, 1) == 0) and np.all(np.triu(G, 1) == 0)
+    assert np.abs(B).max() <= 1.0 + 1e-12            # |q_m| <= 1 by the argmax
+    A = _K(e["X"][:, None] - e["Y"][None], "inv_r")    # A_kl = K(x_k, y_l)
+    assert np.abs(G @ B.T - A).max() <= 1e-12 * np.abs(A).max()
+    np.testing.assert_allclose(np.abs(np.diag(G)), e["piv"][:d], rtol=0)
+    assert e["eps_est"] <= 1e-6 and e["piv"][d] / e["piv"][0] == e["eps_est"]
+
+
+def test_eim_pivots_are_greedy_argmax(orc, eim3):
+    """Each pivot maximises |delta_k K| over the grid, with delta_k K rebuilt
+    from the four-summation form of the first k terms."""
+    X, Y, e = eim3
+    sub_x = np.concatenate([e["ia"], np.arange(0, len(X), 97)])
+    Aall = _K(X[sub_x][:, None] - Y[None], "inv_r")
+    for k in [1, 5, 40, e["d"] - 1]:
+        ek = dict(X=e["X"][:k], Y=e["Y"][:k], Gamma=e["Gamma"][:k, :k], B=e["B"][:k, :k])
+        R = Aall - _interp(ek, X[sub_x], Y, "inv_r", orc)
+        a, b = e["ia"][k], e["ib"][k]
+        ra = np.where(sub_x == a)[0][0]
+        assert abs(abs(R[ra, b]) - e["piv"][k]) <= 1e-9 * e["piv"][0]
+        assert np.abs(R).max() <= e["piv"][k] * (1 + 1e-7) + 1e-12 * e["piv"][0]
+
+
+def test_eim_interpolation_property(orc, eim3):
+    """Property 2.1: I_d K(x, y_m) = K(x, y_m) and I_d K(x_m, y) = K(x_m, y)."""
+    X, Y, e = eim3
+    l = 2.0 ** -4
+    g = wl.rng(4)
+    xr = g.uniform(-1 + l, 1 - l, size=(400, 3))
+    xr = xr[np.abs(xr).max(1) >= 3 * l]
+    yr = g.uniform(-l, l, size=(300, 3))
+    a = _interp(e, xr, e["Y"], "inv_r", orc)
+    ref = _K(xr[:, None] - e["Y"][None], "inv_r")
+    assert np.abs(a - ref).max() <= 1e-10 * np.abs(ref).max()
+    b = _interp(e, e["X"], yr, "inv_r", orc)
+    ref = _K(e["X"][:, None] - yr[None], "inv_r")
+    assert np.abs(b - ref).max() <= 1e-10 * np.abs(ref).max()
+    # off the grid the error stays within a small factor of the estimate
+    c = _interp(e, xr, yr, "inv_r", orc)
+    ref = _K(xr[:, None] - yr[None], "inv_r")
+    assert np.abs(c - ref).max() <= 50 * e["eps_est"] * e["piv"][0]
+
+
+@pytest.mark.parametrize("kern,rank", [("quad", 5), ("one", 1)])
+def test_eim_exact_on_low_rank_kernels(orc, kern, rank):
+    X, Y = orc.train_x(2), orc.train_y(2)
+    e = orc.eim(kern, X, Y, 1e-10)
+    assert e["d"] == rank
+    g = wl.rng(9)
+    xr = g.uniform(-0.875, 0.875, size=(200, 3))
+    yr = g.uniform(-0.125, 0.125, size=(200, 3))
+    ref = _K(xr[:, None] - yr[None], kern)
+    assert np.abs(_interp(e, xr, yr, kern, orc) - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_eim_convergence_tracks_estimate(orc):
+    """Section 2: the error estimate decreases with d and tracks the error."""
+    X, Y = orc.train_x(2), orc.train_y(2)
+    g = wl.rng(10)
+    xr = g.uniform(-0.875, 0.875, size=(300, 3))
+    xr = xr[np.abs(xr).max(1) >= 0.375]
+    yr = g.uniform(-0.125, 0.125, size=(200, 3))
+    ref = _K(xr[:, None] - yr[None], "inv_r")
+    ds, errs, ests = [], [], []
+    for eps in [1e-2, 1e-3, 1e-4, 1e-5, 1e-6]:
+        e = orc.eim("inv_r", X, Y, eps)
+        err = np.abs(_interp(e, xr, yr, "inv_r", orc) - ref).max() / np.abs(ref).max()
+        ds.append(e["d"]); errs.append(err); ests.append(e["eps_est"])
+        assert e["eps_est"] <= eps
+        assert err <= 50 * e["eps_est"]
+    assert ds == sorted(ds) and len(set(ds)) == len(ds)
+    assert errs[-1] < errs[0] * 5e-3
+    assert all(errs[i + 1] < errs[i] for i in range(len(errs) - 1))
+
+
+def test_apply_delta_is_inverse_of_A(orc, eim3):
+    """Delta = B^-t Gamma^-1 = A^-1 (Section 2, reading of Gamma as lower)."""
+    X, Y, e = eim3
+    d = e["d"]
+    A = _K(e["X"][:, None] - e["Y"][None], "inv_r")
+    v = wl.rng(3).standard_normal(d)
+    w = orc.apply_delta(e["Gamma"], e["B"], A @ v)     # Delta A v = v
+    assert np.abs(w - v).max() <= 1e-6 * np.abs(v).max()
+    u = orc.apply_delta(e["Gamma"], e["B"], v, transpose=True)   # A^t Delta^t v = v
+    assert np.abs(A.T @ u - v).max() <= 1e-8 * np.abs(v).max() * np.abs(A).max() * d
+
+
+# --------------------------------------------------------------------------
+# O2: Algorithm 3 + near field
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kern", ["quad", "one"])
+@pytest.mark.parametrize("depth", [2, 3, 4])
+def test_eifmm_exact_for_separable_kernels(orc, kern, depth):
+    """With an exact rank-d kernel every step of Algorithm 3 is exact, so O2
+    must equal the direct sum to rounding at every tree depth."""
+    x = wl.uniform_cube(1500, 30 + depth)
+    s = wl.sigma_uniform(1500, 2, 31)
+    lv = orc.build_levels(kern, 1.0, depth, 1e-10)
+    assert all(lv[k]["d"] == {"quad": 5, "one": 1}[kern] for k in lv)
+    f2, dm = orc.eifmm(kern, 1.0, [0, 0, 0], depth, lv, x, x, s, dump=True)
+    f1 = orc.direct_sum(kern, x, x, s)
+    assert np.linalg.norm(f2 - f1) / np.linalg.norm(f1) <= 1e-12
+    assert dm["domain_violations"] == 0
+    # the far field alone is a large part of the answer for these kernels
+    assert np.linalg.norm(dm["f_far"]) > 0.1 * np.linalg.norm(f1)
+
+
+@pytest.fixture(scope="module")
+def c1_levels(orc):
+    return {eps: orc.build_levels("inv_r", 1.0, 3, eps) for eps in (1e-4, 1e-6)}
+
+
+def test_eifmm_inv_r_c1(orc, c1_levels):
+    x = wl.uniform_cube(4096, 1)
+    s = wl.sigma_uniform(4096, 1, 101)
+    f1 = orc.direct_sum("inv_r", x, x, s)
+    errs = []
+    for eps in (1e-4, 1e-6):
+        f2, dm = orc.eifmm("inv_r", 1.0, [0, 0, 0], 3, c1_levels[eps], x, x, s, dump=True)
+        err = np.linalg.norm(f2 - f1) / np.linalg.norm(f1)
+        errs.append(err)
+        assert err <= eps
+        assert dm["domain_violations"] == 0
+        assert dm["m2l_pairs"] == 3096 + 53352
+        np.testing.assert_allclose(dm["f_far"] + dm["f_near"], f2, rtol=1e-14, atol=1e-14)
+    assert errs[1] < errs[0] / 5
+
+
+def test_eifmm_p2p_pairs_brute_force(orc, c1_levels):
+    x = wl.uniform_cube(600, 8)
+    s = wl.sigma_uniform(600, 1, 9)
+    _, dm = orc.eifmm("inv_r", 1.0, [0, 0, 0], 3, c1_levels[1e-4], x, x, s, dump=True)
+    c = np.minimum(np.floor(x * 8).astype(int), 7)
+    near = (np.abs(c[:, None, :] - c[None]).max(-1) <= 1).sum() - len(x)
+    assert dm["p2p_pairs"] == near
+
+
+def test_eifmm_monolevel_is_algorithm2(orc):
+    """Depth 2: only level 2 carries a far field, Algorithm 3 = Algorithm 2."""
+    x = wl.uniform_cube(2000, 40)
+    s = wl.sigma_uniform(2000, 1, 41)
+    lv = orc.build_levels("inv_r", 1.0, 2, 1e-6)
+    f2 = orc.eifmm("inv_r", 1.0, [0, 0, 0], 2, lv, x, x, s)
+    f1 = orc.direct_sum("inv_r", x, x, s)
+    assert np.linalg.norm(f2 - f1) / np.linalg.norm(f1) <= 1e-6
+
+
+def test_eifmm_multi_rhs_and_separate_sets(orc, c1_levels):
+    lv = c1_levels[1e-4]
+    y = wl.gaussian_mixture(3000, 50)
+    x = wl.uniform_cube(800, 51)
+    s = wl.sigma_uniform(3000, 3, 52)
+    f = orc.eifmm("inv_r", 1.0, [0, 0, 0], 3, lv, x, y, s, exclude_self=False)
+    for r in range(3):
+        fr = orc.eifmm("inv_r", 1.0, [0, 0, 0], 3, lv, x, y, s[:, r], exclude_self=False)
+        np.testing.assert_array_equal(f[:, r], fr[:, 0])
+    f1 = orc.direct_sum("inv_r", x, y, s, exclude_self=False)
+    assert np.linalg.norm(f - f1) / np.linalg.norm(f1) <= 1e-4
+
+
+def test_eifmm_translated_domain(orc):
+    """Translation invariance (Section 3.1): shifting Omega and all points
+    together leaves f unchanged."""
+    x = wl.uniform_cube(1500, 60)
+    s = wl.sigma_uniform(1500, 1, 61)
+    lv = orc.build_levels("inv_r", 2.0, 3, 1e-5)
+    lo = np.array([-3.0, 0.5, 7.0])
+    fa = orc.eifmm("inv_r", 2.0, [0, 0, 0], 3, lv, 2 * x, 2 * x, s)
+    fb = orc.eifmm("inv_r", 2.0, lo, 3, lv, lo + 2 * x, lo + 2 * x, s)
+    assert np.linalg.norm(fa - fb) / np.linalg.norm(fa) <= 1e-9
+    f1 = orc.direct_sum("inv_r", 2 * x, 2 * x, s)
+    assert np.linalg.norm(fa - f1) / np.linalg.norm(f1) <= 1e-5
