@@ -1,0 +1,246 @@
+/*
+ * eifmm.h -- C ABI of the GB300 (sm_103a) library for the evaluation phase of
+ * the Empirical Interpolation Fast Multipole Method (EIFMM) of F. Casenave,
+ * "A Fast Summation Method for translation invariant kernels"
+ * (arXiv:1408.0210).
+ *
+ * The library computes, for N targets x_i and sources y_j in a cube Omega,
+ *     f(x_i) = sum_j sigma_j K(x_i, y_j),   K(x, y) = k(x - y)        (Eq. 1)
+ * for many potential vectors sigma, with the multilevel EIFMM (Algorithm 3,
+ * steps 1-7) for the far field and a direct sum over neighbouring leaves for
+ * the near field f_N (Section 3.2).
+ *
+ * Calls:
+ *   eifmm_training_sets / eifmm_eim_build   Algorithm 1 (offline, on the GPU)
+ *   eifmm_ops_load / eifmm_ops_build        operator assembly (Section 4.1)
+ *   eifmm_tree_build                        octree bin/sort (Section 3.3)
+ *   eifmm_evaluate / _host / _batched       Algorithm 3 + near field
+ *
+ * General rules for every entry point:
+ *   - no exceptions cross the ABI; every call returns an eifmm_status and, on
+ *     failure, leaves a message for eifmm_last_error() (thread local);
+ *   - opaque handles are owned by the library and freed by *_destroy;
+ *   - "device" pointers are CUDA global-memory pointers of the current
+ *     device; "host" pointers are ordinary process memory;
+ *   - `stream` is a cudaStream_t (0 = legacy default stream); device work is
+ *     enqueued on it and the call returns without waiting unless stated.
+ *   - kernels are even functions (k(-z) = k(z)); the paper's second EIM
+ *     (J_0, I_0) is then the transpose of the first (Section 3.3).
+ */
+#ifndef EIFMM_H
+#define EIFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* eifmm_stream; /* same type as cudaStream_t */
+
+typedef enum {
+  EIFMM_OK = 0,
+  EIFMM_EINVAL = 1,       /* invalid argument (null pointer, size, domain)   */
+  EIFMM_ENOMEM = 2,       /* device or host allocation failed               */
+  EIFMM_ECUDA = 3,        /* a CUDA call failed; see eifmm_last_error()      */
+  EIFMM_ETIMEOUT = 4,     /* a bounded device-side wait gave up              */
+  EIFMM_EUNSUPPORTED = 5  /* valid request this build does not implement    */
+} eifmm_status;
+
+/* Kernel k(z), z = x - y (Section 5 kernels plus test kernels). */
+typedef enum {
+  EIFMM_KERNEL_INV_R = 0,     /* 1/|z|  (Laplace, Section 5.3)                */
+  EIFMM_KERNEL_CONFIG3 = 1,   /* exp(-|z|)/|z| + 1/sqrt(z0^2+0.01 z1^2+z2^2+1e-3) */
+  EIFMM_KERNEL_QUAD = 2,      /* |z|^2: separable, rank 5 (exactness checks)  */
+  EIFMM_KERNEL_ONE = 3,       /* 1: rank 1                                    */
+  EIFMM_KERNEL_EXP_R2 = 4,    /* exp(-|z|^2)       (Section 5.4)              */
+  EIFMM_KERNEL_COS20R_R = 5,  /* cos(20|z|)/|z|    (Section 5.4)              */
+  EIFMM_KERNEL_SQRT_R2P1 = 6  /* sqrt(|z|^2 + 1)   (Section 5.4)              */
+} eifmm_kernel;
+
+/* Arithmetic of eifmm_evaluate.
+ *   FP64:  every step in FP64 (the plain GPU EIFMM).
+ *   MIXED: the near field in FP32 with compensated summation on coordinates
+ *          local to each leaf; the far field chooses its arithmetic from the
+ *          operators' EIM tolerance eps (see eifmm_ops_plan):
+ *            eps >= 1e-5: M2L on tcgen05 tensor cores with BF16 hi+lo split
+ *                         operands (3 products, FP32 accumulate), P2M, M2M,
+ *                         L2L, L2P and the Delta solves in FP32;
+ *            1e-6 <= eps < 1e-5: M2L with a three-way BF16 split (6
+ *                         products), Delta solves in FP64, the rest FP32;
+ *            eps < 1e-6:  far field in FP64 (only the near field is FP32).
+ */
+typedef enum { EIFMM_PREC_FP64 = 0, EIFMM_PREC_MIXED = 1 } eifmm_precision;
+
+const char* eifmm_last_error(void);
+const char* eifmm_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 (Section 2): the EIM greedy, FP64 on the GPU.                */
+/* ------------------------------------------------------------------------ */
+
+/* Default training sets of level `level` >= 2 for a cube of side L (the paper
+ * leaves them unspecified; Section 2 "training sets"):
+ *   D_y: nJ^3 tensor grid on [-l_k, l_k]^3 including the faces (nJ >= 2);
+ *   D_x: tensor product of the 1D nodes {0, +-1, ..., +-7} * l_k (while
+ *        <= L - l_k) continued by a geometric progression of ratio 1.35 up
+ *        to L - l_k, restricted to max-norm >= 3 l_k (the domain I_0^k).
+ * l_k = L 2^-(level+1).  Row-major (n x 3) host arrays; pass X == NULL / Y ==
+ * NULL to query the counts *nx / *ny only.  Errors: EINVAL for level < 2,
+ * level > 10, nJ < 2, L <= 0 or null count pointers. */
+eifmm_status eifmm_training_sets(int level, double L, int nJ, double* X,
+                                 int64_t* nx, double* Y, int64_t* ny);
+
+/* Algorithm 1 with the L-infinity norm on the grids X (nx x 3, D_x) and Y
+ * (ny x 3, D_y), host FP64.  At each step the pivot is the first maximiser of
+ * |delta_k K| in row-major (x, y) order; the loop stops before pivot k+1 when
+ * |delta_k K(x_{k+1}, y_{k+1})| <= eps |Gamma_11| or when d_max pivots are
+ * taken.  Host outputs (caller-owned):
+ *   *d                      number of interpolation points d
+ *   ia[d_max], ib[d_max]    training indices of x_k and y_k
+ *   Gamma[d_max*d_max]      row-major, lower triangular (leading d x d)
+ *   B[d_max*d_max]          row-major, unit lower triangular (leading d x d)
+ *   piv[d_max+1]            |Gamma_kk| for k < d, then the first rejected pivot
+ *   *eps_est                built-in error estimate piv[d]/piv[0] (Section 2)
+ * For INV_R, QUAD and ONE the arithmetic is IEEE-exact (no fused multiply-add,
+ * correctly rounded sqrt and divide), so the result is reproducible bit for
+ * bit by any implementation that evaluates the same operations.  Device
+ * scratch of nx*ny doubles is allocated and freed inside; the call
+ * synchronises `stream`.  Errors: EINVAL (null pointers, nx/ny < 1, eps <= 0,
+ * d_max < 1 or > 1024), ENOMEM, ECUDA. */
+eifmm_status eifmm_eim_build(eifmm_kernel kern, const double* X, int64_t nx,
+                             const double* Y, int64_t ny, double eps,
+                             int d_max, int* d, int64_t* ia, int64_t* ib,
+                             double* Gamma, double* B, double* piv,
+                             double* eps_est, eifmm_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Operators (Section 4.1 precomputations; M2L matrices of Section 4.2).    */
+/* ------------------------------------------------------------------------ */
+typedef struct eifmm_ops eifmm_ops;
+
+/* EIM data of one level, host FP64, packed row-major: X = x_m^{I_0^k}
+ * (d x 3), Y = y_l^{J_0^k} (d x 3), Gamma and B (d x d) from eifmm_eim_build. */
+typedef struct {
+  int d;
+  const double* X;
+  const double* Y;
+  const double* Gamma;
+  const double* B;
+  double eps_est;
+} eifmm_level_data;
+
+/* Upload the EIM data of levels 2..depth (levels[k], entries 0 and 1 unused)
+ * and assemble on the GPU, in FP64, the 2^D M2M operators
+ * K_M2M^i = K^{I^k, J^{k+1}} Delta^{k+1} and the L2L operators
+ * K_L2L^i = K' (Delta^{k-1})^t by triangular solves (Section 4.1), the 316
+ * M2L matrices K^delta of every level (Section 4.2) and their reduced-
+ * precision copies.  Ownership of the host arrays stays with the caller.
+ * Errors: EINVAL (depth outside [2, 10], d outside [1, 512], null arrays,
+ * L <= 0), ENOMEM, ECUDA. */
+eifmm_status eifmm_ops_load(eifmm_kernel kern, double L, int depth,
+                            const eifmm_level_data* levels, eifmm_ops** out);
+
+/* Convenience: default training sets + eifmm_eim_build(eps, d_max) for every
+ * level 2..depth + eifmm_ops_load. Synchronises `stream`. */
+eifmm_status eifmm_ops_build(eifmm_kernel kern, double L, int depth,
+                             double eps, int d_max, eifmm_stream stream,
+                             eifmm_ops** out);
+
+/* Built-in error estimate eps_k and rank d_k of level k (Section 2). */
+eifmm_status eifmm_ops_error_estimate(const eifmm_ops* ops, int level,
+                                      double* eps_k, int* d_k);
+
+/* Arithmetic tier that EIFMM_PREC_MIXED uses with these operators:
+ * 0 = BF16x3 M2L + FP32 far field, 1 = BF16x6 M2L + FP64 solves,
+ * 2 = FP64 far field.  `tier_override` >= 0 forces a tier (testing). */
+eifmm_status eifmm_ops_plan(eifmm_ops* ops, int tier_override, int* tier);
+
+void eifmm_ops_destroy(eifmm_ops* ops);
+
+/* ------------------------------------------------------------------------ */
+/* Tree (Section 3.3): uniform octree, Morton order, stable bin/sort.       */
+/* ------------------------------------------------------------------------ */
+typedef struct eifmm_tree eifmm_tree;
+
+/* Bin sources and targets into the 8^depth leaves of the cube
+ * [lo, lo + L]^3: leaf coordinate floor((x - lo) * (2^depth / L)) clamped to
+ * [0, 2^depth - 1], Morton key with the x bit lowest, stable sort by key (ties
+ * keep the input order).  src_xyz / tgt_xyz are DEVICE arrays, row-major
+ * n x 3 FP64; tgt_xyz may equal src_xyz.  exclude_self != 0 drops the pair
+ * (i, i) and requires tgt_xyz == src_xyz.  lo is a host array of 3 doubles.
+ * The tree keeps sorted copies; the inputs may be freed afterwards.  Errors:
+ * EINVAL (null pointers, n < 0, depth outside [2, 10], L <= 0, a point
+ * outside the cube, exclude_self with distinct sets), ENOMEM, ECUDA.
+ * Synchronises `stream`. */
+eifmm_status eifmm_tree_build(const double* src_xyz, int64_t n_src,
+                              const double* tgt_xyz, int64_t n_tgt,
+                              const double lo[3], double L, int depth,
+                              int exclude_self, eifmm_stream stream,
+                              eifmm_tree** out);
+
+/* Copy the sorted Morton keys (n), the permutation perm[p] = input index of
+ * sorted position p (n) and the leaf offsets (8^depth + 1) of the sources
+ * (which = 0) or targets (which = 1) to HOST arrays; any output may be NULL.
+ * Synchronous. */
+eifmm_status eifmm_tree_export(const eifmm_tree* tree, int which,
+                               uint32_t* keys, int32_t* perm,
+                               int64_t* leaf_off);
+
+void eifmm_tree_destroy(eifmm_tree* tree);
+
+/* ------------------------------------------------------------------------ */
+/* Evaluation: Algorithm 3 (steps 1-7) + near field f_N (Section 3.2).      */
+/* ------------------------------------------------------------------------ */
+
+/* f = sum_j sigma_j K(x_i, y_j) for n_rhs potential vectors.  sigma and f are
+ * DEVICE arrays, column-major: sigma[j + r*ld_sigma] (n_src x n_rhs), f[i +
+ * r*ld_f] (n_tgt x n_rhs), both FP64 and in the caller's original point
+ * order.  The ops must have been built with the tree's depth and L.  The
+ * tree owns the workspace; the first call for a given (ops, n_rhs) allocates
+ * it and later calls allocate nothing.  Calls that share a tree must not
+ * overlap.  Errors: EINVAL (null, n_rhs < 1 or > 256, ld < n, depth / L
+ * mismatch), ENOMEM, ECUDA. */
+eifmm_status eifmm_evaluate(eifmm_tree* tree, const eifmm_ops* ops,
+                            const double* sigma, int64_t ld_sigma, int n_rhs,
+                            double* f, int64_t ld_f, eifmm_precision prec,
+                            eifmm_stream stream);
+
+/* Same computation with HOST sigma and f (pinned memory recommended): the
+ * call copies sigma to the device, evaluates, copies f back and synchronises
+ * `stream` before returning. */
+eifmm_status eifmm_evaluate_host(eifmm_tree* tree, const eifmm_ops* ops,
+                                 const double* sigma_host, int64_t ld_sigma,
+                                 int n_rhs, double* f_host, int64_t ld_f,
+                                 eifmm_precision prec, eifmm_stream stream);
+
+/* Many independent problems sharing one operator set (same kernel, L and
+ * depth): problem p evaluates trees[p] with DEVICE sigma[p] and f[p]
+ * (one RHS each, ld = n).  Errors as eifmm_evaluate. */
+eifmm_status eifmm_evaluate_batched(eifmm_tree* const* trees,
+                                    const double* const* sigma,
+                                    double* const* f, int n_problems,
+                                    const eifmm_ops* ops,
+                                    eifmm_precision prec,
+                                    eifmm_stream stream);
+
+/* Intermediates of the last eifmm_evaluate on this tree, copied to a HOST
+ * array in the layout [box][rhs][m] (box in Morton order at `level`), FP64:
+ *   what = 0 W (step 1-2), 1 What (step 3), 2 g (step 4), 3 l (step 5),
+ *          4 lhat (step 6, level = depth), 5 f_far, 6 f_near (n_tgt x n_rhs
+ *          column-major, original target order).
+ * `n` is the capacity of `out` in doubles.  Synchronous.  Errors: EINVAL when
+ * nothing was evaluated, the level is out of range or n is too small. */
+eifmm_status eifmm_debug_export(const eifmm_tree* tree, int what, int level,
+                                double* out, int64_t n);
+
+/* Per-step device times (ms) of the last evaluate when timing was enabled
+ * with eifmm_set_timing(1): [P2M, M2M, solve-W, M2L, L2L, solve-l, L2P,
+ * P2P, other]. */
+void eifmm_set_timing(int on);
+eifmm_status eifmm_last_step_times(const eifmm_tree* tree, float* ms9);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EIFMM_H */

@@ -1,0 +1,493 @@
+// api.cu -- the C ABI (include/eifmm.h): handles, validation, workspaces and
+// the dispatch of the evaluation paths.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace eifmm {
+
+static thread_local std::string g_err;
+static bool g_timing = false;
+
+void set_error(const std::string& msg) { g_err = msg; }
+bool timing_enabled() { return g_timing; }
+
+eifmm_status dmalloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    set_error("device allocation of " + std::to_string(bytes) + " bytes failed: " +
+              cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? EIFMM_ENOMEM : EIFMM_ECUDA;
+  }
+  return EIFMM_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+void free_workspace(Workspace* ws) {
+  for (int k = 0; k <= kMaxLevel; ++k) {
+    dfree(ws->W[k]); dfree(ws->Wh[k]); dfree(ws->g[k]);
+    if (k != 2) dfree(ws->l[k]);
+    ws->l[k] = nullptr;
+    dfree(ws->W32[k]); dfree(ws->Wh32[k]); dfree(ws->g32[k]); dfree(ws->wa[k]);
+    ws->W[k] = ws->Wh[k] = ws->g[k] = nullptr;
+    ws->W32[k] = ws->Wh32[k] = ws->g32[k] = nullptr;
+    ws->wa[k] = nullptr;
+  }
+  dfree(ws->lh); dfree(ws->lh32); dfree(ws->sig); dfree(ws->sig32);
+  dfree(ws->fnear); dfree(ws->ffar);
+  ws->lh = nullptr; ws->lh32 = nullptr; ws->sig = nullptr; ws->sig32 = nullptr;
+  ws->fnear = nullptr; ws->ffar = nullptr;
+  ws->ops_id = nullptr;
+  ws->nrhs = 0;
+  ws->prec = -1;
+  ws->tier = -1;
+  ws->evaluated = false;
+}
+
+static void free_streams(Workspace* ws) {
+  if (ws->side) cudaStreamDestroy(ws->side);
+  if (ws->ev_fork) cudaEventDestroy(ws->ev_fork);
+  if (ws->ev_join) cudaEventDestroy(ws->ev_join);
+  for (auto& e : ws->ev_t)
+    if (e) cudaEventDestroy(e);
+  ws->side = nullptr;
+  ws->ev_fork = ws->ev_join = nullptr;
+  for (auto& e : ws->ev_t) e = nullptr;
+  dfree(ws->host_sig);
+  dfree(ws->host_f);
+  ws->host_sig = ws->host_f = nullptr;
+  ws->host_cap = 0;
+}
+
+eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R);  // fmm32.cu
+
+eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec) {
+  Workspace& ws = t->ws;
+  if (!ws.side) {
+    EIFMM_CUDA(cudaStreamCreateWithFlags(&ws.side, cudaStreamNonBlocking));
+    EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_fork, cudaEventDisableTiming));
+    EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_join, cudaEventDisableTiming));
+    for (auto& e : ws.ev_t) EIFMM_CUDA(cudaEventCreate(&e));
+  }
+  const int tier = (prec == EIFMM_PREC_MIXED) ? ops->tier : -1;
+  if (ws.ops_id == (const void*)ops && ws.nrhs == R && ws.prec == prec && ws.tier == tier)
+    return EIFMM_OK;
+  free_workspace(&ws);
+  const int kap = t->depth;
+  const bool fp64_far = (prec == EIFMM_PREC_FP64) || tier == 2;
+  if (fp64_far) {
+    for (int k = 2; k <= kap; ++k) {
+      const size_t n = ((size_t)1 << (3 * k)) * R * ops->lv[k].d;
+      EIFMM_TRY(dalloc(&ws.W[k], n));
+      EIFMM_TRY(dalloc(&ws.Wh[k], n));
+      EIFMM_TRY(dalloc(&ws.g[k], n));
+      if (k == 2) ws.l[k] = ws.g[k];
+      else EIFMM_TRY(dalloc(&ws.l[k], n));
+    }
+    EIFMM_TRY(dalloc(&ws.lh, ((size_t)1 << (3 * kap)) * R * ops->lv[kap].d));
+  } else {
+    EIFMM_TRY(alloc_mixed_workspace(t, ops, R));
+  }
+  EIFMM_TRY(dalloc(&ws.sig, (size_t)(t->src.n > 0 ? t->src.n : 1) * R));
+  EIFMM_TRY(dalloc(&ws.sig32, (size_t)(t->src.n > 0 ? t->src.n : 1) * R));
+  EIFMM_TRY(dalloc(&ws.fnear, (size_t)(t->tgt.n > 0 ? t->tgt.n : 1) * R));
+  EIFMM_TRY(dalloc(&ws.ffar, (size_t)(t->tgt.n > 0 ? t->tgt.n : 1) * R));
+  ws.ops_id = ops;
+  ws.nrhs = R;
+  ws.prec = prec;
+  ws.tier = tier;
+  return EIFMM_OK;
+}
+
+}  // namespace eifmm
+
+using namespace eifmm;
+
+struct eifmm_ops {
+  Ops o;
+};
+struct eifmm_tree {
+  Tree t;
+};
+
+extern "C" const char* eifmm_last_error(void) { return g_err.c_str(); }
+extern "C" const char* eifmm_version(void) { return "eifmm-gb300 0.1 (sm_103a)"; }
+extern "C" void eifmm_set_timing(int on) { g_timing = on != 0; }
+
+static int tier_for_eps(double eps) {
+  if (eps >= 1e-5 * (1.0 - 1e-9)) return 0;
+  if (eps >= 1e-6 * (1.0 - 1e-9)) return 1;
+  return 2;
+}
+
+extern "C" eifmm_status eifmm_ops_load(eifmm_kernel kern, double L, int depth,
+                                       const eifmm_level_data* levels, eifmm_ops** out) {
+  if (!out || !levels || depth < 2 || depth > kMaxLevel || !(L > 0.0) || (int)kern < 0 ||
+      (int)kern > 6) {
+    set_error("eifmm_ops_load: invalid kernel, L, depth or null pointer");
+    return EIFMM_EINVAL;
+  }
+  *out = nullptr;
+  for (int k = 2; k <= depth; ++k) {
+    const eifmm_level_data& e = levels[k];
+    if (e.d < 1 || e.d > kMaxD || !e.X || !e.Y || !e.Gamma || !e.B) {
+      set_error("eifmm_ops_load: level " + std::to_string(k) + " has d outside [1, 512] or null arrays");
+      return EIFMM_EINVAL;
+    }
+    for (int i = 0; i < e.d; ++i)
+      if (e.Gamma[(int64_t)i * e.d + i] == 0.0) {
+        set_error("eifmm_ops_load: level " + std::to_string(k) + " has a zero pivot in Gamma");
+        return EIFMM_EINVAL;
+      }
+  }
+  eifmm_ops* h = new eifmm_ops();
+  Ops& o = h->o;
+  o.kern = kern;
+  o.L = L;
+  o.depth = depth;
+  double eps_max = 0.0;
+  cudaStream_t s = nullptr;
+  eifmm_status rc = EIFMM_OK;
+  for (int k = 2; k <= depth && rc == EIFMM_OK; ++k) {
+    const eifmm_level_data& e = levels[k];
+    LevelOps& v = o.lv[k];
+    v.d = e.d;
+    v.dp = (e.d + 63) / 64 * 64;
+    v.eps_est = e.eps_est;
+    if (e.eps_est > eps_max) eps_max = e.eps_est;
+    if ((rc = dalloc(&v.X, 3 * e.d)) != EIFMM_OK) break;
+    if ((rc = dalloc(&v.Y, 3 * e.d)) != EIFMM_OK) break;
+    if ((rc = dalloc(&v.G_rm, (size_t)e.d * e.d)) != EIFMM_OK) break;
+    if ((rc = dalloc(&v.B_rm, (size_t)e.d * e.d)) != EIFMM_OK) break;
+    cudaMemcpy(v.X, e.X, 3 * e.d * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(v.Y, e.Y, 3 * e.d * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(v.G_rm, e.Gamma, (size_t)e.d * e.d * sizeof(double), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(v.B_rm, e.B, (size_t)e.d * e.d * sizeof(double), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      set_error("eifmm_ops_load: upload failed");
+      rc = EIFMM_ECUDA;
+    }
+  }
+  if (rc == EIFMM_OK) rc = assemble_ops(&o, s);
+  if (rc != EIFMM_OK) {
+    free_ops(&o);
+    delete h;
+    return rc;
+  }
+  o.tier = tier_for_eps(eps_max > 0.0 ? eps_max : 1e-16);
+  *out = h;
+  return EIFMM_OK;
+}
+
+extern "C" eifmm_status eifmm_ops_build(eifmm_kernel kern, double L, int depth, double eps,
+                                        int d_max, eifmm_stream stream, eifmm_ops** out) {
+  if (!out || depth < 2 || depth > kMaxLevel || !(L > 0.0) || !(eps > 0.0) || d_max < 1 ||
+      d_max > kMaxD) {
+    set_error("eifmm_ops_build: invalid argument");
+    return EIFMM_EINVAL;
+  }
+  std::vector<eifmm_level_data> lv(depth + 1);
+  std::vector<std::vector<double>> keep;
+  for (int k = 2; k <= depth; ++k) {
+    int64_t nx = 0, ny = 0;
+    EIFMM_TRY(eifmm_training_sets(k, L, 9, nullptr, &nx, nullptr, &ny));
+    std::vector<double> X(3 * nx), Y(3 * ny);
+    EIFMM_TRY(eifmm_training_sets(k, L, 9, X.data(), &nx, Y.data(), &ny));
+    std::vector<int64_t> ia(d_max), ib(d_max);
+    std::vector<double> G((size_t)d_max * d_max), B((size_t)d_max * d_max), piv(d_max + 1);
+    int d = 0;
+    double est = 0;
+    EIFMM_TRY(eifmm_eim_build(kern, X.data(), nx, Y.data(), ny, eps, d_max, &d, ia.data(),
+                              ib.data(), G.data(), B.data(), piv.data(), &est, stream));
+    if (d < 1) {
+      set_error("eifmm_ops_build: the EIM selected no point at level " + std::to_string(k));
+      return EIFMM_EINVAL;
+    }
+    std::vector<double> px(3 * d), py(3 * d), pg((size_t)d * d), pb((size_t)d * d);
+    for (int m = 0; m < d; ++m)
+      for (int a = 0; a < 3; ++a) {
+        px[3 * m + a] = X[3 * ia[m] + a];
+        py[3 * m + a] = Y[3 * ib[m] + a];
+      }
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        pg[(size_t)i * d + j] = G[(size_t)i * d_max + j];
+        pb[(size_t)i * d + j] = B[(size_t)i * d_max + j];
+      }
+    keep.push_back(std::move(px));
+    keep.push_back(std::move(py));
+    keep.push_back(std::move(pg));
+    keep.push_back(std::move(pb));
+    const size_t b0 = keep.size() - 4;
+    lv[k] = eifmm_level_data{d, keep[b0].data(), keep[b0 + 1].data(), keep[b0 + 2].data(),
+                             keep[b0 + 3].data(), est};
+  }
+  return eifmm_ops_load(kern, L, depth, lv.data(), out);
+}
+
+extern "C" eifmm_status eifmm_ops_error_estimate(const eifmm_ops* ops, int level, double* eps_k,
+                                                 int* d_k) {
+  if (!ops || level < 2 || level > ops->o.depth) {
+    set_error("eifmm_ops_error_estimate: invalid handle or level");
+    return EIFMM_EINVAL;
+  }
+  if (eps_k) *eps_k = ops->o.lv[level].eps_est;
+  if (d_k) *d_k = ops->o.lv[level].d;
+  return EIFMM_OK;
+}
+
+extern "C" eifmm_status eifmm_ops_plan(eifmm_ops* ops, int tier_override, int* tier) {
+  if (!ops || tier_override > 2) {
+    set_error("eifmm_ops_plan: invalid handle or tier");
+    return EIFMM_EINVAL;
+  }
+  if (tier_override >= 0) ops->o.tier = tier_override;
+  if (tier) *tier = ops->o.tier;
+  return EIFMM_OK;
+}
+
+extern "C" void eifmm_ops_destroy(eifmm_ops* ops) {
+  if (!ops) return;
+  free_ops(&ops->o);
+  delete ops;
+}
+
+extern "C" eifmm_status eifmm_tree_build(const double* src_xyz, int64_t n_src,
+                                         const double* tgt_xyz, int64_t n_tgt, const double lo[3],
+                                         double L, int depth, int exclude_self,
+                                         eifmm_stream stream, eifmm_tree** out) {
+  if (!out || !lo || n_src < 0 || n_tgt < 0 || (n_src > 0 && !src_xyz) ||
+      (n_tgt > 0 && !tgt_xyz) || depth < 2 || depth > kMaxLevel || !(L > 0.0) ||
+      n_src >= ((int64_t)1 << 31) || n_tgt >= ((int64_t)1 << 31)) {
+    set_error("eifmm_tree_build: invalid argument");
+    return EIFMM_EINVAL;
+  }
+  const bool same = (src_xyz == tgt_xyz && n_src == n_tgt);
+  if (exclude_self && !same) {
+    set_error("eifmm_tree_build: exclude_self needs the target array to be the source array");
+    return EIFMM_EINVAL;
+  }
+  *out = nullptr;
+  eifmm_tree* h = new eifmm_tree();
+  Tree& t = h->t;
+  t.depth = depth;
+  t.L = L;
+  for (int a = 0; a < 3; ++a) t.lo[a] = lo[a];
+  t.exclude_self = exclude_self ? 1 : 0;
+  t.same = same;
+  cudaStream_t s = (cudaStream_t)stream;
+  eifmm_status rc = build_pointset(src_xyz, n_src, lo, L, depth, s, &t.src);
+  if (rc == EIFMM_OK) {
+    if (same) t.tgt = t.src;
+    else rc = build_pointset(tgt_xyz, n_tgt, lo, L, depth, s, &t.tgt);
+  }
+  if (rc != EIFMM_OK) {
+    free_pointset(&t.src);
+    if (!same) free_pointset(&t.tgt);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return EIFMM_OK;
+}
+
+extern "C" eifmm_status eifmm_tree_export(const eifmm_tree* tree, int which, uint32_t* keys,
+                                          int32_t* perm, int64_t* leaf_off) {
+  if (!tree || (which != 0 && which != 1)) {
+    set_error("eifmm_tree_export: invalid handle or `which`");
+    return EIFMM_EINVAL;
+  }
+  const PointSet& p = which == 0 ? tree->t.src : tree->t.tgt;
+  if (keys && p.n) EIFMM_CUDA(cudaMemcpy(keys, p.keys, p.n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  if (perm && p.n) EIFMM_CUDA(cudaMemcpy(perm, p.perm, p.n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (leaf_off) {
+    const int64_t nl = ((int64_t)1 << (3 * tree->t.depth)) + 1;
+    std::vector<int32_t> tmp(nl);
+    EIFMM_CUDA(cudaMemcpy(tmp.data(), p.leaf_off, nl * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < nl; ++i) leaf_off[i] = tmp[i];
+  }
+  return EIFMM_OK;
+}
+
+extern "C" void eifmm_tree_destroy(eifmm_tree* tree) {
+  if (!tree) return;
+  cudaDeviceSynchronize();
+  free_workspace(&tree->t.ws);
+  free_streams(&tree->t.ws);
+  free_pointset(&tree->t.src);
+  if (!tree->t.same) free_pointset(&tree->t.tgt);
+  delete tree;
+}
+
+static eifmm_status check_eval(const eifmm_tree* tree, const eifmm_ops* ops, int n_rhs,
+                               int64_t ld_sigma, int64_t ld_f, int prec) {
+  if (!tree || !ops || n_rhs < 1 || n_rhs > kMaxRhs || (prec != 0 && prec != 1)) {
+    set_error("eifmm_evaluate: invalid handle, n_rhs or precision");
+    return EIFMM_EINVAL;
+  }
+  const Tree& t = tree->t;
+  if (ops->o.depth != t.depth || ops->o.L != t.L) {
+    set_error("eifmm_evaluate: operators were built for another depth or L");
+    return EIFMM_EINVAL;
+  }
+  if (ld_sigma < t.src.n || ld_f < t.tgt.n) {
+    set_error("eifmm_evaluate: leading dimension smaller than the number of points");
+    return EIFMM_EINVAL;
+  }
+  return EIFMM_OK;
+}
+
+static eifmm_status evaluate_impl(eifmm_tree* tree, const eifmm_ops* ops, const double* sigma,
+                                  int64_t ld_sigma, int n_rhs, double* f, int64_t ld_f,
+                                  int prec, cudaStream_t s) {
+  Tree& t = tree->t;
+  EIFMM_TRY(ensure_workspace(&t, &ops->o, n_rhs, prec));
+  eifmm_status rc;
+  if (prec == EIFMM_PREC_FP64 || ops->o.tier == 2)
+    rc = (prec == EIFMM_PREC_FP64) ? eval_fp64(&t, &ops->o, sigma, ld_sigma, n_rhs, f, ld_f, s)
+                                   : eval_mixed(&t, &ops->o, sigma, ld_sigma, n_rhs, f, ld_f, s);
+  else
+    rc = eval_mixed(&t, &ops->o, sigma, ld_sigma, n_rhs, f, ld_f, s);
+  if (rc != EIFMM_OK) return rc;
+  t.ws.evaluated = true;
+  if (g_timing) {
+    EIFMM_CUDA(cudaEventSynchronize(t.ws.ev_t[8]));
+    for (int i = 0; i < 8; ++i) cudaEventElapsedTime(&t.ws.step_ms[i], t.ws.ev_t[i], t.ws.ev_t[i + 1]);
+  }
+  return EIFMM_OK;
+}
+
+extern "C" eifmm_status eifmm_evaluate(eifmm_tree* tree, const eifmm_ops* ops, const double* sigma,
+                                       int64_t ld_sigma, int n_rhs, double* f, int64_t ld_f,
+                                       eifmm_precision prec, eifmm_stream stream) {
+  EIFMM_TRY(check_eval(tree, ops, n_rhs, ld_sigma, ld_f, (int)prec));
+  if ((tree->t.src.n > 0 && !sigma) || (tree->t.tgt.n > 0 && !f)) {
+    set_error("eifmm_evaluate: null sigma or f");
+    return EIFMM_EINVAL;
+  }
+  if (tree->t.tgt.n == 0) return EIFMM_OK;
+  return evaluate_impl(tree, ops, sigma, ld_sigma, n_rhs, f, ld_f, (int)prec, (cudaStream_t)stream);
+}
+
+extern "C" eifmm_status eifmm_evaluate_host(eifmm_tree* tree, const eifmm_ops* ops,
+                                            const double* sigma_host, int64_t ld_sigma, int n_rhs,
+                                            double* f_host, int64_t ld_f, eifmm_precision prec,
+                                            eifmm_stream stream) {
+  EIFMM_TRY(check_eval(tree, ops, n_rhs, ld_sigma, ld_f, (int)prec));
+  Tree& t = tree->t;
+  if ((t.src.n > 0 && !sigma_host) || (t.tgt.n > 0 && !f_host)) {
+    set_error("eifmm_evaluate_host: null sigma or f");
+    return EIFMM_EINVAL;
+  }
+  if (t.tgt.n == 0) return EIFMM_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace& ws = t.ws;
+  const size_t need = (size_t)(t.src.n > t.tgt.n ? t.src.n : t.tgt.n) * n_rhs;
+  if (ws.host_cap < need) {
+    dfree(ws.host_sig);
+    dfree(ws.host_f);
+    ws.host_sig = ws.host_f = nullptr;
+    ws.host_cap = 0;
+    EIFMM_TRY(dalloc(&ws.host_sig, need));
+    EIFMM_TRY(dalloc(&ws.host_f, need));
+    ws.host_cap = need;
+  }
+  for (int r = 0; r < n_rhs; ++r)
+    EIFMM_CUDA(cudaMemcpyAsync(ws.host_sig + (size_t)r * t.src.n, sigma_host + (size_t)r * ld_sigma,
+                               t.src.n * sizeof(double), cudaMemcpyHostToDevice, s));
+  EIFMM_TRY(evaluate_impl(tree, ops, ws.host_sig, t.src.n, n_rhs, ws.host_f, t.tgt.n, (int)prec, s));
+  for (int r = 0; r < n_rhs; ++r)
+    EIFMM_CUDA(cudaMemcpyAsync(f_host + (size_t)r * ld_f, ws.host_f + (size_t)r * t.tgt.n,
+                               t.tgt.n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  EIFMM_CUDA(cudaStreamSynchronize(s));
+  return EIFMM_OK;
+}
+
+extern "C" eifmm_status eifmm_evaluate_batched(eifmm_tree* const* trees, const double* const* sigma,
+                                               double* const* f, int n_problems,
+                                               const eifmm_ops* ops, eifmm_precision prec,
+                                               eifmm_stream stream) {
+  if (!trees || !sigma || !f || n_problems < 0 || !ops) {
+    set_error("eifmm_evaluate_batched: invalid argument");
+    return EIFMM_EINVAL;
+  }
+  for (int p = 0; p < n_problems; ++p) {
+    if (!trees[p]) {
+      set_error("eifmm_evaluate_batched: null tree");
+      return EIFMM_EINVAL;
+    }
+    EIFMM_TRY(check_eval(trees[p], ops, 1, trees[p]->t.src.n, trees[p]->t.tgt.n, (int)prec));
+  }
+  for (int p = 0; p < n_problems; ++p) {
+    if (trees[p]->t.tgt.n == 0) continue;
+    EIFMM_TRY(evaluate_impl(trees[p], ops, sigma[p], trees[p]->t.src.n, 1, f[p],
+                            trees[p]->t.tgt.n, (int)prec, (cudaStream_t)stream));
+  }
+  return EIFMM_OK;
+}
+
+namespace eifmm {
+eifmm_status export_mixed(const Tree& t, const Ops& o, int what, int level, double* out, int64_t n);
+}
+
+extern "C" eifmm_status eifmm_debug_export(const eifmm_tree* tree, int what, int level,
+                                           double* out, int64_t n) {
+  if (!tree || !out || !tree->t.ws.evaluated) {
+    set_error("eifmm_debug_export: nothing evaluated on this tree");
+    return EIFMM_EINVAL;
+  }
+  const Tree& t = tree->t;
+  const Workspace& ws = t.ws;
+  const Ops& o = reinterpret_cast<const eifmm_ops*>(ws.ops_id)->o;
+  const int R = ws.nrhs;
+  EIFMM_CUDA(cudaDeviceSynchronize());
+  if (what == 5 || what == 6) {
+    if (n < t.tgt.n * R) {
+      set_error("eifmm_debug_export: output too small");
+      return EIFMM_EINVAL;
+    }
+    const double* src = what == 5 ? ws.ffar : ws.fnear;
+    std::vector<double> tmp((size_t)t.tgt.n * R);
+    std::vector<int32_t> perm(t.tgt.n);
+    EIFMM_CUDA(cudaMemcpy(tmp.data(), src, tmp.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    EIFMM_CUDA(cudaMemcpy(perm.data(), t.tgt.perm, t.tgt.n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < R; ++r)
+      for (int64_t p = 0; p < t.tgt.n; ++p) out[perm[p] + r * t.tgt.n] = tmp[p + r * t.tgt.n];
+    return EIFMM_OK;
+  }
+  if (level < 2 || level > t.depth || what < 0 || what > 4 || (what == 4 && level != t.depth)) {
+    set_error("eifmm_debug_export: invalid `what` or level");
+    return EIFMM_EINVAL;
+  }
+  const int d = o.lv[level].d;
+  const int64_t cnt = ((int64_t)1 << (3 * level)) * R * d;
+  if (n < cnt) {
+    set_error("eifmm_debug_export: output too small");
+    return EIFMM_EINVAL;
+  }
+  if (ws.W[level] == nullptr && ws.lh == nullptr) return export_mixed(t, o, what, level, out, n);
+  const double* src = what == 0 ? ws.W[level] : what == 1 ? ws.Wh[level] : what == 2 ? ws.g[level]
+                     : what == 3 ? ws.l[level] : ws.lh;
+  EIFMM_CUDA(cudaMemcpy(out, src, cnt * sizeof(double), cudaMemcpyDeviceToHost));
+  return EIFMM_OK;
+}
+
+extern "C" eifmm_status eifmm_last_step_times(const eifmm_tree* tree, float* ms9) {
+  if (!tree || !ms9) {
+    set_error("eifmm_last_step_times: null argument");
+    return EIFMM_EINVAL;
+  }
+  for (int i = 0; i < 9; ++i) ms9[i] = tree->t.ws.step_ms[i];
+  return EIFMM_OK;
+}

@@ -1,0 +1,476 @@
+// fmm64.cu -- the plain FP64 GPU EIFMM: Algorithm 3 (steps 1-7) + f_N.
+//
+// Layout of every far-field array of level k: [box (Morton)][rhs][m], FP64.
+// These kernels are the FP64 reference path on the GPU (and the baseline the
+// mixed-precision path is measured against): one thread per output entry,
+// operands staged in shared memory, operators read coalesced along m.
+#include "internal.h"
+
+namespace eifmm {
+namespace {
+
+constexpr int TPB = 128;
+constexpr int RC = 4;  // right-hand sides per pass in the point kernels
+
+__device__ __forceinline__ void leaf_center(int64_t key, int depth, double lo0,
+                                            double lo1, double lo2, double lk,
+                                            double* c) {
+  int ic[3];
+  morton_decode(key, depth, ic);
+  c[0] = lo0 + (2.0 * ic[0] + 1.0) * lk;
+  c[1] = lo1 + (2.0 * ic[1] + 1.0) * lk;
+  c[2] = lo2 + (2.0 * ic[2] + 1.0) * lk;
+}
+
+__global__ void k_gather_sigma(const double* __restrict__ sigma, int64_t ld,
+                               const int32_t* __restrict__ perm, int64_t n, int R,
+                               double* __restrict__ s64, float* __restrict__ s32) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int64_t i = perm[p];
+  for (int r = 0; r < R; ++r) {
+    const double v = sigma[i + r * ld];
+    s64[p + r * n] = v;
+    if (s32) s32[p + r * n] = (float)v;
+  }
+}
+
+// Step 1: W_m^I = sum_{y_j in I} sigma_j K(x_m^{I_0}, y_j - c_I).
+template <int KERN>
+__global__ void __launch_bounds__(TPB)
+k_p2m64(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restrict__ off,
+        const double* __restrict__ px, const double* __restrict__ py,
+        const double* __restrict__ pz, const double* __restrict__ sig, int64_t n,
+        int R, int depth, double lo0, double lo1, double lo2, double lk,
+        const double* __restrict__ X, int d, double* __restrict__ W) {
+  const int kern = KERN >= 0 ? KERN : kern_rt;
+  __shared__ double sz[3][TPB];
+  __shared__ double ss[RC][TPB];
+  const int b = leaves[blockIdx.x];
+  double c[3];
+  leaf_center(b, depth, lo0, lo1, lo2, lk, c);
+  const int beg = off[b], end = off[b + 1];
+  for (int r0 = 0; r0 < R; r0 += RC) {
+    for (int m0 = 0; m0 < d; m0 += TPB) {
+      const int m = m0 + threadIdx.x;
+      double xm0 = 0, xm1 = 0, xm2 = 0;
+      if (m < d) { xm0 = X[3 * m]; xm1 = X[3 * m + 1]; xm2 = X[3 * m + 2]; }
+      double acc[RC] = {0, 0, 0, 0};
+      for (int j0 = beg; j0 < end; j0 += TPB) {
+        const int j = j0 + threadIdx.x;
+        __syncthreads();
+        if (j < end) {
+          sz[0][threadIdx.x] = px[j] - c[0];
+          sz[1][threadIdx.x] = py[j] - c[1];
+          sz[2][threadIdx.x] = pz[j] - c[2];
+#pragma unroll
+          for (int rr = 0; rr < RC; ++rr) ss[rr][threadIdx.x] = (r0 + rr < R) ? sig[j + (r0 + rr) * n] : 0.0;
+        }
+        __syncthreads();
+        const int cnt = min(TPB, end - j0);
+        if (m < d)
+          for (int t = 0; t < cnt; ++t) {
+            const double kv = kern_f64(kern, xm0 - sz[0][t], xm1 - sz[1][t], xm2 - sz[2][t]);
+#pragma unroll
+            for (int rr = 0; rr < RC; ++rr) acc[rr] += ss[rr][t] * kv;
+          }
+      }
+      if (m < d)
+        for (int rr = 0; rr < RC && r0 + rr < R; ++rr) W[((int64_t)b * R + r0 + rr) * d + m] = acc[rr];
+    }
+  }
+}
+
+// Step 2: W^P = sum_i K_M2M^i W^{child_i}; two parents per block.
+__global__ void __launch_bounds__(TPB)
+k_m2m64(int dk, int dc, int R, const double* __restrict__ m2mT,
+        const double* __restrict__ Wc, double* __restrict__ Wp, int64_t nparent) {
+  extern __shared__ double sw[];  // [2][8][dc]
+  const int r = blockIdx.y;
+  const int64_t P0 = 2 * (int64_t)blockIdx.x;
+  for (int t = threadIdx.x; t < 2 * 8 * dc; t += TPB) {
+    const int p = t / (8 * dc), rem = t - p * 8 * dc, i = rem / dc, q = rem - i * dc;
+    const int64_t P = P0 + p;
+    sw[t] = (P < nparent) ? Wc[((8 * P + i) * R + r) * dc + q] : 0.0;
+  }
+  __syncthreads();
+  for (int m = threadIdx.x; m < dk; m += TPB) {
+    double a0 = 0, a1 = 0;
+    for (int i = 0; i < 8; ++i) {
+      const double* op = m2mT + (int64_t)i * dc * dk + m;
+      const double* w0 = sw + i * dc;
+      const double* w1 = sw + (8 + i) * dc;
+      for (int q = 0; q < dc; ++q) {
+        const double o = op[(int64_t)q * dk];
+        a0 += o * w0[q];
+        a1 += o * w1[q];
+      }
+    }
+    Wp[(P0 * R + r) * dk + m] = a0;
+    if (P0 + 1 < nparent) Wp[((P0 + 1) * R + r) * dk + m] = a1;
+  }
+}
+
+// Steps 3 and 6: out = Delta in (transpose = 0) or Delta^t in (transpose = 1),
+// by forward and back substitution, one warp per vector.
+__global__ void __launch_bounds__(TPB)
+k_solve64(int d, int transpose, const double* __restrict__ G_cm,
+          const double* __restrict__ G_rm, const double* __restrict__ B_cm,
+          const double* __restrict__ B_rm, const double* __restrict__ in,
+          double* __restrict__ out, int64_t nvec) {
+  extern __shared__ double sv_all[];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t v = (int64_t)blockIdx.x * (TPB / 32) + w;
+  if (v >= nvec) return;
+  double* sv = sv_all + w * d;
+  for (int j = lane; j < d; j += 32) sv[j] = in[v * d + j];
+  __syncwarp();
+  if (!transpose) {
+    // Gamma z = v (Gamma lower): column k of Gamma updates the rows below.
+    for (int k = 0; k < d; ++k) {
+      const double zk = sv[k] / G_cm[(int64_t)k * d + k];
+      __syncwarp();
+      if (lane == 0) sv[k] = zk;
+      for (int j = k + 1 + lane; j < d; j += 32) sv[j] -= G_cm[(int64_t)k * d + j] * zk;
+      __syncwarp();
+    }
+    // B^t w = z (B^t upper unit): row k of B updates the entries above.
+    for (int k = d - 1; k >= 0; --k) {
+      const double wk = sv[k];
+      for (int j = lane; j < k; j += 32) sv[j] -= B_rm[(int64_t)k * d + j] * wk;
+      __syncwarp();
+    }
+  } else {
+    // B z = v (B lower unit)
+    for (int k = 0; k < d; ++k) {
+      const double zk = sv[k];
+      for (int j = k + 1 + lane; j < d; j += 32) sv[j] -= B_cm[(int64_t)k * d + j] * zk;
+      __syncwarp();
+    }
+    // Gamma^t w = z (Gamma^t upper)
+    for (int k = d - 1; k >= 0; --k) {
+      const double wk = sv[k] / G_rm[(int64_t)k * d + k];
+      __syncwarp();
+      if (lane == 0) sv[k] = wk;
+      for (int j = lane; j < k; j += 32) sv[j] -= G_rm[(int64_t)k * d + j] * wk;
+      __syncwarp();
+    }
+  }
+  for (int j = lane; j < d; j += 32) out[v * d + j] = sv[j];
+}
+
+// Step 4: g^I = sum_{J in I(I)} K^delta What^J.  A block owns 8 target boxes
+// of one parity class (same octant, 8 consecutive parents): they share the
+// 189 candidate offsets; sources outside the cube contribute zero.
+constexpr int M2L_NB = 8;
+constexpr int M2L_MPT = 4;  // rows per thread: d <= 512
+__global__ void __launch_bounds__(TPB)
+k_m2l64(int level, int d, int R, const double* __restrict__ kdT,
+        const int* __restrict__ slot_lists, const double* __restrict__ Wh,
+        double* __restrict__ g) {
+  extern __shared__ double sw[];  // [M2L_NB][d]
+  const int r = blockIdx.y;
+  const int oct = blockIdx.x & 7;
+  const int64_t pg = blockIdx.x >> 3;
+  const int n = 1 << level;
+  int ci[M2L_NB][3];
+  int64_t I[M2L_NB];
+  for (int b = 0; b < M2L_NB; ++b) {
+    I[b] = 8 * (M2L_NB * pg + b) + oct;
+    morton_decode(I[b], level, ci[b]);
+  }
+  double acc[M2L_MPT][M2L_NB];
+#pragma unroll
+  for (int t = 0; t < M2L_MPT; ++t)
+#pragma unroll
+    for (int b = 0; b < M2L_NB; ++b) acc[t][b] = 0.0;
+  const int* lst = slot_lists + oct * kListLen;
+  for (int s = 0; s < kListLen; ++s) {
+    const int slot = lst[s];
+    const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+    __syncthreads();
+    bool any = false;
+    for (int b = 0; b < M2L_NB; ++b) {
+      const int jx = ci[b][0] + dx, jy = ci[b][1] + dy, jz = ci[b][2] + dz;
+      const bool ok = jx >= 0 && jy >= 0 && jz >= 0 && jx < n && jy < n && jz < n;
+      any |= ok;
+      const int64_t J = ok ? morton_encode(jx, jy, jz, level) : 0;
+      for (int l = threadIdx.x; l < d; l += TPB) sw[b * d + l] = ok ? Wh[(J * R + r) * d + l] : 0.0;
+    }
+    __syncthreads();
+    if (!any) continue;
+    const double* K = kdT + (int64_t)slot * d * d;
+    for (int l = 0; l < d; ++l) {
+      double wv[M2L_NB];
+#pragma unroll
+      for (int b = 0; b < M2L_NB; ++b) wv[b] = sw[b * d + l];
+#pragma unroll
+      for (int t = 0; t < M2L_MPT; ++t) {
+        const int mp = threadIdx.x + t * TPB;
+        if (mp < d) {
+          const double kv = K[(int64_t)l * d + mp];
+#pragma unroll
+          for (int b = 0; b < M2L_NB; ++b) acc[t][b] += kv * wv[b];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < M2L_MPT; ++t) {
+    const int mp = threadIdx.x + t * TPB;
+    if (mp < d)
+#pragma unroll
+      for (int b = 0; b < M2L_NB; ++b) g[(I[b] * R + r) * d + mp] = acc[t][b];
+  }
+}
+
+// Step 5: l^I = g^I + K_L2L^i l^{P(I)}.
+__global__ void __launch_bounds__(TPB)
+k_l2l64(int dk, int dp, int R, const double* __restrict__ l2lT,
+        const double* __restrict__ lpar, const double* __restrict__ g,
+        double* __restrict__ lout) {
+  extern __shared__ double sl[];
+  const int64_t P = blockIdx.x;
+  const int r = blockIdx.y;
+  for (int q = threadIdx.x; q < dp; q += TPB) sl[q] = lpar[(P * R + r) * dp + q];
+  __syncthreads();
+  for (int o = threadIdx.x; o < 8 * dk; o += TPB) {
+    const int i = o / dk, mp = o - i * dk;
+    const double* op = l2lT + (int64_t)i * dp * dk + mp;
+    double a = 0.0;
+    for (int q = 0; q < dp; ++q) a += op[(int64_t)q * dk] * sl[q];
+    const int64_t o2 = ((8 * P + i) * R + r) * dk + mp;
+    lout[o2] = g[o2] + a;
+  }
+}
+
+// Step 7 + sum + un-permute: f(x_i) = sum_l' K(x_i - c_I, y_l'^{I_0}) lhat_l'
+// + f_N(x_i), written to the caller's original order.
+template <int KERN>
+__global__ void __launch_bounds__(TPB)
+k_l2p64(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restrict__ off,
+        const int32_t* __restrict__ perm, const double* __restrict__ px,
+        const double* __restrict__ py, const double* __restrict__ pz, int64_t n,
+        int R, int depth, double lo0, double lo1, double lo2, double lk,
+        const double* __restrict__ X, int d, const double* __restrict__ lh,
+        const double* __restrict__ fnear, double* __restrict__ ffar,
+        double* __restrict__ f, int64_t ld_f) {
+  const int kern = KERN >= 0 ? KERN : kern_rt;
+  extern __shared__ double sm[];  // X (3d) then lhat (RC * d)
+  double* sX = sm;
+  double* sl = sm + 3 * d;
+  const int b = leaves[blockIdx.x];
+  double c[3];
+  leaf_center(b, depth, lo0, lo1, lo2, lk, c);
+  const int beg = off[b], end = off[b + 1];
+  for (int t = threadIdx.x; t < 3 * d; t += TPB) sX[t] = X[t];
+  for (int r0 = 0; r0 < R; r0 += RC) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < RC * d; t += TPB) {
+      const int rr = t / d, l = t - rr * d;
+      sl[t] = (r0 + rr < R) ? lh[((int64_t)b * R + r0 + rr) * d + l] : 0.0;
+    }
+    __syncthreads();
+    for (int p = beg + threadIdx.x; p < end; p += TPB) {
+      const double z0 = px[p] - c[0], z1 = py[p] - c[1], z2 = pz[p] - c[2];
+      double acc[RC] = {0, 0, 0, 0};
+      for (int l = 0; l < d; ++l) {
+        const double kv = kern_f64(kern, z0 - sX[3 * l], z1 - sX[3 * l + 1], z2 - sX[3 * l + 2]);
+#pragma unroll
+        for (int rr = 0; rr < RC; ++rr) acc[rr] += kv * sl[rr * d + l];
+      }
+      const int64_t i = perm[p];
+      for (int rr = 0; rr < RC && r0 + rr < R; ++rr) {
+        const int rg = r0 + rr;
+        if (ffar) ffar[p + rg * n] = acc[rr];
+        f[i + rg * ld_f] = acc[rr] + fnear[p + rg * n];
+      }
+    }
+  }
+}
+
+// Near field f_N(x_i) = sum over the 27 neighbouring leaves, FP64.
+template <int KERN>
+__global__ void __launch_bounds__(TPB)
+k_p2p64(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff,
+        const double* __restrict__ tx, const double* __restrict__ ty,
+        const double* __restrict__ tz, int64_t nt, const int32_t* __restrict__ soff,
+        const double* __restrict__ sx, const double* __restrict__ sy,
+        const double* __restrict__ sz, const double* __restrict__ sig, int64_t ns,
+        int R, int depth, int exclude_self, double* __restrict__ fnear) {
+  const int kern = KERN >= 0 ? KERN : kern_rt;
+  __shared__ double s[3][TPB];
+  __shared__ double ssg[RC][TPB];
+  const int b = leaves[blockIdx.x];
+  int c[3];
+  morton_decode(b, depth, c);
+  const int n = 1 << depth;
+  const int beg = toff[b], end = toff[b + 1];
+  for (int r0 = 0; r0 < R; r0 += RC) {
+    for (int p0 = beg; p0 < end; p0 += TPB) {
+      const int p = p0 + threadIdx.x;
+      const bool act = p < end;
+      const double x0 = act ? tx[p] : 0.0, x1 = act ? ty[p] : 0.0, x2 = act ? tz[p] : 0.0;
+      double acc[RC] = {0, 0, 0, 0};
+      for (int nb = 0; nb < 27; ++nb) {
+        const int jx = c[0] + nb % 3 - 1, jy = c[1] + (nb / 3) % 3 - 1, jz = c[2] + nb / 9 - 1;
+        if (jx < 0 || jy < 0 || jz < 0 || jx >= n || jy >= n || jz >= n) continue;
+        const int64_t J = morton_encode(jx, jy, jz, depth);
+        const int sb = soff[J], se = soff[J + 1];
+        for (int q0 = sb; q0 < se; q0 += TPB) {
+          __syncthreads();
+          const int q = q0 + threadIdx.x;
+          if (q < se) {
+            s[0][threadIdx.x] = sx[q];
+            s[1][threadIdx.x] = sy[q];
+            s[2][threadIdx.x] = sz[q];
+#pragma unroll
+            for (int rr = 0; rr < RC; ++rr) ssg[rr][threadIdx.x] = (r0 + rr < R) ? sig[q + (r0 + rr) * ns] : 0.0;
+          }
+          __syncthreads();
+          const int cnt = min(TPB, se - q0);
+          if (act)
+            for (int t = 0; t < cnt; ++t) {
+              if (exclude_self && q0 + t == p) continue;
+              const double kv = kern_f64(kern, x0 - s[0][t], x1 - s[1][t], x2 - s[2][t]);
+#pragma unroll
+              for (int rr = 0; rr < RC; ++rr) acc[rr] += ssg[rr][t] * kv;
+            }
+        }
+      }
+      if (act)
+        for (int rr = 0; rr < RC && r0 + rr < R; ++rr) fnear[p + (int64_t)(r0 + rr) * nt] = acc[rr];
+    }
+  }
+}
+
+}  // namespace
+
+eifmm_status launch_gather_sigma(const double* sigma, int64_t ld, const PointSet& src, int R,
+                                 double* s64, float* s32, cudaStream_t s) {
+  if (src.n == 0) return EIFMM_OK;
+  k_gather_sigma<<<(unsigned)((src.n + 255) / 256), 256, 0, s>>>(sigma, ld, src.perm, src.n, R, s64, s32);
+  EIFMM_CHECK_LAUNCH();
+  return EIFMM_OK;
+}
+
+eifmm_status launch_p2p64(const Tree* t, int kern, const double* sig, int R, double* fnear,
+                          cudaStream_t s) {
+  const PointSet& T = t->tgt;
+  const PointSet& S = t->src;
+  if (T.n_nonempty == 0) return EIFMM_OK;
+  if (kern == EIFMM_KERNEL_INV_R)
+    k_p2p64<EIFMM_KERNEL_INV_R><<<T.n_nonempty, TPB, 0, s>>>(
+        kern, T.nonempty, T.leaf_off, T.x, T.y, T.z, T.n, S.leaf_off, S.x, S.y, S.z, sig, S.n, R,
+        t->depth, t->exclude_self, fnear);
+  else
+    k_p2p64<-1><<<T.n_nonempty, TPB, 0, s>>>(kern, T.nonempty, T.leaf_off, T.x, T.y, T.z, T.n,
+                                             S.leaf_off, S.x, S.y, S.z, sig, S.n, R, t->depth,
+                                             t->exclude_self, fnear);
+  EIFMM_CHECK_LAUNCH();
+  return EIFMM_OK;
+}
+
+eifmm_status launch_solve64(const LevelOps& v, int transpose, const double* in, double* out,
+                            int64_t nvec, cudaStream_t s) {
+  const size_t sm = (size_t)(TPB / 32) * v.d * sizeof(double);
+  k_solve64<<<(unsigned)((nvec + TPB / 32 - 1) / (TPB / 32)), TPB, sm, s>>>(
+      v.d, transpose, v.G_cm, v.G_rm, v.B_cm, v.B_rm, in, out, nvec);
+  EIFMM_CHECK_LAUNCH();
+  return EIFMM_OK;
+}
+
+static void record(Workspace& ws, int i, cudaStream_t s) {
+  if (timing_enabled()) cudaEventRecord(ws.ev_t[i], s);
+}
+
+eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_sigma, int R,
+                       double* f, int64_t ld_f, cudaStream_t s) {
+  Workspace& ws = t->ws;
+  const int kap = t->depth;
+  const int kern = (int)ops->kern;
+  const PointSet& S = t->src;
+  const PointSet& T = t->tgt;
+  const double lk = t->L * ldexp(1.0, -(kap + 1));
+  record(ws, 0, s);
+  EIFMM_TRY(launch_gather_sigma(sigma, ld_sigma, S, R, ws.sig, nullptr, s));
+  // near field on the side stream, concurrent with the far field
+  EIFMM_CUDA(cudaEventRecord(ws.ev_fork, s));
+  EIFMM_CUDA(cudaStreamWaitEvent(ws.side, ws.ev_fork, 0));
+  EIFMM_TRY(launch_p2p64(t, kern, ws.sig, R, ws.fnear, ws.side));
+  EIFMM_CUDA(cudaEventRecord(ws.ev_join, ws.side));
+
+  // step 1
+  const LevelOps& vl = ops->lv[kap];
+  EIFMM_CUDA(cudaMemsetAsync(ws.W[kap], 0, sizeof(double) * ((size_t)1 << (3 * kap)) * R * vl.d, s));
+  if (S.n_nonempty > 0) {
+    if (kern == EIFMM_KERNEL_INV_R)
+      k_p2m64<EIFMM_KERNEL_INV_R><<<S.n_nonempty, TPB, 0, s>>>(
+          kern, S.nonempty, S.leaf_off, S.x, S.y, S.z, ws.sig, S.n, R, kap, t->lo[0], t->lo[1],
+          t->lo[2], lk, vl.X, vl.d, ws.W[kap]);
+    else
+      k_p2m64<-1><<<S.n_nonempty, TPB, 0, s>>>(kern, S.nonempty, S.leaf_off, S.x, S.y, S.z, ws.sig,
+                                               S.n, R, kap, t->lo[0], t->lo[1], t->lo[2], lk, vl.X,
+                                               vl.d, ws.W[kap]);
+    EIFMM_CHECK_LAUNCH();
+  }
+  record(ws, 1, s);
+  // step 2
+  static bool attr_set = false;
+  if (!attr_set) {
+    EIFMM_CUDA(cudaFuncSetAttribute(k_m2m64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    16 * kMaxD * (int)sizeof(double)));
+    attr_set = true;
+  }
+  for (int k = kap - 1; k >= 2; --k) {
+    const int dk = ops->lv[k].d, dc = ops->lv[k + 1].d;
+    const int64_t np = (int64_t)1 << (3 * k);
+    k_m2m64<<<dim3((unsigned)((np + 1) / 2), R), TPB, 16 * dc * sizeof(double), s>>>(
+        dk, dc, R, ops->lv[k].m2mT, ws.W[k + 1], ws.W[k], np);
+    EIFMM_CHECK_LAUNCH();
+  }
+  record(ws, 2, s);
+  // step 3
+  for (int k = 2; k <= kap; ++k)
+    EIFMM_TRY(launch_solve64(ops->lv[k], 0, ws.W[k], ws.Wh[k], ((int64_t)1 << (3 * k)) * R, s));
+  record(ws, 3, s);
+  // step 4
+  for (int k = 2; k <= kap; ++k) {
+    const int d = ops->lv[k].d;
+    const int64_t nb = (int64_t)1 << (3 * k);
+    k_m2l64<<<dim3((unsigned)(nb / 8 / M2L_NB * 8), R), TPB, M2L_NB * d * sizeof(double), s>>>(
+        k, d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.Wh[k], ws.g[k]);
+    EIFMM_CHECK_LAUNCH();
+  }
+  record(ws, 4, s);
+  // step 5 (l^2 = g^2)
+  for (int k = 3; k <= kap; ++k) {
+    const int dk = ops->lv[k].d, dp = ops->lv[k - 1].d;
+    k_l2l64<<<dim3((unsigned)((int64_t)1 << (3 * (k - 1))), R), TPB, dp * sizeof(double), s>>>(
+        dk, dp, R, ops->lv[k].l2lT, ws.l[k - 1], ws.g[k], ws.l[k]);
+    EIFMM_CHECK_LAUNCH();
+  }
+  record(ws, 5, s);
+  // step 6
+  EIFMM_TRY(launch_solve64(vl, 1, ws.l[kap], ws.lh, ((int64_t)1 << (3 * kap)) * R, s));
+  record(ws, 6, s);
+  // step 7 + near field + un-permute
+  EIFMM_CUDA(cudaStreamWaitEvent(s, ws.ev_join, 0));
+  record(ws, 7, s);
+  if (T.n_nonempty > 0) {
+    const size_t sm = (size_t)(3 * vl.d + RC * vl.d) * sizeof(double);
+    if (kern == EIFMM_KERNEL_INV_R)
+      k_l2p64<EIFMM_KERNEL_INV_R><<<T.n_nonempty, TPB, sm, s>>>(
+          kern, T.nonempty, T.leaf_off, T.perm, T.x, T.y, T.z, T.n, R, kap, t->lo[0], t->lo[1],
+          t->lo[2], lk, vl.X, vl.d, ws.lh, ws.fnear, ws.ffar, f, ld_f);
+    else
+      k_l2p64<-1><<<T.n_nonempty, TPB, sm, s>>>(kern, T.nonempty, T.leaf_off, T.perm, T.x, T.y, T.z,
+                                                T.n, R, kap, t->lo[0], t->lo[1], t->lo[2], lk, vl.X,
+                                                vl.d, ws.lh, ws.fnear, ws.ffar, f, ld_f);
+    EIFMM_CHECK_LAUNCH();
+  }
+  record(ws, 8, s);
+  return EIFMM_OK;
+}
+
+}  // namespace eifmm

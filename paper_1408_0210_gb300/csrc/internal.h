@@ -1,0 +1,285 @@
+// internal.h -- shared declarations of the EIFMM GPU library (sm_103a).
+// Not part of the ABI; include/eifmm.h is.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/eifmm.h"
+
+namespace eifmm {
+
+constexpr int kMaxLevel = 10;
+constexpr int kMaxD = 512;
+constexpr int kMaxRhs = 256;
+constexpr int kNumSlots = 343;  // 7^3 offsets delta/(2 l_k) in [-3, 3]^3
+constexpr int kListLen = 189;   // interaction-list length of an interior box
+
+// ---------------------------------------------------------------- errors --
+void set_error(const std::string& msg);
+#define EIFMM_CUDA(call)                                                     \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      ::eifmm::set_error(std::string(#call) + ": " + cudaGetErrorString(e_)); \
+      return EIFMM_ECUDA;                                                    \
+    }                                                                        \
+  } while (0)
+#define EIFMM_CHECK_LAUNCH() EIFMM_CUDA(cudaGetLastError())
+#define EIFMM_TRY(call)                 \
+  do {                                  \
+    eifmm_status s_ = (call);           \
+    if (s_ != EIFMM_OK) return s_;      \
+  } while (0)
+
+eifmm_status dmalloc(void** p, size_t bytes);
+template <class T>
+eifmm_status dalloc(T** p, size_t count) {
+  return dmalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+void dfree(void* p);
+
+// ------------------------------------------------------------- kernels --
+// k(z) in FP64, contracted arithmetic (evaluation path).
+__host__ __device__ inline double kern_f64(int kern, double z0, double z1, double z2);
+
+// ------------------------------------------------------------ operators --
+struct LevelOps {
+  int d = 0;          // EIM rank of the level
+  int dp = 0;         // d padded to a multiple of 64 (tensor-core layouts)
+  double eps_est = 0;
+  double* X = nullptr;     // d x 3, x_m^{I_0^k}
+  double* Y = nullptr;     // d x 3, y_l^{J_0^k}
+  double* G_rm = nullptr;  // Gamma row-major
+  double* G_cm = nullptr;  // Gamma column-major
+  double* B_rm = nullptr;  // B row-major
+  double* B_cm = nullptr;  // B column-major
+  double* m2mT = nullptr;  // [8][q < d_{k+1}][m < d]: (K_M2M^i)^t, levels 2..depth-1
+  double* l2lT = nullptr;  // [8][q' < d_{k-1}][m' < d]: (K_L2L^i)^t, levels 3..depth
+  double* kdT = nullptr;   // [343][l < d][m' < d]: K^delta_{m'l}
+  // reduced-precision copies
+  float* m2mT32 = nullptr;
+  float* l2lT32 = nullptr;
+  float* G32_cm = nullptr;
+  float* G32_rm = nullptr;
+  float* B32_cm = nullptr;
+  float* B32_rm = nullptr;
+  float* X32 = nullptr;    // d x 3
+  // M2L operands for the tensor-core kernel: per slot, 3 BF16 split planes
+  // of K^delta in the canonical K-major 128B-swizzled layout, [slot][plane]
+  // [n-row < dp][k < dp].
+  __nv_bfloat16* kd_bf16 = nullptr;
+};
+
+struct Ops {
+  eifmm_kernel kern;
+  double L = 1.0;
+  int depth = 0;
+  int tier = 0;        // arithmetic tier of the mixed path
+  LevelOps lv[kMaxLevel + 1];
+  int* d_slot_lists = nullptr;  // [8][189] slot ids per parity class
+};
+
+// ------------------------------------------------------------------ tree --
+struct PointSet {
+  int64_t n = 0;
+  int32_t* perm = nullptr;      // sorted position -> input index
+  uint32_t* keys = nullptr;     // sorted Morton keys
+  int32_t* leaf_off = nullptr;  // 8^depth + 1
+  int32_t* nonempty = nullptr;  // non-empty leaves
+  int32_t n_nonempty = 0;
+  double* x = nullptr;          // sorted coordinates (SoA)
+  double* y = nullptr;
+  double* z = nullptr;
+  float* lx = nullptr;          // coordinates relative to the leaf centre
+  float* ly = nullptr;
+  float* lz = nullptr;
+};
+
+struct Workspace {
+  const void* ops_id = nullptr;
+  int nrhs = 0;
+  int prec = -1;
+  int tier = -1;
+  // FP64 far field, [box][r][d] per level
+  double* W[kMaxLevel + 1] = {};
+  double* Wh[kMaxLevel + 1] = {};
+  double* g[kMaxLevel + 1] = {};   // step 4 output
+  double* l[kMaxLevel + 1] = {};   // step 5 output (l[2] aliases g[2])
+  double* lh = nullptr;            // leaf level
+  // FP32 far field
+  float* W32[kMaxLevel + 1] = {};
+  float* Wh32[kMaxLevel + 1] = {};
+  float* g32[kMaxLevel + 1] = {};
+  float* lh32 = nullptr;
+  // tensor-core M2L A operand planes: [box*R + r][plane][dp] bf16
+  __nv_bfloat16* wa[kMaxLevel + 1] = {};
+  double* sig = nullptr;        // sorted sigma, n_src x R (col-major, ld n_src)
+  float* sig32 = nullptr;
+  double* fnear = nullptr;      // n_tgt x R, sorted order
+  double* ffar = nullptr;       // n_tgt x R, sorted order (debug only)
+  double* host_sig = nullptr;   // device staging for evaluate_host
+  double* host_f = nullptr;
+  size_t host_cap = 0;
+  cudaStream_t side = nullptr;  // near field runs here, concurrent with far
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_t[10] = {};
+  bool evaluated = false;
+  float step_ms[9] = {};
+};
+
+struct Tree {
+  int depth = 0;
+  double lo[3] = {0, 0, 0};
+  double L = 1.0;
+  int exclude_self = 0;
+  bool same = false;  // targets are the sources
+  PointSet src, tgt;  // tgt aliases src when `same`
+  Workspace ws;
+};
+
+// ------------------------------------------------------------ launchers --
+eifmm_status build_pointset(const double* xyz, int64_t n, const double lo[3],
+                            double L, int depth, cudaStream_t s, PointSet* ps);
+void free_pointset(PointSet* ps);
+
+eifmm_status assemble_ops(Ops* ops, cudaStream_t s);
+void free_ops(Ops* ops);
+
+eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma,
+                       int64_t ld_sigma, int R, double* f, int64_t ld_f,
+                       cudaStream_t s);
+eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma,
+                        int64_t ld_sigma, int R, double* f, int64_t ld_f,
+                        cudaStream_t s);
+eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec);
+void free_workspace(Workspace* ws);
+bool timing_enabled();
+
+// ----------------------------------------------------------- device util --
+__host__ __device__ inline int64_t morton_encode(int64_t x, int64_t y, int64_t z, int bits) {
+  int64_t key = 0;
+  for (int b = 0; b < bits; ++b) {
+    key |= ((x >> b) & 1) << (3 * b);
+    key |= ((y >> b) & 1) << (3 * b + 1);
+    key |= ((z >> b) & 1) << (3 * b + 2);
+  }
+  return key;
+}
+__host__ __device__ inline void morton_decode(int64_t key, int bits, int* c) {
+  int x = 0, y = 0, z = 0;
+  for (int b = 0; b < bits; ++b) {
+    x |= (int)((key >> (3 * b)) & 1) << b;
+    y |= (int)((key >> (3 * b + 1)) & 1) << b;
+    z |= (int)((key >> (3 * b + 2)) & 1) << b;
+  }
+  c[0] = x;
+  c[1] = y;
+  c[2] = z;
+}
+
+}  // namespace eifmm
+
+// ------------------------------------------------------ kernel functions --
+namespace eifmm {
+__host__ __device__ inline double kern_f64(int kern, double z0, double z1, double z2) {
+  const double r2 = z0 * z0 + z1 * z1 + z2 * z2;
+  switch (kern) {
+    case EIFMM_KERNEL_INV_R:
+#ifdef __CUDA_ARCH__
+      return rsqrt(r2);
+#else
+      return 1.0 / sqrt(r2);
+#endif
+    case EIFMM_KERNEL_CONFIG3: {
+      const double r = sqrt(r2);
+      const double a = z0 * z0 + 0.01 * (z1 * z1) + z2 * z2 + 1e-3;
+#ifdef __CUDA_ARCH__
+      return exp(-r) / r + rsqrt(a);
+#else
+      return exp(-r) / r + 1.0 / sqrt(a);
+#endif
+    }
+    case EIFMM_KERNEL_QUAD:
+      return r2;
+    case EIFMM_KERNEL_ONE:
+      return 1.0;
+    case EIFMM_KERNEL_EXP_R2:
+      return exp(-r2);
+    case EIFMM_KERNEL_COS20R_R: {
+      const double r = sqrt(r2);
+      return cos(20.0 * r) / r;
+    }
+    case EIFMM_KERNEL_SQRT_R2P1:
+      return sqrt(r2 + 1.0);
+    default:
+      return 0.0;
+  }
+}
+
+// k(z) with IEEE-exact operations (no contraction) for the pivot search.
+__device__ inline double kern_f64_ieee(int kern, double z0, double z1, double z2) {
+  const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(z0, z0), __dmul_rn(z1, z1)), __dmul_rn(z2, z2));
+  switch (kern) {
+    case EIFMM_KERNEL_INV_R:
+      return __ddiv_rn(1.0, __dsqrt_rn(r2));
+    case EIFMM_KERNEL_CONFIG3: {
+      const double r = __dsqrt_rn(r2);
+      const double a = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(z0, z0), __dmul_rn(0.01, __dmul_rn(z1, z1))),
+                                           __dmul_rn(z2, z2)), 1e-3);
+      return __dadd_rn(__ddiv_rn(exp(-r), r), __ddiv_rn(1.0, __dsqrt_rn(a)));
+    }
+    case EIFMM_KERNEL_QUAD:
+      return r2;
+    case EIFMM_KERNEL_ONE:
+      return 1.0;
+    case EIFMM_KERNEL_EXP_R2:
+      return exp(-r2);
+    case EIFMM_KERNEL_COS20R_R: {
+      const double r = __dsqrt_rn(r2);
+      return __ddiv_rn(cos(__dmul_rn(20.0, r)), r);
+    }
+    case EIFMM_KERNEL_SQRT_R2P1:
+      return __dsqrt_rn(__dadd_rn(r2, 1.0));
+    default:
+      return 0.0;
+  }
+}
+
+// FP32 evaluation (mixed path): one Newton step after the hardware rsqrt.
+__device__ inline float rsqrt_nr(float a) {
+  float y = rsqrtf(a);
+  // y (3 - a y^2) / 2
+  return y * fmaf(-0.5f * a, y * y, 1.5f);
+}
+__device__ inline float kern_f32(int kern, float z0, float z1, float z2) {
+  const float r2 = fmaf(z0, z0, fmaf(z1, z1, z2 * z2));
+  switch (kern) {
+    case EIFMM_KERNEL_INV_R:
+      return rsqrt_nr(r2);
+    case EIFMM_KERNEL_CONFIG3: {
+      const float ir = rsqrt_nr(r2);
+      const float r = r2 * ir;
+      const float a = fmaf(z0, z0, fmaf(0.01f * z1, z1, fmaf(z2, z2, 1e-3f)));
+      return expf(-r) * ir + rsqrt_nr(a);
+    }
+    case EIFMM_KERNEL_QUAD:
+      return r2;
+    case EIFMM_KERNEL_ONE:
+      return 1.0f;
+    case EIFMM_KERNEL_EXP_R2:
+      return expf(-r2);
+    case EIFMM_KERNEL_COS20R_R: {
+      const float ir = rsqrt_nr(r2);
+      return cosf(20.0f * r2 * ir) * ir;
+    }
+    case EIFMM_KERNEL_SQRT_R2P1:
+      return sqrtf(r2 + 1.0f);
+    default:
+      return 0.0f;
+  }
+}
+}  // namespace eifmm

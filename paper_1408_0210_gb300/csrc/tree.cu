@@ -1,0 +1,269 @@
+// tree.cu -- octree bin/sort of the points (Section 3.3: uniform 2^D-tree
+// with kappa + 1 levels; leaves are the 8^kappa boxes of level kappa).
+//
+// Leaf coordinate floor((x - lo) * (2^kappa / L)) clamped to [0, 2^kappa - 1],
+// Morton key with the x bit lowest, then a stable LSD radix sort of the keys
+// (8-bit digits; a block ranks its tile warp by warp with __match_any_sync so
+// that equal digits keep their input order), leaf offsets from the sorted
+// keys and the gather of sorted FP64 coordinates plus FP32 coordinates
+// relative to the leaf centre.
+#include "internal.h"
+
+namespace eifmm {
+namespace {
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_ITEMS = 8;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;  // 2048 keys per block
+
+__global__ void k_keys(const double* __restrict__ xyz, int64_t n, double lo0,
+                       double lo1, double lo2, double hi0, double hi1,
+                       double hi2, double scale, int depth,
+                       uint32_t* __restrict__ keys, int32_t* __restrict__ idx,
+                       int* __restrict__ bad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double lo[3] = {lo0, lo1, lo2};
+  const double hi[3] = {hi0, hi1, hi2};
+  const int64_t nmax = ((int64_t)1 << depth) - 1;
+  int64_t c[3];
+  bool out = false;
+  for (int a = 0; a < 3; ++a) {
+    const double x = xyz[3 * i + a];
+    if (!(x >= lo[a] && x <= hi[a])) out = true;
+    // (x - lo) * scale: a subtraction then a product, never fused.
+    const double t = floor(__dmul_rn(__dsub_rn(x, lo[a]), scale));
+    int64_t v = (int64_t)t;
+    if (!(t >= 0.0)) v = 0;
+    if (v > nmax) v = nmax;
+    c[a] = v;
+  }
+  if (out) atomicAdd(bad, 1);
+  keys[i] = (uint32_t)morton_encode(c[0], c[1], c[2], depth);
+  idx[i] = (int32_t)i;
+}
+
+__global__ void k_rs_count(const uint32_t* __restrict__ keys, int64_t n,
+                           int shift, uint32_t* __restrict__ counts,
+                           int nblocks) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int i = threadIdx.x; i < RS_TILE; i += RS_THREADS) {
+    const int64_t p = base + i;
+    if (p < n) atomicAdd(&h[(keys[p] >> shift) & 255u], 1u);
+  }
+  __syncthreads();
+  counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of `len` counts in one block of 1024 threads.
+__global__ void k_scan_excl(uint32_t* __restrict__ a, int64_t len) {
+  __shared__ uint32_t part[1024];
+  const int t = threadIdx.x;
+  const int64_t chunk = (len + 1023) / 1024;
+  const int64_t b = t * chunk, e = (b + chunk < len) ? b + chunk : len;
+  uint32_t s = 0;
+  for (int64_t i = b; i < e; ++i) s += a[i];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    uint32_t v = (t >= off) ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  uint32_t run = (t > 0) ? part[t - 1] : 0;
+  for (int64_t i = b; i < e; ++i) {
+    const uint32_t v = a[i];
+    a[i] = run;
+    run += v;
+  }
+}
+
+__global__ void __launch_bounds__(RS_THREADS)
+k_rs_scatter(const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin,
+             uint32_t* __restrict__ kout, int32_t* __restrict__ vout, int64_t n,
+             int shift, const uint32_t* __restrict__ offsets, int nblocks) {
+  __shared__ uint32_t wc[RS_WARPS][257];
+  for (int i = threadIdx.x; i < RS_WARPS * 257; i += RS_THREADS) (&wc[0][0])[i] = 0;
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const int64_t wbase = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * (32 * RS_ITEMS);
+  uint32_t kk[RS_ITEMS];
+  int32_t vv[RS_ITEMS];
+  uint32_t rank[RS_ITEMS];
+  int dig[RS_ITEMS];
+#pragma unroll
+  for (int j = 0; j < RS_ITEMS; ++j) {
+    const int64_t p = wbase + j * 32 + lane;
+    const bool valid = p < n;
+    kk[j] = valid ? kin[p] : 0u;
+    vv[j] = valid ? vin[p] : 0;
+    const int d = valid ? (int)((kk[j] >> shift) & 255u) : 256;
+    dig[j] = d;
+    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    const uint32_t old = wc[w][d];
+    __syncwarp();
+    if (lane == __ffs(peers) - 1) wc[w][d] = old + __popc(peers);
+    __syncwarp();
+    rank[j] = old + __popc(peers & lt);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += RS_THREADS) {
+    uint32_t run = 0;
+    for (int ww = 0; ww < RS_WARPS; ++ww) {
+      const uint32_t t = wc[ww][d];
+      wc[ww][d] = run;
+      run += t;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < RS_ITEMS; ++j) {
+    if (dig[j] == 256) continue;
+    const uint32_t pos = offsets[(int64_t)dig[j] * nblocks + blockIdx.x] + wc[w][dig[j]] + rank[j];
+    kout[pos] = kk[j];
+    vout[pos] = vv[j];
+  }
+}
+
+__global__ void k_leaf_off(const uint32_t* __restrict__ skeys, int64_t n,
+                           int64_t nleaf, int32_t* __restrict__ off) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p > n) return;
+  const int64_t prev = (p == 0) ? -1 : (int64_t)skeys[p - 1];
+  const int64_t cur = (p == n) ? nleaf : (int64_t)skeys[p];
+  for (int64_t b = prev + 1; b <= cur; ++b) off[b] = (int32_t)p;
+}
+
+__global__ void k_gather_points(const double* __restrict__ xyz,
+                                const int32_t* __restrict__ perm,
+                                const uint32_t* __restrict__ skeys, int64_t n,
+                                double lo0, double lo1, double lo2, double lk,
+                                int depth, double* __restrict__ x,
+                                double* __restrict__ y, double* __restrict__ z,
+                                float* __restrict__ lx, float* __restrict__ ly,
+                                float* __restrict__ lz) {
+  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int64_t i = perm[p];
+  const double px = xyz[3 * i], py = xyz[3 * i + 1], pz = xyz[3 * i + 2];
+  int c[3];
+  morton_decode(skeys[p], depth, c);
+  x[p] = px;
+  y[p] = py;
+  z[p] = pz;
+  lx[p] = (float)(px - (lo0 + (2.0 * c[0] + 1.0) * lk));
+  ly[p] = (float)(py - (lo1 + (2.0 * c[1] + 1.0) * lk));
+  lz[p] = (float)(pz - (lo2 + (2.0 * c[2] + 1.0) * lk));
+}
+
+__global__ void k_nonempty(const int32_t* __restrict__ off, int64_t nleaf,
+                           int32_t* __restrict__ list, int32_t* __restrict__ cnt) {
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= nleaf) return;
+  if (off[b + 1] > off[b]) list[atomicAdd(cnt, 1)] = (int32_t)b;
+}
+
+}  // namespace
+
+eifmm_status build_pointset(const double* xyz, int64_t n, const double lo[3],
+                            double L, int depth, cudaStream_t s, PointSet* ps) {
+  ps->n = n;
+  const int64_t nleaf = (int64_t)1 << (3 * depth);
+  const int64_t nn = n > 0 ? n : 1;
+  EIFMM_TRY(dalloc(&ps->perm, nn));
+  EIFMM_TRY(dalloc(&ps->keys, nn));
+  EIFMM_TRY(dalloc(&ps->leaf_off, nleaf + 1));
+  EIFMM_TRY(dalloc(&ps->nonempty, nleaf));
+  EIFMM_TRY(dalloc(&ps->x, nn));
+  EIFMM_TRY(dalloc(&ps->y, nn));
+  EIFMM_TRY(dalloc(&ps->z, nn));
+  EIFMM_TRY(dalloc(&ps->lx, nn));
+  EIFMM_TRY(dalloc(&ps->ly, nn));
+  EIFMM_TRY(dalloc(&ps->lz, nn));
+
+  uint32_t *k2 = nullptr, *counts = nullptr;
+  int32_t* v2 = nullptr;
+  int* dbad = nullptr;
+  const int nblocks = (int)((n + RS_TILE - 1) / RS_TILE);
+  const int nb1 = nblocks > 0 ? nblocks : 1;
+  EIFMM_TRY(dalloc(&k2, nn));
+  EIFMM_TRY(dalloc(&v2, nn));
+  EIFMM_TRY(dalloc(&counts, (size_t)256 * nb1));
+  EIFMM_TRY(dalloc(&dbad, 2));
+  EIFMM_CUDA(cudaMemsetAsync(dbad, 0, 2 * sizeof(int), s));
+
+  const double scale = ldexp(1.0, depth) / L;
+  if (n > 0) {
+    k_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        xyz, n, lo[0], lo[1], lo[2], lo[0] + L, lo[1] + L, lo[2] + L, scale,
+        depth, ps->keys, ps->perm, dbad);
+    EIFMM_CHECK_LAUNCH();
+    uint32_t* kin = ps->keys;
+    int32_t* vin = ps->perm;
+    uint32_t* kout = k2;
+    int32_t* vout = v2;
+    const int bits = 3 * depth;
+    for (int shift = 0; shift < bits; shift += 8) {
+      k_rs_count<<<nblocks, RS_THREADS, 0, s>>>(kin, n, shift, counts, nblocks);
+      EIFMM_CHECK_LAUNCH();
+      k_scan_excl<<<1, 1024, 0, s>>>(counts, (int64_t)256 * nblocks);
+      EIFMM_CHECK_LAUNCH();
+      k_rs_scatter<<<nblocks, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift,
+                                                   counts, nblocks);
+      EIFMM_CHECK_LAUNCH();
+      uint32_t* tk = kin; kin = kout; kout = tk;
+      int32_t* tv = vin; vin = vout; vout = tv;
+    }
+    if (kin != ps->keys) {
+      EIFMM_CUDA(cudaMemcpyAsync(ps->keys, kin, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+      EIFMM_CUDA(cudaMemcpyAsync(ps->perm, vin, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  k_leaf_off<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(ps->keys, n, nleaf, ps->leaf_off);
+  EIFMM_CHECK_LAUNCH();
+  if (n > 0) {
+    const double lk = L * ldexp(1.0, -(depth + 1));
+    k_gather_points<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        xyz, ps->perm, ps->keys, n, lo[0], lo[1], lo[2], lk, depth, ps->x, ps->y,
+        ps->z, ps->lx, ps->ly, ps->lz);
+    EIFMM_CHECK_LAUNCH();
+  }
+  k_nonempty<<<(unsigned)((nleaf + 255) / 256), 256, 0, s>>>(ps->leaf_off, nleaf, ps->nonempty, dbad + 1);
+  EIFMM_CHECK_LAUNCH();
+  int hb[2] = {0, 0};
+  EIFMM_CUDA(cudaMemcpyAsync(hb, dbad, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  EIFMM_CUDA(cudaStreamSynchronize(s));
+  dfree(k2);
+  dfree(v2);
+  dfree(counts);
+  dfree(dbad);
+  ps->n_nonempty = hb[1];
+  if (hb[0] != 0) {
+    set_error("eifmm_tree_build: " + std::to_string(hb[0]) +
+              " coordinates lie outside the cube [lo, lo + L]^3");
+    return EIFMM_EINVAL;
+  }
+  return EIFMM_OK;
+}
+
+void free_pointset(PointSet* ps) {
+  dfree(ps->perm);
+  dfree(ps->keys);
+  dfree(ps->leaf_off);
+  dfree(ps->nonempty);
+  dfree(ps->x);
+  dfree(ps->y);
+  dfree(ps->z);
+  dfree(ps->lx);
+  dfree(ps->ly);
+  dfree(ps->lz);
+  *ps = PointSet();
+}
+
+}  // namespace eifmm

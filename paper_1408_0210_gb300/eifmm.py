@@ -1,0 +1,276 @@
+"""Thin Python binding of the EIFMM C ABI (``include/eifmm.h``).
+
+Every function here has the name of the C entry point it calls and only
+marshals arguments (torch CUDA tensors or numpy arrays to pointers, status
+codes to exceptions).  All arithmetic runs in ``libeifmm.so``; there is no
+fallback: if the library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libeifmm.so")
+
+KERNELS = {"inv_r": 0, "config3": 1, "quad": 2, "one": 3, "exp_r2": 4,
+           "cos20r_r": 5, "sqrt_r2p1": 6}
+PREC = {"fp64": 0, "mixed": 1}
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "EUNSUPPORTED"}
+EXPORTS = [
+    "eifmm_last_error", "eifmm_version", "eifmm_training_sets", "eifmm_eim_build",
+    "eifmm_ops_load", "eifmm_ops_build", "eifmm_ops_error_estimate", "eifmm_ops_plan",
+    "eifmm_ops_destroy", "eifmm_tree_build", "eifmm_tree_export", "eifmm_tree_destroy",
+    "eifmm_evaluate", "eifmm_evaluate_host", "eifmm_evaluate_batched", "eifmm_debug_export",
+    "eifmm_set_timing", "eifmm_last_step_times",
+]
+
+
+class EifmmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class LevelData(C.Structure):
+    _fields_ = [("d", C.c_int), ("X", C.c_void_p), ("Y", C.c_void_p),
+                ("Gamma", C.c_void_p), ("B", C.c_void_p), ("eps_est", C.c_double)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libeifmm.so (built in place by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, dbl = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "eifmm_last_error": (C.c_char_p, []),
+        "eifmm_version": (C.c_char_p, []),
+        "eifmm_training_sets": (i32, [i32, dbl, i32, vp, vp, vp, vp]),
+        "eifmm_eim_build": (i32, [i32, vp, i64, vp, i64, dbl, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "eifmm_ops_load": (i32, [i32, dbl, i32, vp, vp]),
+        "eifmm_ops_build": (i32, [i32, dbl, i32, dbl, i32, vp, vp]),
+        "eifmm_ops_error_estimate": (i32, [vp, i32, vp, vp]),
+        "eifmm_ops_plan": (i32, [vp, i32, vp]),
+        "eifmm_ops_destroy": (None, [vp]),
+        "eifmm_tree_build": (i32, [vp, i64, vp, i64, vp, dbl, i32, i32, vp, vp]),
+        "eifmm_tree_export": (i32, [vp, i32, vp, vp, vp]),
+        "eifmm_tree_destroy": (None, [vp]),
+        "eifmm_evaluate": (i32, [vp, vp, vp, i64, i32, vp, i64, i32, vp]),
+        "eifmm_evaluate_host": (i32, [vp, vp, vp, i64, i32, vp, i64, i32, vp]),
+        "eifmm_evaluate_batched": (i32, [vp, vp, vp, i32, vp, i32, vp]),
+        "eifmm_debug_export": (i32, [vp, i32, i32, vp, i64]),
+        "eifmm_set_timing": (None, [i32]),
+        "eifmm_last_step_times": (i32, [vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != 0:
+        raise EifmmError(status, lib().eifmm_last_error().decode())
+
+
+def _p(a) -> int | None:
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _kid(kern) -> int:
+    return KERNELS[kern] if isinstance(kern, str) else int(kern)
+
+
+def _prec(p) -> int:
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def eifmm_version() -> str:
+    return lib().eifmm_version().decode()
+
+
+def eifmm_training_sets(level: int, L: float = 1.0, nJ: int = 9):
+    nx, ny = C.c_int64(), C.c_int64()
+    _check(lib().eifmm_training_sets(level, L, nJ, None, C.byref(nx), None, C.byref(ny)))
+    X = np.zeros((nx.value, 3))
+    Y = np.zeros((ny.value, 3))
+    _check(lib().eifmm_training_sets(level, L, nJ, _p(X), C.byref(nx), _p(Y), C.byref(ny)))
+    return X, Y
+
+
+def eifmm_eim_build(kern, X, Y, eps: float, d_max: int = 512, stream=None) -> dict:
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    d = C.c_int()
+    est = C.c_double()
+    ia = np.zeros(d_max, dtype=np.int64)
+    ib = np.zeros(d_max, dtype=np.int64)
+    G = np.zeros((d_max, d_max))
+    B = np.zeros((d_max, d_max))
+    piv = np.zeros(d_max + 1)
+    _check(lib().eifmm_eim_build(_kid(kern), _p(X), len(X), _p(Y), len(Y), float(eps), d_max,
+                                 C.byref(d), _p(ia), _p(ib), _p(G), _p(B), _p(piv),
+                                 C.byref(est), _stream(stream)))
+    n = d.value
+    return dict(d=n, ia=ia[:n].copy(), ib=ib[:n].copy(), Gamma=np.ascontiguousarray(G[:n, :n]),
+                B=np.ascontiguousarray(B[:n, :n]), piv=piv[:n + 1].copy(), eps_est=est.value,
+                X=X[ia[:n]].copy(), Y=Y[ib[:n]].copy())
+
+
+class Ops:
+    """Owner of an ``eifmm_ops`` handle."""
+
+    def __init__(self, handle: int, depth: int, L: float):
+        self.handle = handle
+        self.depth = depth
+        self.L = L
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.eifmm_ops_destroy(self.handle)
+            self.handle = None
+
+    def error_estimate(self, level: int):
+        e, d = C.c_double(), C.c_int()
+        _check(lib().eifmm_ops_error_estimate(self.handle, level, C.byref(e), C.byref(d)))
+        return e.value, d.value
+
+    def plan(self, tier_override: int = -1) -> int:
+        t = C.c_int()
+        _check(lib().eifmm_ops_plan(self.handle, tier_override, C.byref(t)))
+        return t.value
+
+
+def eifmm_ops_load(kern, L: float, depth: int, levels: dict) -> Ops:
+    arr = (LevelData * (depth + 1))()
+    keep = []
+    for k in range(2, depth + 1):
+        e = levels[k]
+        parts = [np.ascontiguousarray(e[n], dtype=np.float64) for n in ("X", "Y", "Gamma", "B")]
+        keep += parts
+        arr[k] = LevelData(e["d"], *[p.ctypes.data for p in parts], float(e.get("eps_est", 0.0)))
+    h = C.c_void_p()
+    _check(lib().eifmm_ops_load(_kid(kern), float(L), depth, C.cast(arr, C.c_void_p), C.byref(h)))
+    return Ops(h.value, depth, L)
+
+
+def eifmm_ops_build(kern, L: float, depth: int, eps: float, d_max: int = 512, stream=None) -> Ops:
+    h = C.c_void_p()
+    _check(lib().eifmm_ops_build(_kid(kern), float(L), depth, float(eps), d_max, _stream(stream),
+                                 C.byref(h)))
+    return Ops(h.value, depth, L)
+
+
+class Tree:
+    """Owner of an ``eifmm_tree`` handle."""
+
+    def __init__(self, handle: int, n_src: int, n_tgt: int, depth: int):
+        self.handle = handle
+        self.n_src = n_src
+        self.n_tgt = n_tgt
+        self.depth = depth
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.eifmm_tree_destroy(self.handle)
+            self.handle = None
+
+    def export(self, which: int = 0):
+        n = self.n_src if which == 0 else self.n_tgt
+        keys = np.zeros(n, dtype=np.uint32)
+        perm = np.zeros(n, dtype=np.int32)
+        off = np.zeros((1 << (3 * self.depth)) + 1, dtype=np.int64)
+        _check(lib().eifmm_tree_export(self.handle, which, _p(keys), _p(perm), _p(off)))
+        return keys, perm, off
+
+
+def eifmm_tree_build(src_xyz, tgt_xyz=None, lo=(0.0, 0.0, 0.0), L: float = 1.0, depth: int = 3,
+                     exclude_self: bool = True, stream=None) -> Tree:
+    """src_xyz / tgt_xyz: CUDA float64 tensors of shape (n, 3), contiguous."""
+    tgt = src_xyz if tgt_xyz is None else tgt_xyz
+    for t in (src_xyz, tgt):
+        assert t.is_cuda and t.dtype.is_floating_point and t.is_contiguous() and t.shape[-1] == 3
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    h = C.c_void_p()
+    _check(lib().eifmm_tree_build(_p(src_xyz), src_xyz.shape[0], _p(tgt), tgt.shape[0], _p(lo),
+                                  float(L), depth, int(bool(exclude_self)), _stream(stream),
+                                  C.byref(h)))
+    return Tree(h.value, src_xyz.shape[0], tgt.shape[0], depth)
+
+
+def eifmm_evaluate(tree: Tree, ops: Ops, sigma, f, prec="fp64", stream=None) -> None:
+    """sigma (n_src, R) and f (n_tgt, R): CUDA float64 tensors, column-major
+    (use ``t.T.contiguous().T`` or allocate as ``torch.empty(R, n).T``)."""
+    R = 1 if sigma.dim() == 1 else sigma.shape[1]
+    ld_s = sigma.shape[0] if sigma.dim() == 1 or R == 1 else sigma.stride(1)
+    ld_f = f.shape[0] if f.dim() == 1 or R == 1 else f.stride(1)
+    if R > 1:
+        assert sigma.stride(0) == 1 and f.stride(0) == 1, "sigma and f must be column-major"
+    _check(lib().eifmm_evaluate(tree.handle, ops.handle, _p(sigma), ld_s, R, _p(f), ld_f,
+                                _prec(prec), _stream(stream)))
+
+
+def eifmm_evaluate_host(tree: Tree, ops: Ops, sigma, f=None, prec="fp64", stream=None):
+    """HOST float64 arrays (n, R), column-major; returns f."""
+    sigma = np.asfortranarray(sigma if np.ndim(sigma) == 2 else np.asarray(sigma)[:, None],
+                              dtype=np.float64)
+    R = sigma.shape[1]
+    if f is None:
+        f = np.zeros((tree.n_tgt, R), order="F")
+    _check(lib().eifmm_evaluate_host(tree.handle, ops.handle, _p(sigma), sigma.shape[0], R, _p(f),
+                                     f.shape[0], _prec(prec), _stream(stream)))
+    return f
+
+
+def eifmm_evaluate_batched(trees, sigmas, fs, ops: Ops, prec="fp64", stream=None) -> None:
+    n = len(trees)
+    th = (C.c_void_p * n)(*[t.handle for t in trees])
+    sp = (C.c_void_p * n)(*[_p(s) for s in sigmas])
+    fp = (C.c_void_p * n)(*[_p(x) for x in fs])
+    _check(lib().eifmm_evaluate_batched(C.cast(th, C.c_void_p), C.cast(sp, C.c_void_p),
+                                        C.cast(fp, C.c_void_p), n, ops.handle, _prec(prec),
+                                        _stream(stream)))
+
+
+def eifmm_debug_export(tree: Tree, what: int, level: int, d: int, R: int = 1):
+    if what in (5, 6):
+        out = np.zeros(tree.n_tgt * R)
+        _check(lib().eifmm_debug_export(tree.handle, what, level, _p(out), out.size))
+        return out.reshape(R, tree.n_tgt).T.copy()
+    out = np.zeros((8 ** level, R, d))
+    _check(lib().eifmm_debug_export(tree.handle, what, level, _p(out), out.size))
+    return out
+
+
+def eifmm_set_timing(on: bool) -> None:
+    lib().eifmm_set_timing(int(bool(on)))
+
+
+def eifmm_last_step_times(tree: Tree) -> list[float]:
+    ms = (C.c_float * 9)()
+    _check(lib().eifmm_last_step_times(tree.handle, C.cast(ms, C.c_void_p)))
+    return list(ms)

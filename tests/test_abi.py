@@ -1,0 +1,82 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry point
+declared in include/eifmm.h, validates arguments before touching the device,
+and its host-side training sets equal the CPU checker's bit for bit."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def E():
+    from paper_1408_0210_gb300 import build, eifmm
+    build.build()
+    eifmm.lib()
+    return eifmm
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "eifmm.h")).read()
+    return sorted(set(re.findall(r"\b(eifmm_[a-z_0-9]+)\s*\(", txt)))
+
+
+def test_header_and_exports(E):
+    names = _declared()
+    assert len(names) >= 15
+    lib = C.CDLL(E.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(E.EXPORTS) == names
+
+
+def test_version_and_error_string(E):
+    assert "sm_103a" in E.eifmm_version()
+    assert isinstance(E.lib().eifmm_last_error(), bytes)
+
+
+@pytest.mark.parametrize("level", [2, 3, 4, 5, 6, 7])
+def test_training_sets_equal_checker(E, orc, level):
+    X, Y = E.eifmm_training_sets(level)
+    np.testing.assert_array_equal(X, orc.train_x(level))
+    np.testing.assert_array_equal(Y, orc.train_y(level))
+    X2, _ = E.eifmm_training_sets(level, L=3.0)
+    np.testing.assert_array_equal(X2, orc.train_x(level, 3.0))
+
+
+def test_argument_validation_without_device(E):
+    L = E.lib()
+    nx, ny = C.c_int64(), C.c_int64()
+    assert L.eifmm_training_sets(1, 1.0, 9, None, C.byref(nx), None, C.byref(ny)) == 1
+    assert L.eifmm_training_sets(3, -1.0, 9, None, C.byref(nx), None, C.byref(ny)) == 1
+    assert L.eifmm_training_sets(3, 1.0, 1, None, C.byref(nx), None, C.byref(ny)) == 1
+    h = C.c_void_p()
+    lo = np.zeros(3)
+    assert L.eifmm_tree_build(None, 10, None, 10, lo.ctypes.data, 1.0, 3, 0, None, C.byref(h)) == 1
+    assert L.eifmm_tree_build(1, 10, 1, 10, lo.ctypes.data, 1.0, 1, 0, None, C.byref(h)) == 1
+    assert L.eifmm_tree_build(1, 10, 1, 10, lo.ctypes.data, 1.0, 11, 0, None, C.byref(h)) == 1
+    assert L.eifmm_tree_build(1, 10, 2, 10, lo.ctypes.data, 1.0, 3, 1, None, C.byref(h)) == 1
+    assert b"exclude_self" in L.eifmm_last_error()
+    X = np.zeros((4, 3)); Y = np.ones((4, 3))
+    d = C.c_int(); est = C.c_double()
+    buf = np.zeros(64)
+    assert L.eifmm_eim_build(0, X.ctypes.data, 4, Y.ctypes.data, 4, 0.0, 4, C.byref(d), buf.ctypes.data,
+                             buf.ctypes.data, buf.ctypes.data, buf.ctypes.data, buf.ctypes.data,
+                             C.byref(est), None) == 1
+    assert L.eifmm_ops_load(0, 1.0, 1, None, C.byref(h)) == 1
+    assert L.eifmm_ops_build(0, 1.0, 3, -1.0, 100, None, C.byref(h)) == 1
+    assert L.eifmm_evaluate(None, None, None, 0, 1, None, 0, 0, None) == 1
+    assert L.eifmm_debug_export(None, 0, 2, None, 0) == 1
+
+
+def test_binding_refuses_missing_library(tmp_path, monkeypatch):
+    import importlib
+    from paper_1408_0210_gb300 import eifmm as E
+    monkeypatch.setattr(E, "_lib", None)
+    monkeypatch.setattr(E, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        E.lib()
+    importlib.reload(E)
