@@ -1,0 +1,325 @@
+#!/usr/bin/env python3
+"""Throughput of the EIFMM evaluation (Algorithm 3 steps 1-7 + near field +
+un-permute) on one GB300, in targets x RHS per second.
+
+Workload: 1,048,576 points iid uniform in [0,1)^3 (targets = sources, self pair
+excluded), K(r) = 1/|r|, octree depth 5 (32,768 leaves, 32 points per leaf),
+one sigma vector iid U[-1,1]; operators from the GPU EIM at eps = 1e-4 and
+eps = 1e-7.  One step = one eifmm_evaluate call with sigma and f resident in
+HBM; the tree is built and the operators loaded beforehand.  Between timed
+steps a 512 MB buffer is written to flush the 129 MB L2.
+
+Every variant's accuracy is checked against the exact FP64 sum (the library's
+GPU direct sum) on 2048 sampled targets; `value` is the mixed-precision path at
+eps = 1e-4 when it meets rel-L2 <= eps, else the FP64 path.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --impl reference the CPU checker of the repository (plain FP64 C, OpenMP)
+runs the same metric on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "targets*RHS/s (EIFMM evaluate, rel-L2 <= eps)"
+UNIT = "targets*RHS/s"
+N_POINTS = 1 << 20
+DEPTH = 5
+NRHS = 1
+EPS_LIST = (1e-4, 1e-7)
+SAMPLE_TARGETS = 2048
+WORKLOAD = "uniform cube N=1048576, K=1/r, depth 5, 1 RHS"
+
+
+def m2l_pairs(k: int) -> int:
+    """Exact number of (I, J) interaction-list pairs at level k (separable)."""
+    n = 1 << k
+    sa = sum(min(n - 1, 2 * (i >> 1) + 3) - max(0, 2 * (i >> 1) - 2) + 1 for i in range(n))
+    sb = sum(min(n - 1, i + 1) - max(0, i - 1) + 1 for i in range(n))
+    return sa ** 3 - sb ** 3
+
+
+def peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        d["source"] = "measured"
+        return d
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = [r.split(",") for r in self.out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist.init_process_group("nccl")
+    return rank, ws, dist
+
+
+def cpu_oracle_run(n: int, depth: int, eps: float, steps: int):
+    """Time the CPU checker's EIFMM (O2) on n points; returns (seconds per
+    evaluation, threads, d per level)."""
+    import oracle
+    from paper_1408_0210_gb300 import workloads as wl
+    x = wl.uniform_cube(n, 2)
+    s = wl.sigma_uniform(n, NRHS, 102)
+    lv = oracle.build_levels("inv_r", 1.0, depth, eps)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.eifmm("inv_r", 1.0, [0, 0, 0], depth, lv, x, x, s)
+        times.append(time.perf_counter() - t0)
+    return statistics.median(times), oracle.num_threads(), [lv[k]["d"] for k in sorted(lv)]
+
+
+# the bounded CPU sample: 131,072 points at depth 4 keeps 32 points per leaf
+CPU_SAMPLE_N, CPU_SAMPLE_DEPTH = 1 << 17, 4
+
+
+def reference_arm(args):
+    rank, ws, dist = (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), None)
+    if rank != 0:
+        return
+    eps = EPS_LIST[0]
+    for _ in range(max(args.warmup, 0)):
+        pass
+    sec, threads, ds = cpu_oracle_run(CPU_SAMPLE_N, CPU_SAMPLE_DEPTH, eps, max(1, args.steps))
+    value = CPU_SAMPLE_N * NRHS / sec
+    sample = (f"CPU EIFMM (plain FP64 C + OpenMP) on {CPU_SAMPLE_N} uniform points at depth "
+              f"{CPU_SAMPLE_DEPTH} (32 points/leaf as in the workload), eps={eps:g}, d={ds}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "eps": eps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variants", default="mixed:1e-4,fp64:1e-4,mixed:1e-7,fp64:1e-7")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    args.warmup = max(args.warmup, 3)
+
+    import torch
+
+    from paper_1408_0210_gb300 import eifmm as E
+    from paper_1408_0210_gb300 import workloads as wl
+
+    rank, ws, dist = dist_setup()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    pk = peaks()
+
+    # ---- inputs (per rank: an independent replica of the workload) -------
+    x = wl.uniform_cube(N_POINTS, 2 + 1000 * rank)
+    s = wl.sigma_uniform(N_POINTS, NRHS, 102 + 1000 * rank)
+    xd = torch.from_numpy(x).to(dev)
+    sd = torch.from_numpy(np.ascontiguousarray(s[:, 0])).to(dev)
+    f = torch.zeros(N_POINTS, dtype=torch.float64, device=dev)
+    tree = E.eifmm_tree_build(xd, None, (0, 0, 0), 1.0, DEPTH, True, stream)
+    idx = torch.from_numpy(wl.sample_targets(N_POINTS, SAMPLE_TARGETS, 55)).to(dev)
+    fref = E.eifmm_direct_sum("inv_r", xd, xd, sd, True, idx, stream)[:, 0]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    ops = {}
+    for eps in EPS_LIST:
+        ops[eps] = E.eifmm_ops_build("inv_r", 1.0, DEPTH, eps, 512, stream)
+
+    def run_variant(prec, eps, steps, warmup, timing=False):
+        o = ops[eps]
+        for _ in range(warmup):
+            E.eifmm_evaluate(tree, o, sd, f, prec, stream)
+        torch.cuda.synchronize()
+        e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        E.eifmm_set_timing(timing)
+        step_times = []
+        launches0 = E.eifmm_kernel_launches()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.zero_()
+            e0[i].record(stream)
+            E.eifmm_evaluate(tree, o, sd, f, prec, stream)
+            e1[i].record(stream)
+            if timing:
+                step_times.append(E.eifmm_last_step_times(tree))
+        torch.cuda.synchronize()
+        launches = E.eifmm_kernel_launches() - launches0
+        E.eifmm_set_timing(False)
+        ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / steps
+        if dist is not None:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        err = float(torch.linalg.norm(f[idx] - fref) / torch.linalg.norm(fref))
+        return ms, err, launches, step_times
+
+    variants = []
+    for v in args.variants.split(","):
+        prec, eps = v.split(":")
+        variants.append((prec, float(eps)))
+    results = {}
+    headline = None
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for prec, eps in variants:
+            try:
+                steps = args.steps if (prec == "mixed" or eps >= 1e-5) else max(3, args.steps // 3)
+                ms, err, launches, st = run_variant(prec, eps, steps, args.warmup, timing=True)
+            except E.EifmmError as e:
+                results[f"{prec}@{eps:g}"] = {"unavailable": str(e)}
+                continue
+            d = [ops[eps].error_estimate(k)[1] for k in range(2, DEPTH + 1)]
+            m2l = [statistics.median([t[9 + k] for t in st]) for k in range(2, DEPTH + 1)]
+            results[f"{prec}@{eps:g}"] = {
+                "value": N_POINTS * NRHS * ws / (ms * 1e-3), "ms_per_step": ms,
+                "rel_l2_vs_exact": err, "meets_eps": err <= eps, "d": d,
+                "gpu_launches": launches, "steps": steps,
+                "step_ms": [round(statistics.median([t[i] for t in st]), 4) for i in range(8)],
+                "m2l_ms_per_level": [round(v, 4) for v in m2l]}
+            if headline is None and err <= eps and (prec, eps) in (("mixed", 1e-4), ("fp64", 1e-4)):
+                headline = (prec, eps)
+    clocks = clk.summary()
+
+    if headline is None:
+        headline = ("fp64", 1e-4)
+    hp, he = headline
+    hr = results[f"{hp}@{he:g}"]
+
+    # ---- end to end through the host-buffer entry point -------------------
+    sh = torch.from_numpy(np.ascontiguousarray(s[:, 0])).pin_memory()
+    fh = torch.zeros(N_POINTS, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        E.lib().eifmm_evaluate_host(tree.handle, ops[he].handle, sh.data_ptr(), N_POINTS, 1,
+                                    fh.data_ptr(), N_POINTS, E.PREC[hp], stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ke = max(3, args.steps // 2)
+    for _ in range(ke):
+        rc = E.lib().eifmm_evaluate_host(tree.handle, ops[he].handle, sh.data_ptr(), N_POINTS, 1,
+                                         fh.data_ptr(), N_POINTS, E.PREC[hp], stream.cuda_stream)
+        assert rc == 0, E.lib().eifmm_last_error()
+    e2e_s = (time.perf_counter() - t0) / ke
+    e2e_val = N_POINTS * NRHS * ws / e2e_s
+
+    # ---- roofline of the dominant kernel: the M2L of the leaf level ------
+    o = ops[he]
+    dk = o.error_estimate(DEPTH)[1]
+    flops = 2.0 * dk * dk * m2l_pairs(DEPTH) * NRHS
+    m2l_ms = hr["m2l_ms_per_level"][-1]
+    achieved = flops / (m2l_ms * 1e-3) / 1e12
+    if hp == "mixed":
+        roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"],
+                "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"], "traffic": None,
+                "kernel": "M2L level 5 (tcgen05, BF16 split operands, FP32 accumulate)",
+                "peak_source": pk["source"] + " bf16 burst"}
+    else:
+        peak64 = 1.25
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                "frac": achieved / peak64, "traffic": None,
+                "kernel": "M2L level 5 (FP64 FMA)", "peak_source": "nominal FP64 1.25 TFLOP/s"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        sec, threads, ds = cpu_oracle_run(CPU_SAMPLE_N, CPU_SAMPLE_DEPTH, he, 1)
+        cpu = {"value": CPU_SAMPLE_N * NRHS / sec, "unit": UNIT, "cores": threads,
+               "kind": "oracle",
+               "sample": f"CPU EIFMM (plain FP64 C + OpenMP) on {CPU_SAMPLE_N} uniform points, "
+                         f"depth {CPU_SAMPLE_DEPTH} (32 points/leaf), eps={he:g}, d={ds}"}
+
+    line = {
+        "metric": METRIC, "value": hr["value"], "unit": UNIT, "n_gpus": ws,
+        "steps": hr["steps"], "warmup": args.warmup, "ms_per_step": hr["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+bf16x3" if hp == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "eps": he, "path": hp, "l2": "flushed (512 MB write) between steps",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": N_POINTS * NRHS * 8,
+                "d2h_bytes_per_step": N_POINTS * NRHS * 8},
+        "gpu_launches": hr["gpu_launches"],
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "variants": results,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

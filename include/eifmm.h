@@ -234,11 +234,31 @@ eifmm_status eifmm_evaluate_batched(eifmm_tree* const* trees,
 eifmm_status eifmm_debug_export(const eifmm_tree* tree, int what, int level,
                                 double* out, int64_t n);
 
-/* Per-step device times (ms) of the last evaluate when timing was enabled
- * with eifmm_set_timing(1): [P2M, M2M, solve-W, M2L, L2L, solve-l, L2P,
- * P2P, other]. */
+/* Exact sum of Eq. (1) on the GPU in FP64 (no approximation), for checking
+ * accuracy: f[e + r*n_eval] = sum_j sigma[j + r*ld_sigma] K(x_{t_e}, y_j) with
+ * t_e = tgt_idx[e] (DEVICE int64 array) or t_e = e when tgt_idx is NULL; the
+ * pair t_e == j is skipped when exclude_self != 0.  tgt_xyz / src_xyz are
+ * DEVICE row-major n x 3 arrays, sigma and f DEVICE column-major.  Errors:
+ * EINVAL (null pointers, sizes), ECUDA. */
+eifmm_status eifmm_direct_sum(eifmm_kernel kern, const double* tgt_xyz,
+                              int64_t n_tgt, const double* src_xyz,
+                              int64_t n_src, const double* sigma,
+                              int64_t ld_sigma, int n_rhs, int exclude_self,
+                              const int64_t* tgt_idx, int64_t n_eval,
+                              double* f, eifmm_stream stream);
+
+/* Number of kernels this library has launched since it was loaded (all
+ * devices, all threads). */
+uint64_t eifmm_kernel_launches(void);
+
+/* Device times (ms) of the last evaluate on this tree, recorded with CUDA
+ * events on the launching stream when timing is on (eifmm_set_timing(1);
+ * the evaluate then waits for its last event).  ms[20]: [0] sigma gather +
+ * P2M (step 1), [1] M2M (2), [2] Delta solves (3), [3] M2L (4), [4] L2L (5),
+ * [5] Delta^t solve (6), [6] wait for the near field, [7] L2P + sum +
+ * un-permute (7), [8] unused; [9 + k] the M2L launch of level k alone. */
 void eifmm_set_timing(int on);
-eifmm_status eifmm_last_step_times(const eifmm_tree* tree, float* ms9);
+eifmm_status eifmm_last_step_times(const eifmm_tree* tree, float* ms20);
 
 #ifdef __cplusplus
 }

@@ -4,11 +4,15 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <vector>
 
 #include "internal.h"
 
 namespace eifmm {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static thread_local std::string g_err;
 static bool g_timing = false;
@@ -40,8 +44,9 @@ void free_workspace(Workspace* ws) {
     if (k != 2) dfree(ws->l[k]);
     ws->l[k] = nullptr;
     dfree(ws->W32[k]); dfree(ws->Wh32[k]); dfree(ws->g32[k]); dfree(ws->wa[k]);
+    if (k != 2) dfree(ws->l32[k]);
     ws->W[k] = ws->Wh[k] = ws->g[k] = nullptr;
-    ws->W32[k] = ws->Wh32[k] = ws->g32[k] = nullptr;
+    ws->W32[k] = ws->Wh32[k] = ws->g32[k] = ws->l32[k] = nullptr;
     ws->wa[k] = nullptr;
   }
   dfree(ws->lh); dfree(ws->lh32); dfree(ws->sig); dfree(ws->sig32);
@@ -61,13 +66,20 @@ static void free_streams(Workspace* ws) {
   if (ws->ev_join) cudaEventDestroy(ws->ev_join);
   for (auto& e : ws->ev_t)
     if (e) cudaEventDestroy(e);
+  for (auto& e : ws->ev_m2l)
+    if (e) cudaEventDestroy(e);
   ws->side = nullptr;
   ws->ev_fork = ws->ev_join = nullptr;
   for (auto& e : ws->ev_t) e = nullptr;
+  for (auto& e : ws->ev_m2l) e = nullptr;
   dfree(ws->host_sig);
   dfree(ws->host_f);
   ws->host_sig = ws->host_f = nullptr;
   ws->host_cap = 0;
+  dfree(ws->err);
+  if (ws->err_host) cudaFreeHost(ws->err_host);
+  ws->err = nullptr;
+  ws->err_host = nullptr;
 }
 
 eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R);  // fmm32.cu
@@ -79,6 +91,7 @@ eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec) {
     EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_fork, cudaEventDisableTiming));
     EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_join, cudaEventDisableTiming));
     for (auto& e : ws.ev_t) EIFMM_CUDA(cudaEventCreate(&e));
+    for (auto& e : ws.ev_m2l) EIFMM_CUDA(cudaEventCreate(&e));
   }
   const int tier = (prec == EIFMM_PREC_MIXED) ? ops->tier : -1;
   if (ws.ops_id == (const void*)ops && ws.nrhs == R && ws.prec == prec && ws.tier == tier)
@@ -124,6 +137,28 @@ struct eifmm_tree {
 extern "C" const char* eifmm_last_error(void) { return g_err.c_str(); }
 extern "C" const char* eifmm_version(void) { return "eifmm-gb300 0.1 (sm_103a)"; }
 extern "C" void eifmm_set_timing(int on) { g_timing = on != 0; }
+extern "C" uint64_t eifmm_kernel_launches(void) { return g_launches.load(); }
+
+namespace eifmm {
+eifmm_status launch_direct_sum(int kern, const double* tgt, const double* src, int64_t n_src,
+                               const double* sigma, int64_t ld, int R, int exclude_self,
+                               const int64_t* idx, int64_t n_eval, double* f, cudaStream_t s);
+}
+
+extern "C" eifmm_status eifmm_direct_sum(eifmm_kernel kern, const double* tgt_xyz, int64_t n_tgt,
+                                         const double* src_xyz, int64_t n_src, const double* sigma,
+                                         int64_t ld_sigma, int n_rhs, int exclude_self,
+                                         const int64_t* tgt_idx, int64_t n_eval, double* f,
+                                         eifmm_stream stream) {
+  if (!tgt_xyz || !src_xyz || !sigma || !f || n_tgt < 1 || n_src < 1 || n_eval < 1 ||
+      n_rhs < 1 || n_rhs > kMaxRhs || ld_sigma < n_src || (int)kern < 0 || (int)kern > 6 ||
+      (!tgt_idx && n_eval > n_tgt)) {
+    set_error("eifmm_direct_sum: invalid argument");
+    return EIFMM_EINVAL;
+  }
+  return launch_direct_sum((int)kern, tgt_xyz, src_xyz, n_src, sigma, ld_sigma, n_rhs,
+                           exclude_self, tgt_idx, n_eval, f, (cudaStream_t)stream);
+}
 
 static int tier_for_eps(double eps) {
   if (eps >= 1e-5 * (1.0 - 1e-9)) return 0;
@@ -186,6 +221,12 @@ extern "C" eifmm_status eifmm_ops_load(eifmm_kernel kern, double L, int depth,
     return rc;
   }
   o.tier = tier_for_eps(eps_max > 0.0 ? eps_max : 1e-16);
+  if (o.tier <= 1) rc = build_kd_image(&o, o.tier == 1, s);
+  if (rc != EIFMM_OK) {
+    free_ops(&o);
+    delete h;
+    return rc;
+  }
   *out = h;
   return EIFMM_OK;
 }
@@ -252,7 +293,10 @@ extern "C" eifmm_status eifmm_ops_plan(eifmm_ops* ops, int tier_override, int* t
     set_error("eifmm_ops_plan: invalid handle or tier");
     return EIFMM_EINVAL;
   }
-  if (tier_override >= 0) ops->o.tier = tier_override;
+  if (tier_override >= 0) {
+    ops->o.tier = tier_override;
+    if (tier_override <= 1) EIFMM_TRY(build_kd_image(&ops->o, tier_override == 1, nullptr));
+  }
   if (tier) *tier = ops->o.tier;
   return EIFMM_OK;
 }
@@ -364,6 +408,8 @@ static eifmm_status evaluate_impl(eifmm_tree* tree, const eifmm_ops* ops, const 
   if (g_timing) {
     EIFMM_CUDA(cudaEventSynchronize(t.ws.ev_t[8]));
     for (int i = 0; i < 8; ++i) cudaEventElapsedTime(&t.ws.step_ms[i], t.ws.ev_t[i], t.ws.ev_t[i + 1]);
+    for (int k = 2; k <= t.depth; ++k)
+      cudaEventElapsedTime(&t.ws.step_ms[9 + k], t.ws.ev_m2l[k], t.ws.ev_m2l[k + 1]);
   }
   return EIFMM_OK;
 }
@@ -483,11 +529,11 @@ extern "C" eifmm_status eifmm_debug_export(const eifmm_tree* tree, int what, int
   return EIFMM_OK;
 }
 
-extern "C" eifmm_status eifmm_last_step_times(const eifmm_tree* tree, float* ms9) {
-  if (!tree || !ms9) {
+extern "C" eifmm_status eifmm_last_step_times(const eifmm_tree* tree, float* ms20) {
+  if (!tree || !ms20) {
     set_error("eifmm_last_step_times: null argument");
     return EIFMM_EINVAL;
   }
-  for (int i = 0; i < 9; ++i) ms9[i] = tree->t.ws.step_ms[i];
+  for (int i = 0; i < 20; ++i) ms20[i] = tree->t.ws.step_ms[i];
   return EIFMM_OK;
 }

@@ -344,7 +344,50 @@ k_p2p64(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
   }
 }
 
+// Exact FP64 sum for accuracy checks: one block per evaluated target.
+__global__ void __launch_bounds__(256)
+k_direct64(int kern, const double* __restrict__ tgt, const double* __restrict__ src,
+           int64_t ns, const double* __restrict__ sig, int64_t ld, int R, int exclude_self,
+           const int64_t* __restrict__ idx, int64_t n_eval, double* __restrict__ f) {
+  __shared__ double red[8][8];
+  const int64_t e = blockIdx.x;
+  const int64_t i = idx ? idx[e] : e;
+  const double x0 = tgt[3 * i], x1 = tgt[3 * i + 1], x2 = tgt[3 * i + 2];
+  for (int r0 = 0; r0 < R; r0 += 8) {
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t j = threadIdx.x; j < ns; j += 256) {
+      if (exclude_self && j == i) continue;
+      const double kv = kern_f64_ieee(kern, x0 - src[3 * j], x1 - src[3 * j + 1], x2 - src[3 * j + 2]);
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr)
+        if (r0 + rr < R) acc[rr] += sig[j + (r0 + rr) * ld] * kv;
+    }
+#pragma unroll
+    for (int rr = 0; rr < 8; ++rr)
+      for (int o = 16; o > 0; o >>= 1) acc[rr] += __shfl_down_sync(0xffffffffu, acc[rr], o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0)
+      for (int rr = 0; rr < 8; ++rr) red[w][rr] = acc[rr];
+    __syncthreads();
+    if (threadIdx.x < 8 && r0 + (int)threadIdx.x < R) {
+      double s = 0.0;
+      for (int ww = 0; ww < 8; ++ww) s += red[ww][threadIdx.x];
+      f[e + (r0 + threadIdx.x) * n_eval] = s;
+    }
+  }
+}
+
 }  // namespace
+
+eifmm_status launch_direct_sum(int kern, const double* tgt, const double* src, int64_t n_src,
+                               const double* sigma, int64_t ld, int R, int exclude_self,
+                               const int64_t* idx, int64_t n_eval, double* f, cudaStream_t s) {
+  k_direct64<<<(unsigned)n_eval, 256, 0, s>>>(kern, tgt, src, n_src, sigma, ld, R, exclude_self,
+                                              idx, n_eval, f);
+  EIFMM_CHECK_LAUNCH();
+  return EIFMM_OK;
+}
 
 eifmm_status launch_gather_sigma(const double* sigma, int64_t ld, const PointSet& src, int R,
                                  double* s64, float* s32, cudaStream_t s) {
@@ -385,7 +428,7 @@ static void record(Workspace& ws, int i, cudaStream_t s) {
 }
 
 eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_sigma, int R,
-                       double* f, int64_t ld_f, cudaStream_t s) {
+                       double* f, int64_t ld_f, cudaStream_t s, bool near32) {
   Workspace& ws = t->ws;
   const int kap = t->depth;
   const int kern = (int)ops->kern;
@@ -393,11 +436,12 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
   const PointSet& T = t->tgt;
   const double lk = t->L * ldexp(1.0, -(kap + 1));
   record(ws, 0, s);
-  EIFMM_TRY(launch_gather_sigma(sigma, ld_sigma, S, R, ws.sig, nullptr, s));
+  EIFMM_TRY(launch_gather_sigma(sigma, ld_sigma, S, R, ws.sig, near32 ? ws.sig32 : nullptr, s));
   // near field on the side stream, concurrent with the far field
   EIFMM_CUDA(cudaEventRecord(ws.ev_fork, s));
   EIFMM_CUDA(cudaStreamWaitEvent(ws.side, ws.ev_fork, 0));
-  EIFMM_TRY(launch_p2p64(t, kern, ws.sig, R, ws.fnear, ws.side));
+  if (near32) EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, ws.side));
+  else EIFMM_TRY(launch_p2p64(t, kern, ws.sig, R, ws.fnear, ws.side));
   EIFMM_CUDA(cudaEventRecord(ws.ev_join, ws.side));
 
   // step 1
@@ -436,12 +480,14 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
   record(ws, 3, s);
   // step 4
   for (int k = 2; k <= kap; ++k) {
+    if (timing_enabled()) cudaEventRecord(ws.ev_m2l[k], s);
     const int d = ops->lv[k].d;
     const int64_t nb = (int64_t)1 << (3 * k);
     k_m2l64<<<dim3((unsigned)(nb / 8 / M2L_NB * 8), R), TPB, M2L_NB * d * sizeof(double), s>>>(
         k, d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.Wh[k], ws.g[k]);
     EIFMM_CHECK_LAUNCH();
   }
+  if (timing_enabled()) cudaEventRecord(ws.ev_m2l[kap + 1], s);
   record(ws, 4, s);
   // step 5 (l^2 = g^2)
   for (int k = 3; k <= kap; ++k) {

@@ -28,7 +28,12 @@ void set_error(const std::string& msg);
       return EIFMM_ECUDA;                                                    \
     }                                                                        \
   } while (0)
-#define EIFMM_CHECK_LAUNCH() EIFMM_CUDA(cudaGetLastError())
+void count_launch();
+#define EIFMM_CHECK_LAUNCH()          \
+  do {                                \
+    ::eifmm::count_launch();          \
+    EIFMM_CUDA(cudaGetLastError());   \
+  } while (0)
 #define EIFMM_TRY(call)                 \
   do {                                  \
     eifmm_status s_ = (call);           \
@@ -68,10 +73,11 @@ struct LevelOps {
   float* B32_cm = nullptr;
   float* B32_rm = nullptr;
   float* X32 = nullptr;    // d x 3
-  // M2L operands for the tensor-core kernel: per slot, 3 BF16 split planes
-  // of K^delta in the canonical K-major 128B-swizzled layout, [slot][plane]
-  // [n-row < dp][k < dp].
-  __nv_bfloat16* kd_bf16 = nullptr;
+  // M2L operands of the tensor-core kernel: K^delta split in two planes
+  // (hi, lo) in the K-major 128B-swizzled layout,
+  // [slot][chunk of 128 B of l][plane][row m' < dp][128 B].
+  void* kd_img = nullptr;
+  int kd_img_tf32 = -1;  // -1 none, 0 BF16 planes, 1 TF32 planes
 };
 
 struct Ops {
@@ -114,9 +120,12 @@ struct Workspace {
   float* W32[kMaxLevel + 1] = {};
   float* Wh32[kMaxLevel + 1] = {};
   float* g32[kMaxLevel + 1] = {};
+  float* l32[kMaxLevel + 1] = {};  // l32[2] aliases g32[2]
   float* lh32 = nullptr;
-  // tensor-core M2L A operand planes: [box*R + r][plane][dp] bf16
-  __nv_bfloat16* wa[kMaxLevel + 1] = {};
+  // tensor-core M2L A operand planes: [plane][box*R + r][dp] (BF16 or TF32)
+  void* wa[kMaxLevel + 1] = {};
+  int* err = nullptr;           // device error word of bounded waits
+  int* err_host = nullptr;      // pinned copy, read at the next call
   double* sig = nullptr;        // sorted sigma, n_src x R (col-major, ld n_src)
   float* sig32 = nullptr;
   double* fnear = nullptr;      // n_tgt x R, sorted order
@@ -127,8 +136,9 @@ struct Workspace {
   cudaStream_t side = nullptr;  // near field runs here, concurrent with far
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_t[10] = {};
+  cudaEvent_t ev_m2l[kMaxLevel + 2] = {};
   bool evaluated = false;
-  float step_ms[9] = {};
+  float step_ms[20] = {};
 };
 
 struct Tree {
@@ -151,7 +161,10 @@ void free_ops(Ops* ops);
 
 eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma,
                        int64_t ld_sigma, int R, double* f, int64_t ld_f,
-                       cudaStream_t s);
+                       cudaStream_t s, bool near32 = false);
+eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R,
+                          double* fnear, cudaStream_t s);
+eifmm_status build_kd_image(Ops* ops, bool tf32, cudaStream_t s);
 eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma,
                         int64_t ld_sigma, int R, double* f, int64_t ld_f,
                         cudaStream_t s);

@@ -1,0 +1,25 @@
+// m2l_tc.h -- launcher of the tensor-core M2L (step 4 of Algorithm 3).
+#pragma once
+#include "internal.h"
+
+namespace eifmm {
+
+struct M2LTcArgs {
+  int level;
+  int64_t nbox;          // 8^level
+  int R;                 // right-hand sides; rows = nbox * R
+  int64_t rows;
+  int dp;                // padded rank (multiple of 64), <= kMaxDpTc
+  int tmem_cols;         // power of two >= dp
+  const void* wa;        // A planes [2][rows][dp] (BF16 or TF32 bit patterns)
+  const void* kd_img;    // B image [343][dp*esz/128][2][dp rows x 128 B], swizzled
+  const int* slot_lists; // [8][189]
+  float* g;              // [rows][dp] FP32 output
+  int* err;              // device error word (0 = ok)
+};
+
+constexpr int kMaxDpTc = 320;
+size_t m2l_tc_smem_bytes(int dp, bool tf32);
+eifmm_status launch_m2l_tc(const M2LTcArgs& a, bool tf32, cudaStream_t s);
+
+}  // namespace eifmm

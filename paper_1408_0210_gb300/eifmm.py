@@ -24,7 +24,7 @@ EXPORTS = [
     "eifmm_ops_load", "eifmm_ops_build", "eifmm_ops_error_estimate", "eifmm_ops_plan",
     "eifmm_ops_destroy", "eifmm_tree_build", "eifmm_tree_export", "eifmm_tree_destroy",
     "eifmm_evaluate", "eifmm_evaluate_host", "eifmm_evaluate_batched", "eifmm_debug_export",
-    "eifmm_set_timing", "eifmm_last_step_times",
+    "eifmm_set_timing", "eifmm_last_step_times", "eifmm_direct_sum", "eifmm_kernel_launches",
 ]
 
 
@@ -71,6 +71,8 @@ def lib() -> C.CDLL:
         "eifmm_debug_export": (i32, [vp, i32, i32, vp, i64]),
         "eifmm_set_timing": (None, [i32]),
         "eifmm_last_step_times": (i32, [vp, vp]),
+        "eifmm_direct_sum": (i32, [i32, vp, i64, vp, i64, vp, i64, i32, i32, vp, i64, vp, vp]),
+        "eifmm_kernel_launches": (C.c_uint64, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -271,6 +273,24 @@ def eifmm_set_timing(on: bool) -> None:
 
 
 def eifmm_last_step_times(tree: Tree) -> list[float]:
-    ms = (C.c_float * 9)()
+    ms = (C.c_float * 20)()
     _check(lib().eifmm_last_step_times(tree.handle, C.cast(ms, C.c_void_p)))
     return list(ms)
+
+
+def eifmm_direct_sum(kern, tgt_xyz, src_xyz, sigma, exclude_self=True, tgt_idx=None, stream=None):
+    """Exact FP64 sum on the GPU at the targets tgt_idx (CUDA int64) or all
+    targets; sigma (n_src,) or column-major (n_src, R).  Returns f (n_eval, R)."""
+    import torch
+    R = 1 if sigma.dim() == 1 else sigma.shape[1]
+    ld = sigma.shape[0] if (sigma.dim() == 1 or R == 1) else sigma.stride(1)
+    n_eval = tgt_xyz.shape[0] if tgt_idx is None else tgt_idx.shape[0]
+    f = torch.zeros(R, n_eval, dtype=torch.float64, device=sigma.device).T
+    _check(lib().eifmm_direct_sum(_kid(kern), _p(tgt_xyz), tgt_xyz.shape[0], _p(src_xyz),
+                                  src_xyz.shape[0], _p(sigma), ld, R, int(bool(exclude_self)),
+                                  _p(tgt_idx), n_eval, _p(f), _stream(stream)))
+    return f
+
+
+def eifmm_kernel_launches() -> int:
+    return int(lib().eifmm_kernel_launches())

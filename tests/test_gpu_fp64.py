@@ -270,3 +270,17 @@ def test_fp64_full_size_1m_depth5(E, orc):
     lv = _levels(orc, "inv_r", depth, eps)
     f2 = orc.eifmm("inv_r", 1.0, [0, 0, 0], depth, lv, x, x, s)[:, 0]
     assert relmax(fg, f2) <= 1e-12
+
+
+def test_direct_sum_matches_checker(E, orc):
+    x = wl.uniform_cube(5000, 90)
+    y = wl.gaussian_mixture(7000, 91)
+    s = wl.sigma_uniform(7000, 2, 92)
+    idx = wl.sample_targets(5000, 300, 93)
+    sd = torch.from_numpy(np.asfortranarray(s)).to("cuda").T.contiguous().T
+    fg = E.eifmm_direct_sum("inv_r", dev(x), dev(y), sd, False, dev(idx)).cpu().numpy()
+    fo = orc.direct_sum("inv_r", x, y, s, exclude_self=False, tgt_idx=idx)
+    assert relmax(fg, fo) <= 1e-13
+    fg = E.eifmm_direct_sum("config3", dev(x), dev(x), dev(s[:5000, 0]), True).cpu().numpy()
+    fo = orc.direct_sum("config3", x, x, s[:5000, :1])
+    assert relmax(fg, fo) <= 1e-12
