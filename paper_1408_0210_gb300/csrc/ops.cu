@@ -200,7 +200,7 @@ void free_ops(Ops* ops) {
     dfree(v.X); dfree(v.Y); dfree(v.G_rm); dfree(v.G_cm); dfree(v.B_rm); dfree(v.B_cm);
     dfree(v.m2mT); dfree(v.l2lT); dfree(v.kdT); dfree(v.m2mT32); dfree(v.l2lT32);
     dfree(v.G32_cm); dfree(v.G32_rm); dfree(v.B32_cm); dfree(v.B32_rm); dfree(v.X32);
-    dfree(v.kd_bf16);
+    dfree(v.kd_img);
     v = LevelOps();
   }
   dfree(ops->d_slot_lists);
