@@ -49,8 +49,10 @@ void free_workspace(Workspace* ws) {
     ws->W32[k] = ws->Wh32[k] = ws->g32[k] = ws->l32[k] = nullptr;
     ws->wa[k] = nullptr;
   }
-  dfree(ws->lh); dfree(ws->lh32); dfree(ws->sig); dfree(ws->sig32);
-  dfree(ws->fnear); dfree(ws->ffar);
+  dfree(ws->lh); dfree(ws->lh32); dfree(ws->sig); dfree(ws->sig32); dfree(ws->m2l_part);
+  ws->m2l_part = nullptr;
+  dfree(ws->fnear); dfree(ws->ffar); dfree(ws->tmp);
+  ws->tmp = nullptr;
   ws->lh = nullptr; ws->lh32 = nullptr; ws->sig = nullptr; ws->sig32 = nullptr;
   ws->fnear = nullptr; ws->ffar = nullptr;
   ws->ops_id = nullptr;
@@ -111,6 +113,11 @@ eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec) {
     EIFMM_TRY(dalloc(&ws.lh, ((size_t)1 << (3 * kap)) * R * ops->lv[kap].d));
   } else {
     EIFMM_TRY(alloc_mixed_workspace(t, ops, R));
+  }
+  {
+    int dpmax = 0;
+    for (int k = 2; k <= kap; ++k) dpmax = ops->lv[k].dp > dpmax ? ops->lv[k].dp : dpmax;
+    EIFMM_TRY(dmalloc(&ws.tmp, ((size_t)1 << (3 * kap)) * R * dpmax * sizeof(double)));
   }
   EIFMM_TRY(dalloc(&ws.sig, (size_t)(t->src.n > 0 ? t->src.n : 1) * R));
   EIFMM_TRY(dalloc(&ws.sig32, (size_t)(t->src.n > 0 ? t->src.n : 1) * R));
@@ -301,8 +308,11 @@ extern "C" eifmm_status eifmm_ops_plan(eifmm_ops* ops, int tier_override, int* t
   return EIFMM_OK;
 }
 
+static void invalidate_batch(const void* h);
+
 extern "C" void eifmm_ops_destroy(eifmm_ops* ops) {
   if (!ops) return;
+  invalidate_batch(ops);
   free_ops(&ops->o);
   delete ops;
 }
@@ -366,6 +376,7 @@ extern "C" eifmm_status eifmm_tree_export(const eifmm_tree* tree, int which, uin
 
 extern "C" void eifmm_tree_destroy(eifmm_tree* tree) {
   if (!tree) return;
+  invalidate_batch(tree);
   cudaDeviceSynchronize();
   free_workspace(&tree->t.ws);
   free_streams(&tree->t.ws);
@@ -460,11 +471,36 @@ extern "C" eifmm_status eifmm_evaluate_host(eifmm_tree* tree, const eifmm_ops* o
   return EIFMM_OK;
 }
 
+// The batch is recorded once into a CUDA graph (after one direct pass that
+// sizes every workspace) and replayed by a single cudaGraphLaunch while the
+// same trees, operators, precision and array pointers are passed again.
+namespace {
+struct BatchGraph {
+  std::vector<const void*> key;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t stream = nullptr;
+};
+BatchGraph g_batch;
+}  // namespace
+
+// A graph refers to the workspaces of its trees and operators: drop it when
+// one of them is destroyed.
+static void invalidate_batch(const void* h) {
+  if (!g_batch.exec) return;
+  for (const void* k : g_batch.key)
+    if (k == h) {
+      cudaGraphExecDestroy(g_batch.exec);
+      g_batch.exec = nullptr;
+      g_batch.key.clear();
+      return;
+    }
+}
+
 extern "C" eifmm_status eifmm_evaluate_batched(eifmm_tree* const* trees, const double* const* sigma,
                                                double* const* f, int n_problems,
                                                const eifmm_ops* ops, eifmm_precision prec,
                                                eifmm_stream stream) {
-  if (!trees || !sigma || !f || n_problems < 0 || !ops) {
+  if (!trees || !sigma || !f || n_problems < 0 || !ops || (prec != 0 && prec != 1)) {
     set_error("eifmm_evaluate_batched: invalid argument");
     return EIFMM_EINVAL;
   }
@@ -475,11 +511,61 @@ extern "C" eifmm_status eifmm_evaluate_batched(eifmm_tree* const* trees, const d
     }
     EIFMM_TRY(check_eval(trees[p], ops, 1, trees[p]->t.src.n, trees[p]->t.tgt.n, (int)prec));
   }
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<const void*> key;
+  key.push_back(ops);
+  key.push_back((const void*)(intptr_t)prec);
+  key.push_back((const void*)(intptr_t)ops->o.tier);
+  key.push_back((const void*)s);
+  for (int p = 0; p < n_problems; ++p) {
+    key.push_back(trees[p]);
+    key.push_back(sigma[p]);
+    key.push_back(f[p]);
+  }
+  if (g_batch.exec && g_batch.key == key && !g_timing) {
+    EIFMM_CUDA(cudaGraphLaunch(g_batch.exec, s));
+    for (int p = 0; p < n_problems; ++p) trees[p]->t.ws.evaluated = true;
+    return EIFMM_OK;
+  }
+  // direct pass (sizes the workspaces; also the result of this call)
   for (int p = 0; p < n_problems; ++p) {
     if (trees[p]->t.tgt.n == 0) continue;
-    EIFMM_TRY(evaluate_impl(trees[p], ops, sigma[p], trees[p]->t.src.n, 1, f[p],
-                            trees[p]->t.tgt.n, (int)prec, (cudaStream_t)stream));
+    EIFMM_TRY(evaluate_impl(trees[p], ops, sigma[p], trees[p]->t.src.n, 1, f[p], trees[p]->t.tgt.n,
+                            (int)prec, s));
   }
+  if (g_timing || s == nullptr) return EIFMM_OK;  // the legacy stream cannot be captured
+  if (g_batch.exec) {
+    cudaGraphExecDestroy(g_batch.exec);
+    g_batch.exec = nullptr;
+    g_batch.key.clear();
+  }
+  EIFMM_CUDA(cudaStreamSynchronize(s));
+  cudaGraph_t graph = nullptr;
+  EIFMM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  eifmm_status rc = EIFMM_OK;
+  for (int p = 0; p < n_problems && rc == EIFMM_OK; ++p) {
+    if (trees[p]->t.tgt.n == 0) continue;
+    rc = evaluate_impl(trees[p], ops, sigma[p], trees[p]->t.src.n, 1, f[p], trees[p]->t.tgt.n,
+                       (int)prec, s);
+  }
+  cudaError_t e = cudaStreamEndCapture(s, &graph);
+  if (rc != EIFMM_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) {
+    set_error(std::string("eifmm_evaluate_batched: stream capture failed: ") + cudaGetErrorString(e));
+    return EIFMM_ECUDA;
+  }
+  e = cudaGraphInstantiate(&g_batch.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    g_batch.exec = nullptr;
+    set_error(std::string("eifmm_evaluate_batched: graph instantiation failed: ") + cudaGetErrorString(e));
+    return EIFMM_ECUDA;
+  }
+  g_batch.key = key;
+  g_batch.stream = s;
   return EIFMM_OK;
 }
 

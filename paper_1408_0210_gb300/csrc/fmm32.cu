@@ -9,8 +9,12 @@
 //
 // Far-field arrays: [row = box * R + r][dp] FP32, dp = d rounded up to 64,
 // padding columns zero.
+#include <algorithm>
+
 #include "internal.h"
 #include "m2l_tc.h"
+#include "transfer.cuh"
+#include "solve.cuh"
 
 namespace eifmm {
 
@@ -68,131 +72,6 @@ k_p2m32(int kern_rt, const int32_t* __restrict__ off, const float* __restrict__ 
   }
 }
 
-// ---------------------------------------------------------------- step 2 --
-__global__ void __launch_bounds__(TPB)
-k_m2m32(int dk, int dc, int dpk, int dpc, int R, const float* __restrict__ m2mT,
-        const float* __restrict__ Wc, float* __restrict__ Wp, int64_t nparent) {
-  extern __shared__ float swf[];  // [4][8][dc]
-  const int r = blockIdx.y;
-  const int64_t P0 = 4 * (int64_t)blockIdx.x;
-  for (int t = threadIdx.x; t < 4 * 8 * dc; t += TPB) {
-    const int p = t / (8 * dc), rem = t - p * 8 * dc, i = rem / dc, q = rem - i * dc;
-    const int64_t P = P0 + p;
-    swf[t] = (P < nparent) ? Wc[((8 * P + i) * R + r) * dpc + q] : 0.f;
-  }
-  __syncthreads();
-  for (int m = threadIdx.x; m < dpk; m += TPB) {
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-    if (m < dk)
-      for (int i = 0; i < 8; ++i) {
-        const float* op = m2mT + (int64_t)i * dc * dk + m;
-        const float* w0 = swf + i * dc;
-        for (int q = 0; q < dc; ++q) {
-          const float o = op[(int64_t)q * dk];
-          a0 = fmaf(o, w0[q], a0);
-          a1 = fmaf(o, w0[q + 8 * dc], a1);
-          a2 = fmaf(o, w0[q + 16 * dc], a2);
-          a3 = fmaf(o, w0[q + 24 * dc], a3);
-        }
-      }
-    const float av[4] = {a0, a1, a2, a3};
-    for (int p = 0; p < 4; ++p)
-      if (P0 + p < nparent) Wp[((P0 + p) * R + r) * dpk + m] = av[p];
-  }
-}
-
-// ------------------------------------------------------------ steps 3, 6 --
-// One warp per vector; out = Delta v (transpose = 0) or Delta^t v (= 1) by the
-// triangular solves of Section 4.1 in precision Tc.  Output: FP32 array
-// (out32, ld dp) and/or the two M2L operand planes (BF16 or TF32 bits).
-__device__ __forceinline__ float tf32_round(float v) {
-  uint32_t u = __float_as_uint(v);
-  u = (u + 0x1000u) & ~0x1FFFu;
-  return __uint_as_float(u);
-}
-
-template <typename Tc, int PLANES>  // PLANES: 0 none, 1 BF16, 2 TF32
-__global__ void __launch_bounds__(TPB)
-k_solve_mixed(int d, int dp, int transpose, const Tc* __restrict__ G_cm, const Tc* __restrict__ G_rm,
-              const Tc* __restrict__ B_cm, const Tc* __restrict__ B_rm, const float* __restrict__ in,
-              float* __restrict__ out32, void* __restrict__ planes, int64_t nvec) {
-  extern __shared__ unsigned char sraw[];
-  Tc* sv_all = (Tc*)sraw;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t v = (int64_t)blockIdx.x * (TPB / 32) + w;
-  if (v >= nvec) return;
-  Tc* sv = sv_all + w * d;
-  for (int j = lane; j < d; j += 32) sv[j] = (Tc)in[v * dp + j];
-  __syncwarp();
-  if (!transpose) {
-    for (int k = 0; k < d; ++k) {
-      const Tc zk = sv[k] / G_cm[(int64_t)k * d + k];
-      __syncwarp();
-      if (lane == 0) sv[k] = zk;
-      for (int j = k + 1 + lane; j < d; j += 32) sv[j] -= G_cm[(int64_t)k * d + j] * zk;
-      __syncwarp();
-    }
-    for (int k = d - 1; k >= 0; --k) {
-      const Tc wk = sv[k];
-      for (int j = lane; j < k; j += 32) sv[j] -= B_rm[(int64_t)k * d + j] * wk;
-      __syncwarp();
-    }
-  } else {
-    for (int k = 0; k < d; ++k) {
-      const Tc zk = sv[k];
-      for (int j = k + 1 + lane; j < d; j += 32) sv[j] -= B_cm[(int64_t)k * d + j] * zk;
-      __syncwarp();
-    }
-    for (int k = d - 1; k >= 0; --k) {
-      const Tc wk = sv[k] / G_rm[(int64_t)k * d + k];
-      __syncwarp();
-      if (lane == 0) sv[k] = wk;
-      for (int j = lane; j < k; j += 32) sv[j] -= G_rm[(int64_t)k * d + j] * wk;
-      __syncwarp();
-    }
-  }
-  for (int j = lane; j < dp; j += 32) {
-    const Tc x = j < d ? sv[j] : (Tc)0;
-    if (out32) out32[v * dp + j] = (float)x;
-    if (PLANES == 1) {
-      __nv_bfloat16* pl = (__nv_bfloat16*)planes;
-      const float xf = (float)x;
-      const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
-      const __nv_bfloat16 lo = __float2bfloat16_rn((float)(x - (Tc)__bfloat162float(hi)));
-      pl[v * dp + j] = hi;
-      pl[nvec * dp + v * dp + j] = lo;
-    } else if (PLANES == 2) {
-      float* pl = (float*)planes;
-      const float hi = tf32_round((float)x);
-      const float lo = tf32_round((float)(x - (Tc)hi));
-      pl[v * dp + j] = hi;
-      pl[nvec * dp + v * dp + j] = lo;
-    }
-  }
-}
-
-// ---------------------------------------------------------------- step 5 --
-__global__ void __launch_bounds__(TPB)
-k_l2l32(int dk, int dp, int dpk, int dpp, int R, const float* __restrict__ l2lT,
-        const float* __restrict__ lpar, const float* __restrict__ g, float* __restrict__ lout) {
-  extern __shared__ float slf[];
-  const int64_t P = blockIdx.x;
-  const int r = blockIdx.y;
-  for (int q = threadIdx.x; q < dp; q += TPB) slf[q] = lpar[(P * R + r) * dpp + q];
-  __syncthreads();
-  for (int o = threadIdx.x; o < 8 * dpk; o += TPB) {
-    const int i = o / dpk, mp = o - i * dpk;
-    const int64_t o2 = ((8 * P + i) * R + r) * dpk + mp;
-    if (mp >= dk) {
-      lout[o2] = 0.f;
-      continue;
-    }
-    const float* op = l2lT + (int64_t)i * dp * dk + mp;
-    float a = 0.f;
-    for (int q = 0; q < dp; ++q) a = fmaf(op[(int64_t)q * dk], slf[q], a);
-    lout[o2] = g[o2] + a;
-  }
-}
 
 // ---------------------------------------------------------------- step 7 --
 template <int KERN>
@@ -255,7 +134,8 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, int nleaves,
         const float* __restrict__ sig, int64_t ns, int R, int depth, float two_l,
         int exclude_self, double* __restrict__ fnear) {
   const int kern = KERN >= 0 ? KERN : kern_rt;
-  __shared__ float4 src[P2P_WARPS][P2P_CHUNK];
+  __shared__ float4 src[P2P_WARPS][P2P_CHUNK];        // xyz in the target frame
+  __shared__ float ssig[P2P_WARPS][RC][P2P_CHUNK];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * P2P_WARPS + w;
   if (gw >= nleaves) return;
@@ -273,8 +153,10 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, int nleaves,
     const bool act = ti < nT;
     const int p = t0 + (act ? ti : 0);
     const float x0 = tlx[p], x1 = tly[p], x2 = tlz[p];
-    for (int r = 0; r < R; ++r) {
-      float sum = 0.f, comp = 0.f;
+    for (int r0 = 0; r0 < R; r0 += RC) {
+      float sum[RC], comp[RC];
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr) sum[rr] = comp[rr] = 0.f;
       for (int nb = 0; nb < 27; ++nb) {
         const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
         const int jx = c[0] + dx, jy = c[1] + dy, jz = c[2] + dz;
@@ -287,7 +169,12 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, int nleaves,
           __syncwarp();
           for (int t = lane; t < P2P_CHUNK; t += 32) {
             const int q = q0 + t;
-            if (q < se) src[w][t] = make_float4(slx[q] + s0, sly[q] + s1, slz[q] + s2, sig[q + (int64_t)r * ns]);
+            if (q < se) {
+              src[w][t] = make_float4(slx[q] + s0, sly[q] + s1, slz[q] + s2, 0.f);
+#pragma unroll
+              for (int rr = 0; rr < RC; ++rr)
+                ssig[w][rr][t] = (r0 + rr < R) ? sig[q + (int64_t)(r0 + rr) * ns] : 0.f;
+            }
           }
           __syncwarp();
           const int cnt = min(P2P_CHUNK, se - q0);
@@ -295,17 +182,25 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, int nleaves,
             for (int j = si; j < cnt; j += S) {
               if (exclude_self && q0 + j == p) continue;
               const float4 y = src[w][j];
-              const float term = y.w * kern_f32(kern, x0 - y.x, x1 - y.y, x2 - y.z);
-              const float yk = term - comp;
-              const float tk = sum + yk;
-              comp = (tk - sum) - yk;
-              sum = tk;
+              const float kv = kern_f32(kern, x0 - y.x, x1 - y.y, x2 - y.z);
+#pragma unroll
+              for (int rr = 0; rr < RC; ++rr) {
+                if (r0 + rr >= R) break;
+                const float yk = ssig[w][rr][j] * kv - comp[rr];
+                const float tk = sum[rr] + yk;
+                comp[rr] = (tk - sum[rr]) - yk;
+                sum[rr] = tk;
+              }
             }
         }
       }
-      double tot = act ? (double)sum - (double)comp : 0.0;
-      for (int o = Tp; o < 32; o <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-      if (act && si == 0) fnear[p + (int64_t)r * nt] = tot;
+#pragma unroll
+      for (int rr = 0; rr < RC; ++rr) {
+        if (r0 + rr >= R) break;
+        double tot = act ? (double)sum[rr] - (double)comp[rr] : 0.0;
+        for (int o = Tp; o < 32; o <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        if (act && si == 0) fnear[p + (int64_t)(r0 + rr) * nt] = tot;
+      }
     }
   }
 }
@@ -334,8 +229,8 @@ __global__ void k_build_img(const double* __restrict__ kdT, int d, int dp, int t
       const int l = c * E + j * per + e;
       const double v = (l < d && nrow < d) ? kdT[((int64_t)slot * d + l) * d + nrow] : 0.0;
       if (tf32) {
-        const float hi = tf32_round((float)v);
-        const float lo = tf32_round((float)(v - (double)hi));
+        const float hi = tf32_rn((float)v);
+        const float lo = tf32_rn((float)(v - (double)hi));
         ((float*)(base0 + off))[e] = hi;
         ((float*)(base1 + off))[e] = lo;
       } else {
@@ -418,6 +313,19 @@ eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R) {
     EIFMM_TRY(dmalloc(&ws.wa[k], 2 * n * 4));
   }
   EIFMM_TRY(dalloc(&ws.lh32, (size_t)nboxes(kap) * R * ops->lv[kap].dp));
+  {
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    size_t need = 0;
+    for (int k = 2; k <= kap; ++k) {
+      const int64_t rows = nboxes(k) * R;
+      const int64_t tiles = (nboxes(k) / 8 * R + 127) / 128;
+      const int G = m2l_tc_groups(tiles * 8, nsm, ops->lv[k].dp);
+      if (G > 1) need = std::max(need, (size_t)G * rows * ops->lv[k].dp);
+    }
+    if (need) EIFMM_TRY(dalloc(&ws.m2l_part, need));
+  }
   if (!ws.err) {
     EIFMM_TRY(dalloc(&ws.err, 1));
     EIFMM_CUDA(cudaMemset(ws.err, 0, sizeof(int)));
@@ -486,37 +394,33 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   EIFMM_CHECK_LAUNCH();
   record(ws, 1, s);
   // step 2
-  static bool attr = false;
-  if (!attr) {
-    EIFMM_CUDA(cudaFuncSetAttribute(k_m2m32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    32 * kMaxD * (int)sizeof(float)));
-    EIFMM_CUDA(cudaFuncSetAttribute(k_solve_mixed<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    4 * kMaxD * (int)sizeof(double)));
-    EIFMM_CUDA(cudaFuncSetAttribute(k_solve_mixed<double, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    4 * kMaxD * (int)sizeof(double)));
-    attr = true;
-  }
   for (int k = kap - 1; k >= 2; --k) {
     const LevelOps& a = ops->lv[k];
     const LevelOps& c = ops->lv[k + 1];
     const int64_t np = nboxes(k);
-    k_m2m32<<<dim3((unsigned)((np + 3) / 4), R), TPB, 32 * c.d * sizeof(float), s>>>(
-        a.d, c.d, a.dp, c.dp, R, a.m2mT32, ws.W32[k + 1], ws.W32[k], np);
+    k_m2m_warp<float><<<xfer_blocks(np, R, a.dp), 128, 0, s>>>(a.d, c.d, a.dp, c.dp, R, a.m2m32,
+                                                              ws.W32[k + 1], ws.W32[k], np);
     EIFMM_CHECK_LAUNCH();
   }
   record(ws, 2, s);
-  // step 3: What = Delta W, written as the two M2L operand planes
+  // step 3: What = Delta W (Gamma z = W, then B^t What = z), written as the
+  // two M2L operand planes
   for (int k = 2; k <= kap; ++k) {
     const LevelOps& v = ops->lv[k];
     const int64_t nvec = nboxes(k) * R;
-    const unsigned g = (unsigned)((nvec + 3) / 4);
-    if (tf32)
-      k_solve_mixed<double, 2><<<g, TPB, 4 * v.d * sizeof(double), s>>>(
-          v.d, v.dp, 0, v.G_cm, v.G_rm, v.B_cm, v.B_rm, ws.W32[k], nullptr, ws.wa[k], nvec);
-    else
-      k_solve_mixed<float, 1><<<g, TPB, 4 * v.d * sizeof(float), s>>>(
-          v.d, v.dp, 0, v.G32_cm, v.G32_rm, v.B32_cm, v.B32_rm, ws.W32[k], nullptr, ws.wa[k], nvec);
-    EIFMM_CHECK_LAUNCH();
+    if (tf32) {
+      double* z = (double*)ws.tmp;
+      EIFMM_TRY((launch_tri_sweep<double, true, true, float, double, 0>(v.d, v.G_colp, ws.W32[k], v.dp, z,
+                                                                        v.d, nullptr, nvec, s)));
+      EIFMM_TRY((launch_tri_sweep<double, false, false, double, float, 2>(v.d, v.B_rowp, z, v.d, nullptr,
+                                                                          v.dp, ws.wa[k], nvec, s)));
+    } else {
+      float* z = (float*)ws.tmp;
+      EIFMM_TRY((launch_tri_sweep<float, true, true, float, float, 0>(v.d, v.G32_colp, ws.W32[k], v.dp, z,
+                                                                      v.d, nullptr, nvec, s)));
+      EIFMM_TRY((launch_tri_sweep<float, false, false, float, float, 1>(v.d, v.B32_rowp, z, v.d, nullptr,
+                                                                        v.dp, ws.wa[k], nvec, s)));
+    }
   }
   record(ws, 3, s);
   // step 4
@@ -539,6 +443,13 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     a.slot_lists = ops->d_slot_lists;
     a.g = ws.g32[k];
     a.err = ws.err;
+    {
+      int dev = 0, nsm = 148;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      a.groups = m2l_tc_groups((a.nbox / 8 * R + 127) / 128 * 8, nsm, a.dp);
+      a.part = ws.m2l_part;
+    }
     EIFMM_TRY(launch_m2l_tc(a, tf32, s));
   }
   if (timing_enabled()) cudaEventRecord(ws.ev_m2l[kap + 1], s);
@@ -547,23 +458,27 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   for (int k = 3; k <= kap; ++k) {
     const LevelOps& v = ops->lv[k];
     const LevelOps& pv = ops->lv[k - 1];
-    k_l2l32<<<dim3((unsigned)nboxes(k - 1), R), TPB, pv.d * sizeof(float), s>>>(
-        v.d, pv.d, v.dp, pv.dp, R, v.l2lT32, ws.l32[k - 1], ws.g32[k], ws.l32[k]);
+    k_l2l_warp<float><<<xfer_blocks(nboxes(k), R, v.dp), 128, 0, s>>>(
+        v.d, pv.d, v.dp, pv.dp, R, v.l2l32, ws.l32[k - 1], ws.g32[k], ws.l32[k], nboxes(k));
     EIFMM_CHECK_LAUNCH();
   }
   record(ws, 5, s);
-  // step 6
+  // step 6: lhat = Delta^t l (B z = l, then Gamma^t lhat = z)
   {
     const int64_t nvec = nboxes(kap) * R;
-    const unsigned g = (unsigned)((nvec + 3) / 4);
-    if (tf32)
-      k_solve_mixed<double, 0><<<g, TPB, 4 * vl.d * sizeof(double), s>>>(
-          vl.d, vl.dp, 1, vl.G_cm, vl.G_rm, vl.B_cm, vl.B_rm, ws.l32[kap], ws.lh32, nullptr, nvec);
-    else
-      k_solve_mixed<float, 0><<<g, TPB, 4 * vl.d * sizeof(float), s>>>(
-          vl.d, vl.dp, 1, vl.G32_cm, vl.G32_rm, vl.B32_cm, vl.B32_rm, ws.l32[kap], ws.lh32, nullptr,
-          nvec);
-    EIFMM_CHECK_LAUNCH();
+    if (tf32) {
+      double* z = (double*)ws.tmp;
+      EIFMM_TRY((launch_tri_sweep<double, true, false, float, double, 0>(vl.d, vl.B_colp, ws.l32[kap], vl.dp,
+                                                                         z, vl.d, nullptr, nvec, s)));
+      EIFMM_TRY((launch_tri_sweep<double, false, true, double, float, 0>(vl.d, vl.G_rowp, z, vl.d, ws.lh32,
+                                                                         vl.dp, nullptr, nvec, s)));
+    } else {
+      float* z = (float*)ws.tmp;
+      EIFMM_TRY((launch_tri_sweep<float, true, false, float, float, 0>(vl.d, vl.B32_colp, ws.l32[kap], vl.dp,
+                                                                       z, vl.d, nullptr, nvec, s)));
+      EIFMM_TRY((launch_tri_sweep<float, false, true, float, float, 0>(vl.d, vl.G32_rowp, z, vl.d, ws.lh32,
+                                                                       vl.dp, nullptr, nvec, s)));
+    }
   }
   record(ws, 6, s);
   EIFMM_CUDA(cudaStreamWaitEvent(s, ws.ev_join, 0));

@@ -5,6 +5,8 @@
 // mixed-precision path is measured against): one thread per output entry,
 // operands staged in shared memory, operators read coalesced along m.
 #include "internal.h"
+#include "transfer.cuh"
+#include "solve.cuh"
 
 namespace eifmm {
 namespace {
@@ -81,35 +83,6 @@ k_p2m64(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
   }
 }
 
-// Step 2: W^P = sum_i K_M2M^i W^{child_i}; two parents per block.
-__global__ void __launch_bounds__(TPB)
-k_m2m64(int dk, int dc, int R, const double* __restrict__ m2mT,
-        const double* __restrict__ Wc, double* __restrict__ Wp, int64_t nparent) {
-  extern __shared__ double sw[];  // [2][8][dc]
-  const int r = blockIdx.y;
-  const int64_t P0 = 2 * (int64_t)blockIdx.x;
-  for (int t = threadIdx.x; t < 2 * 8 * dc; t += TPB) {
-    const int p = t / (8 * dc), rem = t - p * 8 * dc, i = rem / dc, q = rem - i * dc;
-    const int64_t P = P0 + p;
-    sw[t] = (P < nparent) ? Wc[((8 * P + i) * R + r) * dc + q] : 0.0;
-  }
-  __syncthreads();
-  for (int m = threadIdx.x; m < dk; m += TPB) {
-    double a0 = 0, a1 = 0;
-    for (int i = 0; i < 8; ++i) {
-      const double* op = m2mT + (int64_t)i * dc * dk + m;
-      const double* w0 = sw + i * dc;
-      const double* w1 = sw + (8 + i) * dc;
-      for (int q = 0; q < dc; ++q) {
-        const double o = op[(int64_t)q * dk];
-        a0 += o * w0[q];
-        a1 += o * w1[q];
-      }
-    }
-    Wp[(P0 * R + r) * dk + m] = a0;
-    if (P0 + 1 < nparent) Wp[((P0 + 1) * R + r) * dk + m] = a1;
-  }
-}
 
 // Steps 3 and 6: out = Delta in (transpose = 0) or Delta^t in (transpose = 1),
 // by forward and back substitution, one warp per vector.
@@ -224,25 +197,6 @@ k_m2l64(int level, int d, int R, const double* __restrict__ kdT,
   }
 }
 
-// Step 5: l^I = g^I + K_L2L^i l^{P(I)}.
-__global__ void __launch_bounds__(TPB)
-k_l2l64(int dk, int dp, int R, const double* __restrict__ l2lT,
-        const double* __restrict__ lpar, const double* __restrict__ g,
-        double* __restrict__ lout) {
-  extern __shared__ double sl[];
-  const int64_t P = blockIdx.x;
-  const int r = blockIdx.y;
-  for (int q = threadIdx.x; q < dp; q += TPB) sl[q] = lpar[(P * R + r) * dp + q];
-  __syncthreads();
-  for (int o = threadIdx.x; o < 8 * dk; o += TPB) {
-    const int i = o / dk, mp = o - i * dk;
-    const double* op = l2lT + (int64_t)i * dp * dk + mp;
-    double a = 0.0;
-    for (int q = 0; q < dp; ++q) a += op[(int64_t)q * dk] * sl[q];
-    const int64_t o2 = ((8 * P + i) * R + r) * dk + mp;
-    lout[o2] = g[o2] + a;
-  }
-}
 
 // Step 7 + sum + un-permute: f(x_i) = sum_l' K(x_i - c_I, y_l'^{I_0}) lhat_l'
 // + f_N(x_i), written to the caller's original order.
@@ -415,7 +369,21 @@ eifmm_status launch_p2p64(const Tree* t, int kern, const double* sig, int R, dou
 }
 
 eifmm_status launch_solve64(const LevelOps& v, int transpose, const double* in, double* out,
-                            int64_t nvec, cudaStream_t s) {
+                            int64_t nvec, cudaStream_t s, double* tmp) {
+  if (tmp && solve_smem_bytes(v.d, sizeof(double)) <= 227 * 1024) {
+    if (!transpose) {
+      EIFMM_TRY((launch_tri_sweep<double, true, true, double, double, 0>(v.d, v.G_colp, in, v.d, tmp, v.d,
+                                                                         nullptr, nvec, s)));
+      EIFMM_TRY((launch_tri_sweep<double, false, false, double, double, 0>(v.d, v.B_rowp, tmp, v.d, out,
+                                                                           v.d, nullptr, nvec, s)));
+    } else {
+      EIFMM_TRY((launch_tri_sweep<double, true, false, double, double, 0>(v.d, v.B_colp, in, v.d, tmp, v.d,
+                                                                          nullptr, nvec, s)));
+      EIFMM_TRY((launch_tri_sweep<double, false, true, double, double, 0>(v.d, v.G_rowp, tmp, v.d, out,
+                                                                          v.d, nullptr, nvec, s)));
+    }
+    return EIFMM_OK;
+  }
   const size_t sm = (size_t)(TPB / 32) * v.d * sizeof(double);
   k_solve64<<<(unsigned)((nvec + TPB / 32 - 1) / (TPB / 32)), TPB, sm, s>>>(
       v.d, transpose, v.G_cm, v.G_rm, v.B_cm, v.B_rm, in, out, nvec);
@@ -460,23 +428,18 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
   }
   record(ws, 1, s);
   // step 2
-  static bool attr_set = false;
-  if (!attr_set) {
-    EIFMM_CUDA(cudaFuncSetAttribute(k_m2m64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    16 * kMaxD * (int)sizeof(double)));
-    attr_set = true;
-  }
   for (int k = kap - 1; k >= 2; --k) {
     const int dk = ops->lv[k].d, dc = ops->lv[k + 1].d;
     const int64_t np = (int64_t)1 << (3 * k);
-    k_m2m64<<<dim3((unsigned)((np + 1) / 2), R), TPB, 16 * dc * sizeof(double), s>>>(
-        dk, dc, R, ops->lv[k].m2mT, ws.W[k + 1], ws.W[k], np);
+    k_m2m_warp<double><<<xfer_blocks(np, R, dk), 128, 0, s>>>(dk, dc, dk, dc, R, ops->lv[k].m2m,
+                                                             ws.W[k + 1], ws.W[k], np);
     EIFMM_CHECK_LAUNCH();
   }
   record(ws, 2, s);
   // step 3
   for (int k = 2; k <= kap; ++k)
-    EIFMM_TRY(launch_solve64(ops->lv[k], 0, ws.W[k], ws.Wh[k], ((int64_t)1 << (3 * k)) * R, s));
+    EIFMM_TRY(launch_solve64(ops->lv[k], 0, ws.W[k], ws.Wh[k], ((int64_t)1 << (3 * k)) * R, s,
+                             (double*)ws.tmp));
   record(ws, 3, s);
   // step 4
   for (int k = 2; k <= kap; ++k) {
@@ -492,13 +455,14 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
   // step 5 (l^2 = g^2)
   for (int k = 3; k <= kap; ++k) {
     const int dk = ops->lv[k].d, dp = ops->lv[k - 1].d;
-    k_l2l64<<<dim3((unsigned)((int64_t)1 << (3 * (k - 1))), R), TPB, dp * sizeof(double), s>>>(
-        dk, dp, R, ops->lv[k].l2lT, ws.l[k - 1], ws.g[k], ws.l[k]);
+    const int64_t nb = (int64_t)1 << (3 * k);
+    k_l2l_warp<double><<<xfer_blocks(nb, R, dk), 128, 0, s>>>(dk, dp, dk, dp, R, ops->lv[k].l2l,
+                                                             ws.l[k - 1], ws.g[k], ws.l[k], nb);
     EIFMM_CHECK_LAUNCH();
   }
   record(ws, 5, s);
   // step 6
-  EIFMM_TRY(launch_solve64(vl, 1, ws.l[kap], ws.lh, ((int64_t)1 << (3 * kap)) * R, s));
+  EIFMM_TRY(launch_solve64(vl, 1, ws.l[kap], ws.lh, ((int64_t)1 << (3 * kap)) * R, s, (double*)ws.tmp));
   record(ws, 6, s);
   // step 7 + near field + un-permute
   EIFMM_CUDA(cudaStreamWaitEvent(s, ws.ev_join, 0));

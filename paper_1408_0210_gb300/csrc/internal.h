@@ -65,6 +65,19 @@ struct LevelOps {
   double* m2mT = nullptr;  // [8][q < d_{k+1}][m < d]: (K_M2M^i)^t, levels 2..depth-1
   double* l2lT = nullptr;  // [8][q' < d_{k-1}][m' < d]: (K_L2L^i)^t, levels 3..depth
   double* kdT = nullptr;   // [343][l < d][m' < d]: K^delta_{m'l}
+  double* m2m = nullptr;   // [8][m < d][q < d_{k+1}]: K_M2M^i row-major
+  double* l2l = nullptr;   // [8][m' < d][q' < d_{k-1}]: K_L2L^i row-major
+  float* m2m32 = nullptr;
+  float* l2l32 = nullptr;
+  // packed triangles for the shared-memory sweeps (solve.cuh)
+  double* G_colp = nullptr;
+  double* G_rowp = nullptr;
+  double* B_colp = nullptr;
+  double* B_rowp = nullptr;
+  float* G32_colp = nullptr;
+  float* G32_rowp = nullptr;
+  float* B32_colp = nullptr;
+  float* B32_rowp = nullptr;
   // reduced-precision copies
   float* m2mT32 = nullptr;
   float* l2lT32 = nullptr;
@@ -124,8 +137,10 @@ struct Workspace {
   float* lh32 = nullptr;
   // tensor-core M2L A operand planes: [plane][box*R + r][dp] (BF16 or TF32)
   void* wa[kMaxLevel + 1] = {};
+  float* m2l_part = nullptr;    // partial M2L sums of the split offset lists
   int* err = nullptr;           // device error word of bounded waits
   int* err_host = nullptr;      // pinned copy, read at the next call
+  void* tmp = nullptr;          // intermediate of the two Delta sweeps
   double* sig = nullptr;        // sorted sigma, n_src x R (col-major, ld n_src)
   float* sig32 = nullptr;
   double* fnear = nullptr;      // n_tgt x R, sorted order

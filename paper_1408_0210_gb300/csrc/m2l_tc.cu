@@ -20,6 +20,8 @@
 // the previous one; tcgen05.commit on an mbarrier releases a stage.  Every
 // wait is bounded: on time-out the kernel records an error code, drains its
 // copies, frees its TMEM and returns.
+#include <stdlib.h>
+
 #include "internal.h"
 #include "m2l_tc.h"
 
@@ -132,173 +134,246 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Template parameters: TF32 selects kind::tf32 (4-byte elements) instead of
-// kind::f16 with BF16 (2-byte elements).  Two operand planes on each side.
+// Template parameter TF32 selects kind::tf32 (4-byte elements) instead of
+// kind::f16 with BF16 (2-byte elements); two operand planes on each side.
+//
+// Warps 0-3 (threads 0..127) gather the A rows (thread t = tile row t) with
+// cp.async and, at the end, read the accumulator (TMEM lane t = row t); warp
+// 4 issues the MMAs.  An S-stage ring of shared memory with `full` barriers
+// (128 producer arrivals after their copies landed and were fenced for the
+// async proxy, plus the expect-tx arrival of the bulk copy of B) and `empty`
+// barriers (tcgen05.commit of the MMAs that read the stage).
+constexpr int kMaxStages = 3;
+
 template <bool TF32>
-__global__ void __launch_bounds__(kRows, 1)
+__global__ void __launch_bounds__(160, 1)
 k_m2l_tc(M2LTcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte alignment for the swizzle atoms
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int tid = threadIdx.x;
   const int esz = TF32 ? 4 : 2;
   const int dp = a.dp;
+  const int S = a.stages;
   const int nchunk = dp * esz / 128;
-  const uint32_t a_bytes = 16384u;                  // 128 rows x 128 B per plane
-  const uint32_t b_bytes = (uint32_t)dp * 128u;     // dp rows x 128 B per plane
+  const uint32_t a_bytes = 16384u;               // 128 rows x 128 B per plane
+  const uint32_t b_bytes = (uint32_t)dp * 128u;  // dp rows x 128 B per plane
   const uint32_t stage = 2 * a_bytes + 2 * b_bytes;
-  uint64_t* bars = (uint64_t*)(smem + 2 * stage);   // [0,1] loads, [2,3] mma
-  uint32_t* tslot = (uint32_t*)(bars + 4);
+  uint64_t* bars = (uint64_t*)(smem + S * stage);  // full[S], empty[S], done
+  uint32_t* tslot = (uint32_t*)(bars + 2 * kMaxStages + 1);
+  int* flags = (int*)(tslot + 1);                    // [kListLen]
+  short* act = (short*)(flags + kListLen);           // active slot ids
+  int* nact_p = (int*)(act + kListLen + 1);
   const uint32_t sbase = smem_u32(smem);
-  const uint32_t bar_ld[2] = {smem_u32(&bars[0]), smem_u32(&bars[1])};
-  const uint32_t bar_mma[2] = {smem_u32(&bars[2]), smem_u32(&bars[3])};
+  auto full = [&](int st) { return smem_u32(&bars[st]); };
+  auto empty = [&](int st) { return smem_u32(&bars[kMaxStages + st]); };
+  const uint32_t done_bar = smem_u32(&bars[2 * kMaxStages]);
 
-  // tile -> rows
+  // ---- tile rows and the offset group of this CTA ----
   const int oct = blockIdx.x % 8;
-  const int64_t tile = blockIdx.x / 8;
-  const int64_t q = tile * kRows + tid;  // row within the parity class
+  const int grp = (blockIdx.x / 8) % a.groups;
+  const int64_t tile = blockIdx.x / (8 * a.groups);
+  const int s_beg = grp * kListLen / a.groups, s_end = (grp + 1) * kListLen / a.groups;
+  const int64_t q = tile * kRows + (tid < kRows ? tid : 0);
   const int64_t nclass = a.nbox / 8 * a.R;
-  const bool valid = q < nclass;
+  const bool valid = tid < kRows && q < nclass;
   const int64_t p = valid ? q / a.R : 0;
   const int r = valid ? (int)(q % a.R) : 0;
   const int64_t I = 8 * p + oct;
   int ci[3];
   morton_decode(I, a.level, ci);
   const int n = 1 << a.level;
+  const int* lst = a.slot_lists + oct * kListLen;
 
+  for (int i = tid; i < kListLen; i += blockDim.x) flags[i] = 0;
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init(smem_u32(&bars[i]), 1);
+    for (int i = 0; i < kMaxStages; ++i) {
+      mbar_init(full(i), kRows + 1);
+      mbar_init(empty(i), 1);
+    }
+    mbar_init(done_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (tid < 32) {
+  if (tid >= 128) {  // warp 4 owns the TMEM allocation
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
                  "r"((uint32_t)a.tmem_cols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  __syncthreads();
+  // offsets of the group that reach at least one row of the tile
+  if (valid)
+    for (int s = s_beg; s < s_end; ++s) {
+      const int slot = lst[s];
+      const int jx = ci[0] + slot % 7 - 3, jy = ci[1] + (slot / 7) % 7 - 3, jz = ci[2] + slot / 49 - 3;
+      if (jx >= 0 && jy >= 0 && jz >= 0 && jx < n && jy < n && jz < n) flags[s] = 1;
+    }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if (tid == 0) {
+    int na = 0;
+    for (int s = s_beg; s < s_end; ++s)
+      if (flags[s]) act[na++] = (short)s;
+    *nact_p = na;
+  }
+  __syncthreads();
   const uint32_t tmem = *tslot;
-
-  const char* wbase = (const char*)a.wa;
-  const size_t plane_stride = (size_t)a.rows * dp * esz;  // bytes between A planes
-  const int* lst = a.slot_lists + oct * kListLen;
-  const uint32_t id_lo = idesc(TF32 ? 2u : 1u, dp > 256 ? 256u : (uint32_t)dp);
-  const uint32_t id_hi = idesc(TF32 ? 2u : 1u, dp > 256 ? (uint32_t)(dp - 256) : 16u);
-
-  int it = 0;
-  bool accum = false;
+  const int nit = *nact_p * nchunk;
   bool ok = true;
-  for (int s = 0; s <= kListLen && ok; ++s) {
-    int slot = -1;
-    int64_t src_row = -1;
-    if (s < kListLen) {
-      slot = lst[s];
-      const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
-      const int jx = ci[0] + dx, jy = ci[1] + dy, jz = ci[2] + dz;
+
+  if (tid < kRows) {
+    // ------------------------------------------------------- producers --
+    const char* wbase = (const char*)a.wa;
+    const size_t plane_stride = (size_t)a.rows * dp * esz;
+    const uint32_t rowoff = (uint32_t)(tid >> 3) * 1024u + (uint32_t)(tid & 7) * 128u;
+    for (int it = 0; it < nit && ok; ++it) {
+      const int st = it % S, u = it / S;
+      if (it >= S) ok = mbar_wait(empty(st), (u - 1) & 1, a.err, 1);
+      if (!ok) break;
+      const int s = act[it / nchunk], c = it % nchunk;
+      const int slot = lst[s];
+      const int jx = ci[0] + slot % 7 - 3, jy = ci[1] + (slot / 7) % 7 - 3, jz = ci[2] + slot / 49 - 3;
+      int64_t src_row = -1;
       if (valid && jx >= 0 && jy >= 0 && jz >= 0 && jx < n && jy < n && jz < n)
         src_row = morton_encode(jx, jy, jz, a.level) * a.R + r;
-      if (!__syncthreads_or(src_row >= 0)) continue;  // no row of the tile reaches this delta
-    }
-    const int nc = (s < kListLen) ? nchunk : 1;
-    for (int c = 0; c < nc && ok; ++c) {
-      // ---- issue the copies of iteration `it` (skip on the drain pass) ----
-      if (s < kListLen) {
-        const int b = it & 1;
-        if (it >= 2) ok = mbar_wait(bar_mma[b], ((it >> 1) - 1) & 1, a.err, 1);
-        if (!__syncthreads_and(ok)) { ok = false; break; }
-        const uint32_t sA = sbase + b * stage;
-        const uint32_t sB = sA + 2 * a_bytes;
-        if (tid == 0) {
-          const char* src = (const char*)a.kd_img + (((size_t)slot * nchunk + c) * 2) * b_bytes;
-          mbar_expect_tx(bar_ld[b], 2 * b_bytes);
-          bulk_g2s(sB, src, 2 * b_bytes, bar_ld[b]);
-        }
-        const uint32_t rowoff = (uint32_t)(tid >> 3) * 1024u + (uint32_t)(tid & 7) * 128u;
-        const char* gsrc = wbase + (size_t)(src_row >= 0 ? src_row : 0) * dp * esz + (size_t)c * 128;
-        const uint32_t nb = src_row >= 0 ? 16u : 0u;
-#pragma unroll
-        for (int pl = 0; pl < 2; ++pl)
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            cp16(sA + pl * a_bytes + rowoff + (uint32_t)((j ^ (tid & 7)) << 4), gsrc + pl * plane_stride + j * 16, nb);
-        cp_commit();
+      const uint32_t sA = sbase + st * stage;
+      if (tid == 0) {
+        const char* src = (const char*)a.kd_img + (((size_t)slot * nchunk + c) * 2) * b_bytes;
+        mbar_expect_tx(full(st), 2 * b_bytes);
+        bulk_g2s(sA + 2 * a_bytes, src, 2 * b_bytes, full(st));
       }
-      // ---- MMAs of iteration it - 1 ----
-      if (it >= 1) {
-        if (s < kListLen) cp_wait1(); else cp_wait0();
+      const char* gsrc = wbase + (size_t)(src_row >= 0 ? src_row : 0) * dp * esz + (size_t)c * 128;
+      const uint32_t nb = src_row >= 0 ? 16u : 0u;
+#pragma unroll
+      for (int pl = 0; pl < 2; ++pl)
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          cp16(sA + pl * a_bytes + rowoff + (uint32_t)((j ^ (tid & 7)) << 4), gsrc + pl * plane_stride + j * 16, nb);
+      cp_commit();
+      if (it >= 1) {  // the previous stage has landed: make it visible to the MMAs
+        cp_wait1();
         fence_async_smem();
-        __syncthreads();
-        const int bp = (it - 1) & 1;
-        if (tid == 0) {
-          if (!mbar_wait(bar_ld[bp], ((it - 1) >> 1) & 1, a.err, 2)) {
-            ok = false;
-          } else {
-            tc_fence_after();
-            const uint32_t sA = sbase + bp * stage;
-            const uint32_t sB = sA + 2 * a_bytes;
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              // hi*hi, hi*lo, lo*hi
-#pragma unroll
-              for (int pr = 0; pr < 3; ++pr) {
-                const int pa = (pr == 2) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
-                const uint64_t ad = sdesc(sA + pa * a_bytes + kk * 32);
-                const uint32_t bB = sB + pb * b_bytes + kk * 32;
-                mma<TF32>(tmem, ad, sdesc(bB), id_lo, accum ? 1u : 0u);
-                if (dp > 256) mma<TF32>(tmem + 256, ad, sdesc(bB + 32 * 1024), id_hi, accum ? 1u : 0u);
-                accum = true;
-              }
-            }
-            mma_commit(bar_mma[bp]);
-          }
-        }
-        ok = __syncthreads_and(ok);
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(full((it - 1) % S)) : "memory");
       }
-      if (s < kListLen) ++it;
     }
-  }
-  cp_wait0();
-  // wait for the last commit (it tracks every earlier MMA of the thread)
-  bool done = ok;
-  if (it >= 1 && ok) done = mbar_wait(bar_mma[(it - 1) & 1], ((it - 1) >> 1) & 1, a.err, 3);
-  done = __syncthreads_and(done);
-  tc_fence_after();
-  // ---- epilogue: TMEM lane tid -> row; FP32 out.  The TMEM loads are
-  // warp-collective, so every thread executes them; only stores are masked.
-  const bool has_acc = it >= 1;  // uniform: some MMA was issued
-  if (done) {
-    float* out = a.g + (size_t)(I * a.R + r) * dp;
-    const uint32_t lane_base = (uint32_t)((tid & ~31) << 16);
-    for (int c0 = 0; c0 < dp; c0 += 16) {
-      float v[16];
-      if (has_acc) {
-        tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+    cp_wait0();
+    if (ok && nit >= 1) {
+      fence_async_smem();
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(full((nit - 1) % S)) : "memory");
+    }
+  } else if (tid == kRows) {
+    // ----------------------------------------------------- MMA issuer --
+    const uint32_t id_lo = idesc(TF32 ? 2u : 1u, dp > 256 ? 256u : (uint32_t)dp);
+    const uint32_t id_hi = idesc(TF32 ? 2u : 1u, dp > 256 ? (uint32_t)(dp - 256) : 16u);
+    for (int it = 0; it < nit; ++it) {
+      const int st = it % S;
+      if (!mbar_wait(full(st), (it / S) & 1, a.err, 2)) {
+        ok = false;
+        break;
       }
+      tc_fence_after();
+      const uint32_t sA = sbase + st * stage;
+      const uint32_t sB = sA + 2 * a_bytes;
+      // offsets go round-robin to `chains` accumulators: shorter FP32
+      // accumulation chains, summed in FP64 by the epilogue
+      const int e = it / nchunk;
+      const uint32_t dacc = tmem + (uint32_t)((e % a.chains) * dp);
+      const bool first = e < a.chains && (it % nchunk) == 0;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int pr = 0; pr < 3; ++pr) {  // hi*hi, hi*lo, lo*hi
+          const int pa = (pr == 2) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
+          const uint32_t acc = (!first || kk > 0 || pr > 0) ? 1u : 0u;
+          const uint64_t ad = sdesc(sA + pa * a_bytes + kk * 32);
+          const uint32_t bB = sB + pb * b_bytes + kk * 32;
+          mma<TF32>(dacc, ad, sdesc(bB), id_lo, acc);
+          if (dp > 256) mma<TF32>(dacc + 256, ad, sdesc(bB + 32 * 1024), id_hi, acc);
+        }
+      mma_commit(empty(st));
+    }
+    if (ok && nit >= 1) mma_commit(done_bar);
+  }
+  // ---------------------------------------------------------- epilogue --
+  if (tid < kRows) {
+    bool have = nit >= 1 && ok;
+    if (have) have = mbar_wait(done_bar, 0, a.err, 3);
+    have = __all_sync(0xffffffffu, have);  // uniform per warp for tcgen05.ld
+    tc_fence_after();
+    float* out = a.out + (size_t)grp * a.part_stride + (size_t)(I * a.R + r) * dp;
+    const uint32_t lane_base = (uint32_t)((tid & ~31) << 16);
+    const int used = min(a.chains, *nact_p);
+    for (int c0 = 0; c0 < dp; c0 += 16) {
+      double v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = 0.0;
+      if (have)
+        for (int ch = 0; ch < used; ++ch) {
+          float t[16];
+          tmem_ld16(tmem + lane_base + (uint32_t)(ch * dp + c0), t);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += (double)t[i];
+        }
       if (valid) {
         float4* o4 = (float4*)(out + c0);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) o4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+        for (int i = 0; i < 4; ++i)
+          o4[i] = make_float4((float)v[4 * i], (float)v[4 * i + 1], (float)v[4 * i + 2], (float)v[4 * i + 3]);
       }
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (tid < 32)
+  if (tid >= 128)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)a.tmem_cols));
+}
+
+__global__ void k_sum_parts(const float4* __restrict__ parts, int groups, int64_t n4, int64_t stride4,
+                            float4* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    double x = 0, y = 0, z = 0, w = 0;
+    for (int g = 0; g < groups; ++g) {
+      const float4 v = parts[g * stride4 + i];
+      x += v.x;
+      y += v.y;
+      z += v.z;
+      w += v.w;
+    }
+    out[i] = make_float4((float)x, (float)y, (float)z, (float)w);
+  }
 }
 
 }  // namespace
 
-size_t m2l_tc_smem_bytes(int dp, bool tf32) {
-  (void)tf32;
-  return 2 * (2 * 16384 + 2 * (size_t)dp * 128) + 64 + 1024;
+int m2l_tc_stages(int dp) {
+  const size_t stage = 2 * 16384 + 2 * (size_t)dp * 128;
+  return (3 * stage + 4096 <= 227 * 1024) ? 3 : 2;
 }
 
-eifmm_status launch_m2l_tc(const M2LTcArgs& a, bool tf32, cudaStream_t s) {
+size_t m2l_tc_smem_bytes(int dp, bool tf32) {
+  (void)tf32;
+  const size_t stage = 2 * 16384 + 2 * (size_t)dp * 128;
+  return (size_t)m2l_tc_stages(dp) * stage + 1024 /* align */ + 2048 /* barriers, slot lists */;
+}
+
+int m2l_tc_groups(int64_t tiles8, int nsm, int dp) {
+  // Split the interaction list over more CTAs (partial sums added in FP64
+  // by k_sum_parts): at least two waves of CTAs, and at least 16 FP32
+  // accumulation chains per output together with the in-CTA chains.
+  const int chains = dp <= 128 ? 4 : (dp <= 256 ? 2 : 1);
+  static const int gmin = [] {
+    const char* e = getenv("EIFMM_M2L_MIN_CHAINS");
+    return e ? atoi(e) : 16;
+  }();
+  int g = 1;
+  while (g < 16 && (tiles8 * g < 2 * nsm || chains * g < gmin)) g *= 2;
+  return g;
+}
+
+eifmm_status launch_m2l_tc(const M2LTcArgs& a0, bool tf32, cudaStream_t s) {
+  M2LTcArgs a = a0;
+  a.stages = m2l_tc_stages(a.dp);
+  a.chains = a.dp <= 128 ? 4 : (a.dp <= 256 ? 2 : 1);
+  a.tmem_cols = 512;
   const size_t sm = m2l_tc_smem_bytes(a.dp, tf32);
   static bool attr[2] = {false, false};
   if (!attr[tf32]) {
@@ -309,10 +384,23 @@ eifmm_status launch_m2l_tc(const M2LTcArgs& a, bool tf32, cudaStream_t s) {
     attr[tf32] = true;
   }
   const int64_t tiles = (a.nbox / 8 * a.R + kRows - 1) / kRows;
-  const unsigned grid = (unsigned)(tiles * 8);
-  if (tf32) k_m2l_tc<true><<<grid, kRows, sm, s>>>(a);
-  else k_m2l_tc<false><<<grid, kRows, sm, s>>>(a);
+  if (a.groups > 1) {
+    a.out = a.part;
+    a.part_stride = a.rows * (int64_t)a.dp;
+  } else {
+    a.out = a.g;
+    a.part_stride = 0;
+  }
+  const unsigned grid = (unsigned)(tiles * 8 * a.groups);
+  if (tf32) k_m2l_tc<true><<<grid, 160, sm, s>>>(a);
+  else k_m2l_tc<false><<<grid, 160, sm, s>>>(a);
   EIFMM_CHECK_LAUNCH();
+  if (a.groups > 1) {
+    const int64_t n4 = a.rows * (int64_t)a.dp / 4;
+    k_sum_parts<<<(unsigned)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096), 256, 0, s>>>(
+        (const float4*)a.part, a.groups, n4, a.part_stride / 4, (float4*)a.g);
+    EIFMM_CHECK_LAUNCH();
+  }
   return EIFMM_OK;
 }
 

@@ -16,10 +16,18 @@ struct M2LTcArgs {
   const int* slot_lists; // [8][189]
   float* g;              // [rows][dp] FP32 output
   int* err;              // device error word (0 = ok)
+  int groups = 1;        // CTAs sharing one tile, each over 189/groups offsets
+  float* part = nullptr; // [groups][rows][dp] partial sums when groups > 1
+  // set by the launcher
+  float* out = nullptr;
+  int64_t part_stride = 0;
+  int stages = 2;
+  int chains = 1;        // accumulators in TMEM (round-robin over offsets)
 };
 
 constexpr int kMaxDpTc = 320;
 size_t m2l_tc_smem_bytes(int dp, bool tf32);
+int m2l_tc_groups(int64_t tiles8, int nsm, int dp);
 eifmm_status launch_m2l_tc(const M2LTcArgs& a, bool tf32, cudaStream_t s);
 
 }  // namespace eifmm

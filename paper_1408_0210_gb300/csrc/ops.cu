@@ -54,7 +54,7 @@ __global__ void k_build_m2m(int kern, int dk, int dc, double lc1,
                             const double* __restrict__ Gc,
                             const double* __restrict__ Bc,
                             double* __restrict__ scratch,
-                            double* __restrict__ m2mT) {
+                            double* __restrict__ m2mT, double* __restrict__ m2m_rm) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 8 * dk) return;
   const int i = t / dk, m = t - i * dk;
@@ -66,6 +66,7 @@ __global__ void k_build_m2m(int kern, int dk, int dc, double lc1,
     row[p] = kern_f64_ieee(kern, x0 - Yc[3 * p], x1 - Yc[3 * p + 1], x2 - Yc[3 * p + 2]);
   dev_delta_t(dc, Gc, Bc, row);
   for (int q = 0; q < dc; ++q) m2mT[((int64_t)i * dc + q) * dk + m] = row[q];
+  for (int q = 0; q < dc; ++q) m2m_rm[((int64_t)i * dk + m) * dc + q] = row[q];
 }
 
 __global__ void k_build_l2l(int kern, int dk, int dp, double lk,
@@ -74,7 +75,7 @@ __global__ void k_build_l2l(int kern, int dk, int dp, double lk,
                             const double* __restrict__ Gp,
                             const double* __restrict__ Bp,
                             double* __restrict__ scratch,
-                            double* __restrict__ l2lT) {
+                            double* __restrict__ l2lT, double* __restrict__ l2l_rm) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 8 * dk) return;
   const int i = t / dk, m = t - i * dk;
@@ -86,6 +87,7 @@ __global__ void k_build_l2l(int kern, int dk, int dp, double lk,
     row[p] = kern_f64_ieee(kern, x0 - Xp[3 * p], x1 - Xp[3 * p + 1], x2 - Xp[3 * p + 2]);
   dev_delta(dp, Gp, Bp, row);
   for (int q = 0; q < dp; ++q) l2lT[((int64_t)i * dp + q) * dk + m] = row[q];
+  for (int q = 0; q < dp; ++q) l2l_rm[((int64_t)i * dk + m) * dp + q] = row[q];
 }
 
 // kdT[slot][l][m'] = K(Y_{m'}, Y_l + delta_slot)
@@ -102,6 +104,19 @@ __global__ void k_build_kd(int kern, int d, double lk, const double* __restrict_
       v = kern_f64_ieee(kern, Y[3 * mp] - (Y[3 * l] + d0), Y[3 * mp + 1] - (Y[3 * l + 1] + d1),
                         Y[3 * mp + 2] - (Y[3 * l + 2] + d2));
     kdT[((int64_t)slot * d + l) * d + mp] = v;
+  }
+}
+
+// packed triangles: colp[k*d - k(k-1)/2 + (j-k)] = M[j][k] (j >= k),
+// rowp[k(k+1)/2 + j] = M[k][j] (j <= k).
+__global__ void k_pack_tri(const double* __restrict__ M, int d, double* __restrict__ colp,
+                           double* __restrict__ rowp) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d * d) return;
+  const int i = t / d, j = t - i * d;  // M[i][j]
+  if (j <= i) {
+    colp[(int64_t)j * d - (int64_t)j * (j - 1) / 2 + (i - j)] = M[t];
+    rowp[(int64_t)i * (i + 1) / 2 + j] = M[t];
   }
 }
 
@@ -150,18 +165,22 @@ eifmm_status assemble_ops(Ops* ops, cudaStream_t s) {
     if (k < depth) {
       const LevelOps& c = ops->lv[k + 1];
       EIFMM_TRY(dalloc(&v.m2mT, (size_t)8 * v.d * c.d));
+      EIFMM_TRY(dalloc(&v.m2m, (size_t)8 * v.d * c.d));
       k_build_m2m<<<(8 * v.d + 63) / 64, 64, 0, s>>>(kern, v.d, c.d, ops->L * ldexp(1.0, -(k + 2)),
-                                                     v.X, c.Y, c.G_rm, c.B_rm, scratch, v.m2mT);
+                                                     v.X, c.Y, c.G_rm, c.B_rm, scratch, v.m2mT, v.m2m);
       EIFMM_CHECK_LAUNCH();
       EIFMM_TRY(to_f32(v.m2mT, &v.m2mT32, (int64_t)8 * v.d * c.d, s));
+      EIFMM_TRY(to_f32(v.m2m, &v.m2m32, (int64_t)8 * v.d * c.d, s));
     }
     if (k > 2) {
       const LevelOps& p = ops->lv[k - 1];
       EIFMM_TRY(dalloc(&v.l2lT, (size_t)8 * v.d * p.d));
+      EIFMM_TRY(dalloc(&v.l2l, (size_t)8 * v.d * p.d));
       k_build_l2l<<<(8 * v.d + 63) / 64, 64, 0, s>>>(kern, v.d, p.d, lk, v.Y, p.X, p.G_rm, p.B_rm,
-                                                     scratch, v.l2lT);
+                                                     scratch, v.l2lT, v.l2l);
       EIFMM_CHECK_LAUNCH();
       EIFMM_TRY(to_f32(v.l2lT, &v.l2lT32, (int64_t)8 * v.d * p.d, s));
+      EIFMM_TRY(to_f32(v.l2l, &v.l2l32, (int64_t)8 * v.d * p.d, s));
     }
     EIFMM_TRY(dalloc(&v.kdT, (size_t)kNumSlots * v.d * v.d));
     k_build_kd<<<dim3((v.d * v.d + 255) / 256 < 64 ? (v.d * v.d + 255) / 256 : 64, kNumSlots), 256, 0, s>>>(
@@ -172,6 +191,19 @@ eifmm_status assemble_ops(Ops* ops, cudaStream_t s) {
     EIFMM_TRY(to_f32(v.B_cm, &v.B32_cm, (int64_t)v.d * v.d, s));
     EIFMM_TRY(to_f32(v.B_rm, &v.B32_rm, (int64_t)v.d * v.d, s));
     EIFMM_TRY(to_f32(v.X, &v.X32, (int64_t)3 * v.d, s));
+    const int64_t np = (int64_t)v.d * (v.d + 1) / 2;
+    EIFMM_TRY(dalloc(&v.G_colp, np));
+    EIFMM_TRY(dalloc(&v.G_rowp, np));
+    EIFMM_TRY(dalloc(&v.B_colp, np));
+    EIFMM_TRY(dalloc(&v.B_rowp, np));
+    k_pack_tri<<<(v.d * v.d + 255) / 256, 256, 0, s>>>(v.G_rm, v.d, v.G_colp, v.G_rowp);
+    EIFMM_CHECK_LAUNCH();
+    k_pack_tri<<<(v.d * v.d + 255) / 256, 256, 0, s>>>(v.B_rm, v.d, v.B_colp, v.B_rowp);
+    EIFMM_CHECK_LAUNCH();
+    EIFMM_TRY(to_f32(v.G_colp, &v.G32_colp, np, s));
+    EIFMM_TRY(to_f32(v.G_rowp, &v.G32_rowp, np, s));
+    EIFMM_TRY(to_f32(v.B_colp, &v.B32_colp, np, s));
+    EIFMM_TRY(to_f32(v.B_rowp, &v.B32_rowp, np, s));
   }
   // slot lists of the 8 parity classes: offsets o in {-2..3} for an even
   // coordinate and {-3..2} for an odd one, minus the 27 neighbours.
@@ -199,6 +231,9 @@ void free_ops(Ops* ops) {
     LevelOps& v = ops->lv[k];
     dfree(v.X); dfree(v.Y); dfree(v.G_rm); dfree(v.G_cm); dfree(v.B_rm); dfree(v.B_cm);
     dfree(v.m2mT); dfree(v.l2lT); dfree(v.kdT); dfree(v.m2mT32); dfree(v.l2lT32);
+    dfree(v.m2m); dfree(v.l2l); dfree(v.m2m32); dfree(v.l2l32);
+    dfree(v.G_colp); dfree(v.G_rowp); dfree(v.B_colp); dfree(v.B_rowp);
+    dfree(v.G32_colp); dfree(v.G32_rowp); dfree(v.B32_colp); dfree(v.B32_rowp);
     dfree(v.G32_cm); dfree(v.G32_rm); dfree(v.B32_cm); dfree(v.B32_rm); dfree(v.X32);
     dfree(v.kd_img);
     v = LevelOps();

@@ -166,3 +166,61 @@ def test_mixed_full_size_1m_depth5(E, orc):
         f = torch.zeros(n, dtype=torch.float64, device="cuda")
         E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
         assert rel2(f.cpu().numpy()[idx], f1) <= eps
+
+
+def test_batched_graph_replay_matches_individual(E, orc):
+    ops = E.eifmm_ops_build("inv_r", 1.0, 3, 1e-4)
+    sizes = wl.batch_sizes(5, 2000, 9000, 77)
+    xs = [wl.uniform_cube(n, 500 + i) for i, n in enumerate(sizes)]
+    ss = [dev(wl.sigma_uniform(len(x), 1, 600 + i)[:, 0]) for i, x in enumerate(xs)]
+    trees = [E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, 3, True) for x in xs]
+    stream = torch.cuda.Stream()
+    fb = [torch.zeros(len(x), dtype=torch.float64, device="cuda") for x in xs]
+    with torch.cuda.stream(stream):
+        E.eifmm_evaluate_batched(trees, ss, fb, ops, "mixed", stream)   # direct pass + capture
+        for f in fb:
+            f.zero_()
+        n0 = E.eifmm_kernel_launches()
+        E.eifmm_evaluate_batched(trees, ss, fb, ops, "mixed", stream)   # one graph launch
+        assert E.eifmm_kernel_launches() == n0
+    stream.synchronize()
+    for x, s, t, f in zip(xs, ss, trees, fb):
+        fi = torch.zeros(len(x), dtype=torch.float64, device="cuda")
+        E.eifmm_evaluate(t, ops, s, fi, "mixed")
+        assert torch.equal(fi, f)
+        f1 = orc.direct_sum("inv_r", x, x, s.cpu().numpy())[:, 0]
+        assert rel2(f.cpu().numpy(), f1) <= 1e-4
+
+
+def test_config3_kernel_nonuniform(E, orc):
+    """The inhomogeneous kernel exp(-r)/r + 1/sqrt(r1^2 + 0.01 r2^2 + r3^2 +
+    1e-3) on a Gaussian mixture; per-level d from the estimate."""
+    n, depth, eps = 6000, 4, 1e-6
+    x = wl.gaussian_mixture(n, 3)
+    s = wl.sigma_uniform(n, 1, 4)
+    ops = E.eifmm_ops_build("config3", 1.0, depth, eps)
+    ds = [ops.error_estimate(k)[1] for k in range(2, depth + 1)]
+    assert all(dd > 5 for dd in ds)
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    f1 = orc.direct_sum("config3", x, x, s)[:, 0]
+    for prec in ("fp64", "mixed"):
+        f = torch.zeros(n, dtype=torch.float64, device="cuda")
+        E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, prec)
+        assert rel2(f.cpu().numpy(), f1) <= eps, prec
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 2e-5)])
+def test_many_rhs_64(E, orc, prec, tol):
+    n, depth, eps, R = 6000, 3, 1e-4, 64
+    x = wl.uniform_cube(n, 8)
+    s = wl.sigma_uniform(n, R, 9)
+    lv = orc.build_levels("inv_r", 1.0, depth, eps)
+    f2 = orc.eifmm("inv_r", 1.0, [0, 0, 0], depth, lv, x, x, s)
+    ops = E.eifmm_ops_build("inv_r", 1.0, depth, eps)
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    sd = torch.from_numpy(np.asfortranarray(s)).to("cuda").T.contiguous().T
+    f = torch.zeros(R, n, dtype=torch.float64, device="cuda").T
+    E.eifmm_evaluate(tree, ops, sd, f, prec)
+    fg = f.cpu().numpy()
+    errs = [rel2(fg[:, r], f2[:, r]) for r in range(R)]
+    assert max(errs) <= tol
