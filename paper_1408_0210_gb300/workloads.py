@@ -56,3 +56,12 @@ def batch_sizes(n_problems: int, lo: int, hi: int, seed: int) -> list[int]:
 def sample_targets(n: int, n_sample: int, seed: int) -> np.ndarray:
     """Sorted distinct target indices for sampled accuracy checks."""
     return np.sort(rng(seed).choice(n, size=min(n, n_sample), replace=False)).astype(np.int64)
+
+
+def sphere_surface(n: int, seed: int, radius: float = 0.5) -> np.ndarray:
+    """(n, 3) points iid uniform on the sphere of the given radius centred in
+    the unit cube (the paper's "sphere" test case, Section 5.2), clipped to
+    [0, 1]^3 against rounding."""
+    g = rng(seed).standard_normal((n, 3))
+    g /= np.linalg.norm(g, axis=1, keepdims=True)
+    return np.clip(0.5 + radius * g, 0.0, 1.0)

@@ -224,3 +224,39 @@ def test_many_rhs_64(E, orc, prec, tol):
     fg = f.cpu().numpy()
     errs = [rel2(fg[:, r], f2[:, r]) for r in range(R)]
     assert max(errs) <= tol
+
+
+@pytest.mark.parametrize("kern,eps", [("exp_r2", 1e-6), ("cos20r_r", 1e-4), ("sqrt_r2p1", 1e-5)])
+def test_other_inhomogeneous_kernels(E, orc, kern, eps):
+    """The kernels of the paper's inhomogeneous experiments (Section 5.4) on
+    the cube; the FP64 path against the CPU EIFMM and both paths against the
+    exact sum."""
+    n, depth = 5000, 3
+    x = wl.uniform_cube(n, 13)
+    s = wl.sigma_uniform(n, 1, 14)
+    ops = E.eifmm_ops_build(kern, 1.0, depth, eps)
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    f1 = orc.direct_sum(kern, x, x, s)[:, 0]
+    for prec in ("fp64", "mixed"):
+        f = torch.zeros(n, dtype=torch.float64, device="cuda")
+        E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, prec)
+        assert rel2(f.cpu().numpy(), f1) <= eps, prec
+    # inhomogeneous kernels: the EIM needs fewer points deeper in the tree
+    if kern == "exp_r2":
+        d = [ops.error_estimate(k)[1] for k in range(2, depth + 1)]
+        assert d[-1] < d[0]
+
+
+def test_sphere_surface_points(E, orc):
+    """Points on the sphere of radius 0.5 (Section 5.2): most leaves empty."""
+    n, depth, eps = 20000, 5, 1e-5
+    x = wl.sphere_surface(n, 21)
+    s = wl.sigma_uniform(n, 1, 22)
+    ops = E.eifmm_ops_build("inv_r", 1.0, depth, eps)
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    idx = wl.sample_targets(n, 500, 23)
+    f1 = orc.direct_sum("inv_r", x, x, s, tgt_idx=idx)[:, 0]
+    for prec in ("fp64", "mixed"):
+        f = torch.zeros(n, dtype=torch.float64, device="cuda")
+        E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, prec)
+        assert rel2(f.cpu().numpy()[idx], f1) <= eps, prec

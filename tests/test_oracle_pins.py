@@ -387,3 +387,16 @@ def test_eifmm_translated_domain(orc):
     assert np.linalg.norm(fa - fb) / np.linalg.norm(fa) <= 1e-9
     f1 = orc.direct_sum("inv_r", 2 * x, 2 * x, s)
     assert np.linalg.norm(fa - f1) / np.linalg.norm(f1) <= 1e-5
+
+
+def test_eim_inhomogeneous_kernel_rank_decreases_with_depth(orc):
+    """Section 5.4: for e^{-r^2} the EIM selects fewer points deeper in the
+    tree (the approximation problem gets easier as boxes shrink)."""
+    d = [orc.eim("exp_r2", orc.train_x(k), orc.train_y(k), 1e-6)["d"] for k in (2, 3, 4)]
+    assert d[0] > d[1] > d[2]
+
+
+def test_sphere_points_on_surface():
+    x = wl.sphere_surface(1000, 3)
+    r = np.linalg.norm(x - 0.5, axis=1)
+    assert np.abs(r - 0.5).max() < 1e-12 and (x >= 0).all() and (x <= 1).all()
