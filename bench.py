@@ -166,6 +166,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="mixed:1e-4,fp64:1e-4,mixed:1e-7,fp64:1e-7")
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="run this many evaluations of the first variant between "
+                         "cudaProfilerStart/Stop (for ncu --profile-from-start off) and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
@@ -193,9 +196,26 @@ def main():
     fref = E.eifmm_direct_sum("inv_r", xd, xd, sd, True, idx, stream)[:, 0]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
+    variants = []
+    for v in args.variants.split(","):
+        prec, eps = v.split(":")
+        variants.append((prec, float(eps)))
     ops = {}
-    for eps in EPS_LIST:
-        ops[eps] = E.eifmm_ops_build("inv_r", 1.0, DEPTH, eps, 512, stream)
+    for _, eps in variants:
+        if eps not in ops:
+            ops[eps] = E.eifmm_ops_build("inv_r", 1.0, DEPTH, eps, 512, stream)
+
+    if args.profile_steps > 0:
+        prec, eps = variants[0]
+        for _ in range(max(args.warmup, 1)):
+            E.eifmm_evaluate(tree, ops[eps], sd, f, prec, stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        for _ in range(args.profile_steps):
+            E.eifmm_evaluate(tree, ops[eps], sd, f, prec, stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        return
 
     def run_variant(prec, eps, steps, warmup, timing=False):
         o = ops[eps]
@@ -228,10 +248,6 @@ def main():
         err = float(torch.linalg.norm(f[idx] - fref) / torch.linalg.norm(fref))
         return ms, err, launches, step_times
 
-    variants = []
-    for v in args.variants.split(","):
-        prec, eps = v.split(":")
-        variants.append((prec, float(eps)))
     results = {}
     headline = None
     with ClockSampler(torch.cuda.current_device()) as clk:

@@ -167,9 +167,14 @@ extern "C" eifmm_status eifmm_direct_sum(eifmm_kernel kern, const double* tgt_xy
                            exclude_self, tgt_idx, n_eval, f, (cudaStream_t)stream);
 }
 
-static int tier_for_eps(double eps) {
-  if (eps >= 1e-5 * (1.0 - 1e-9)) return 0;
-  if (eps >= 1e-6 * (1.0 - 1e-9)) return 1;
+// Arithmetic tier of the mixed path from the EIM tolerance: the requested
+// tolerance when the operators were built here, otherwise the largest
+// built-in estimate of the levels (which the greedy keeps just below the
+// tolerance, hence the factor 1/3 in the thresholds).
+static int tier_for_eps(double eps, bool requested) {
+  const double f = requested ? 1.0 - 1e-9 : 1.0 / 3.0;
+  if (eps >= 1e-5 * f) return 0;
+  if (eps >= 1e-6 * f) return 1;
   return 2;
 }
 
@@ -227,7 +232,7 @@ extern "C" eifmm_status eifmm_ops_load(eifmm_kernel kern, double L, int depth,
     delete h;
     return rc;
   }
-  o.tier = tier_for_eps(eps_max > 0.0 ? eps_max : 1e-16);
+  o.tier = tier_for_eps(eps_max > 0.0 ? eps_max : 1e-16, false);
   if (o.tier <= 1) rc = build_kd_image(&o, o.tier == 1, s);
   if (rc != EIFMM_OK) {
     free_ops(&o);
@@ -281,7 +286,17 @@ extern "C" eifmm_status eifmm_ops_build(eifmm_kernel kern, double L, int depth, 
     lv[k] = eifmm_level_data{d, keep[b0].data(), keep[b0 + 1].data(), keep[b0 + 2].data(),
                              keep[b0 + 3].data(), est};
   }
-  return eifmm_ops_load(kern, L, depth, lv.data(), out);
+  EIFMM_TRY(eifmm_ops_load(kern, L, depth, lv.data(), out));
+  const int tier = tier_for_eps(eps, true);
+  if (tier != (*out)->o.tier) {
+    eifmm_status rc = eifmm_ops_plan(*out, tier, nullptr);
+    if (rc != EIFMM_OK) {
+      eifmm_ops_destroy(*out);
+      *out = nullptr;
+      return rc;
+    }
+  }
+  return EIFMM_OK;
 }
 
 extern "C" eifmm_status eifmm_ops_error_estimate(const eifmm_ops* ops, int level, double* eps_k,
