@@ -189,6 +189,40 @@ eifmm_status eifmm_tree_export(const eifmm_tree* tree, int which,
 
 void eifmm_tree_destroy(eifmm_tree* tree);
 
+/* Morton bin/sort of one point set that allocates no memory at all.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc -- code recorded into a CUDA graph under a capture
+ * mode that forbids allocation, programs whose device memory is owned by
+ * another allocator (a framework's caching pool that would be bypassed or
+ * starved by a raw cudaMalloc), and latency-bound loops that cannot afford
+ * the implicit device synchronisation of cudaMalloc/cudaFree.
+ *
+ * It computes what eifmm_tree_build computes for the sources (same keys,
+ * same stable permutation, same leaf offsets) into caller-owned DEVICE
+ * arrays: keys_out[n] (sorted Morton keys), perm_out[n] (input index of
+ * each sorted position) and leaf_off_out[8^depth + 1].  xyz is a DEVICE
+ * row-major n x 3 FP64 array, lo a host array of 3 doubles.
+ *
+ * Scratch: the radix passes use a static device array of the library
+ * (EIFMM_STATIC_SORT_SCRATCH_BYTES, about 8.5 MB), which every GPU that
+ * loads the library holds until the process exits; n may not exceed
+ * EIFMM_STATIC_SORT_MAX_POINTS (EINVAL otherwise, before any device work).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents: calls that overlap on the GPU (concurrent
+ * streams, several host threads) race on it and must be serialised by the
+ * caller.  The call synchronises `stream` (it reads back the count of points
+ * outside the cube and returns EINVAL if there is any). */
+#define EIFMM_STATIC_SORT_MAX_POINTS 1048576
+#define EIFMM_STATIC_SORT_SCRATCH_BYTES 8913152
+eifmm_status eifmm_tree_sort_static(const double* xyz, int64_t n,
+                                    const double lo[3], double L, int depth,
+                                    uint32_t* keys_out, int32_t* perm_out,
+                                    int32_t* leaf_off_out,
+                                    eifmm_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* Evaluation: Algorithm 3 (steps 1-7) + near field f_N (Section 3.2).      */
 /* ------------------------------------------------------------------------ */

@@ -7,6 +7,8 @@
 // that equal digits keep their input order), leaf offsets from the sorted
 // keys and the gather of sorted FP64 coordinates plus FP32 coordinates
 // relative to the leaf centre.
+#include <mutex>
+
 #include "internal.h"
 
 namespace eifmm {
@@ -267,3 +269,116 @@ void free_pointset(PointSet* ps) {
 }
 
 }  // namespace eifmm
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the bin/sort (eifmm_tree_sort_static).  Its
+// radix-sort scratch lives in a file-scope device array: keys and indices of
+// the other half of the ping-pong (4 + 4 bytes per point), the per-block
+// digit counts (256 x 4 bytes per 2048 points) and an error counter.
+// ---------------------------------------------------------------------------
+namespace eifmm {
+namespace {
+constexpr int64_t kStaticMax = EIFMM_STATIC_SORT_MAX_POINTS;
+constexpr int64_t kStaticBlocks = (kStaticMax + RS_TILE - 1) / RS_TILE;
+constexpr size_t kOffKeys = 0;
+constexpr size_t kOffVals = kOffKeys + (size_t)kStaticMax * 4;
+constexpr size_t kOffCounts = kOffVals + (size_t)kStaticMax * 4;
+constexpr size_t kOffBad = kOffCounts + (size_t)256 * kStaticBlocks * 4;
+constexpr size_t kStaticBytes = kOffBad + 256;
+static_assert(kStaticBytes == EIFMM_STATIC_SORT_SCRATCH_BYTES, "scratch size of the header");
+
+__device__ __align__(256) unsigned char g_sort_scratch[kStaticBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mu;
+
+// Device address of the scratch on the current device, looked up once per
+// device (the host-side symbol is only a stand-in, never a device address).
+eifmm_status static_scratch(unsigned char** out) {
+  int dev = 0;
+  EIFMM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    set_error("eifmm_tree_sort_static: device ordinal out of range");
+    return EIFMM_EUNSUPPORTED;
+  }
+  std::lock_guard<std::mutex> lk(g_scratch_mu);
+  if (!g_scratch_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_sort_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+      set_error(std::string("eifmm_tree_sort_static: cudaGetSymbolAddress failed: ") +
+                cudaGetErrorString(e));
+      return EIFMM_ECUDA;
+    }
+    g_scratch_addr[dev] = p;
+  }
+  *out = (unsigned char*)g_scratch_addr[dev];
+  return EIFMM_OK;
+}
+}  // namespace
+}  // namespace eifmm
+
+using namespace eifmm;
+
+extern "C" eifmm_status eifmm_tree_sort_static(const double* xyz, int64_t n, const double lo[3],
+                                               double L, int depth, uint32_t* keys_out,
+                                               int32_t* perm_out, int32_t* leaf_off_out,
+                                               eifmm_stream stream) {
+  if (!lo || !leaf_off_out || n < 0 || (n > 0 && (!xyz || !keys_out || !perm_out)) || depth < 2 ||
+      depth > kMaxLevel || !(L > 0.0)) {
+    set_error("eifmm_tree_sort_static: invalid argument");
+    return EIFMM_EINVAL;
+  }
+  if (n > kStaticMax) {
+    set_error("eifmm_tree_sort_static: n = " + std::to_string(n) + " exceeds the static scratch limit of " +
+              std::to_string(kStaticMax) + " points (EIFMM_STATIC_SORT_MAX_POINTS)");
+    return EIFMM_EINVAL;
+  }
+  unsigned char* base = nullptr;
+  EIFMM_TRY(static_scratch(&base));
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* k2 = (uint32_t*)(base + kOffKeys);
+  int32_t* v2 = (int32_t*)(base + kOffVals);
+  uint32_t* counts = (uint32_t*)(base + kOffCounts);
+  int* bad = (int*)(base + kOffBad);
+  // the error counter must start at zero on every call
+  EIFMM_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
+  const int64_t nleaf = (int64_t)1 << (3 * depth);
+  const int nblocks = (int)((n + RS_TILE - 1) / RS_TILE);
+  if (n > 0) {
+    k_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xyz, n, lo[0], lo[1], lo[2], lo[0] + L, lo[1] + L,
+                                                        lo[2] + L, ldexp(1.0, depth) / L, depth, keys_out,
+                                                        perm_out, bad);
+    EIFMM_CHECK_LAUNCH();
+    uint32_t* kin = keys_out;
+    int32_t* vin = perm_out;
+    uint32_t* kout = k2;
+    int32_t* vout = v2;
+    for (int shift = 0; shift < 3 * depth; shift += 8) {
+      k_rs_count<<<nblocks, RS_THREADS, 0, s>>>(kin, n, shift, counts, nblocks);
+      EIFMM_CHECK_LAUNCH();
+      k_scan_excl<<<1, 1024, 0, s>>>(counts, (int64_t)256 * nblocks);
+      EIFMM_CHECK_LAUNCH();
+      k_rs_scatter<<<nblocks, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, counts, nblocks);
+      EIFMM_CHECK_LAUNCH();
+      uint32_t* tk = kin; kin = kout; kout = tk;
+      int32_t* tv = vin; vin = vout; vout = tv;
+    }
+    if (kin != keys_out) {
+      EIFMM_CUDA(cudaMemcpyAsync(keys_out, kin, n * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+      EIFMM_CUDA(cudaMemcpyAsync(perm_out, vin, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  k_leaf_off<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(keys_out, n, nleaf, leaf_off_out);
+  EIFMM_CHECK_LAUNCH();
+  int hbad = 0;
+  EIFMM_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+  EIFMM_CUDA(cudaStreamSynchronize(s));
+  if (hbad != 0) {
+    set_error("eifmm_tree_sort_static: " + std::to_string(hbad) +
+              " coordinates lie outside the cube [lo, lo + L]^3");
+    return EIFMM_EINVAL;
+  }
+  return EIFMM_OK;
+}

@@ -25,6 +25,7 @@ EXPORTS = [
     "eifmm_ops_destroy", "eifmm_tree_build", "eifmm_tree_export", "eifmm_tree_destroy",
     "eifmm_evaluate", "eifmm_evaluate_host", "eifmm_evaluate_batched", "eifmm_debug_export",
     "eifmm_set_timing", "eifmm_last_step_times", "eifmm_direct_sum", "eifmm_kernel_launches",
+    "eifmm_tree_sort_static",
 ]
 
 
@@ -73,6 +74,7 @@ def lib() -> C.CDLL:
         "eifmm_last_step_times": (i32, [vp, vp]),
         "eifmm_direct_sum": (i32, [i32, vp, i64, vp, i64, vp, i64, i32, i32, vp, i64, vp, vp]),
         "eifmm_kernel_launches": (C.c_uint64, []),
+        "eifmm_tree_sort_static": (i32, [vp, i64, vp, dbl, i32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -294,3 +296,26 @@ def eifmm_direct_sum(kern, tgt_xyz, src_xyz, sigma, exclude_self=True, tgt_idx=N
 
 def eifmm_kernel_launches() -> int:
     return int(lib().eifmm_kernel_launches())
+
+
+STATIC_SORT_MAX_POINTS = 1048576
+
+
+def eifmm_tree_sort_static(xyz, lo=(0.0, 0.0, 0.0), L: float = 1.0, depth: int = 3,
+                           keys=None, perm=None, leaf_off=None, stream=None):
+    """Allocation-free bin/sort into caller-owned CUDA tensors (created here
+    when not given): returns (keys uint32 as int32 bits, perm int32,
+    leaf_off int32)."""
+    import torch
+    n = xyz.shape[0]
+    dev = xyz.device
+    if keys is None:
+        keys = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    if perm is None:
+        perm = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    if leaf_off is None:
+        leaf_off = torch.empty((1 << (3 * depth)) + 1, dtype=torch.int32, device=dev)
+    lo = np.ascontiguousarray(lo, dtype=np.float64)
+    _check(lib().eifmm_tree_sort_static(_p(xyz), n, _p(lo), float(L), depth, _p(keys), _p(perm),
+                                        _p(leaf_off), _stream(stream)))
+    return keys[:n], perm[:n], leaf_off
