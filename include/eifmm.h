@@ -60,15 +60,15 @@ typedef enum {
 
 /* Arithmetic of eifmm_evaluate.
  *   FP64:  every step in FP64 (the plain GPU EIFMM).
- *   MIXED: the near field in FP32 with compensated summation on coordinates
- *          local to each leaf; the far field chooses its arithmetic from the
- *          operators' EIM tolerance eps (see eifmm_ops_plan):
- *            eps >= 1e-5: M2L on tcgen05 tensor cores with BF16 hi+lo split
- *                         operands (3 products, FP32 accumulate), P2M, M2M,
- *                         L2L, L2P and the Delta solves in FP32;
- *            1e-6 <= eps < 1e-5: M2L with a three-way BF16 split (6
- *                         products), Delta solves in FP64, the rest FP32;
- *            eps < 1e-6:  far field in FP64 (only the near field is FP32).
+ *   MIXED: the arithmetic tier of the operators (eifmm_ops_plan,
+ *          eifmm_ops_calibrate):
+ *            tier 0: M2L on tcgen05 tensor cores with BF16 hi+lo operands (3
+ *                    products, FP32 accumulation in several chains), P2M,
+ *                    M2M, L2L, L2P, the Delta solves and the near field in
+ *                    FP32 on coordinates local to each leaf;
+ *            tier 1: M2L with TF32 hi+lo operands, Delta solves in FP64;
+ *            tier 2: far field in FP64, near field in FP32 (Kahan sums);
+ *            tier 3: FP64 everywhere.
  */
 typedef enum { EIFMM_PREC_FP64 = 0, EIFMM_PREC_MIXED = 1 } eifmm_precision;
 
@@ -142,7 +142,8 @@ eifmm_status eifmm_ops_load(eifmm_kernel kern, double L, int depth,
                             const eifmm_level_data* levels, eifmm_ops** out);
 
 /* Convenience: default training sets + eifmm_eim_build(eps, d_max) for every
- * level 2..depth + eifmm_ops_load. Synchronises `stream`. */
+ * level 2..depth + eifmm_ops_load + eifmm_ops_calibrate(eps).  Synchronises
+ * `stream`. */
 eifmm_status eifmm_ops_build(eifmm_kernel kern, double L, int depth,
                              double eps, int d_max, eifmm_stream stream,
                              eifmm_ops** out);
@@ -152,9 +153,20 @@ eifmm_status eifmm_ops_error_estimate(const eifmm_ops* ops, int level,
                                       double* eps_k, int* d_k);
 
 /* Arithmetic tier that EIFMM_PREC_MIXED uses with these operators:
- * 0 = BF16x3 M2L + FP32 far field, 1 = BF16x6 M2L + FP64 solves,
- * 2 = FP64 far field.  `tier_override` >= 0 forces a tier (testing). */
+ * 0 = BF16 hi+lo M2L and an FP32 far field, 1 = TF32 hi+lo M2L and FP64
+ * Delta solves, 2 = FP64 far field, 3 = FP64 everywhere (near field too).
+ * eifmm_ops_load sets it from the built-in error estimate; `tier_override`
+ * >= 0 forces a tier. */
 eifmm_status eifmm_ops_plan(eifmm_ops* ops, int tier_override, int* tier);
+
+/* Measured choice of the tier (no counterpart in the paper, which computes in
+ * FP64): a uniform problem of 8 points per leaf at depth min(depth, 4) is
+ * evaluated in FP64 and in tiers 0, 1, 2; the cheapest tier whose relative L2
+ * difference to FP64 is at most eps/4 is kept, else tier 3.  Allocates and
+ * frees its own device memory; synchronises `stream`.  Errors: EINVAL,
+ * ENOMEM, ECUDA. */
+eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_stream stream,
+                                 int* tier);
 
 void eifmm_ops_destroy(eifmm_ops* ops);
 

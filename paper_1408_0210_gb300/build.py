@@ -42,7 +42,7 @@ def _stale(obj: str, src: str, deps: list[str]) -> bool:
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    deps = sorted(glob.glob(os.path.join(CSRC, "*.h"))) + [
+    deps = sorted(glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))) + [
         os.path.join(os.path.dirname(HERE), "include", "eifmm.h")]
     cc = nvcc()
 

@@ -100,7 +100,7 @@ eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec) {
     return EIFMM_OK;
   free_workspace(&ws);
   const int kap = t->depth;
-  const bool fp64_far = (prec == EIFMM_PREC_FP64) || tier == 2;
+  const bool fp64_far = (prec == EIFMM_PREC_FP64) || tier >= 2;
   if (fp64_far) {
     for (int k = 2; k <= kap; ++k) {
       const size_t n = ((size_t)1 << (3 * k)) * R * ops->lv[k].d;
@@ -287,16 +287,12 @@ extern "C" eifmm_status eifmm_ops_build(eifmm_kernel kern, double L, int depth, 
                              keep[b0 + 3].data(), est};
   }
   EIFMM_TRY(eifmm_ops_load(kern, L, depth, lv.data(), out));
-  const int tier = tier_for_eps(eps, true);
-  if (tier != (*out)->o.tier) {
-    eifmm_status rc = eifmm_ops_plan(*out, tier, nullptr);
-    if (rc != EIFMM_OK) {
-      eifmm_ops_destroy(*out);
-      *out = nullptr;
-      return rc;
-    }
+  eifmm_status rc = eifmm_ops_calibrate(*out, eps, stream, nullptr);
+  if (rc != EIFMM_OK) {
+    eifmm_ops_destroy(*out);
+    *out = nullptr;
   }
-  return EIFMM_OK;
+  return rc;
 }
 
 extern "C" eifmm_status eifmm_ops_error_estimate(const eifmm_ops* ops, int level, double* eps_k,
@@ -311,7 +307,7 @@ extern "C" eifmm_status eifmm_ops_error_estimate(const eifmm_ops* ops, int level
 }
 
 extern "C" eifmm_status eifmm_ops_plan(eifmm_ops* ops, int tier_override, int* tier) {
-  if (!ops || tier_override > 2) {
+  if (!ops || tier_override > 3) {
     set_error("eifmm_ops_plan: invalid handle or tier");
     return EIFMM_EINVAL;
   }
@@ -424,9 +420,8 @@ static eifmm_status evaluate_impl(eifmm_tree* tree, const eifmm_ops* ops, const 
   Tree& t = tree->t;
   EIFMM_TRY(ensure_workspace(&t, &ops->o, n_rhs, prec));
   eifmm_status rc;
-  if (prec == EIFMM_PREC_FP64 || ops->o.tier == 2)
-    rc = (prec == EIFMM_PREC_FP64) ? eval_fp64(&t, &ops->o, sigma, ld_sigma, n_rhs, f, ld_f, s)
-                                   : eval_mixed(&t, &ops->o, sigma, ld_sigma, n_rhs, f, ld_f, s);
+  if (prec == EIFMM_PREC_FP64 || ops->o.tier >= 3)
+    rc = eval_fp64(&t, &ops->o, sigma, ld_sigma, n_rhs, f, ld_f, s);
   else
     rc = eval_mixed(&t, &ops->o, sigma, ld_sigma, n_rhs, f, ld_f, s);
   if (rc != EIFMM_OK) return rc;
@@ -437,6 +432,93 @@ static eifmm_status evaluate_impl(eifmm_tree* tree, const eifmm_ops* ops, const 
     for (int k = 2; k <= t.depth; ++k)
       cudaEventElapsedTime(&t.ws.step_ms[9 + k], t.ws.ev_m2l[k], t.ws.ev_m2l[k + 1]);
   }
+  return EIFMM_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Measured choice of the mixed-precision tier.  A uniform problem of 8 points
+// per leaf is evaluated at depth min(depth, 4) with the operators' own kernel
+// in FP64 and in every mixed tier; the cheapest tier whose relative L2
+// difference to FP64 stays below eps/4 is kept (tier 3: all FP64).
+// ---------------------------------------------------------------------------
+extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_stream stream,
+                                            int* tier_out) {
+  if (!ops || !(eps > 0.0)) {
+    set_error("eifmm_ops_calibrate: invalid handle or eps");
+    return EIFMM_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int depth = ops->o.depth < 4 ? ops->o.depth : 4;
+  const int64_t n = (int64_t)8 << (3 * depth);
+  const double L = ops->o.L;
+  std::vector<double> hx(3 * n), hs(n);
+  uint64_t st = 0x9E3779B97F4A7C15ull;
+  auto next = [&]() {  // splitmix64
+    st += 0x9E3779B97F4A7C15ull;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return (double)((z ^ (z >> 31)) >> 11) * 0x1.0p-53;
+  };
+  for (int64_t i = 0; i < 3 * n; ++i) hx[i] = L * next();
+  for (int64_t i = 0; i < n; ++i) hs[i] = 2.0 * next() - 1.0;
+  double *dx = nullptr, *ds = nullptr, *fr = nullptr, *fm = nullptr;
+  eifmm_tree* tree = nullptr;
+  eifmm_status rc = EIFMM_OK;
+  int best = 3;
+  do {
+    if ((rc = dalloc(&dx, 3 * n)) != EIFMM_OK) break;
+    if ((rc = dalloc(&ds, n)) != EIFMM_OK) break;
+    if ((rc = dalloc(&fr, n)) != EIFMM_OK) break;
+    if ((rc = dalloc(&fm, n)) != EIFMM_OK) break;
+    cudaMemcpy(dx, hx.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(ds, hs.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    const double lo[3] = {0.0, 0.0, 0.0};
+    if ((rc = eifmm_tree_build(dx, n, dx, n, lo, L, depth, 1, stream, &tree)) != EIFMM_OK) break;
+    // a view of the operators restricted to the calibration depth
+    eifmm_ops view;
+    view.o = ops->o;
+    view.o.depth = depth;
+    if ((rc = evaluate_impl(tree, &view, ds, n, 1, fr, n, EIFMM_PREC_FP64, s)) != EIFMM_OK) break;
+    std::vector<double> href(n), hm(n);
+    if (cudaMemcpyAsync(href.data(), fr, n * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = EIFMM_ECUDA;
+      set_error("eifmm_ops_calibrate: copy failed");
+      break;
+    }
+    double nref = 0.0;
+    for (double v : href) nref += v * v;
+    for (int t = 0; t <= 2 && rc == EIFMM_OK; ++t) {
+      if (t <= 1 && (rc = build_kd_image(&ops->o, t == 1, s)) != EIFMM_OK) break;
+      view.o = ops->o;
+      view.o.depth = depth;
+      view.o.tier = t;
+      if ((rc = evaluate_impl(tree, &view, ds, n, 1, fm, n, EIFMM_PREC_MIXED, s)) != EIFMM_OK) break;
+      cudaMemcpyAsync(hm.data(), fm, n * sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (cudaStreamSynchronize(s) != cudaSuccess) {
+        rc = EIFMM_ECUDA;
+        set_error("eifmm_ops_calibrate: evaluation failed");
+        break;
+      }
+      double ne = 0.0;
+      for (int64_t i = 0; i < n; ++i) ne += (hm[i] - href[i]) * (hm[i] - href[i]);
+      const double err = sqrt(ne / (nref > 0 ? nref : 1.0));
+      if (err <= 0.25 * eps) {
+        best = t;
+        break;
+      }
+    }
+  } while (false);
+  if (tree) eifmm_tree_destroy(tree);
+  dfree(dx);
+  dfree(ds);
+  dfree(fr);
+  dfree(fm);
+  if (rc != EIFMM_OK) return rc;
+  EIFMM_TRY(eifmm_ops_plan(ops, best, nullptr));
+  if (tier_out) *tier_out = best;
   return EIFMM_OK;
 }
 

@@ -124,7 +124,11 @@ k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
 constexpr int P2P_WARPS = 4;
 constexpr int P2P_CHUNK = 64;
 
-template <int KERN>
+// ACC: Newton-refined 1/r and Kahan summation of every term (tiers 1, 2);
+// otherwise the hardware rsqrt and plain FP32 sums per neighbour leaf, the
+// 27 leaf sums combined with Kahan summation (tier 0).  RCT: right-hand
+// sides per pass (the kernel value is reused across them).
+template <int KERN, int RCT, bool ACC>
 __global__ void __launch_bounds__(32 * P2P_WARPS)
 k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, int nleaves,
         const int32_t* __restrict__ toff, const float* __restrict__ tlx,
@@ -135,7 +139,7 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, int nleaves,
         int exclude_self, double* __restrict__ fnear) {
   const int kern = KERN >= 0 ? KERN : kern_rt;
   __shared__ float4 src[P2P_WARPS][P2P_CHUNK];        // xyz in the target frame
-  __shared__ float ssig[P2P_WARPS][RC][P2P_CHUNK];
+  __shared__ float ssig[P2P_WARPS][RCT][P2P_CHUNK];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gw = blockIdx.x * P2P_WARPS + w;
   if (gw >= nleaves) return;
@@ -152,11 +156,12 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, int nleaves,
     const int ti = lane & (Tp - 1), si = lane / Tp;
     const bool act = ti < nT;
     const int p = t0 + (act ? ti : 0);
+    const int pself = (exclude_self && act) ? p : -1;
     const float x0 = tlx[p], x1 = tly[p], x2 = tlz[p];
-    for (int r0 = 0; r0 < R; r0 += RC) {
-      float sum[RC], comp[RC];
+    for (int r0 = 0; r0 < R; r0 += RCT) {
+      float sum[RCT], comp[RCT];
 #pragma unroll
-      for (int rr = 0; rr < RC; ++rr) sum[rr] = comp[rr] = 0.f;
+      for (int rr = 0; rr < RCT; ++rr) sum[rr] = comp[rr] = 0.f;
       for (int nb = 0; nb < 27; ++nb) {
         const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
         const int jx = c[0] + dx, jy = c[1] + dy, jz = c[2] + dz;
@@ -165,6 +170,9 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, int nleaves,
         const int sb = soff[J], se = soff[J + 1];
         // y - c_I = (y - c_J) + (c_J - c_I)
         const float s0 = dx * two_l, s1 = dy * two_l, s2 = dz * two_l;
+        float part[RCT];
+#pragma unroll
+        for (int rr = 0; rr < RCT; ++rr) part[rr] = 0.f;
         for (int q0 = sb; q0 < se; q0 += P2P_CHUNK) {
           __syncwarp();
           for (int t = lane; t < P2P_CHUNK; t += 32) {
@@ -172,34 +180,48 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, int nleaves,
             if (q < se) {
               src[w][t] = make_float4(slx[q] + s0, sly[q] + s1, slz[q] + s2, 0.f);
 #pragma unroll
-              for (int rr = 0; rr < RC; ++rr)
+              for (int rr = 0; rr < RCT; ++rr)
                 ssig[w][rr][t] = (r0 + rr < R) ? sig[q + (int64_t)(r0 + rr) * ns] : 0.f;
             }
           }
           __syncwarp();
           const int cnt = min(P2P_CHUNK, se - q0);
+          const int jself = pself - q0;  // the self pair, if it is in this chunk
           if (act)
             for (int j = si; j < cnt; j += S) {
-              if (exclude_self && q0 + j == p) continue;
               const float4 y = src[w][j];
-              const float kv = kern_f32(kern, x0 - y.x, x1 - y.y, x2 - y.z);
+              float kv = ACC ? kern_f32(kern, x0 - y.x, x1 - y.y, x2 - y.z)
+                             : kern_f32_fast(kern, x0 - y.x, x1 - y.y, x2 - y.z);
+              if (j == jself) kv = 0.f;
 #pragma unroll
-              for (int rr = 0; rr < RC; ++rr) {
-                if (r0 + rr >= R) break;
-                const float yk = ssig[w][rr][j] * kv - comp[rr];
-                const float tk = sum[rr] + yk;
-                comp[rr] = (tk - sum[rr]) - yk;
-                sum[rr] = tk;
+              for (int rr = 0; rr < RCT; ++rr) {
+                const float term = ssig[w][rr][j] * kv;
+                if (ACC) {
+                  const float yk = term - comp[rr];
+                  const float tk = sum[rr] + yk;
+                  comp[rr] = (tk - sum[rr]) - yk;
+                  sum[rr] = tk;
+                } else {
+                  part[rr] += term;
+                }
               }
             }
         }
+        if (!ACC) {
+#pragma unroll
+          for (int rr = 0; rr < RCT; ++rr) {
+            const float yk = part[rr] - comp[rr];
+            const float tk = sum[rr] + yk;
+            comp[rr] = (tk - sum[rr]) - yk;
+            sum[rr] = tk;
+          }
+        }
       }
 #pragma unroll
-      for (int rr = 0; rr < RC; ++rr) {
-        if (r0 + rr >= R) break;
+      for (int rr = 0; rr < RCT; ++rr) {
         double tot = act ? (double)sum[rr] - (double)comp[rr] : 0.0;
         for (int o = Tp; o < 32; o <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        if (act && si == 0) fnear[p + (int64_t)(r0 + rr) * nt] = tot;
+        if (act && si == 0 && r0 + rr < R) fnear[p + (int64_t)(r0 + rr) * nt] = tot;
       }
     }
   }
@@ -335,22 +357,39 @@ eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R) {
   return EIFMM_OK;
 }
 
-eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R, double* fnear,
-                          cudaStream_t s) {
+template <int KERN, int RCT, bool ACC>
+static void p2p_launch(const Tree* t, int kern, const float* sig32, int R, double* fnear, float two_l,
+                       cudaStream_t s) {
   const PointSet& T = t->tgt;
   const PointSet& S = t->src;
-  if (T.n_nonempty == 0) return EIFMM_OK;
-  const float two_l = (float)(t->L * ldexp(1.0, -t->depth));
   const unsigned grid = (unsigned)((T.n_nonempty + P2P_WARPS - 1) / P2P_WARPS);
-  if (kern == EIFMM_KERNEL_INV_R)
-    k_p2p32<EIFMM_KERNEL_INV_R><<<grid, 32 * P2P_WARPS, 0, s>>>(
-        kern, T.nonempty, T.n_nonempty, T.leaf_off, T.lx, T.ly, T.lz, T.n, S.leaf_off, S.lx, S.ly,
-        S.lz, sig32, S.n, R, t->depth, two_l, t->exclude_self, fnear);
-  else
-    k_p2p32<-1><<<grid, 32 * P2P_WARPS, 0, s>>>(kern, T.nonempty, T.n_nonempty, T.leaf_off, T.lx,
-                                                T.ly, T.lz, T.n, S.leaf_off, S.lx, S.ly, S.lz,
-                                                sig32, S.n, R, t->depth, two_l, t->exclude_self,
-                                                fnear);
+  k_p2p32<KERN, RCT, ACC><<<grid, 32 * P2P_WARPS, 0, s>>>(
+      kern, T.nonempty, T.n_nonempty, T.leaf_off, T.lx, T.ly, T.lz, T.n, S.leaf_off, S.lx, S.ly, S.lz,
+      sig32, S.n, R, t->depth, two_l, t->exclude_self, fnear);
+}
+
+eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R, double* fnear,
+                          cudaStream_t s, bool accurate) {
+  if (t->tgt.n_nonempty == 0) return EIFMM_OK;
+  const float two_l = (float)(t->L * ldexp(1.0, -t->depth));
+  const bool inv = kern == EIFMM_KERNEL_INV_R;
+  if (R == 1) {
+    if (inv) {
+      if (accurate) p2p_launch<EIFMM_KERNEL_INV_R, 1, true>(t, kern, sig32, R, fnear, two_l, s);
+      else p2p_launch<EIFMM_KERNEL_INV_R, 1, false>(t, kern, sig32, R, fnear, two_l, s);
+    } else {
+      if (accurate) p2p_launch<-1, 1, true>(t, kern, sig32, R, fnear, two_l, s);
+      else p2p_launch<-1, 1, false>(t, kern, sig32, R, fnear, two_l, s);
+    }
+  } else {
+    if (inv) {
+      if (accurate) p2p_launch<EIFMM_KERNEL_INV_R, 4, true>(t, kern, sig32, R, fnear, two_l, s);
+      else p2p_launch<EIFMM_KERNEL_INV_R, 4, false>(t, kern, sig32, R, fnear, two_l, s);
+    } else {
+      if (accurate) p2p_launch<-1, 4, true>(t, kern, sig32, R, fnear, two_l, s);
+      else p2p_launch<-1, 4, false>(t, kern, sig32, R, fnear, two_l, s);
+    }
+  }
   EIFMM_CHECK_LAUNCH();
   return EIFMM_OK;
 }
@@ -380,7 +419,7 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   EIFMM_TRY(launch_gather_sigma(sigma, ld_sigma, S, R, ws.sig, ws.sig32, s));
   EIFMM_CUDA(cudaEventRecord(ws.ev_fork, s));
   EIFMM_CUDA(cudaStreamWaitEvent(ws.side, ws.ev_fork, 0));
-  EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, ws.side));
+  EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, ws.side, ops->tier >= 1));
   EIFMM_CUDA(cudaEventRecord(ws.ev_join, ws.side));
 
   // step 1 (every leaf, empty ones get zeros)
@@ -397,10 +436,12 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   for (int k = kap - 1; k >= 2; --k) {
     const LevelOps& a = ops->lv[k];
     const LevelOps& c = ops->lv[k + 1];
-    const int64_t np = nboxes(k);
-    k_m2m_warp<float><<<xfer_blocks(np, R, a.dp), 128, 0, s>>>(a.d, c.d, a.dp, c.dp, R, a.m2m32,
-                                                              ws.W32[k + 1], ws.W32[k], np);
-    EIFMM_CHECK_LAUNCH();
+    XferGemm x;
+    x.mode = 0;
+    x.dk = a.d; x.ldk = a.dp; x.dc = c.d; x.ldc = c.dp; x.R = R;
+    x.ncol = nboxes(k) * R;
+    x.A = a.m2m32; x.B = ws.W32[k + 1]; x.G = nullptr; x.C = ws.W32[k];
+    EIFMM_TRY(launch_xfer_gemm(x, s));
   }
   record(ws, 2, s);
   // step 3: What = Delta W (Gamma z = W, then B^t What = z), written as the
@@ -458,9 +499,12 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   for (int k = 3; k <= kap; ++k) {
     const LevelOps& v = ops->lv[k];
     const LevelOps& pv = ops->lv[k - 1];
-    k_l2l_warp<float><<<xfer_blocks(nboxes(k), R, v.dp), 128, 0, s>>>(
-        v.d, pv.d, v.dp, pv.dp, R, v.l2l32, ws.l32[k - 1], ws.g32[k], ws.l32[k], nboxes(k));
-    EIFMM_CHECK_LAUNCH();
+    XferGemm x;
+    x.mode = 1;
+    x.dk = v.d; x.ldk = v.dp; x.dc = pv.d; x.ldc = pv.dp; x.R = R;
+    x.ncol = nboxes(k - 1) * R;
+    x.A = v.l2l32; x.B = ws.l32[k - 1]; x.G = ws.g32[k]; x.C = ws.l32[k];
+    EIFMM_TRY(launch_xfer_gemm(x, s));
   }
   record(ws, 5, s);
   // step 6: lhat = Delta^t l (B z = l, then Gamma^t lhat = z)

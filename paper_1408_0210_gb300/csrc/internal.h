@@ -178,7 +178,7 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma,
                        int64_t ld_sigma, int R, double* f, int64_t ld_f,
                        cudaStream_t s, bool near32 = false);
 eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R,
-                          double* fnear, cudaStream_t s);
+                          double* fnear, cudaStream_t s, bool accurate);
 eifmm_status build_kd_image(Ops* ops, bool tf32, cudaStream_t s);
 eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma,
                         int64_t ld_sigma, int R, double* f, int64_t ld_f,
@@ -188,14 +188,19 @@ void free_workspace(Workspace* ws);
 bool timing_enabled();
 
 // ----------------------------------------------------------- device util --
+// spread the low 10 bits of v to every third bit (bit b -> bit 3b)
+__host__ __device__ inline uint32_t spread3(uint32_t v) {
+  v &= 0x3ffu;
+  v = (v | (v << 16)) & 0x030000ffu;
+  v = (v | (v << 8)) & 0x0300f00fu;
+  v = (v | (v << 4)) & 0x030c30c3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+// Morton key of box (x, y, z) with `bits` <= 10 bits per axis, x bit lowest.
 __host__ __device__ inline int64_t morton_encode(int64_t x, int64_t y, int64_t z, int bits) {
-  int64_t key = 0;
-  for (int b = 0; b < bits; ++b) {
-    key |= ((x >> b) & 1) << (3 * b);
-    key |= ((y >> b) & 1) << (3 * b + 1);
-    key |= ((z >> b) & 1) << (3 * b + 2);
-  }
-  return key;
+  (void)bits;
+  return (int64_t)(spread3((uint32_t)x) | (spread3((uint32_t)y) << 1) | (spread3((uint32_t)z) << 2));
 }
 __host__ __device__ inline void morton_decode(int64_t key, int bits, int* c) {
   int x = 0, y = 0, z = 0;
@@ -309,5 +314,11 @@ __device__ inline float kern_f32(int kern, float z0, float z1, float z2) {
     default:
       return 0.0f;
   }
+}
+// Without the Newton step (about 2 ulp for 1/r); used where the tolerance
+// allows it.
+__device__ inline float kern_f32_fast(int kern, float z0, float z1, float z2) {
+  if (kern == EIFMM_KERNEL_INV_R) return rsqrtf(fmaf(z0, z0, fmaf(z1, z1, z2 * z2)));
+  return kern_f32(kern, z0, z1, z2);
 }
 }  // namespace eifmm

@@ -330,15 +330,17 @@ k_m2l_tc(M2LTcArgs a) {
 __global__ void k_sum_parts(const float4* __restrict__ parts, int groups, int64_t n4, int64_t stride4,
                             float4* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
-    double x = 0, y = 0, z = 0, w = 0;
-    for (int g = 0; g < groups; ++g) {
-      const float4 v = parts[g * stride4 + i];
-      x += v.x;
-      y += v.y;
-      z += v.z;
-      w += v.w;
-    }
-    out[i] = make_float4((float)x, (float)y, (float)z, (float)w);
+    // pairwise over the groups (at most 16 partial sums)
+    float4 v[16];
+    for (int g = 0; g < groups; ++g) v[g] = parts[g * stride4 + i];
+    for (int w = 1; w < groups; w <<= 1)
+      for (int g = 0; g + w < groups; g += 2 * w) {
+        v[g].x += v[g + w].x;
+        v[g].y += v[g + w].y;
+        v[g].z += v[g + w].z;
+        v[g].w += v[g + w].w;
+      }
+    out[i] = v[0];
   }
 }
 

@@ -111,7 +111,9 @@ eifmm_status launch_tri_sweep(int d, const T* Mp, const Ti* in, int ldi, To* out
   int dev = 0, nsm = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = sm <= 110 * 1024 ? 2 : 1;
+  int per_sm = (int)((200 * 1024) / (sm > 0 ? sm : 1));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 2048 / (32 * kSolveWarps)) per_sm = 2048 / (32 * kSolveWarps);
   int64_t blocks = (nvec + kSolveWarps - 1) / kSolveWarps;
   if (blocks > (int64_t)nsm * per_sm) blocks = (int64_t)nsm * per_sm;
   k_tri_sweep<T, FWD, DIAG, Ti, To, PLANES><<<(unsigned)blocks, 32 * kSolveWarps, sm, s>>>(

@@ -92,3 +92,118 @@ inline unsigned xfer_blocks(int64_t nout, int R, int ldk) {
 }
 
 }  // namespace eifmm
+
+namespace eifmm {
+
+// ---------------------------------------------------------------------------
+// The same two steps as tiled GEMMs for the FP32 path: over all parents at
+// once, C = A B with A the precomputed operator (rows m) and B the columns of
+// child (M2M) or parent (L2L) coefficient vectors.  Block tile 64 x 64, K
+// step 16, 256 threads with 4 x 4 outputs each.
+//   M2M: C[m][c] = sum_{i, q} (K_M2M^i)_{m q} W^{child i of P}_q, c = P R + r,
+//        the reduction index k = i * dc + q runs over the 8 children.
+//   L2L: C[m][c] = g[m][c] + sum_q (K_L2L^i)_{m q} l^P_q for the child i of
+//        blockIdx.z, c = P R + r.
+// Rows m in [d, ld) of every output column are written as zeros.
+// ---------------------------------------------------------------------------
+struct XferGemm {
+  int mode;          // 0 = M2M, 1 = L2L
+  int dk, ldk;       // output rank and leading dimension
+  int dc, ldc;       // input rank and leading dimension (child for M2M, parent for L2L)
+  int R;
+  int64_t ncol;      // parents * R
+  const float* A;    // [8][dk][dc] row-major
+  const float* B;    // input coefficient rows
+  const float* G;    // L2L: g of the output level (same layout as C)
+  float* C;          // output coefficient rows
+};
+
+static __global__ void __launch_bounds__(256) k_xfer_gemm(XferGemm a) {
+  __shared__ float As[16][64 + 4];
+  __shared__ float Bs[16][64 + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.x * 64;
+  const int64_t c0 = (int64_t)blockIdx.y * 64;
+  const int i_l2l = blockIdx.z;
+  const int K = a.mode == 0 ? 8 * a.dc : a.dc;
+  float acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int e = tid + 256 * j;      // 0..1023
+      const int kk = e & 15, rr = e >> 4;  // rr: row of A tile / column of B tile
+      const int k = k0 + kk;
+      // A(m, k)
+      const int m = m0 + rr;
+      float av = 0.f;
+      if (m < a.dk && k < K) {
+        if (a.mode == 0) {
+          const int i = k / a.dc, q = k - i * a.dc;
+          av = a.A[((int64_t)i * a.dk + m) * a.dc + q];
+        } else {
+          av = a.A[((int64_t)i_l2l * a.dk + m) * a.dc + k];
+        }
+      }
+      As[kk][rr] = av;
+      // B(k, c)
+      const int64_t c = c0 + rr;
+      float bv = 0.f;
+      if (c < a.ncol && k < K) {
+        const int64_t P = c / a.R;
+        const int r = (int)(c - P * a.R);
+        if (a.mode == 0) {
+          const int i = k / a.dc, q = k - i * a.dc;
+          bv = a.B[((8 * P + i) * a.R + r) * a.ldc + q];
+        } else {
+          bv = a.B[(P * a.R + r) * a.ldc + k];
+        }
+      }
+      Bs[kk][rr] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float ar[4], br[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ar[u] = As[kk][ty * 4 + u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) br[v] = Bs[kk][tx * 4 + v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ar[u], br[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int64_t c = c0 + tx * 4 + v;
+    if (c >= a.ncol) continue;
+    const int64_t P = c / a.R;
+    const int r = (int)(c - P * a.R);
+    const int64_t row = a.mode == 0 ? (P * a.R + r) : ((8 * P + i_l2l) * a.R + r);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int m = m0 + ty * 4 + u;
+      if (m >= a.ldk) continue;
+      const int64_t o = row * a.ldk + m;
+      float val = 0.f;
+      if (m < a.dk) val = a.mode == 0 ? acc[u][v] : a.G[o] + acc[u][v];
+      a.C[o] = val;
+    }
+  }
+}
+
+inline eifmm_status launch_xfer_gemm(const XferGemm& a, cudaStream_t s) {
+  const dim3 grid((unsigned)((a.ldk + 63) / 64), (unsigned)((a.ncol + 63) / 64), a.mode == 0 ? 1 : 8);
+  k_xfer_gemm<<<grid, 256, 0, s>>>(a);
+  EIFMM_CHECK_LAUNCH();
+  return EIFMM_OK;
+}
+
+}  // namespace eifmm

@@ -25,7 +25,7 @@ EXPORTS = [
     "eifmm_ops_destroy", "eifmm_tree_build", "eifmm_tree_export", "eifmm_tree_destroy",
     "eifmm_evaluate", "eifmm_evaluate_host", "eifmm_evaluate_batched", "eifmm_debug_export",
     "eifmm_set_timing", "eifmm_last_step_times", "eifmm_direct_sum", "eifmm_kernel_launches",
-    "eifmm_tree_sort_static",
+    "eifmm_tree_sort_static", "eifmm_ops_calibrate",
 ]
 
 
@@ -75,6 +75,7 @@ def lib() -> C.CDLL:
         "eifmm_direct_sum": (i32, [i32, vp, i64, vp, i64, vp, i64, i32, i32, vp, i64, vp, vp]),
         "eifmm_kernel_launches": (C.c_uint64, []),
         "eifmm_tree_sort_static": (i32, [vp, i64, vp, dbl, i32, vp, vp, vp, vp]),
+        "eifmm_ops_calibrate": (i32, [vp, dbl, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -162,6 +163,11 @@ class Ops:
         e, d = C.c_double(), C.c_int()
         _check(lib().eifmm_ops_error_estimate(self.handle, level, C.byref(e), C.byref(d)))
         return e.value, d.value
+
+    def calibrate(self, eps: float, stream=None) -> int:
+        t = C.c_int()
+        _check(lib().eifmm_ops_calibrate(self.handle, float(eps), _stream(stream), C.byref(t)))
+        return t.value
 
     def plan(self, tier_override: int = -1) -> int:
         t = C.c_int()
