@@ -201,9 +201,13 @@ def main():
         prec, eps = v.split(":")
         variants.append((prec, float(eps)))
     ops = {}
+    ops_err = {}
     for _, eps in variants:
-        if eps not in ops:
-            ops[eps] = E.eifmm_ops_build("inv_r", 1.0, DEPTH, eps, 512, stream)
+        if eps not in ops and eps not in ops_err:
+            try:
+                ops[eps] = E.eifmm_ops_build("inv_r", 1.0, DEPTH, eps, 512, stream)
+            except E.EifmmError as e:
+                ops_err[eps] = str(e)
 
     if args.profile_steps > 0:
         prec, eps = variants[0]
@@ -252,6 +256,9 @@ def main():
     headline = None
     with ClockSampler(torch.cuda.current_device()) as clk:
         for prec, eps in variants:
+            if eps in ops_err:
+                results[f"{prec}@{eps:g}"] = {"unavailable": ops_err[eps]}
+                continue
             try:
                 steps = args.steps if (prec == "mixed" or eps >= 1e-5) else max(3, args.steps // 3)
                 ms, err, launches, st = run_variant(prec, eps, steps, args.warmup, timing=True)
@@ -262,6 +269,7 @@ def main():
             m2l = [statistics.median([t[9 + k] for t in st]) for k in range(2, DEPTH + 1)]
             results[f"{prec}@{eps:g}"] = {
                 "value": N_POINTS * NRHS * ws / (ms * 1e-3), "ms_per_step": ms,
+                "tier": ops[eps].plan() if prec == "mixed" else None,
                 "rel_l2_vs_exact": err, "meets_eps": err <= eps, "d": d,
                 "gpu_launches": launches, "steps": steps,
                 "step_ms": [round(statistics.median([t[i] for t in st]), 4) for i in range(8)],

@@ -492,10 +492,20 @@ extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_st
     for (double v : href) nref += v * v;
     for (int t = 0; t <= 2 && rc == EIFMM_OK; ++t) {
       if (t <= 1 && (rc = build_kd_image(&ops->o, t == 1, s)) != EIFMM_OK) break;
+      // a tier whose M2L operands could not be built (d too large) is skipped
+      bool have_img = true;
+      for (int k = 2; k <= depth; ++k)
+        if (t <= 1 && ops->o.lv[k].kd_img == nullptr) have_img = false;
+      if (!have_img) continue;
       view.o = ops->o;
       view.o.depth = depth;
       view.o.tier = t;
-      if ((rc = evaluate_impl(tree, &view, ds, n, 1, fm, n, EIFMM_PREC_MIXED, s)) != EIFMM_OK) break;
+      rc = evaluate_impl(tree, &view, ds, n, 1, fm, n, EIFMM_PREC_MIXED, s);
+      if (rc == EIFMM_EUNSUPPORTED) {  // this tier cannot run these operators
+        rc = EIFMM_OK;
+        continue;
+      }
+      if (rc != EIFMM_OK) break;
       cudaMemcpyAsync(hm.data(), fm, n * sizeof(double), cudaMemcpyDeviceToHost, s);
       if (cudaStreamSynchronize(s) != cudaSuccess) {
         rc = EIFMM_ECUDA;

@@ -267,11 +267,12 @@ __global__ void k_build_img(const double* __restrict__ kdT, int d, int dp, int t
 
 // planes -> FP64 [row][d] (debug export of What)
 __global__ void k_planes_to_f64(const void* __restrict__ planes, int tf32, int64_t nvec, int d, int dp,
-                                double* __restrict__ out) {
+                                int grid_level, int R, double* __restrict__ out) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nvec * d;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = t / d;
-    const int j = (int)(t - v * d);
+    const int64_t v0 = t / d;
+    const int j = (int)(t - v0 * d);
+    const int64_t v = plane_row(v0, grid_level, R);
     double x;
     if (tf32) {
       const float* p = (const float*)planes;
@@ -333,6 +334,17 @@ eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R) {
     if (k == 2) ws.l32[k] = ws.g32[k];
     else EIFMM_TRY(dalloc(&ws.l32[k], n));
     EIFMM_TRY(dmalloc(&ws.wa[k], 2 * n * 4));
+    // TMA-tiled M2L when the rhs count has a tile shape: planes on the
+    // per-class grid, one tensor map per plane
+    int bx, by, bz;
+    ws.wa_grid[k] = false;
+    const bool tf32 = ops->tier == 1;
+    if (ops->tier <= 1 && ops->lv[k].dp <= kMaxDpTc && m2l_tma_block(R, &bx, &by, &bz)) {
+      const size_t plane = n * (tf32 ? 4 : 2);
+      EIFMM_TRY(make_plane_map(ws.tmap[k][0], ws.wa[k], k, R, dp, tf32));
+      EIFMM_TRY(make_plane_map(ws.tmap[k][1], (char*)ws.wa[k] + plane, k, R, dp, tf32));
+      ws.wa_grid[k] = true;
+    }
   }
   EIFMM_TRY(dalloc(&ws.lh32, (size_t)nboxes(kap) * R * ops->lv[kap].dp));
   {
@@ -412,6 +424,12 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   }
   const bool tf32 = ops->tier == 1;
   const int kap = t->depth;
+  if (tf32)
+    for (int k = 2; k <= kap; ++k)
+      if (solve_smem_bytes(ops->lv[k].d, sizeof(double)) > 227 * 1024) {
+        set_error("eifmm_evaluate: tier 1 needs d <= 230 (FP64 triangle in shared memory)");
+        return EIFMM_EUNSUPPORTED;
+      }
   const int kern = (int)ops->kern;
   const PointSet& S = t->src;
   const PointSet& T = t->tgt;
@@ -441,6 +459,7 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     x.dk = a.d; x.ldk = a.dp; x.dc = c.d; x.ldc = c.dp; x.R = R;
     x.ncol = nboxes(k) * R;
     x.A = a.m2m32; x.B = ws.W32[k + 1]; x.G = nullptr; x.C = ws.W32[k];
+    x.P8 = (float*)ws.tmp;  // 8 x nboxes(k) x R x dp floats fit in the sweep scratch
     EIFMM_TRY(launch_xfer_gemm(x, s));
   }
   record(ws, 2, s);
@@ -453,14 +472,14 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
       double* z = (double*)ws.tmp;
       EIFMM_TRY((launch_tri_sweep<double, true, true, float, double, 0>(v.d, v.G_colp, ws.W32[k], v.dp, z,
                                                                         v.d, nullptr, nvec, s)));
-      EIFMM_TRY((launch_tri_sweep<double, false, false, double, float, 2>(v.d, v.B_rowp, z, v.d, nullptr,
-                                                                          v.dp, ws.wa[k], nvec, s)));
+      EIFMM_TRY((launch_tri_sweep<double, false, false, double, float, 2>(
+          v.d, v.B_rowp, z, v.d, nullptr, v.dp, ws.wa[k], nvec, s, ws.wa_grid[k] ? k : -1, R)));
     } else {
       float* z = (float*)ws.tmp;
       EIFMM_TRY((launch_tri_sweep<float, true, true, float, float, 0>(v.d, v.G32_colp, ws.W32[k], v.dp, z,
                                                                       v.d, nullptr, nvec, s)));
-      EIFMM_TRY((launch_tri_sweep<float, false, false, float, float, 1>(v.d, v.B32_rowp, z, v.d, nullptr,
-                                                                        v.dp, ws.wa[k], nvec, s)));
+      EIFMM_TRY((launch_tri_sweep<float, false, false, float, float, 1>(
+          v.d, v.B32_rowp, z, v.d, nullptr, v.dp, ws.wa[k], nvec, s, ws.wa_grid[k] ? k : -1, R)));
     }
   }
   record(ws, 3, s);
@@ -491,7 +510,8 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
       a.groups = m2l_tc_groups((a.nbox / 8 * R + 127) / 128 * 8, nsm, a.dp);
       a.part = ws.m2l_part;
     }
-    EIFMM_TRY(launch_m2l_tc(a, tf32, s));
+    if (ws.wa_grid[k]) EIFMM_TRY(launch_m2l_tma(a, ws.tmap[k][0], ws.tmap[k][1], tf32, s));
+    else EIFMM_TRY(launch_m2l_tc(a, tf32, s));
   }
   if (timing_enabled()) cudaEventRecord(ws.ev_m2l[kap + 1], s);
   record(ws, 4, s);
@@ -504,6 +524,7 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     x.dk = v.d; x.ldk = v.dp; x.dc = pv.d; x.ldc = pv.dp; x.R = R;
     x.ncol = nboxes(k - 1) * R;
     x.A = v.l2l32; x.B = ws.l32[k - 1]; x.G = ws.g32[k]; x.C = ws.l32[k];
+    x.P8 = nullptr;
     EIFMM_TRY(launch_xfer_gemm(x, s));
   }
   record(ws, 5, s);
@@ -556,7 +577,8 @@ eifmm_status export_mixed(const Tree& t, const Ops& o, int what, int level, doub
   double* tmp = nullptr;
   EIFMM_TRY(dalloc(&tmp, cnt));
   if (what == 1) {
-    k_planes_to_f64<<<grid_for(cnt, 256), 256>>>(ws.wa[level], ws.tier == 1, nvec, v.d, v.dp, tmp);
+    k_planes_to_f64<<<grid_for(cnt, 256), 256>>>(ws.wa[level], ws.tier == 1, nvec, v.d, v.dp,
+                                                 ws.wa_grid[level] ? level : -1, ws.nrhs, tmp);
   } else {
     const float* src = what == 0 ? ws.W32[level] : what == 2 ? ws.g32[level] : what == 3 ? ws.l32[level] : ws.lh32;
     k_f32_to_f64<<<grid_for(cnt, 256), 256>>>(src, nvec, v.d, v.dp, tmp);

@@ -137,6 +137,8 @@ struct Workspace {
   float* lh32 = nullptr;
   // tensor-core M2L A operand planes: [plane][box*R + r][dp] (BF16 or TF32)
   void* wa[kMaxLevel + 1] = {};
+  bool wa_grid[kMaxLevel + 1] = {};  // planes in the per-class grid layout (TMA M2L)
+  alignas(64) unsigned char tmap[kMaxLevel + 1][2][128] = {};  // CUtensorMap per plane
   float* m2l_part = nullptr;    // partial M2L sums of the split offset lists
   int* err = nullptr;           // device error word of bounded waits
   int* err_host = nullptr;      // pinned copy, read at the next call

@@ -20,6 +20,7 @@
 // the previous one; tcgen05.commit on an mbarrier releases a stage.  Every
 // wait is bounded: on time-out the kernel records an error code, drains its
 // copies, frees its TMEM and returns.
+#include <cuda.h>
 #include <stdlib.h>
 
 #include "internal.h"
@@ -327,6 +328,182 @@ k_m2l_tc(M2LTcArgs a) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)a.tmem_cols));
 }
 
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            int c3, int c4, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(mbar)
+      : "memory");
+}
+
+// TMA variant.  What is stored per parity class on a grid,
+// [plane][class][Z][Y][X*R + r][dp] with (X, Y, Z) = box coordinates / 2, so
+// the 128 source rows of a tile for one offset form a regular box of that
+// grid: one 5-D TMA tile load per plane brings them in, zero-filled outside
+// the cube.  Warp 4 produces (TMA for A, bulk copy for B), warp 5 issues the
+// MMAs, warps 0-3 drain the accumulators.
+template <bool TF32>
+__global__ void __launch_bounds__(192, 1)
+k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1, M2LTcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x;
+  const int esz = TF32 ? 4 : 2;
+  const int E = 128 / esz;
+  const int dp = a.dp;
+  const int S = a.stages;
+  const int nchunk = dp * esz / 128;
+  const uint32_t a_bytes = 16384u;
+  const uint32_t b_bytes = (uint32_t)dp * 128u;
+  const uint32_t stage = 2 * a_bytes + 2 * b_bytes;
+  uint64_t* bars = (uint64_t*)(smem + S * stage);
+  uint32_t* tslot = (uint32_t*)(bars + 2 * kMaxStages + 1);
+  const uint32_t sbase = smem_u32(smem);
+  auto full = [&](int st) { return smem_u32(&bars[st]); };
+  auto empty = [&](int st) { return smem_u32(&bars[kMaxStages + st]); };
+  const uint32_t done_bar = smem_u32(&bars[2 * kMaxStages]);
+
+  const int h = a.h, R = a.R;
+  const int bxr = a.bx * R;  // merged (x, r) rows of the tile
+  const int oct = blockIdx.x % 8;
+  const int grp = (blockIdx.x / 8) % a.groups;
+  int tile = blockIdx.x / (8 * a.groups);
+  const int ntx = (h * R + bxr - 1) / bxr, nty = (h + a.by - 1) / a.by;
+  const int tx = tile % ntx;
+  tile /= ntx;
+  const int ty = tile % nty, tz = tile / nty;
+  const int xr0 = tx * bxr, y0 = ty * a.by, z0 = tz * a.bz;
+  const int cx = oct & 1, cy = (oct >> 1) & 1, cz = (oct >> 2) & 1;
+  const int s_beg = grp * kListLen / a.groups, s_end = (grp + 1) * kListLen / a.groups;
+  const int* lst = a.slot_lists + oct * kListLen;
+
+  // the source block of an offset; empty when it misses the class grid
+  auto source = [&](int slot, int* sc, int* sxr, int* sy, int* sz) {
+    const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+    *sc = ((cx + dx) & 1) | (((cy + dy) & 1) << 1) | (((cz + dz) & 1) << 2);
+    *sxr = xr0 + ((cx + dx) >> 1) * R;
+    *sy = y0 + ((cy + dy) >> 1);
+    *sz = z0 + ((cz + dz) >> 1);
+    return *sxr < h * R && *sxr + bxr > 0 && *sy < h && *sy + a.by > 0 && *sz < h && *sz + a.bz > 0;
+  };
+
+  if (tid == 0) {
+    for (int i = 0; i < kMaxStages; ++i) {
+      mbar_init(full(i), 1);
+      mbar_init(empty(i), 1);
+    }
+    mbar_init(done_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (tid >= 128 && tid < 160) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"((uint32_t)a.tmem_cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  // number of active offsets (same count in every thread)
+  int nact = 0;
+  for (int s = s_beg; s < s_end; ++s) {
+    int sc, sxr, sy, sz;
+    nact += source(lst[s], &sc, &sxr, &sy, &sz) ? 1 : 0;
+  }
+  const int nit = nact * nchunk;
+  bool ok = true;
+
+  if (tid == 128) {
+    // -------------------------------------------------------- producer --
+    int it = 0;
+    for (int s = s_beg; s < s_end && ok; ++s) {
+      const int slot = lst[s];
+      int sc, sxr, sy, sz;
+      if (!source(slot, &sc, &sxr, &sy, &sz)) continue;
+      for (int c = 0; c < nchunk && ok; ++c, ++it) {
+        const int st = it % S, u = it / S;
+        if (it >= S && !mbar_wait(empty(st), (u - 1) & 1, a.err, 1)) {
+          ok = false;
+          break;
+        }
+        const uint32_t sA = sbase + st * stage;
+        mbar_expect_tx(full(st), 2 * a_bytes + 2 * b_bytes);
+        tma_load_5d(sA, &tA0, c * E, sxr, sy, sz, sc, full(st));
+        tma_load_5d(sA + a_bytes, &tA1, c * E, sxr, sy, sz, sc, full(st));
+        const char* src = (const char*)a.kd_img + (((size_t)slot * nchunk + c) * 2) * b_bytes;
+        bulk_g2s(sA + 2 * a_bytes, src, 2 * b_bytes, full(st));
+      }
+    }
+  } else if (tid == 160) {
+    // ----------------------------------------------------- MMA issuer --
+    const uint32_t id_lo = idesc(TF32 ? 2u : 1u, dp > 256 ? 256u : (uint32_t)dp);
+    const uint32_t id_hi = idesc(TF32 ? 2u : 1u, dp > 256 ? (uint32_t)(dp - 256) : 16u);
+    for (int it = 0; it < nit; ++it) {
+      const int st = it % S;
+      if (!mbar_wait(full(st), (it / S) & 1, a.err, 2)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t sA = sbase + st * stage;
+      const uint32_t sB = sA + 2 * a_bytes;
+      const int e = it / nchunk;
+      const uint32_t dacc = tmem + (uint32_t)((e % a.chains) * dp);
+      const bool first = e < a.chains && (it % nchunk) == 0;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+        for (int pr = 0; pr < 3; ++pr) {
+          const int pa = (pr == 2) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
+          const uint32_t acc = (!first || kk > 0 || pr > 0) ? 1u : 0u;
+          const uint64_t ad = sdesc(sA + pa * a_bytes + kk * 32);
+          const uint32_t bB = sB + pb * b_bytes + kk * 32;
+          mma<TF32>(dacc, ad, sdesc(bB), id_lo, acc);
+          if (dp > 256) mma<TF32>(dacc + 256, ad, sdesc(bB + 32 * 1024), id_hi, acc);
+        }
+      mma_commit(empty(st));
+    }
+    if (ok && nit >= 1) mma_commit(done_bar);
+  } else if (tid < 128) {
+    // --------------------------------------------------------- epilogue --
+    const int xr = xr0 + tid % bxr;
+    const int yy = y0 + (tid / bxr) % a.by;
+    const int zz = z0 + tid / (bxr * a.by);
+    const bool valid = xr < h * R && yy < h && zz < h;
+    const int x = valid ? xr / R : 0, r = valid ? xr % R : 0;
+    const int64_t I = valid ? morton_encode(2 * x + cx, 2 * (valid ? yy : 0) + cy, 2 * (valid ? zz : 0) + cz, a.level) : 0;
+    bool have = nit >= 1;
+    if (have) have = mbar_wait(done_bar, 0, a.err, 3);
+    have = __all_sync(0xffffffffu, have);
+    tc_fence_after();
+    float* out = a.out + (size_t)grp * a.part_stride + (size_t)(I * R + r) * dp;
+    const uint32_t lane_base = (uint32_t)((tid & ~31) << 16);
+    const int used = min(a.chains, nact);
+    for (int c0 = 0; c0 < dp; c0 += 16) {
+      float v[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      if (have)
+        for (int ch = 0; ch < used; ++ch) {
+          float t[16];
+          tmem_ld16(tmem + lane_base + (uint32_t)(ch * dp + c0), t);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] += t[i];
+        }
+      if (valid) {
+        float4* o4 = (float4*)(out + c0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (tid >= 128 && tid < 160)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)a.tmem_cols));
+}
+
 __global__ void k_sum_parts(const float4* __restrict__ parts, int groups, int64_t n4, int64_t stride4,
                             float4* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
@@ -369,6 +546,107 @@ int m2l_tc_groups(int64_t tiles8, int nsm, int dp) {
   int g = 1;
   while (g < 16 && (tiles8 * g < 2 * nsm || chains * g < gmin)) g *= 2;
   return g;
+}
+
+// Tile block of the grid layout for R right-hand sides (R a power of two <= 128):
+// bx boxes x R rhs along x, by along y, bz along z, 128 rows in all.
+bool m2l_tma_block(int R, int* bx, int* by, int* bz) {
+  if (R < 1 || R > 128 || (R & (R - 1))) return false;
+  *bx = R >= 8 ? 1 : 8 / R;
+  const int rem = 128 / (*bx * R);
+  *by = rem >= 4 ? 4 : rem;
+  *bz = rem / *by;
+  return true;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// Tensor map of one What plane in the grid layout of level `level`.
+eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, bool tf32) {
+  auto fn = encode_fn();
+  if (!fn) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return EIFMM_ECUDA;
+  }
+  int bx, by, bz;
+  if (!m2l_tma_block(R, &bx, &by, &bz)) {
+    set_error("no TMA tile shape for this number of right-hand sides");
+    return EIFMM_EUNSUPPORTED;
+  }
+  const int esz = tf32 ? 4 : 2;
+  const uint64_t h = (uint64_t)1 << (level - 1);
+  cuuint64_t dims[5] = {(cuuint64_t)dp, h * R, h, h, 8};
+  cuuint64_t strides[4] = {(cuuint64_t)dp * esz, h * R * dp * esz, h * h * R * dp * esz, h * h * h * R * dp * esz};
+  cuuint32_t box[5] = {(cuuint32_t)(128 / esz), (cuuint32_t)(bx * R), (cuuint32_t)by, (cuuint32_t)bz, 1};
+  cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = fn((CUtensorMap*)map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                        5, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_error("cuTensorMapEncodeTiled failed with code " + std::to_string((int)r));
+    return EIFMM_ECUDA;
+  }
+  return EIFMM_OK;
+}
+
+eifmm_status launch_m2l_tma(const M2LTcArgs& a0, const void* map0, const void* map1, bool tf32,
+                            cudaStream_t s) {
+  M2LTcArgs a = a0;
+  a.stages = m2l_tc_stages(a.dp);
+  a.chains = a.dp <= 128 ? 4 : (a.dp <= 256 ? 2 : 1);
+  a.tmem_cols = 512;
+  if (!m2l_tma_block(a.R, &a.bx, &a.by, &a.bz)) {
+    set_error("no TMA tile shape for this number of right-hand sides");
+    return EIFMM_EUNSUPPORTED;
+  }
+  a.h = 1 << (a.level - 1);
+  const size_t sm = m2l_tc_smem_bytes(a.dp, tf32);
+  static bool attr[2] = {false, false};
+  if (!attr[tf32]) {
+    if (tf32)
+      EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    else
+      EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr[tf32] = true;
+  }
+  const int bxr = a.bx * a.R;
+  const int64_t tiles = (int64_t)((a.h * a.R + bxr - 1) / bxr) * ((a.h + a.by - 1) / a.by) * ((a.h + a.bz - 1) / a.bz);
+  if (a.groups > 1) {
+    a.out = a.part;
+    a.part_stride = a.rows * (int64_t)a.dp;
+  } else {
+    a.out = a.g;
+    a.part_stride = 0;
+  }
+  const unsigned grid = (unsigned)(tiles * 8 * a.groups);
+  const CUtensorMap& m0 = *(const CUtensorMap*)map0;
+  const CUtensorMap& m1 = *(const CUtensorMap*)map1;
+  if (tf32) k_m2l_tma<true><<<grid, 192, sm, s>>>(m0, m1, a);
+  else k_m2l_tma<false><<<grid, 192, sm, s>>>(m0, m1, a);
+  EIFMM_CHECK_LAUNCH();
+  if (a.groups > 1) {
+    const int64_t n4 = a.rows * (int64_t)a.dp / 4;
+    k_sum_parts<<<(unsigned)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096), 256, 0, s>>>(
+        (const float4*)a.part, a.groups, n4, a.part_stride / 4, (float4*)a.g);
+    EIFMM_CHECK_LAUNCH();
+  }
+  return EIFMM_OK;
 }
 
 eifmm_status launch_m2l_tc(const M2LTcArgs& a0, bool tf32, cudaStream_t s) {

@@ -23,11 +23,19 @@ struct M2LTcArgs {
   int64_t part_stride = 0;
   int stages = 2;
   int chains = 1;        // accumulators in TMEM (round-robin over offsets)
+  int h = 0;             // TMA variant: boxes per axis per parity class
+  int bx = 0, by = 0, bz = 0;  // TMA variant: tile block
 };
 
 constexpr int kMaxDpTc = 320;
 size_t m2l_tc_smem_bytes(int dp, bool tf32);
 int m2l_tc_groups(int64_t tiles8, int nsm, int dp);
+bool m2l_tma_block(int R, int* bx, int* by, int* bz);
+// Tensor map (a 128-byte CUtensorMap, 64-byte aligned) of one What plane in
+// the per-class grid layout [class][Z][Y][X*R + r][dp].
+eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, bool tf32);
+eifmm_status launch_m2l_tma(const M2LTcArgs& a, const void* map0, const void* map1, bool tf32,
+                            cudaStream_t s);
 eifmm_status launch_m2l_tc(const M2LTcArgs& a, bool tf32, cudaStream_t s);
 
 }  // namespace eifmm

@@ -40,10 +40,25 @@ __device__ __forceinline__ float tf32_rn(float v) {
   return __uint_as_float(u);
 }
 
+// Destination row of vector v = box * R + r in the What planes: Morton order,
+// or (grid_level >= 0) the per-parity-class grid [class][Z][Y][X*R + r] of
+// that level read by the TMA M2L.
+__device__ __forceinline__ int64_t plane_row(int64_t v, int grid_level, int R) {
+  if (grid_level < 0) return v;
+  const int64_t box = v / R;
+  const int r = (int)(v - box * R);
+  int c[3];
+  morton_decode(box, grid_level, c);
+  const int64_t h = (int64_t)1 << (grid_level - 1);
+  const int cls = (int)(box & 7);
+  return ((((int64_t)cls * h + (c[2] >> 1)) * h + (c[1] >> 1)) * h + (c[0] >> 1)) * R + r;
+}
+
 template <typename T, bool FWD, bool DIAG, typename Ti, typename To, int PLANES>
 __global__ void __launch_bounds__(32 * kSolveWarps)
 k_tri_sweep(int d, const T* __restrict__ Mp, const Ti* __restrict__ in, int ldi,
-            To* __restrict__ out, int ldo, void* __restrict__ planes, int64_t nvec) {
+            To* __restrict__ out, int ldo, void* __restrict__ planes, int64_t nvec, int grid_level,
+            int R) {
   extern __shared__ unsigned char s_raw[];
   T* sM = (T*)s_raw;
   const int64_t np = (int64_t)d * (d + 1) / 2;
@@ -77,20 +92,21 @@ k_tri_sweep(int d, const T* __restrict__ Mp, const Ti* __restrict__ in, int ldi,
     if (PLANES == 0) {
       for (int j = lane; j < ldo; j += 32) out[v * ldo + j] = j < d ? (To)sv[j] : (To)0;
     } else {
+      const int64_t prow = plane_row(v, grid_level, R);
       for (int j = lane; j < ldo; j += 32) {
         const T x = j < d ? sv[j] : (T)0;
         if (PLANES == 1) {
           __nv_bfloat16* pl = (__nv_bfloat16*)planes;
           const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
           const __nv_bfloat16 lo = __float2bfloat16_rn((float)(x - (T)__bfloat162float(hi)));
-          pl[v * ldo + j] = hi;
-          pl[nvec * ldo + v * ldo + j] = lo;
+          pl[prow * ldo + j] = hi;
+          pl[nvec * ldo + prow * ldo + j] = lo;
         } else {
           float* pl = (float*)planes;
           const float hi = tf32_rn((float)x);
           const float lo = tf32_rn((float)(x - (T)hi));
-          pl[v * ldo + j] = hi;
-          pl[nvec * ldo + v * ldo + j] = lo;
+          pl[prow * ldo + j] = hi;
+          pl[nvec * ldo + prow * ldo + j] = lo;
         }
       }
     }
@@ -100,7 +116,8 @@ k_tri_sweep(int d, const T* __restrict__ Mp, const Ti* __restrict__ in, int ldi,
 
 template <typename T, bool FWD, bool DIAG, typename Ti, typename To, int PLANES>
 eifmm_status launch_tri_sweep(int d, const T* Mp, const Ti* in, int ldi, To* out, int ldo,
-                              void* planes, int64_t nvec, cudaStream_t s) {
+                              void* planes, int64_t nvec, cudaStream_t s, int grid_level = -1,
+                              int R = 1) {
   static bool attr = false;
   const size_t sm = solve_smem_bytes(d, sizeof(T));
   if (!attr) {
@@ -117,7 +134,7 @@ eifmm_status launch_tri_sweep(int d, const T* Mp, const Ti* in, int ldi, To* out
   int64_t blocks = (nvec + kSolveWarps - 1) / kSolveWarps;
   if (blocks > (int64_t)nsm * per_sm) blocks = (int64_t)nsm * per_sm;
   k_tri_sweep<T, FWD, DIAG, Ti, To, PLANES><<<(unsigned)blocks, 32 * kSolveWarps, sm, s>>>(
-      d, Mp, in, ldi, out, ldo, planes, nvec);
+      d, Mp, in, ldi, out, ldo, planes, nvec, grid_level, R);
   EIFMM_CHECK_LAUNCH();
   return EIFMM_OK;
 }

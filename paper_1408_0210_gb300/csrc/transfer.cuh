@@ -107,7 +107,7 @@ namespace eifmm {
 // Rows m in [d, ld) of every output column are written as zeros.
 // ---------------------------------------------------------------------------
 struct XferGemm {
-  int mode;          // 0 = M2M, 1 = L2L
+  int mode;          // 0 = M2M (child blockIdx.z, partial sums in P8), 1 = L2L
   int dk, ldk;       // output rank and leading dimension
   int dc, ldc;       // input rank and leading dimension (child for M2M, parent for L2L)
   int R;
@@ -116,6 +116,7 @@ struct XferGemm {
   const float* B;    // input coefficient rows
   const float* G;    // L2L: g of the output level (same layout as C)
   float* C;          // output coefficient rows
+  float* P8;         // M2M: [8][ncol][ldk] partial sums, one per child
 };
 
 static __global__ void __launch_bounds__(256) k_xfer_gemm(XferGemm a) {
@@ -125,8 +126,8 @@ static __global__ void __launch_bounds__(256) k_xfer_gemm(XferGemm a) {
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.x * 64;
   const int64_t c0 = (int64_t)blockIdx.y * 64;
-  const int i_l2l = blockIdx.z;
-  const int K = a.mode == 0 ? 8 * a.dc : a.dc;
+  const int i_l2l = blockIdx.z;  // the child octant (both modes)
+  const int K = a.dc;
   float acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
@@ -142,12 +143,7 @@ static __global__ void __launch_bounds__(256) k_xfer_gemm(XferGemm a) {
       const int m = m0 + rr;
       float av = 0.f;
       if (m < a.dk && k < K) {
-        if (a.mode == 0) {
-          const int i = k / a.dc, q = k - i * a.dc;
-          av = a.A[((int64_t)i * a.dk + m) * a.dc + q];
-        } else {
-          av = a.A[((int64_t)i_l2l * a.dk + m) * a.dc + k];
-        }
+        av = a.A[((int64_t)i_l2l * a.dk + m) * a.dc + k];
       }
       As[kk][rr] = av;
       // B(k, c)
@@ -156,12 +152,8 @@ static __global__ void __launch_bounds__(256) k_xfer_gemm(XferGemm a) {
       if (c < a.ncol && k < K) {
         const int64_t P = c / a.R;
         const int r = (int)(c - P * a.R);
-        if (a.mode == 0) {
-          const int i = k / a.dc, q = k - i * a.dc;
-          bv = a.B[((8 * P + i) * a.R + r) * a.ldc + q];
-        } else {
-          bv = a.B[(P * a.R + r) * a.ldc + k];
-        }
+        if (a.mode == 0) bv = a.B[((8 * P + i_l2l) * a.R + r) * a.ldc + k];
+        else bv = a.B[(P * a.R + r) * a.ldc + k];
       }
       Bs[kk][rr] = bv;
     }
@@ -192,17 +184,44 @@ static __global__ void __launch_bounds__(256) k_xfer_gemm(XferGemm a) {
       const int m = m0 + ty * 4 + u;
       if (m >= a.ldk) continue;
       const int64_t o = row * a.ldk + m;
-      float val = 0.f;
-      if (m < a.dk) val = a.mode == 0 ? acc[u][v] : a.G[o] + acc[u][v];
-      a.C[o] = val;
+      if (a.mode == 0) {
+        a.P8[(int64_t)i_l2l * a.ncol * a.ldk + o] = m < a.dk ? acc[u][v] : 0.f;
+      } else {
+        a.C[o] = m < a.dk ? a.G[o] + acc[u][v] : 0.f;
+      }
     }
   }
 }
 
+// W = sum over the 8 children of the partial sums, in a fixed order.
+static __global__ void k_sum8(const float4* __restrict__ p8, int64_t n4, float4* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+    float4 v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = p8[c * n4 + i];
+#pragma unroll
+    for (int w = 1; w < 8; w <<= 1)
+#pragma unroll
+      for (int c = 0; c < 8; c += 2 * w) {
+        v[c].x += v[c + w].x;
+        v[c].y += v[c + w].y;
+        v[c].z += v[c + w].z;
+        v[c].w += v[c + w].w;
+      }
+    out[i] = v[0];
+  }
+}
+
 inline eifmm_status launch_xfer_gemm(const XferGemm& a, cudaStream_t s) {
-  const dim3 grid((unsigned)((a.ldk + 63) / 64), (unsigned)((a.ncol + 63) / 64), a.mode == 0 ? 1 : 8);
+  const dim3 grid((unsigned)((a.ldk + 63) / 64), (unsigned)((a.ncol + 63) / 64), 8);
   k_xfer_gemm<<<grid, 256, 0, s>>>(a);
   EIFMM_CHECK_LAUNCH();
+  if (a.mode == 0) {
+    const int64_t n4 = a.ncol * a.ldk / 4;
+    k_sum8<<<(unsigned)((n4 + 255) / 256 < 8192 ? (n4 + 255) / 256 : 8192), 256, 0, s>>>(
+        (const float4*)a.P8, n4, (float4*)a.C);
+    EIFMM_CHECK_LAUNCH();
+  }
   return EIFMM_OK;
 }
 
