@@ -424,12 +424,6 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   }
   const bool tf32 = ops->tier == 1;
   const int kap = t->depth;
-  if (tf32)
-    for (int k = 2; k <= kap; ++k)
-      if (solve_smem_bytes(ops->lv[k].d, sizeof(double)) > 227 * 1024) {
-        set_error("eifmm_evaluate: tier 1 needs d <= 230 (FP64 triangle in shared memory)");
-        return EIFMM_EUNSUPPORTED;
-      }
   const int kern = (int)ops->kern;
   const PointSet& S = t->src;
   const PointSet& T = t->tgt;
@@ -459,28 +453,24 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     x.dk = a.d; x.ldk = a.dp; x.dc = c.d; x.ldc = c.dp; x.R = R;
     x.ncol = nboxes(k) * R;
     x.A = a.m2m32; x.B = ws.W32[k + 1]; x.G = nullptr; x.C = ws.W32[k];
-    x.P8 = (float*)ws.tmp;  // 8 x nboxes(k) x R x dp floats fit in the sweep scratch
+    x.P8 = (float*)ws.tmp;  // 8 x nboxes(k) x R x dp floats fit in the scratch
     EIFMM_TRY(launch_xfer_gemm(x, s));
   }
   record(ws, 2, s);
   // step 3: What = Delta W (Gamma z = W, then B^t What = z), written as the
   // two M2L operand planes
-  for (int k = 2; k <= kap; ++k) {
-    const LevelOps& v = ops->lv[k];
-    const int64_t nvec = nboxes(k) * R;
-    if (tf32) {
-      double* z = (double*)ws.tmp;
-      EIFMM_TRY((launch_tri_sweep<double, true, true, float, double, 0>(v.d, v.G_colp, ws.W32[k], v.dp, z,
-                                                                        v.d, nullptr, nvec, s)));
-      EIFMM_TRY((launch_tri_sweep<double, false, false, double, float, 2>(
-          v.d, v.B_rowp, z, v.d, nullptr, v.dp, ws.wa[k], nvec, s, ws.wa_grid[k] ? k : -1, R)));
-    } else {
-      float* z = (float*)ws.tmp;
-      EIFMM_TRY((launch_tri_sweep<float, true, true, float, float, 0>(v.d, v.G32_colp, ws.W32[k], v.dp, z,
-                                                                      v.d, nullptr, nvec, s)));
-      EIFMM_TRY((launch_tri_sweep<float, false, false, float, float, 1>(
-          v.d, v.B32_rowp, z, v.d, nullptr, v.dp, ws.wa[k], nvec, s, ws.wa_grid[k] ? k : -1, R)));
+  {
+    DeltaBatch b;
+    for (int k = 2; k <= kap; ++k) {
+      const LevelOps& v = ops->lv[k];
+      const int gl = ws.wa_grid[k] ? k : -1;
+      b.lv[b.nlev++] = tf32 ? delta_level(v.d, delta_ops64(v), false, ws.W32[k], v.dp, nullptr, v.dp, ws.wa[k],
+                                          nboxes(k) * R, gl, R)
+                            : delta_level(v.d, delta_ops32(v), false, ws.W32[k], v.dp, nullptr, v.dp, ws.wa[k],
+                                          nboxes(k) * R, gl, R);
     }
+    if (tf32) EIFMM_TRY((launch_delta_batch<double, float, float, 2>(b, false, s)));
+    else EIFMM_TRY((launch_delta_batch<float, float, float, 1>(b, false, s)));
   }
   record(ws, 3, s);
   // step 4
@@ -530,19 +520,16 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   record(ws, 5, s);
   // step 6: lhat = Delta^t l (B z = l, then Gamma^t lhat = z)
   {
-    const int64_t nvec = nboxes(kap) * R;
+    DeltaBatch b;
+    b.nlev = 1;
     if (tf32) {
-      double* z = (double*)ws.tmp;
-      EIFMM_TRY((launch_tri_sweep<double, true, false, float, double, 0>(vl.d, vl.B_colp, ws.l32[kap], vl.dp,
-                                                                         z, vl.d, nullptr, nvec, s)));
-      EIFMM_TRY((launch_tri_sweep<double, false, true, double, float, 0>(vl.d, vl.G_rowp, z, vl.d, ws.lh32,
-                                                                         vl.dp, nullptr, nvec, s)));
+      b.lv[0] = delta_level(vl.d, delta_ops64(vl), true, ws.l32[kap], vl.dp, ws.lh32, vl.dp, nullptr,
+                            nboxes(kap) * R);
+      EIFMM_TRY((launch_delta_batch<double, float, float, 0>(b, true, s)));
     } else {
-      float* z = (float*)ws.tmp;
-      EIFMM_TRY((launch_tri_sweep<float, true, false, float, float, 0>(vl.d, vl.B32_colp, ws.l32[kap], vl.dp,
-                                                                       z, vl.d, nullptr, nvec, s)));
-      EIFMM_TRY((launch_tri_sweep<float, false, true, float, float, 0>(vl.d, vl.G32_rowp, z, vl.d, ws.lh32,
-                                                                       vl.dp, nullptr, nvec, s)));
+      b.lv[0] = delta_level(vl.d, delta_ops32(vl), true, ws.l32[kap], vl.dp, ws.lh32, vl.dp, nullptr,
+                            nboxes(kap) * R);
+      EIFMM_TRY((launch_delta_batch<float, float, float, 0>(b, true, s)));
     }
   }
   record(ws, 6, s);

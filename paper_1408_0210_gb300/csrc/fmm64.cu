@@ -84,53 +84,6 @@ k_p2m64(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
 }
 
 
-// Steps 3 and 6: out = Delta in (transpose = 0) or Delta^t in (transpose = 1),
-// by forward and back substitution, one warp per vector.
-__global__ void __launch_bounds__(TPB)
-k_solve64(int d, int transpose, const double* __restrict__ G_cm,
-          const double* __restrict__ G_rm, const double* __restrict__ B_cm,
-          const double* __restrict__ B_rm, const double* __restrict__ in,
-          double* __restrict__ out, int64_t nvec) {
-  extern __shared__ double sv_all[];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t v = (int64_t)blockIdx.x * (TPB / 32) + w;
-  if (v >= nvec) return;
-  double* sv = sv_all + w * d;
-  for (int j = lane; j < d; j += 32) sv[j] = in[v * d + j];
-  __syncwarp();
-  if (!transpose) {
-    // Gamma z = v (Gamma lower): column k of Gamma updates the rows below.
-    for (int k = 0; k < d; ++k) {
-      const double zk = sv[k] / G_cm[(int64_t)k * d + k];
-      __syncwarp();
-      if (lane == 0) sv[k] = zk;
-      for (int j = k + 1 + lane; j < d; j += 32) sv[j] -= G_cm[(int64_t)k * d + j] * zk;
-      __syncwarp();
-    }
-    // B^t w = z (B^t upper unit): row k of B updates the entries above.
-    for (int k = d - 1; k >= 0; --k) {
-      const double wk = sv[k];
-      for (int j = lane; j < k; j += 32) sv[j] -= B_rm[(int64_t)k * d + j] * wk;
-      __syncwarp();
-    }
-  } else {
-    // B z = v (B lower unit)
-    for (int k = 0; k < d; ++k) {
-      const double zk = sv[k];
-      for (int j = k + 1 + lane; j < d; j += 32) sv[j] -= B_cm[(int64_t)k * d + j] * zk;
-      __syncwarp();
-    }
-    // Gamma^t w = z (Gamma^t upper)
-    for (int k = d - 1; k >= 0; --k) {
-      const double wk = sv[k] / G_rm[(int64_t)k * d + k];
-      __syncwarp();
-      if (lane == 0) sv[k] = wk;
-      for (int j = lane; j < k; j += 32) sv[j] -= G_rm[(int64_t)k * d + j] * wk;
-      __syncwarp();
-    }
-  }
-  for (int j = lane; j < d; j += 32) out[v * d + j] = sv[j];
-}
 
 // Step 4: g^I = sum_{J in I(I)} K^delta What^J.  A block owns 8 target boxes
 // of one parity class (same octant, 8 consecutive parents): they share the
@@ -368,28 +321,6 @@ eifmm_status launch_p2p64(const Tree* t, int kern, const double* sig, int R, dou
   return EIFMM_OK;
 }
 
-eifmm_status launch_solve64(const LevelOps& v, int transpose, const double* in, double* out,
-                            int64_t nvec, cudaStream_t s, double* tmp) {
-  if (tmp && solve_smem_bytes(v.d, sizeof(double)) <= 227 * 1024) {
-    if (!transpose) {
-      EIFMM_TRY((launch_tri_sweep<double, true, true, double, double, 0>(v.d, v.G_colp, in, v.d, tmp, v.d,
-                                                                         nullptr, nvec, s)));
-      EIFMM_TRY((launch_tri_sweep<double, false, false, double, double, 0>(v.d, v.B_rowp, tmp, v.d, out,
-                                                                           v.d, nullptr, nvec, s)));
-    } else {
-      EIFMM_TRY((launch_tri_sweep<double, true, false, double, double, 0>(v.d, v.B_colp, in, v.d, tmp, v.d,
-                                                                          nullptr, nvec, s)));
-      EIFMM_TRY((launch_tri_sweep<double, false, true, double, double, 0>(v.d, v.G_rowp, tmp, v.d, out,
-                                                                          v.d, nullptr, nvec, s)));
-    }
-    return EIFMM_OK;
-  }
-  const size_t sm = (size_t)(TPB / 32) * v.d * sizeof(double);
-  k_solve64<<<(unsigned)((nvec + TPB / 32 - 1) / (TPB / 32)), TPB, sm, s>>>(
-      v.d, transpose, v.G_cm, v.G_rm, v.B_cm, v.B_rm, in, out, nvec);
-  EIFMM_CHECK_LAUNCH();
-  return EIFMM_OK;
-}
 
 static void record(Workspace& ws, int i, cudaStream_t s) {
   if (timing_enabled()) cudaEventRecord(ws.ev_t[i], s);
@@ -437,9 +368,13 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
   }
   record(ws, 2, s);
   // step 3
-  for (int k = 2; k <= kap; ++k)
-    EIFMM_TRY(launch_solve64(ops->lv[k], 0, ws.W[k], ws.Wh[k], ((int64_t)1 << (3 * k)) * R, s,
-                             (double*)ws.tmp));
+  {
+    DeltaBatch b;
+    for (int k = 2; k <= kap; ++k)
+      b.lv[b.nlev++] = delta_level(ops->lv[k].d, delta_ops64(ops->lv[k]), false, ws.W[k], ops->lv[k].d,
+                                   ws.Wh[k], ops->lv[k].d, nullptr, ((int64_t)1 << (3 * k)) * R);
+    EIFMM_TRY((launch_delta_batch<double, double, double, 0>(b, false, s)));
+  }
   record(ws, 3, s);
   // step 4
   for (int k = 2; k <= kap; ++k) {
@@ -462,7 +397,13 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
   }
   record(ws, 5, s);
   // step 6
-  EIFMM_TRY(launch_solve64(vl, 1, ws.l[kap], ws.lh, ((int64_t)1 << (3 * kap)) * R, s, (double*)ws.tmp));
+  {
+    DeltaBatch b;
+    b.nlev = 1;
+    b.lv[0] = delta_level(vl.d, delta_ops64(vl), true, ws.l[kap], vl.d, ws.lh, vl.d, nullptr,
+                          ((int64_t)1 << (3 * kap)) * R);
+    EIFMM_TRY((launch_delta_batch<double, double, double, 0>(b, true, s)));
+  }
   record(ws, 6, s);
   // step 7 + near field + un-permute
   EIFMM_CUDA(cudaStreamWaitEvent(s, ws.ev_join, 0));

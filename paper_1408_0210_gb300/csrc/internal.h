@@ -59,9 +59,7 @@ struct LevelOps {
   double* X = nullptr;     // d x 3, x_m^{I_0^k}
   double* Y = nullptr;     // d x 3, y_l^{J_0^k}
   double* G_rm = nullptr;  // Gamma row-major
-  double* G_cm = nullptr;  // Gamma column-major
   double* B_rm = nullptr;  // B row-major
-  double* B_cm = nullptr;  // B column-major
   double* m2mT = nullptr;  // [8][q < d_{k+1}][m < d]: (K_M2M^i)^t, levels 2..depth-1
   double* l2lT = nullptr;  // [8][q' < d_{k-1}][m' < d]: (K_L2L^i)^t, levels 3..depth
   double* kdT = nullptr;   // [343][l < d][m' < d]: K^delta_{m'l}
@@ -69,22 +67,16 @@ struct LevelOps {
   double* l2l = nullptr;   // [8][m' < d][q' < d_{k-1}]: K_L2L^i row-major
   float* m2m32 = nullptr;
   float* l2l32 = nullptr;
-  // packed triangles for the shared-memory sweeps (solve.cuh)
-  double* G_colp = nullptr;
-  double* G_rowp = nullptr;
-  double* B_colp = nullptr;
-  double* B_rowp = nullptr;
-  float* G32_colp = nullptr;
-  float* G32_rowp = nullptr;
-  float* B32_colp = nullptr;
-  float* B32_rowp = nullptr;
+  // Delta and Delta^t as tiled triangular solves (solve.cuh): tiles [0]
+  // Gamma, [1] B^t reversed, [2] B, [3] Gamma^t reversed; pivots [0] of
+  // Gamma, [1] of Gamma^t reversed (FP64: the pivots, FP32: reciprocals)
+  double* dt64[4] = {};
+  float* dt32[4] = {};
+  double* piv64[2] = {};
+  float* piv32[2] = {};
   // reduced-precision copies
   float* m2mT32 = nullptr;
   float* l2lT32 = nullptr;
-  float* G32_cm = nullptr;
-  float* G32_rm = nullptr;
-  float* B32_cm = nullptr;
-  float* B32_rm = nullptr;
   float* X32 = nullptr;    // d x 3
   // M2L operands of the tensor-core kernel: K^delta split in two planes
   // (hi, lo) in the K-major 128B-swizzled layout,

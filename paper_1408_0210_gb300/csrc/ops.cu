@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "solve.cuh"
 
 namespace eifmm {
 namespace {
@@ -107,17 +108,37 @@ __global__ void k_build_kd(int kern, int d, double lk, const double* __restrict_
   }
 }
 
-// packed triangles: colp[k*d - k(k-1)/2 + (j-k)] = M[j][k] (j >= k),
-// rowp[k(k+1)/2 + j] = M[k][j] (j <= k).
-__global__ void k_pack_tri(const double* __restrict__ M, int d, double* __restrict__ colp,
-                           double* __restrict__ rowp) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= d * d) return;
-  const int i = t / d, j = t - i * d;  // M[i][j]
-  if (j <= i) {
-    colp[(int64_t)j * d - (int64_t)j * (j - 1) / 2 + (i - j)] = M[t];
-    rowp[(int64_t)i * (i + 1) / 2 + j] = M[t];
+// Tiles of one lower-triangular solve operator L' (layout in solve.cuh):
+// L'[a][b] = M[p][q] with (p, q) = (a, b), or (dpad-1-a, dpad-1-b) when
+// `rev`; `transpose` reads M[q][p].  Entries beyond d are those of the
+// identity; entries above the diagonal are zero.
+__global__ void k_build_delta_tiles(const double* __restrict__ M, int d, int nb, int transpose, int rev,
+                                    double* __restrict__ t64, float* __restrict__ t32,
+                                    double* __restrict__ piv64, float* __restrict__ piv32) {
+  const int dpad = nb * 32;
+  const int64_t n = (int64_t)nb * (nb + 1) / 2 * 1024;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int tile = (int)(e >> 10), J = 0;
+    while (tile > J) { tile -= J + 1; ++J; }
+    const int K = tile, k = (int)((e >> 5) & 31), i = (int)(e & 31);
+    const int a = J * 32 + i, b = K * 32 + k;
+    double v = 0.0;
+    if (b <= a) {
+      const int p = rev ? dpad - 1 - a : a, q = rev ? dpad - 1 - b : b;
+      if (p < d && q < d) v = transpose ? M[(int64_t)q * d + p] : M[(int64_t)p * d + q];
+      else v = p == q ? 1.0 : 0.0;
+    }
+    t64[e] = v;
+    t32[e] = (float)v;
   }
+  if (piv64 != nullptr)
+    for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < dpad; a += gridDim.x * blockDim.x) {
+      const int p = rev ? dpad - 1 - a : a;
+      const double g = p < d ? M[(int64_t)p * d + p] : 1.0;
+      piv64[a] = g;
+      piv32[a] = (float)(1.0 / g);
+    }
 }
 
 __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
@@ -125,12 +146,6 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, in
     b[i] = (float)a[i];
 }
 
-__global__ void k_transpose(const double* __restrict__ a, double* __restrict__ b, int d) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= d * d) return;
-  const int i = t / d, j = t - i * d;
-  b[j * d + i] = a[t];
-}
 
 eifmm_status to_f32(const double* a, float** b, int64_t n, cudaStream_t s) {
   EIFMM_TRY(dalloc(b, n > 0 ? n : 1));
@@ -146,17 +161,6 @@ eifmm_status to_f32(const double* a, float** b, int64_t n, cudaStream_t s) {
 eifmm_status assemble_ops(Ops* ops, cudaStream_t s) {
   const int depth = ops->depth;
   const int kern = (int)ops->kern;
-  // column-major copies of Gamma and B
-  for (int k = 2; k <= depth; ++k) {
-    LevelOps& v = ops->lv[k];
-    const int d = v.d;
-    EIFMM_TRY(dalloc(&v.G_cm, (size_t)d * d));
-    EIFMM_TRY(dalloc(&v.B_cm, (size_t)d * d));
-    k_transpose<<<(d * d + 255) / 256, 256, 0, s>>>(v.G_rm, v.G_cm, d);
-    EIFMM_CHECK_LAUNCH();
-    k_transpose<<<(d * d + 255) / 256, 256, 0, s>>>(v.B_rm, v.B_cm, d);
-    EIFMM_CHECK_LAUNCH();
-  }
   double* scratch = nullptr;
   EIFMM_TRY(dalloc(&scratch, (size_t)8 * kMaxD * kMaxD));
   for (int k = 2; k <= depth; ++k) {
@@ -186,24 +190,24 @@ eifmm_status assemble_ops(Ops* ops, cudaStream_t s) {
     k_build_kd<<<dim3((v.d * v.d + 255) / 256 < 64 ? (v.d * v.d + 255) / 256 : 64, kNumSlots), 256, 0, s>>>(
         kern, v.d, lk, v.Y, v.kdT);
     EIFMM_CHECK_LAUNCH();
-    EIFMM_TRY(to_f32(v.G_cm, &v.G32_cm, (int64_t)v.d * v.d, s));
-    EIFMM_TRY(to_f32(v.G_rm, &v.G32_rm, (int64_t)v.d * v.d, s));
-    EIFMM_TRY(to_f32(v.B_cm, &v.B32_cm, (int64_t)v.d * v.d, s));
-    EIFMM_TRY(to_f32(v.B_rm, &v.B32_rm, (int64_t)v.d * v.d, s));
     EIFMM_TRY(to_f32(v.X, &v.X32, (int64_t)3 * v.d, s));
-    const int64_t np = (int64_t)v.d * (v.d + 1) / 2;
-    EIFMM_TRY(dalloc(&v.G_colp, np));
-    EIFMM_TRY(dalloc(&v.G_rowp, np));
-    EIFMM_TRY(dalloc(&v.B_colp, np));
-    EIFMM_TRY(dalloc(&v.B_rowp, np));
-    k_pack_tri<<<(v.d * v.d + 255) / 256, 256, 0, s>>>(v.G_rm, v.d, v.G_colp, v.G_rowp);
-    EIFMM_CHECK_LAUNCH();
-    k_pack_tri<<<(v.d * v.d + 255) / 256, 256, 0, s>>>(v.B_rm, v.d, v.B_colp, v.B_rowp);
-    EIFMM_CHECK_LAUNCH();
-    EIFMM_TRY(to_f32(v.G_colp, &v.G32_colp, np, s));
-    EIFMM_TRY(to_f32(v.G_rowp, &v.G32_rowp, np, s));
-    EIFMM_TRY(to_f32(v.B_colp, &v.B32_colp, np, s));
-    EIFMM_TRY(to_f32(v.B_rowp, &v.B32_rowp, np, s));
+    // Delta: Gamma then B^t; Delta^t: B then Gamma^t (reversed order)
+    const int nb = (v.d + 31) / 32;
+    const int64_t nt = delta_tiles_elems(v.d);
+    const double* src[4] = {v.G_rm, v.B_rm, v.B_rm, v.G_rm};
+    const int trans[4] = {0, 1, 0, 1}, rev[4] = {0, 1, 0, 1}, piv[4] = {0, -1, -1, 1};
+    for (int o = 0; o < 4; ++o) {
+      EIFMM_TRY(dalloc(&v.dt64[o], nt));
+      EIFMM_TRY(dalloc(&v.dt32[o], nt));
+      if (piv[o] >= 0) {
+        EIFMM_TRY(dalloc(&v.piv64[piv[o]], nb * 32));
+        EIFMM_TRY(dalloc(&v.piv32[piv[o]], nb * 32));
+      }
+      k_build_delta_tiles<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(
+          src[o], v.d, nb, trans[o], rev[o], v.dt64[o], v.dt32[o], piv[o] >= 0 ? v.piv64[piv[o]] : nullptr,
+          piv[o] >= 0 ? v.piv32[piv[o]] : nullptr);
+      EIFMM_CHECK_LAUNCH();
+    }
   }
   // slot lists of the 8 parity classes: offsets o in {-2..3} for an even
   // coordinate and {-3..2} for an odd one, minus the 27 neighbours.
@@ -229,12 +233,12 @@ eifmm_status assemble_ops(Ops* ops, cudaStream_t s) {
 void free_ops(Ops* ops) {
   for (int k = 0; k <= kMaxLevel; ++k) {
     LevelOps& v = ops->lv[k];
-    dfree(v.X); dfree(v.Y); dfree(v.G_rm); dfree(v.G_cm); dfree(v.B_rm); dfree(v.B_cm);
+    dfree(v.X); dfree(v.Y); dfree(v.G_rm); dfree(v.B_rm);
     dfree(v.m2mT); dfree(v.l2lT); dfree(v.kdT); dfree(v.m2mT32); dfree(v.l2lT32);
     dfree(v.m2m); dfree(v.l2l); dfree(v.m2m32); dfree(v.l2l32);
-    dfree(v.G_colp); dfree(v.G_rowp); dfree(v.B_colp); dfree(v.B_rowp);
-    dfree(v.G32_colp); dfree(v.G32_rowp); dfree(v.B32_colp); dfree(v.B32_rowp);
-    dfree(v.G32_cm); dfree(v.G32_rm); dfree(v.B32_cm); dfree(v.B32_rm); dfree(v.X32);
+    for (int o = 0; o < 4; ++o) { dfree(v.dt64[o]); dfree(v.dt32[o]); }
+    for (int o = 0; o < 2; ++o) { dfree(v.piv64[o]); dfree(v.piv32[o]); }
+    dfree(v.X32);
     dfree(v.kd_img);
     v = LevelOps();
   }

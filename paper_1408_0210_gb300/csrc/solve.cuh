@@ -1,39 +1,44 @@
 // solve.cuh -- the Delta applications of Algorithm 3 (steps 3 and 6) as two
-// triangular sweeps (Section 4.1: Delta = B^-t Gamma^-1 applied by solving
+// triangular solves (Section 4.1: Delta = B^-t Gamma^-1 is applied by solving
 // with Gamma and with B^t rather than through an explicit inverse).
 //
-//   Delta v   : Gamma z = v (forward, columns of Gamma), B^t w = z (backward,
-//               rows of B)
-//   Delta^t v : B z = v (forward, columns of B), Gamma^t w = z (backward, rows
-//               of Gamma)
+//   Delta v   : Gamma z = v (lower, forward), B^t w = z (upper, backward)
+//   Delta^t v : B z = v (lower, forward),     Gamma^t w = z (upper, backward)
 //
-// One sweep per launch: the packed triangle of one matrix (d(d+1)/2 entries)
-// is staged once in shared memory and reused by every warp of the CTA; each
-// warp runs the substitution of one vector at a time (lanes own strided
-// entries, one __syncwarp per column), grid-striding over the vectors.
+// Both solves of one application run in one kernel.  A warp owns 32 vectors,
+// one per lane, kept transposed in shared memory ([entry][lane], row stride
+// 33 so both the transposing copy and the lane-wise access are free of bank
+// conflicts).  Each solve walks 32-row blocks (blocked left-looking
+// substitution): the block's 32 entries of the lane's vector sit in
+// registers, every earlier block contributes a dense 32 x 32 tile product
+// (32 FMAs per lane for each solved entry read back from shared memory), and
+// the diagonal 32 x 32 block is solved in registers.  The tile entries are
+// warp-uniform broadcast loads, so there is no synchronisation inside a
+// solve: the cost is the d^2/2 FMAs per vector and solve.
+//
+// The backward (upper) solve is run as a forward solve in reversed entry
+// order: with p(a) = dpad-1-a, U w = z becomes L' w' = z' with
+// L'[a][b] = U[p(a)][p(b)] lower triangular; the host stores L' tiles and
+// the kernel maps logical to physical entries.
 #pragma once
+#include <type_traits>
+
 #include "internal.h"
 
 namespace eifmm {
 
-constexpr int kSolveWarps = 8;
+constexpr int kDeltaTile = 32;
+constexpr int kDeltaLd = 33;       // shared row stride (floats or doubles)
+constexpr int kDeltaMaxWarps = 4;  // warps per CTA
 
-// Packed layouts (diagonal always stored; ignored for the unit B):
-//   column-packed: column k holds rows k..d-1 at offset k*d - k*(k-1)/2
-//   row-packed:    row k holds columns 0..k at offset k*(k+1)/2
-__host__ __device__ inline int64_t colp_off(int k, int d) { return (int64_t)k * d - (int64_t)k * (k - 1) / 2; }
-__host__ __device__ inline int64_t rowp_off(int k) { return (int64_t)k * (k + 1) / 2; }
-
-inline size_t solve_smem_bytes(int d, size_t elem) {
-  return ((size_t)d * (d + 1) / 2 + (size_t)kSolveWarps * d) * elem;
+// Tiles of one solve: tile (J, K), K <= J, at (J(J+1)/2 + K) * 1024, entry
+// [k][i] = L'[32J + i][32K + k]; the diagonal tiles are zero above the
+// diagonal.  Pivots: FP32 stores 1/L'[a][a], FP64 stores L'[a][a].
+inline int64_t delta_tiles_elems(int d) {
+  const int nb = (d + kDeltaTile - 1) / kDeltaTile;
+  return (int64_t)nb * (nb + 1) / 2 * kDeltaTile * kDeltaTile;
 }
 
-// FWD: for k = 0..d-1: z_k = v_k (/ M_kk if DIAG); v_j -= M_jk z_k, j > k.
-// BWD: for k = d-1..0: w_k = v_k (/ M_kk if DIAG); v_j -= M_kj w_k, j < k.
-// Input `in` (element type Ti, row stride ldi), output `out` (To, ldo): the
-// entries d..ldo-1 of each output row are written as zeros.  When PLANES is
-// 1 or 2 the result is written as the two M2L operand planes (BF16 or TF32
-// hi + lo) of `planes` instead.
 __device__ __forceinline__ float tf32_rn(float v) {
   uint32_t u = __float_as_uint(v);
   u = (u + 0x1000u) & ~0x1FFFu;
@@ -54,55 +59,168 @@ __device__ __forceinline__ int64_t plane_row(int64_t v, int grid_level, int R) {
   return ((((int64_t)cls * h + (c[2] >> 1)) * h + (c[1] >> 1)) * h + (c[0] >> 1)) * R + r;
 }
 
-template <typename T, bool FWD, bool DIAG, typename Ti, typename To, int PLANES>
-__global__ void __launch_bounds__(32 * kSolveWarps)
-k_tri_sweep(int d, const T* __restrict__ Mp, const Ti* __restrict__ in, int ldi,
-            To* __restrict__ out, int ldo, void* __restrict__ planes, int64_t nvec, int grid_level,
-            int R) {
-  extern __shared__ unsigned char s_raw[];
-  T* sM = (T*)s_raw;
-  const int64_t np = (int64_t)d * (d + 1) / 2;
-  for (int64_t t = threadIdx.x; t < np; t += blockDim.x) sM[t] = Mp[t];
-  __syncthreads();
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* sv = sM + np + (int64_t)w * d;
-  for (int64_t v = (int64_t)blockIdx.x * kSolveWarps + w; v < nvec;
-       v += (int64_t)gridDim.x * kSolveWarps) {
-    for (int j = lane; j < d; j += 32) sv[j] = (T)in[v * ldi + j];
-    __syncwarp();
-    if (FWD) {
-      for (int k = 0; k < d; ++k) {
-        const T* col = sM + colp_off(k, d);  // col[j - k] = M_jk
-        const T zk = DIAG ? sv[k] / col[0] : sv[k];
-        __syncwarp();
-        if (DIAG && lane == 0) sv[k] = zk;
-        for (int j = k + 1 + lane; j < d; j += 32) sv[j] -= col[j - k] * zk;
-        __syncwarp();
-      }
-    } else {
-      for (int k = d - 1; k >= 0; --k) {
-        const T* row = sM + rowp_off(k);  // row[j] = M_kj
-        const T wk = DIAG ? sv[k] / row[k] : sv[k];
-        __syncwarp();
-        if (DIAG && lane == 0) sv[k] = wk;
-        for (int j = lane; j < k; j += 32) sv[j] -= row[j] * wk;
-        __syncwarp();
+// acc[i] -= col[i] * z for the 32 rows of one tile column (16-byte loads of
+// a warp-uniform address: shared memory when SH, else global through L1).
+template <bool SH>
+__device__ __forceinline__ void tile_col_update(float (&acc)[kDeltaTile], const float* __restrict__ col,
+                                                float z) {
+#pragma unroll
+  for (int q = 0; q < kDeltaTile / 4; ++q) {
+    const float4 m = SH ? reinterpret_cast<const float4*>(col)[q] : __ldg(reinterpret_cast<const float4*>(col) + q);
+    acc[4 * q + 0] -= m.x * z;
+    acc[4 * q + 1] -= m.y * z;
+    acc[4 * q + 2] -= m.z * z;
+    acc[4 * q + 3] -= m.w * z;
+  }
+}
+template <bool SH>
+__device__ __forceinline__ void tile_col_update(double (&acc)[kDeltaTile], const double* __restrict__ col,
+                                                double z) {
+#pragma unroll
+  for (int q = 0; q < kDeltaTile / 2; ++q) {
+    const double2 m =
+        SH ? reinterpret_cast<const double2*>(col)[q] : __ldg(reinterpret_cast<const double2*>(col) + q);
+    acc[2 * q + 0] -= m.x * z;
+    acc[2 * q + 1] -= m.y * z;
+  }
+}
+
+template <bool SH, typename T>
+__device__ __forceinline__ T tile_ld(const T* p) {
+  return SH ? *p : __ldg(p);
+}
+
+__device__ __forceinline__ float apply_pivot(float v, float rp) { return v * rp; }
+__device__ __forceinline__ double apply_pivot(double v, double p) { return v / p; }
+
+// One forward solve L' x = v over the warp's 32 vectors held in sz (physical
+// entry e of lane l at sz[e * 33 + l]); REV maps logical entry a to physical
+// dpad-1-a.  The solution overwrites sz.
+template <typename T, bool DIAG, bool REV, bool SH>
+__device__ __forceinline__ void tiled_solve(T* __restrict__ sz, int nb, const T* __restrict__ tiles,
+                                            const T* __restrict__ piv, int lane) {
+  constexpr int TL = kDeltaTile;
+  for (int J = 0; J < nb; ++J) {
+    const int pj = REV ? nb - 1 - J : J;
+    T acc[TL];
+#pragma unroll
+    for (int i = 0; i < TL; ++i) acc[i] = sz[(pj * TL + (REV ? TL - 1 - i : i)) * kDeltaLd + lane];
+    const T* tJ = tiles + (int64_t)(J * (J + 1) / 2) * TL * TL;
+    for (int K = 0; K < J; ++K) {
+      const T* tk = tJ + (int64_t)K * TL * TL;
+      const T* zK = sz + (REV ? (nb - 1 - K) * TL + TL - 1 : K * TL) * kDeltaLd + lane;
+#pragma unroll 4
+      for (int k = 0; k < TL; ++k) {
+        const T zk = zK[(REV ? -k : k) * kDeltaLd];
+        tile_col_update<SH>(acc, tk + k * TL, zk);
       }
     }
+    const T* td = tJ + (int64_t)J * TL * TL;
+#pragma unroll
+    for (int k = 0; k < TL; ++k) {
+      const T zk = DIAG ? apply_pivot(acc[k], __ldg(piv + J * TL + k)) : acc[k];
+      acc[k] = zk;
+#pragma unroll
+      for (int i = k + 1; i < TL; ++i) acc[i] -= tile_ld<SH>(td + k * TL + i) * zk;
+    }
+#pragma unroll
+    for (int i = 0; i < TL; ++i) sz[(pj * TL + (REV ? TL - 1 - i : i)) * kDeltaLd + lane] = acc[i];
+  }
+}
+
+// One level of a batched application: vectors `in` (row v at v * ldi, d
+// entries) -> rows of `out` (ldo; entries d..ldo-1 written as zeros) or the
+// two M2L operand planes at plane_row(v).  Blocks block0.. serve this level.
+struct DeltaLevel {
+  const void* t1 = nullptr;  // tiles and pivots of the first solve
+  const void* p1 = nullptr;
+  const void* t2 = nullptr;  // and of the second (reversed) solve
+  const void* p2 = nullptr;
+  const void* in = nullptr;
+  void* out = nullptr;
+  void* planes = nullptr;
+  int64_t nvec = 0;
+  int d = 0, nb = 0, ldi = 0, ldo = 0, grid_level = -1, R = 1;
+  int block0 = 0;
+};
+struct DeltaBatch {
+  DeltaLevel lv[kMaxLevel + 1];
+  int nlev = 0;
+};
+
+__device__ __forceinline__ void copy_tiles(void* dst, const void* src, int64_t bytes) {
+  const int4* s4 = (const int4*)src;
+  int4* d4 = (int4*)dst;
+  for (int64_t i = threadIdx.x; i < bytes / 16; i += blockDim.x) d4[i] = __ldg(s4 + i);
+}
+
+// out = M2^-1 M1^-1 in, both solves in one pass over the vectors.  SH: the
+// tiles of the running solve are staged in shared memory (one copy per CTA,
+// read by all its warps); otherwise they are read through L1.
+template <typename T, bool DIAG1, bool DIAG2, typename Ti, typename To, int PLANES, bool SH>
+__global__ void __launch_bounds__(32 * kDeltaMaxWarps)
+k_delta(const __grid_constant__ DeltaBatch b) {
+  extern __shared__ __align__(16) unsigned char s_raw[];
+  int li = 0;
+  while (li + 1 < b.nlev && (int)blockIdx.x >= b.lv[li + 1].block0) ++li;
+  const DeltaLevel& L = b.lv[li];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nb = L.nb, d = L.d;
+  const int dpad = nb * kDeltaTile;
+  const int64_t tile_elems = (int64_t)nb * (nb + 1) / 2 * kDeltaTile * kDeltaTile;
+  T* s_tiles = reinterpret_cast<T*>(s_raw);
+  T* sz = s_tiles + (SH ? tile_elems : 0) + (int64_t)w * dpad * kDeltaLd;
+  const int64_t v0 = ((int64_t)(blockIdx.x - L.block0) * (blockDim.x >> 5) + w) * 32;
+  const int64_t nvec = L.nvec;
+  const bool live = v0 < nvec;
+  const Ti* in = (const Ti*)L.in;
+  if (live) {
+    // transposing load: row v0+vv -> column vv
+    for (int vv = 0; vv < 32; ++vv) {
+      const int64_t v = v0 + vv;
+      const Ti* row = in + v * L.ldi;
+      for (int j = lane; j < dpad; j += 32)
+        sz[j * kDeltaLd + vv] = (v < nvec && j < d) ? (T)row[j] : (T)0;
+    }
+  }
+  const T* t1 = (const T*)L.t1;
+  const T* t2 = (const T*)L.t2;
+  if (SH) {
+    copy_tiles(s_tiles, t1, tile_elems * (int64_t)sizeof(T));
+    __syncthreads();
+    t1 = s_tiles;
+  } else {
+    __syncwarp();
+  }
+  if (live) tiled_solve<T, DIAG1, false, SH>(sz, nb, t1, (const T*)L.p1, lane);
+  if (SH) {
+    __syncthreads();
+    copy_tiles(s_tiles, t2, tile_elems * (int64_t)sizeof(T));
+    __syncthreads();
+    t2 = s_tiles;
+  }
+  if (!live) return;
+  tiled_solve<T, DIAG2, true, SH>(sz, nb, t2, (const T*)L.p2, lane);
+  __syncwarp();
+  To* out = (To*)L.out;
+  const int ldo = L.ldo;
+  for (int vv = 0; vv < 32; ++vv) {
+    const int64_t v = v0 + vv;
+    if (v >= nvec) break;
     if (PLANES == 0) {
-      for (int j = lane; j < ldo; j += 32) out[v * ldo + j] = j < d ? (To)sv[j] : (To)0;
+      for (int j = lane; j < ldo; j += 32) out[v * ldo + j] = j < d ? (To)sz[j * kDeltaLd + vv] : (To)0;
     } else {
-      const int64_t prow = plane_row(v, grid_level, R);
+      const int64_t prow = plane_row(v, L.grid_level, L.R);
       for (int j = lane; j < ldo; j += 32) {
-        const T x = j < d ? sv[j] : (T)0;
+        const T x = j < d ? sz[j * kDeltaLd + vv] : (T)0;
         if (PLANES == 1) {
-          __nv_bfloat16* pl = (__nv_bfloat16*)planes;
+          __nv_bfloat16* pl = (__nv_bfloat16*)L.planes;
           const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
           const __nv_bfloat16 lo = __float2bfloat16_rn((float)(x - (T)__bfloat162float(hi)));
           pl[prow * ldo + j] = hi;
           pl[nvec * ldo + prow * ldo + j] = lo;
         } else {
-          float* pl = (float*)planes;
+          float* pl = (float*)L.planes;
           const float hi = tf32_rn((float)x);
           const float lo = tf32_rn((float)(x - (T)hi));
           pl[prow * ldo + j] = hi;
@@ -110,33 +228,81 @@ k_tri_sweep(int d, const T* __restrict__ Mp, const Ti* __restrict__ in, int ldi,
         }
       }
     }
-    __syncwarp();
   }
 }
 
-template <typename T, bool FWD, bool DIAG, typename Ti, typename To, int PLANES>
-eifmm_status launch_tri_sweep(int d, const T* Mp, const Ti* in, int ldi, To* out, int ldo,
-                              void* planes, int64_t nvec, cudaStream_t s, int grid_level = -1,
-                              int R = 1) {
+// Tiled operands of one level in precision T: [0] Gamma, [1] B^t reversed
+// (Delta); [2] B, [3] Gamma^t reversed (Delta^t); pivots [0] of Gamma,
+// [1] of Gamma^t reversed.
+template <typename T>
+struct DeltaOps {
+  const T* tiles[4];
+  const T* piv[2];
+};
+inline DeltaOps<double> delta_ops64(const LevelOps& v) {
+  return {{v.dt64[0], v.dt64[1], v.dt64[2], v.dt64[3]}, {v.piv64[0], v.piv64[1]}};
+}
+inline DeltaOps<float> delta_ops32(const LevelOps& v) {
+  return {{v.dt32[0], v.dt32[1], v.dt32[2], v.dt32[3]}, {v.piv32[0], v.piv32[1]}};
+}
+
+// One level's entry of a batch (Delta, or Delta^t when `transpose`).
+template <typename T>
+DeltaLevel delta_level(int d, const DeltaOps<T>& op, bool transpose, const void* in, int ldi, void* out,
+                       int ldo, void* planes, int64_t nvec, int grid_level = -1, int R = 1) {
+  DeltaLevel L;
+  L.t1 = op.tiles[transpose ? 2 : 0];
+  L.p1 = transpose ? nullptr : op.piv[0];
+  L.t2 = op.tiles[transpose ? 3 : 1];
+  L.p2 = transpose ? op.piv[1] : nullptr;
+  L.in = in; L.out = out; L.planes = planes;
+  L.nvec = nvec; L.d = d; L.nb = (d + kDeltaTile - 1) / kDeltaTile;
+  L.ldi = ldi; L.ldo = ldo; L.grid_level = grid_level; L.R = R;
+  return L;
+}
+
+template <auto KFN>
+eifmm_status delta_launch(const DeltaBatch& b, int blocks, int warps, size_t sm, cudaStream_t s) {
   static bool attr = false;
-  const size_t sm = solve_smem_bytes(d, sizeof(T));
   if (!attr) {
-    EIFMM_CUDA(cudaFuncSetAttribute(k_tri_sweep<T, FWD, DIAG, Ti, To, PLANES>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    EIFMM_CUDA(cudaFuncSetAttribute(KFN, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     attr = true;
   }
-  int dev = 0, nsm = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int per_sm = (int)((200 * 1024) / (sm > 0 ? sm : 1));
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 2048 / (32 * kSolveWarps)) per_sm = 2048 / (32 * kSolveWarps);
-  int64_t blocks = (nvec + kSolveWarps - 1) / kSolveWarps;
-  if (blocks > (int64_t)nsm * per_sm) blocks = (int64_t)nsm * per_sm;
-  k_tri_sweep<T, FWD, DIAG, Ti, To, PLANES><<<(unsigned)blocks, 32 * kSolveWarps, sm, s>>>(
-      d, Mp, in, ldi, out, ldo, planes, nvec, grid_level, R);
+  KFN<<<(unsigned)blocks, 32 * warps, sm, s>>>(b);
   EIFMM_CHECK_LAUNCH();
   return EIFMM_OK;
+}
+
+// All levels of `b` in one launch (Delta if !transpose, else Delta^t).  The
+// warps per CTA and the staging of the tiles follow the largest level.
+template <typename T, typename Ti, typename To, int PLANES>
+eifmm_status launch_delta_batch(DeltaBatch& b, bool transpose, cudaStream_t s) {
+  int nbmax = 0;
+  for (int i = 0; i < b.nlev; ++i) nbmax = b.lv[i].nvec > 0 && b.lv[i].nb > nbmax ? b.lv[i].nb : nbmax;
+  if (nbmax == 0) return EIFMM_OK;
+  const size_t per_warp = (size_t)nbmax * kDeltaTile * kDeltaLd * sizeof(T);
+  const size_t tiles = (size_t)nbmax * (nbmax + 1) / 2 * kDeltaTile * kDeltaTile * sizeof(T);
+  const size_t cap = 227 * 1024;
+  bool sh = tiles + per_warp <= cap;
+  int warps = kDeltaMaxWarps;
+  while (warps > 1 && (sh ? tiles : 0) + warps * per_warp > cap) --warps;
+  if ((sh ? tiles : 0) + warps * per_warp > cap) {
+    set_error("Delta application: d too large for one warp's vectors in shared memory");
+    return EIFMM_EUNSUPPORTED;
+  }
+  int blocks = 0;
+  for (int i = 0; i < b.nlev; ++i) {
+    b.lv[i].block0 = blocks;
+    const int64_t nw = (b.lv[i].nvec + 31) / 32;
+    blocks += (int)((nw + warps - 1) / warps);
+  }
+  if (blocks == 0) return EIFMM_OK;
+  const size_t sm = (sh ? tiles : 0) + warps * per_warp;
+  if (!transpose)
+    return sh ? delta_launch<k_delta<T, true, false, Ti, To, PLANES, true>>(b, blocks, warps, sm, s)
+              : delta_launch<k_delta<T, true, false, Ti, To, PLANES, false>>(b, blocks, warps, sm, s);
+  return sh ? delta_launch<k_delta<T, false, true, Ti, To, PLANES, true>>(b, blocks, warps, sm, s)
+            : delta_launch<k_delta<T, false, true, Ti, To, PLANES, false>>(b, blocks, warps, sm, s);
 }
 
 }  // namespace eifmm
