@@ -437,8 +437,8 @@ static eifmm_status evaluate_impl(eifmm_tree* tree, const eifmm_ops* ops, const 
 
 
 // ---------------------------------------------------------------------------
-// Measured choice of the mixed-precision tier.  A uniform problem of 8 points
-// per leaf is evaluated at depth min(depth, 4) with the operators' own kernel
+// Measured choice of the mixed-precision tier.  A uniform problem of 32 points
+// per leaf (the near field carries its usual share of the result) is evaluated at depth min(depth, 4) with the operators' own kernel
 // in FP64 and in every mixed tier; the cheapest tier whose relative L2
 // difference to FP64 stays below eps/4 is kept (tier 3: all FP64).
 // ---------------------------------------------------------------------------
@@ -450,7 +450,7 @@ extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_st
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int depth = ops->o.depth < 4 ? ops->o.depth : 4;
-  const int64_t n = (int64_t)8 << (3 * depth);
+  const int64_t n = (int64_t)32 << (3 * depth);
   const double L = ops->o.L;
   std::vector<double> hx(3 * n), hs(n);
   uint64_t st = 0x9E3779B97F4A7C15ull;

@@ -30,51 +30,75 @@ __host__ __device__ inline int64_t nboxes(int k) { return (int64_t)1 << (3 * k);
 
 // ---------------------------------------------------------------- step 1 --
 // W_m^I = sum_{y_j in I} sigma_j K(x_m^{I_0}, y_j - c_I), FP32, local coords.
-template <int KERN>
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// K(z) in FP32 for the point kernels.  1/r: the approximate reciprocal square
+// root (about 2 ulp), with one Newton step when ACC.  Other kernels:
+// kern_f32 / kern_f32_fast.
+template <int KERN, bool ACC>
+__device__ __forceinline__ float kern_pt(int kern, float z0, float z1, float z2) {
+  if (KERN == EIFMM_KERNEL_INV_R) {
+    const float r2 = fmaf(z0, z0, fmaf(z1, z1, z2 * z2));
+    const float y = rsqrt_approx(r2);
+    return ACC ? y * fmaf(-0.5f * r2, y * y, 1.5f) : y;
+  }
+  return ACC ? kern_f32(kern, z0, z1, z2) : kern_f32_fast(kern, z0, z1, z2);
+}
+
+// Step 1: one CTA per leaf, threads = m (the d coefficients); the leaf's
+// points are staged as (x, y, z, sigma_r0) in shared memory.
+template <int KERN, int RCT>
 __global__ void __launch_bounds__(TPB)
 k_p2m32(int kern_rt, const int32_t* __restrict__ off, const float* __restrict__ lx,
         const float* __restrict__ ly, const float* __restrict__ lz,
         const float* __restrict__ sig, int64_t n, int R, const float* __restrict__ X, int d,
         int dp, float* __restrict__ W) {
   const int kern = KERN >= 0 ? KERN : kern_rt;
-  __shared__ float sz[3][TPB];
-  __shared__ float ss[RC][TPB];
+  __shared__ float4 sp[TPB];
+  __shared__ float ss[RCT > 1 ? RCT : 1][TPB];
   const int64_t b = blockIdx.x;
   const int beg = off[b], end = off[b + 1];
-  for (int r0 = 0; r0 < R; r0 += RC) {
+  for (int r0 = 0; r0 < R; r0 += RCT) {
     for (int m0 = 0; m0 < dp; m0 += TPB) {
       const int m = m0 + threadIdx.x;
       float x0 = 0.f, x1 = 0.f, x2 = 0.f;
       if (m < d) { x0 = X[3 * m]; x1 = X[3 * m + 1]; x2 = X[3 * m + 2]; }
-      float acc[RC] = {0.f, 0.f, 0.f, 0.f};
+      float acc[RCT];
+#pragma unroll
+      for (int rr = 0; rr < RCT; ++rr) acc[rr] = 0.f;
       for (int j0 = beg; j0 < end; j0 += TPB) {
         const int j = j0 + threadIdx.x;
         __syncthreads();
         if (j < end) {
-          sz[0][threadIdx.x] = lx[j];
-          sz[1][threadIdx.x] = ly[j];
-          sz[2][threadIdx.x] = lz[j];
+          sp[threadIdx.x] = make_float4(lx[j], ly[j], lz[j], RCT == 1 ? sig[j + r0 * n] : 0.f);
+          if (RCT > 1)
 #pragma unroll
-          for (int rr = 0; rr < RC; ++rr) ss[rr][threadIdx.x] = (r0 + rr < R) ? sig[j + (r0 + rr) * n] : 0.f;
+            for (int rr = 0; rr < RCT; ++rr) ss[rr][threadIdx.x] = (r0 + rr < R) ? sig[j + (r0 + rr) * n] : 0.f;
         }
         __syncthreads();
         const int cnt = min(TPB, end - j0);
         if (m < d)
+#pragma unroll 4
           for (int t = 0; t < cnt; ++t) {
-            const float kv = kern_f32(kern, x0 - sz[0][t], x1 - sz[1][t], x2 - sz[2][t]);
+            const float4 y = sp[t];
+            const float kv = kern_pt<KERN, true>(kern, x0 - y.x, x1 - y.y, x2 - y.z);
 #pragma unroll
-            for (int rr = 0; rr < RC; ++rr) acc[rr] = fmaf(ss[rr][t], kv, acc[rr]);
+            for (int rr = 0; rr < RCT; ++rr) acc[rr] = fmaf(RCT == 1 ? y.w : ss[rr][t], kv, acc[rr]);
           }
       }
       if (m < dp)
-        for (int rr = 0; rr < RC && r0 + rr < R; ++rr) W[(b * R + r0 + rr) * dp + m] = acc[rr];
+        for (int rr = 0; rr < RCT && r0 + rr < R; ++rr) W[(b * R + r0 + rr) * dp + m] = acc[rr];
     }
   }
 }
-
-
-// ---------------------------------------------------------------- step 7 --
-template <int KERN>
+// Step 7 with the near field and the un-permute: one CTA per non-empty
+// target leaf, threads = (point, slice of l): P points of the leaf (up to
+// TPB per pass) times S = TPB / P interleaved slices of the d terms.
+template <int KERN, int RCT>
 __global__ void __launch_bounds__(TPB)
 k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restrict__ off,
         const int32_t* __restrict__ perm, const float* __restrict__ lx,
@@ -83,146 +107,224 @@ k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
         const double* __restrict__ fnear, double* __restrict__ ffar, double* __restrict__ f,
         int64_t ld_f) {
   const int kern = KERN >= 0 ? KERN : kern_rt;
-  extern __shared__ float smf[];  // X (3d) then lhat (RC d)
-  float* sX = smf;
-  float* sl = smf + 3 * d;
+  // (x_l, lhat_l of the first right-hand side) [d], lhat of the pass [RCT d]
+  // when RCT > 1, slice partials [RCT TPB]
+  extern __shared__ float4 smf4[];
+  float4* sX = smf4;
+  float* sl = (float*)(smf4 + d);
+  float* sp = sl + (RCT > 1 ? RCT * d : 0);
+  const int tid = threadIdx.x;
   const int b = leaves[blockIdx.x];
   const int beg = off[b], end = off[b + 1];
-  for (int t = threadIdx.x; t < 3 * d; t += TPB) sX[t] = X[t];
-  for (int r0 = 0; r0 < R; r0 += RC) {
+  for (int r0 = 0; r0 < R; r0 += RCT) {
     __syncthreads();
-    for (int t = threadIdx.x; t < RC * d; t += TPB) {
-      const int rr = t / d, l = t - rr * d;
-      sl[t] = (r0 + rr < R) ? lh[((int64_t)b * R + r0 + rr) * dp + l] : 0.f;
-    }
-    __syncthreads();
-    for (int p = beg + threadIdx.x; p < end; p += TPB) {
-      const float z0 = lx[p], z1 = ly[p], z2 = lz[p];
-      float acc[RC] = {0.f, 0.f, 0.f, 0.f};
-      for (int l = 0; l < d; ++l) {
-        const float kv = kern_f32(kern, z0 - sX[3 * l], z1 - sX[3 * l + 1], z2 - sX[3 * l + 2]);
-#pragma unroll
-        for (int rr = 0; rr < RC; ++rr) acc[rr] = fmaf(kv, sl[rr * d + l], acc[rr]);
+    for (int l = tid; l < d; l += TPB)
+      sX[l] = make_float4(X[3 * l], X[3 * l + 1], X[3 * l + 2], lh[((int64_t)b * R + r0) * dp + l]);
+    if (RCT > 1)
+      for (int t = tid; t < RCT * d; t += TPB) {
+        const int rr = t / d, l = t - rr * d;
+        sl[t] = (r0 + rr < R) ? lh[((int64_t)b * R + r0 + rr) * dp + l] : 0.f;
       }
-      const int64_t i = perm[p];
-      for (int rr = 0; rr < RC && r0 + rr < R; ++rr) {
-        const int rg = r0 + rr;
-        if (ffar) ffar[p + rg * n] = acc[rr];
-        f[i + rg * ld_f] = (double)acc[rr] + fnear[p + rg * n];
+    __syncthreads();
+    for (int t0 = beg; t0 < end; t0 += TPB) {
+      const int P = min(TPB, end - t0), S = TPB / P;
+      const int ti = tid % P, si = tid / P;
+      const int p = t0 + ti;
+      float acc[RCT];
+#pragma unroll
+      for (int rr = 0; rr < RCT; ++rr) acc[rr] = 0.f;
+      if (si < S) {
+        const float z0 = lx[p], z1 = ly[p], z2 = lz[p];
+#pragma unroll 4
+        for (int l = si; l < d; l += S) {
+          const float4 x = sX[l];
+          const float kv = kern_pt<KERN, true>(kern, z0 - x.x, z1 - x.y, z2 - x.z);
+#pragma unroll
+          for (int rr = 0; rr < RCT; ++rr) acc[rr] = fmaf(kv, RCT == 1 ? x.w : sl[rr * d + l], acc[rr]);
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int rr = 0; rr < RCT; ++rr) sp[rr * TPB + tid] = acc[rr];
+      __syncthreads();
+      if (tid < P) {
+        const int64_t i = perm[p];
+#pragma unroll
+        for (int rr = 0; rr < RCT; ++rr) {
+          if (r0 + rr >= R) break;
+          float s = 0.f;
+          for (int k = 0; k < S; ++k) s += sp[rr * TPB + ti + k * P];
+          const int rg = r0 + rr;
+          if (ffar) ffar[p + rg * n] = s;
+          f[i + rg * ld_f] = (double)s + fnear[p + rg * n];
+        }
       }
     }
   }
 }
 
 // ------------------------------------------------------------ near field --
-// One warp per target leaf.  Lanes = (target, slice): a chunk of up to 32
-// targets is spread over Tp = next power of two >= count lanes and the
-// sources over 32/Tp slices, so leaves of 8 points keep every lane busy.
-// Sources are staged per warp in shared memory, expressed in the frame of
-// the target leaf (exact shift by the leaf-centre offset); FP32 kernel,
-// Kahan-compensated FP32 sums, slices combined in FP64.
-constexpr int P2P_WARPS = 4;
-constexpr int P2P_CHUNK = 64;
+// One CTA (128 threads) per non-empty target leaf.  The sources of the 27
+// neighbour leaves are staged in shared memory (in chunks of P2P_SRC) as
+// (x, y, z, sigma) in the frame of the target leaf (exact shift by the
+// leaf-centre offset), with the target leaf itself last so that only its
+// segment needs the self-pair test; warp w stages segments w, w + 4, ...
+// Threads = (target t, slice s), thread = t + P s: P targets of the pass
+// (up to 128) times S = 128 / P contiguous slices of the staged list.  Slice
+// starts are spaced by L = 2 (mod 8) float4, so the few slices a warp reads
+// at once fall in different banks.  The slices of a target are added in FP64
+// in a fixed order; FP32 sums run over at most 64 terms before they are
+// flushed into a compensated total.
+constexpr int P2P_THREADS = 128;
+constexpr int P2P_SRC = 1024;
+constexpr int P2P_FLUSH = 64;
 
-// ACC: Newton-refined 1/r and Kahan summation of every term (tiers 1, 2);
-// otherwise the hardware rsqrt and plain FP32 sums per neighbour leaf, the
-// 27 leaf sums combined with Kahan summation (tier 0).  RCT: right-hand
-// sides per pass (the kernel value is reused across them).
+// Kahan step: (s, c) += v.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  const float y = v - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Adds the staged sources jb <= j < je; SELF: position js (the target
+// itself) contributes nothing.  ACC: compensated sums of every term and an
+// FP64 flush; otherwise plain FP32 sums flushed into FP32 Kahan totals.
+template <int KERN, int RCT, bool ACC, bool SELF>
+__device__ __forceinline__ void p2p_span(int kern, const float4* __restrict__ src, const float* __restrict__ ssig,
+                                         int jb, int je, int js, float x0, float x1, float x2, float (&th)[RCT],
+                                         float (&tc)[RCT], double (&td)[RCT]) {
+  for (int j0 = jb; j0 < je; j0 += P2P_FLUSH) {
+    const int j1 = min(je, j0 + P2P_FLUSH);
+    float sa[RCT], ca[RCT];
+#pragma unroll
+    for (int rr = 0; rr < RCT; ++rr) sa[rr] = ca[rr] = 0.f;
+    auto term = [&](int j) {
+      const float4 y = src[j];
+      float kv = kern_pt<KERN, ACC>(kern, x0 - y.x, x1 - y.y, x2 - y.z);
+      if (SELF && j == js) kv = 0.f;
+#pragma unroll
+      for (int rr = 0; rr < RCT; ++rr) {
+        const float sg = RCT == 1 ? y.w : ssig[rr * P2P_SRC + j];
+        if (ACC) kahan_add(sa[rr], ca[rr], sg * kv);
+        else sa[rr] = fmaf(sg, kv, sa[rr]);
+      }
+    };
+    int j = j0;
+    for (; j + 8 <= j1; j += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) term(j + u);
+    }
+    for (; j < j1; ++j) term(j);
+#pragma unroll
+    for (int rr = 0; rr < RCT; ++rr) {
+      if (ACC) td[rr] += (double)sa[rr] - (double)ca[rr];
+      else kahan_add(th[rr], tc[rr], sa[rr]);
+    }
+  }
+}
+
 template <int KERN, int RCT, bool ACC>
-__global__ void __launch_bounds__(32 * P2P_WARPS)
-k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, int nleaves,
-        const int32_t* __restrict__ toff, const float* __restrict__ tlx,
-        const float* __restrict__ tly, const float* __restrict__ tlz, int64_t nt,
-        const int32_t* __restrict__ soff, const float* __restrict__ slx,
-        const float* __restrict__ sly, const float* __restrict__ slz,
-        const float* __restrict__ sig, int64_t ns, int R, int depth, float two_l,
-        int exclude_self, double* __restrict__ fnear) {
+__global__ void __launch_bounds__(P2P_THREADS)
+k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff,
+        const float* __restrict__ tlx, const float* __restrict__ tly, const float* __restrict__ tlz,
+        int64_t nt, const int32_t* __restrict__ soff, const float* __restrict__ slx,
+        const float* __restrict__ sly, const float* __restrict__ slz, const float* __restrict__ sig,
+        int64_t ns, int R, int depth, float two_l, int exclude_self, double* __restrict__ fnear) {
   const int kern = KERN >= 0 ? KERN : kern_rt;
-  __shared__ float4 src[P2P_WARPS][P2P_CHUNK];        // xyz in the target frame
-  __shared__ float ssig[P2P_WARPS][RCT][P2P_CHUNK];
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * P2P_WARPS + w;
-  if (gw >= nleaves) return;
-  const int b = leaves[gw];
+  __shared__ float4 s_src[P2P_SRC + 8];  // x, y, z in the target frame; w = sigma when RCT == 1
+  __shared__ float s_sig[RCT > 1 ? RCT * P2P_SRC : 1];
+  __shared__ double s_red[RCT][P2P_THREADS];
+  __shared__ int s_pos[28];     // prefix of the segment lengths
+  __shared__ int s_beg[27];     // first source of each segment
+  __shared__ float s_sh[27][3];  // leaf-centre offset of each segment
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int b = leaves[blockIdx.x];
   int c[3];
   morton_decode(b, depth, c);
   const int n = 1 << depth;
+  if (tid < 27) {
+    // segments 0..25: the neighbours other than the leaf itself, 26: itself
+    const int nb = tid < 13 ? tid : (tid < 26 ? tid + 1 : 13);
+    const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
+    const int jx = c[0] + dx, jy = c[1] + dy, jz = c[2] + dz;
+    int beg = 0, len = 0;
+    if (jx >= 0 && jy >= 0 && jz >= 0 && jx < n && jy < n && jz < n) {
+      const int64_t J = morton_encode(jx, jy, jz, depth);
+      beg = soff[J];
+      len = soff[J + 1] - beg;
+    }
+    s_beg[tid] = beg;
+    s_pos[tid + 1] = len;
+    // y - c_I = (y - c_J) + (c_J - c_I)
+    s_sh[tid][0] = dx * two_l;
+    s_sh[tid][1] = dy * two_l;
+    s_sh[tid][2] = dz * two_l;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    s_pos[0] = 0;
+    for (int i = 1; i <= 27; ++i) s_pos[i] += s_pos[i - 1];
+  }
+  __syncthreads();
+  const int n_other = s_pos[26], n_all = s_pos[27];
   const int beg = toff[b], end = toff[b + 1];
-  for (int t0 = beg; t0 < end; t0 += 32) {
-    const int nT = min(32, end - t0);
-    int Tp = 1;
-    while (Tp < nT) Tp <<= 1;
-    const int S = 32 / Tp;
-    const int ti = lane & (Tp - 1), si = lane / Tp;
-    const bool act = ti < nT;
-    const int p = t0 + (act ? ti : 0);
-    const int pself = (exclude_self && act) ? p : -1;
+  for (int t0 = beg; t0 < end; t0 += P2P_THREADS) {
+    const int P = min(P2P_THREADS, end - t0);
+    const int S = P2P_THREADS / P;
+    const int ti = tid % P, si = tid / P;
+    const bool act = si < S;
+    const int p = t0 + ti;
     const float x0 = tlx[p], x1 = tly[p], x2 = tlz[p];
+    // the self pair sits at n_other + (p - beg) of the staged list
+    const int js_all = exclude_self ? n_other + (p - beg) : -1;
     for (int r0 = 0; r0 < R; r0 += RCT) {
-      float sum[RCT], comp[RCT];
+      float th[RCT], tc[RCT];
+      double td[RCT];
 #pragma unroll
-      for (int rr = 0; rr < RCT; ++rr) sum[rr] = comp[rr] = 0.f;
-      for (int nb = 0; nb < 27; ++nb) {
-        const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
-        const int jx = c[0] + dx, jy = c[1] + dy, jz = c[2] + dz;
-        if (jx < 0 || jy < 0 || jz < 0 || jx >= n || jy >= n || jz >= n) continue;
-        const int64_t J = morton_encode(jx, jy, jz, depth);
-        const int sb = soff[J], se = soff[J + 1];
-        // y - c_I = (y - c_J) + (c_J - c_I)
-        const float s0 = dx * two_l, s1 = dy * two_l, s2 = dz * two_l;
-        float part[RCT];
-#pragma unroll
-        for (int rr = 0; rr < RCT; ++rr) part[rr] = 0.f;
-        for (int q0 = sb; q0 < se; q0 += P2P_CHUNK) {
-          __syncwarp();
-          for (int t = lane; t < P2P_CHUNK; t += 32) {
-            const int q = q0 + t;
-            if (q < se) {
-              src[w][t] = make_float4(slx[q] + s0, sly[q] + s1, slz[q] + s2, 0.f);
+      for (int rr = 0; rr < RCT; ++rr) th[rr] = tc[rr] = 0.f, td[rr] = 0.0;
+      for (int c0 = 0; c0 < n_all; c0 += P2P_SRC) {
+        const int cn = min(P2P_SRC, n_all - c0);
+        __syncthreads();
+        for (int sg = w; sg < 27; sg += P2P_THREADS / 32) {
+          const int pb = s_pos[sg], pe = s_pos[sg + 1];
+          const int lo = max(pb, c0), hi = min(pe, c0 + cn);
+          const float sx = s_sh[sg][0], sy = s_sh[sg][1], sz = s_sh[sg][2];
+          for (int pos = lo + lane; pos < hi; pos += 32) {
+            const int sj = s_beg[sg] + (pos - pb);
+            const int q = pos - c0;
+            const float w0 = (RCT == 1 && r0 < R) ? sig[sj + (int64_t)r0 * ns] : 0.f;
+            s_src[q] = make_float4(slx[sj] + sx, sly[sj] + sy, slz[sj] + sz, w0);
+            if (RCT > 1)
 #pragma unroll
               for (int rr = 0; rr < RCT; ++rr)
-                ssig[w][rr][t] = (r0 + rr < R) ? sig[q + (int64_t)(r0 + rr) * ns] : 0.f;
-            }
-          }
-          __syncwarp();
-          const int cnt = min(P2P_CHUNK, se - q0);
-          const int jself = pself - q0;  // the self pair, if it is in this chunk
-          if (act)
-            for (int j = si; j < cnt; j += S) {
-              const float4 y = src[w][j];
-              float kv = ACC ? kern_f32(kern, x0 - y.x, x1 - y.y, x2 - y.z)
-                             : kern_f32_fast(kern, x0 - y.x, x1 - y.y, x2 - y.z);
-              if (j == jself) kv = 0.f;
-#pragma unroll
-              for (int rr = 0; rr < RCT; ++rr) {
-                const float term = ssig[w][rr][j] * kv;
-                if (ACC) {
-                  const float yk = term - comp[rr];
-                  const float tk = sum[rr] + yk;
-                  comp[rr] = (tk - sum[rr]) - yk;
-                  sum[rr] = tk;
-                } else {
-                  part[rr] += term;
-                }
-              }
-            }
-        }
-        if (!ACC) {
-#pragma unroll
-          for (int rr = 0; rr < RCT; ++rr) {
-            const float yk = part[rr] - comp[rr];
-            const float tk = sum[rr] + yk;
-            comp[rr] = (tk - sum[rr]) - yk;
-            sum[rr] = tk;
+                s_sig[rr * P2P_SRC + q] = (r0 + rr < R) ? sig[sj + (int64_t)(r0 + rr) * ns] : 0.f;
           }
         }
+        __syncthreads();
+        if (act) {
+          // slice si: [si L, min(cn, (si + 1) L)), L = 2 (mod 8)
+          int L = (cn + S - 1) / S;
+          L += (10 - (L & 7)) & 7;
+          const int jb = min(cn, si * L), je = min(cn, jb + L);
+          const int a_end = max(jb, min(je, n_other - c0));
+          p2p_span<KERN, RCT, ACC, false>(kern, s_src, s_sig, jb, a_end, -1, x0, x1, x2, th, tc, td);
+          p2p_span<KERN, RCT, ACC, true>(kern, s_src, s_sig, a_end, je, js_all - c0, x0, x1, x2, th, tc, td);
+        }
       }
+      __syncthreads();
 #pragma unroll
-      for (int rr = 0; rr < RCT; ++rr) {
-        double tot = act ? (double)sum[rr] - (double)comp[rr] : 0.0;
-        for (int o = Tp; o < 32; o <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
-        if (act && si == 0 && r0 + rr < R) fnear[p + (int64_t)(r0 + rr) * nt] = tot;
-      }
+      for (int rr = 0; rr < RCT; ++rr)
+        s_red[rr][tid] = act ? (ACC ? td[rr] : (double)th[rr] - (double)tc[rr]) : 0.0;
+      __syncthreads();
+      if (tid < P)
+#pragma unroll
+        for (int rr = 0; rr < RCT; ++rr) {
+          if (r0 + rr >= R) break;
+          double s = 0.0;
+          for (int k = 0; k < S; ++k) s += s_red[rr][ti + k * P];
+          fnear[p + (int64_t)(r0 + rr) * nt] = s;
+        }
     }
   }
 }
@@ -374,9 +476,8 @@ static void p2p_launch(const Tree* t, int kern, const float* sig32, int R, doubl
                        cudaStream_t s) {
   const PointSet& T = t->tgt;
   const PointSet& S = t->src;
-  const unsigned grid = (unsigned)((T.n_nonempty + P2P_WARPS - 1) / P2P_WARPS);
-  k_p2p32<KERN, RCT, ACC><<<grid, 32 * P2P_WARPS, 0, s>>>(
-      kern, T.nonempty, T.n_nonempty, T.leaf_off, T.lx, T.ly, T.lz, T.n, S.leaf_off, S.lx, S.ly, S.lz,
+  k_p2p32<KERN, RCT, ACC><<<(unsigned)T.n_nonempty, P2P_THREADS, 0, s>>>(
+      kern, T.nonempty, T.leaf_off, T.lx, T.ly, T.lz, T.n, S.leaf_off, S.lx, S.ly, S.lz,
       sig32, S.n, R, t->depth, two_l, t->exclude_self, fnear);
 }
 
@@ -436,13 +537,22 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
 
   // step 1 (every leaf, empty ones get zeros)
   const LevelOps& vl = ops->lv[kap];
-  if (kern == EIFMM_KERNEL_INV_R)
-    k_p2m32<EIFMM_KERNEL_INV_R><<<(unsigned)nboxes(kap), TPB, 0, s>>>(
-        kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32, S.n, R, vl.X32, vl.d, vl.dp, ws.W32[kap]);
-  else
-    k_p2m32<-1><<<(unsigned)nboxes(kap), TPB, 0, s>>>(kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32,
-                                                      S.n, R, vl.X32, vl.d, vl.dp, ws.W32[kap]);
-  EIFMM_CHECK_LAUNCH();
+  {
+    const unsigned nb = (unsigned)nboxes(kap);
+    if (kern == EIFMM_KERNEL_INV_R && R == 1)
+      k_p2m32<EIFMM_KERNEL_INV_R, 1><<<nb, TPB, 0, s>>>(kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32, S.n, R,
+                                                       vl.X32, vl.d, vl.dp, ws.W32[kap]);
+    else if (kern == EIFMM_KERNEL_INV_R)
+      k_p2m32<EIFMM_KERNEL_INV_R, RC><<<nb, TPB, 0, s>>>(kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32, S.n, R,
+                                                        vl.X32, vl.d, vl.dp, ws.W32[kap]);
+    else if (R == 1)
+      k_p2m32<-1, 1><<<nb, TPB, 0, s>>>(kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32, S.n, R, vl.X32, vl.d,
+                                        vl.dp, ws.W32[kap]);
+    else
+      k_p2m32<-1, RC><<<nb, TPB, 0, s>>>(kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32, S.n, R, vl.X32, vl.d,
+                                         vl.dp, ws.W32[kap]);
+    EIFMM_CHECK_LAUNCH();
+  }
   record(ws, 1, s);
   // step 2
   for (int k = kap - 1; k >= 2; --k) {
@@ -536,15 +646,23 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   EIFMM_CUDA(cudaStreamWaitEvent(s, ws.ev_join, 0));
   record(ws, 7, s);
   if (T.n_nonempty > 0) {
-    const size_t sm = (size_t)(3 * vl.d + RC * vl.d) * sizeof(float);
-    if (kern == EIFMM_KERNEL_INV_R)
-      k_l2p32<EIFMM_KERNEL_INV_R><<<T.n_nonempty, TPB, sm, s>>>(
-          kern, T.nonempty, T.leaf_off, T.perm, T.lx, T.ly, T.lz, T.n, R, vl.X32, vl.d, vl.dp,
-          ws.lh32, ws.fnear, ws.ffar, f, ld_f);
+    const unsigned nl = (unsigned)T.n_nonempty;
+    const int rct = R == 1 ? 1 : RC;
+    const size_t sm = (size_t)vl.d * sizeof(float4) + (size_t)((rct > 1 ? rct * vl.d : 0) + rct * TPB) * sizeof(float);
+    if (kern == EIFMM_KERNEL_INV_R && R == 1)
+      k_l2p32<EIFMM_KERNEL_INV_R, 1><<<nl, TPB, sm, s>>>(kern, T.nonempty, T.leaf_off, T.perm, T.lx, T.ly,
+                                                        T.lz, T.n, R, vl.X32, vl.d, vl.dp, ws.lh32, ws.fnear,
+                                                        ws.ffar, f, ld_f);
+    else if (kern == EIFMM_KERNEL_INV_R)
+      k_l2p32<EIFMM_KERNEL_INV_R, RC><<<nl, TPB, sm, s>>>(kern, T.nonempty, T.leaf_off, T.perm, T.lx, T.ly,
+                                                         T.lz, T.n, R, vl.X32, vl.d, vl.dp, ws.lh32, ws.fnear,
+                                                         ws.ffar, f, ld_f);
+    else if (R == 1)
+      k_l2p32<-1, 1><<<nl, TPB, sm, s>>>(kern, T.nonempty, T.leaf_off, T.perm, T.lx, T.ly, T.lz, T.n, R,
+                                         vl.X32, vl.d, vl.dp, ws.lh32, ws.fnear, ws.ffar, f, ld_f);
     else
-      k_l2p32<-1><<<T.n_nonempty, TPB, sm, s>>>(kern, T.nonempty, T.leaf_off, T.perm, T.lx, T.ly,
-                                                T.lz, T.n, R, vl.X32, vl.d, vl.dp, ws.lh32, ws.fnear,
-                                                ws.ffar, f, ld_f);
+      k_l2p32<-1, RC><<<nl, TPB, sm, s>>>(kern, T.nonempty, T.leaf_off, T.perm, T.lx, T.ly, T.lz, T.n, R,
+                                          vl.X32, vl.d, vl.dp, ws.lh32, ws.fnear, ws.ffar, f, ld_f);
     EIFMM_CHECK_LAUNCH();
   }
   EIFMM_CUDA(cudaMemcpyAsync(ws.err_host, ws.err, sizeof(int), cudaMemcpyDeviceToHost, s));

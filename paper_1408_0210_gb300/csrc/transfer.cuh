@@ -119,58 +119,77 @@ struct XferGemm {
   float* P8;         // M2M: [8][ncol][ldk] partial sums, one per child
 };
 
+// 64 x 64 output tile per CTA, 4 x 4 per thread, K in steps of 16 through a
+// double-buffered shared tile: the global loads of step k+1 are issued into
+// registers before the FMAs of step k.
 static __global__ void __launch_bounds__(256) k_xfer_gemm(XferGemm a) {
-  __shared__ float As[16][64 + 4];
-  __shared__ float Bs[16][64 + 4];
+  __shared__ __align__(16) float As[2][16][64 + 4];
+  __shared__ __align__(16) float Bs[2][16][64 + 4];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int m0 = blockIdx.x * 64;
   const int64_t c0 = (int64_t)blockIdx.y * 64;
   const int i_l2l = blockIdx.z;  // the child octant (both modes)
   const int K = a.dc;
+  // this thread's four (k, row) load slots: k = tid & 15, rows (tid >> 4) + 16 j
+  const int kk_ld = tid & 15;
+  const float* arow[4];
+  const float* brow[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int rr = (tid >> 4) + 16 * j;
+    const int m = m0 + rr;
+    arow[j] = m < a.dk ? a.A + ((int64_t)i_l2l * a.dk + m) * a.dc : nullptr;
+    const int64_t c = c0 + rr;
+    brow[j] = nullptr;
+    if (c < a.ncol) {
+      const int64_t P = c / a.R;
+      const int r = (int)(c - P * a.R);
+      brow[j] = a.mode == 0 ? a.B + ((8 * P + i_l2l) * a.R + r) * a.ldc : a.B + (P * a.R + r) * a.ldc;
+    }
+  }
+  float ra[4], rb[4];
+  auto gload = [&](int k0) {
+    const int k = k0 + kk_ld;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      ra[j] = (arow[j] != nullptr && k < K) ? __ldg(arow[j] + k) : 0.f;
+      rb[j] = (brow[j] != nullptr && k < K) ? __ldg(brow[j] + k) : 0.f;
+    }
+  };
+  auto sstore = [&](int buf) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      As[buf][kk_ld][(tid >> 4) + 16 * j] = ra[j];
+      Bs[buf][kk_ld][(tid >> 4) + 16 * j] = rb[j];
+    }
+  };
   float acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+  gload(0);
+  sstore(0);
+  __syncthreads();
+  int buf = 0;
   for (int k0 = 0; k0 < K; k0 += 16) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int e = tid + 256 * j;      // 0..1023
-      const int kk = e & 15, rr = e >> 4;  // rr: row of A tile / column of B tile
-      const int k = k0 + kk;
-      // A(m, k)
-      const int m = m0 + rr;
-      float av = 0.f;
-      if (m < a.dk && k < K) {
-        av = a.A[((int64_t)i_l2l * a.dk + m) * a.dc + k];
-      }
-      As[kk][rr] = av;
-      // B(k, c)
-      const int64_t c = c0 + rr;
-      float bv = 0.f;
-      if (c < a.ncol && k < K) {
-        const int64_t P = c / a.R;
-        const int r = (int)(c - P * a.R);
-        if (a.mode == 0) bv = a.B[((8 * P + i_l2l) * a.R + r) * a.ldc + k];
-        else bv = a.B[(P * a.R + r) * a.ldc + k];
-      }
-      Bs[kk][rr] = bv;
-    }
-    __syncthreads();
+    const bool more = k0 + 16 < K;
+    if (more) gload(k0 + 16);
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      float ar[4], br[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) ar[u] = As[kk][ty * 4 + u];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) br[v] = Bs[kk][tx * 4 + v];
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      const float ar[4] = {a4.x, a4.y, a4.z, a4.w};
+      const float br[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(ar[u], br[v], acc[u][v]);
     }
+    if (more) sstore(buf ^ 1);
     __syncthreads();
+    buf ^= 1;
   }
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
