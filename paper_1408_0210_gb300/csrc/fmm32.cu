@@ -11,6 +11,9 @@
 // padding columns zero.
 #include <algorithm>
 
+#include <cstring>
+#include <cstdlib>
+
 #include "internal.h"
 #include "m2l_tc.h"
 #include "transfer.cuh"
@@ -446,6 +449,12 @@ eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R) {
       EIFMM_TRY(make_plane_map(ws.tmap[k][0], ws.wa[k], k, R, dp, tf32));
       EIFMM_TRY(make_plane_map(ws.tmap[k][1], (char*)ws.wa[k] + plane, k, R, dp, tf32));
       ws.wa_grid[k] = true;
+      ws.wa_t256[k] = false;
+      if (dp == 128 && m2l_t256_block(R, &bx, &by, &bz)) {
+        EIFMM_TRY(make_plane_map(ws.tmap2[k][0], ws.wa[k], k, R, dp, tf32, 256));
+        EIFMM_TRY(make_plane_map(ws.tmap2[k][1], (char*)ws.wa[k] + plane, k, R, dp, tf32, 256));
+        ws.wa_t256[k] = true;
+      }
     }
   }
   EIFMM_TRY(dalloc(&ws.lh32, (size_t)nboxes(kap) * R * ops->lv[kap].dp));
@@ -459,6 +468,8 @@ eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R) {
       const int64_t tiles = (nboxes(k) / 8 * R + 127) / 128;
       const int G = m2l_tc_groups(tiles * 8, nsm, ops->lv[k].dp);
       if (G > 1) need = std::max(need, (size_t)G * rows * ops->lv[k].dp);
+      const int G2 = m2l_t256_groups(m2l_t256_ctas(k, R), nsm);
+      if (G2 > 1) need = std::max(need, (size_t)G2 * rows * ops->lv[k].dp);
     }
     if (need) EIFMM_TRY(dalloc(&ws.m2l_part, need));
   }
@@ -505,6 +516,13 @@ eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R, do
   }
   EIFMM_CHECK_LAUNCH();
   return EIFMM_OK;
+}
+
+// The transposed M2L serves dp = 128 unless EIFMM_M2L_KERNEL=128 asks for the
+// 128-row kernel (read at every evaluate, for comparisons).
+static bool use_m2l_t256() {
+  const char* e = getenv("EIFMM_M2L_KERNEL");
+  return !(e && strcmp(e, "128") == 0);
 }
 
 static void record(Workspace& ws, int i, cudaStream_t s) {
@@ -610,8 +628,19 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
       a.groups = m2l_tc_groups((a.nbox / 8 * R + 127) / 128 * 8, nsm, a.dp);
       a.part = ws.m2l_part;
     }
-    if (ws.wa_grid[k]) EIFMM_TRY(launch_m2l_tma(a, ws.tmap[k][0], ws.tmap[k][1], tf32, s));
-    else EIFMM_TRY(launch_m2l_tc(a, tf32, s));
+    // the transposed kernel where a parity class fills at least one of its
+    // 256-row tiles; the 128-row kernel at the coarse levels
+    if (ws.wa_t256[k] && nboxes(k) / 8 * R >= 256 && use_m2l_t256()) {
+      int dev = 0, nsm = 148;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      a.groups = m2l_t256_groups(m2l_t256_ctas(k, R), nsm);
+      EIFMM_TRY(launch_m2l_t256(a, ws.tmap2[k][0], ws.tmap2[k][1], tf32, s));
+    } else if (ws.wa_grid[k]) {
+      EIFMM_TRY(launch_m2l_tma(a, ws.tmap[k][0], ws.tmap[k][1], tf32, s));
+    } else {
+      EIFMM_TRY(launch_m2l_tc(a, tf32, s));
+    }
   }
   if (timing_enabled()) cudaEventRecord(ws.ev_m2l[kap + 1], s);
   record(ws, 4, s);

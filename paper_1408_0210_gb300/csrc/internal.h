@@ -131,6 +131,9 @@ struct Workspace {
   void* wa[kMaxLevel + 1] = {};
   bool wa_grid[kMaxLevel + 1] = {};  // planes in the per-class grid layout (TMA M2L)
   alignas(64) unsigned char tmap[kMaxLevel + 1][2][128] = {};  // CUtensorMap per plane
+  // 256-row boxes of the transposed M2L (dp = 128)
+  bool wa_t256[kMaxLevel + 1] = {};
+  alignas(64) unsigned char tmap2[kMaxLevel + 1][2][128] = {};
   float* m2l_part = nullptr;    // partial M2L sums of the split offset lists
   int* err = nullptr;           // device error word of bounded waits
   int* err_host = nullptr;      // pinned copy, read at the next call

@@ -118,6 +118,27 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint3
         "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 
+// The 4 k-steps x 3 split products of one 128-byte chunk of l:
+//   D (+)= A_hi B_hi^t + A_hi B_lo^t + A_lo B_hi^t.
+// da / db: descriptors of plane 0 of the stage's A and B; plane 1 sits
+// pa16 / pb16 descriptor units (16 bytes) further and k-step kk at 2 kk (32
+// bytes), which never carries out of the 14-bit address field.  `wide`: a
+// second MMA covers accumulator columns 256.. (dp > 256).
+template <bool TF32>
+__device__ __forceinline__ void issue_chunk(uint32_t dacc, uint64_t da, uint64_t db, uint32_t pa16, uint32_t pb16,
+                                            uint32_t id_lo, uint32_t id_hi, bool wide, bool first) {
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+    for (int pr = 0; pr < 3; ++pr) {
+      const uint64_t ad = da + (pr == 2 ? pa16 : 0u) + 2u * kk;
+      const uint64_t bd = db + (pr == 1 ? pb16 : 0u) + 2u * kk;
+      const uint32_t acc = (first && kk == 0 && pr == 0) ? 0u : 1u;
+      mma<TF32>(dacc, ad, bd, id_lo, acc);
+      if (wide) mma<TF32>(dacc + 256, ad, bd + 2048u, id_hi, acc);
+    }
+}
+
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
                : "memory");
@@ -265,32 +286,32 @@ k_m2l_tc(M2LTcArgs a) {
     // ----------------------------------------------------- MMA issuer --
     const uint32_t id_lo = idesc(TF32 ? 2u : 1u, dp > 256 ? 256u : (uint32_t)dp);
     const uint32_t id_hi = idesc(TF32 ? 2u : 1u, dp > 256 ? (uint32_t)(dp - 256) : 16u);
+    // descriptors of the stages' A and B plane 0 (S <= 3), counters instead
+    // of divisions in this single-thread loop
+    const uint64_t dA0 = sdesc(sbase), dA1 = sdesc(sbase + stage), dA2 = sdesc(sbase + 2 * stage);
+    const uint64_t dB0 = dA0 + (2 * a_bytes >> 4), dB1 = dA1 + (2 * a_bytes >> 4), dB2 = dA2 + (2 * a_bytes >> 4);
+    int st = 0, c = 0, e = 0, ch = 0;
+    uint32_t ph = 0;
     for (int it = 0; it < nit; ++it) {
-      const int st = it % S;
-      if (!mbar_wait(full(st), (it / S) & 1, a.err, 2)) {
+      if (!mbar_wait(full(st), ph, a.err, 2)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const uint32_t sA = sbase + st * stage;
-      const uint32_t sB = sA + 2 * a_bytes;
       // offsets go round-robin to `chains` accumulators: shorter FP32
       // accumulation chains, summed in FP64 by the epilogue
-      const int e = it / nchunk;
-      const uint32_t dacc = tmem + (uint32_t)((e % a.chains) * dp);
-      const bool first = e < a.chains && (it % nchunk) == 0;
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-#pragma unroll
-        for (int pr = 0; pr < 3; ++pr) {  // hi*hi, hi*lo, lo*hi
-          const int pa = (pr == 2) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
-          const uint32_t acc = (!first || kk > 0 || pr > 0) ? 1u : 0u;
-          const uint64_t ad = sdesc(sA + pa * a_bytes + kk * 32);
-          const uint32_t bB = sB + pb * b_bytes + kk * 32;
-          mma<TF32>(dacc, ad, sdesc(bB), id_lo, acc);
-          if (dp > 256) mma<TF32>(dacc + 256, ad, sdesc(bB + 32 * 1024), id_hi, acc);
-        }
+      const uint32_t dacc = tmem + (uint32_t)(ch * dp);
+      const bool first = e < a.chains && c == 0;
+      const uint64_t da = st == 0 ? dA0 : (st == 1 ? dA1 : dA2);
+      const uint64_t db = st == 0 ? dB0 : (st == 1 ? dB1 : dB2);
+      issue_chunk<TF32>(dacc, da, db, a_bytes >> 4, b_bytes >> 4, id_lo, id_hi, dp > 256, first);
       mma_commit(empty(st));
+      if (++st == S) st = 0, ph ^= 1u;
+      if (++c == nchunk) {
+        c = 0;
+        ++e;
+        if (++ch == a.chains) ch = 0;
+      }
     }
     if (ok && nit >= 1) mma_commit(done_bar);
   }
@@ -455,17 +476,19 @@ k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
 
   if (tid == 128) {
     // -------------------------------------------------------- producer --
-    int it = 0;
+    int it = 0, pst = 0;
+    uint32_t pph = 0;  // phase of the current round of the ring
     for (int s = s_beg; s < s_end && ok; ++s) {
       const int slot = lst[s];
       int sc, sxr, sy, sz;
       if (!source(slot, &sc, &sxr, &sy, &sz) && CN == 1) continue;
       for (int c = 0; c < nchunk && ok; ++c, ++it) {
-        const int st = it % S, u = it / S;
-        if (it >= S && !mbar_wait(empty(st), (u - 1) & 1, a.err, 1)) {
+        if (it >= S && !mbar_wait(empty(pst), pph ^ 1u, a.err, 1)) {
           ok = false;
           break;
         }
+        const int st = pst;
+        if (++pst == S) pst = 0, pph ^= 1u;
         const uint32_t sA = sbase + st * stage;
         mbar_expect_tx(full(st), 2 * a_bytes + 2 * b_bytes);
         tma_load_5d(sA, &tA0, c * E, sxr, sy, sz, sc, full(st));
@@ -483,31 +506,31 @@ k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
     // ----------------------------------------------------- MMA issuer --
     const uint32_t id_lo = idesc(TF32 ? 2u : 1u, dp > 256 ? 256u : (uint32_t)dp);
     const uint32_t id_hi = idesc(TF32 ? 2u : 1u, dp > 256 ? (uint32_t)(dp - 256) : 16u);
+    // descriptors of the stages' A and B plane 0 (S <= 3), counters instead
+    // of divisions in this single-thread loop
+    const uint64_t dA0 = sdesc(sbase), dA1 = sdesc(sbase + stage), dA2 = sdesc(sbase + 2 * stage);
+    const uint64_t dB0 = dA0 + (2 * a_bytes >> 4), dB1 = dA1 + (2 * a_bytes >> 4), dB2 = dA2 + (2 * a_bytes >> 4);
+    int st = 0, c = 0, e = 0, ch = 0;
+    uint32_t ph = 0;
     for (int it = 0; it < nit; ++it) {
-      const int st = it % S;
-      if (!mbar_wait(full(st), (it / S) & 1, a.err, 2)) {
+      if (!mbar_wait(full(st), ph, a.err, 2)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      const uint32_t sA = sbase + st * stage;
-      const uint32_t sB = sA + 2 * a_bytes;
-      const int e = it / nchunk;
-      const uint32_t dacc = tmem + (uint32_t)((e % a.chains) * dp);
-      const bool first = e < a.chains && (it % nchunk) == 0;
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk)
-#pragma unroll
-        for (int pr = 0; pr < 3; ++pr) {
-          const int pa = (pr == 2) ? 1 : 0, pb = (pr == 1) ? 1 : 0;
-          const uint32_t acc = (!first || kk > 0 || pr > 0) ? 1u : 0u;
-          const uint64_t ad = sdesc(sA + pa * a_bytes + kk * 32);
-          const uint32_t bB = sB + pb * b_bytes + kk * 32;
-          mma<TF32>(dacc, ad, sdesc(bB), id_lo, acc);
-          if (dp > 256) mma<TF32>(dacc + 256, ad, sdesc(bB + 32 * 1024), id_hi, acc);
-        }
+      const uint32_t dacc = tmem + (uint32_t)(ch * dp);
+      const bool first = e < a.chains && c == 0;
+      const uint64_t da = st == 0 ? dA0 : (st == 1 ? dA1 : dA2);
+      const uint64_t db = st == 0 ? dB0 : (st == 1 ? dB1 : dB2);
+      issue_chunk<TF32>(dacc, da, db, a_bytes >> 4, b_bytes >> 4, id_lo, id_hi, dp > 256, first);
       if (CN == 1) mma_commit(empty(st));
       else mma_commit_mc(empty(st), cmask);
+      if (++st == S) st = 0, ph ^= 1u;
+      if (++c == nchunk) {
+        c = 0;
+        ++e;
+        if (++ch == a.chains) ch = 0;
+      }
     }
     if (ok && nit >= 1) mma_commit(done_bar);
   } else if (tid < 128) {
@@ -550,6 +573,234 @@ k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
   if (CN > 1) cluster_sync();
   if (tid >= 128 && tid < 160)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)a.tmem_cols));
+}
+
+// ---------------------------------------------------------------------------
+// Transposed TMA M2L for dp = 128: D^t[m' x row] = K^delta[m' x l] What[row x l]^t
+// with M = 128 (m'), N = 256 (target rows), K = l.  One tcgen05.mma then does
+// twice the work of an M = 128, N = 128 one at the same issue cost, and the
+// shared-memory operand traffic per flop drops by a quarter.
+//
+// The offsets are walked in segments of kSegOffsets.  A segment accumulates in
+// one of two 256-column TMEM buffers (short FP32 accumulation chains) while
+// the eight epilogue warps drain the other into FP32 registers; the register
+// totals are stored once at the end.  Warp 8 produces (one bulk copy of the
+// K^delta image, two 5-D TMA loads of the What planes per stage), warp 9
+// issues the MMAs.
+// ---------------------------------------------------------------------------
+constexpr int kT2Rows = 256;
+constexpr int kT2Stages = 2;
+constexpr int kSegOffsets = 4;
+constexpr int kT2Threads = 320;
+
+// Bounded wait that also gives up when another role has set *abort.
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t a, uint32_t parity, int* err, int code,
+                                             volatile int* abort) {
+  const long long t0 = clock64();
+  while (!mbar_try(a, parity)) {
+    if (*abort) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      atomicExch(err, code);
+      *abort = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+      "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(kT2Threads, 1)
+k_m2l_t256(const __grid_constant__ CUtensorMap tW0, const __grid_constant__ CUtensorMap tW1, M2LTcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int esz = TF32 ? 4 : 2;
+  const int E = 128 / esz;
+  const int dp = a.dp;  // 128
+  const int nchunk = dp * esz / 128;
+  const uint32_t k_bytes = 128u * 128u;         // one K^delta plane: 128 rows x 128 B
+  const uint32_t w_bytes = kT2Rows * 128u;      // one What plane: 256 rows x 128 B
+  const uint32_t stage = 2 * k_bytes + 2 * w_bytes;
+  uint64_t* bars = (uint64_t*)(smem + kT2Stages * stage);  // full[2] empty[2] sfull[2] sempty[2]
+  uint32_t* tslot = (uint32_t*)(bars + 8);
+  volatile int* abort = (volatile int*)(tslot + 1);
+  int64_t* s_row = (int64_t*)(bars + 9);  // [256] output rows of the tile
+  const uint32_t sbase = smem_u32(smem);
+  auto full = [&](int st) { return smem_u32(&bars[st]); };
+  auto empty = [&](int st) { return smem_u32(&bars[2 + st]); };
+  auto sfull = [&](int b) { return smem_u32(&bars[4 + b]); };
+  auto sempty = [&](int b) { return smem_u32(&bars[6 + b]); };
+
+  const int h = a.h, R = a.R;
+  const int bxr = a.bx * R;
+  const int oct = blockIdx.x % 8;
+  const int grp = (blockIdx.x / 8) % a.groups;
+  int tile = blockIdx.x / (8 * a.groups);
+  const int ntx = (h * R + bxr - 1) / bxr, nty = (h + a.by - 1) / a.by;
+  const int tx = tile % ntx;
+  tile /= ntx;
+  const int ty = tile % nty, tz = tile / nty;
+  const int xr0 = tx * bxr, y0 = ty * a.by, z0 = tz * a.bz;
+  const int cx = oct & 1, cy = (oct >> 1) & 1, cz = (oct >> 2) & 1;
+  const int s_beg = grp * kListLen / a.groups, s_end = (grp + 1) * kListLen / a.groups;
+  const int* lst = a.slot_lists + oct * kListLen;
+
+  // the source block of an offset; empty when it misses the class grid
+  auto source = [&](int slot, int* sc, int* sxr, int* sy, int* sz) {
+    const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+    *sc = ((cx + dx) & 1) | (((cy + dy) & 1) << 1) | (((cz + dz) & 1) << 2);
+    *sxr = xr0 + ((cx + dx) >> 1) * R;
+    *sy = y0 + ((cy + dy) >> 1);
+    *sz = z0 + ((cz + dz) >> 1);
+    return *sxr < h * R && *sxr + bxr > 0 && *sy < h && *sy + a.by > 0 && *sz < h && *sz + a.bz > 0;
+  };
+
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(full(i), 1);
+      mbar_init(empty(i), 1);
+      mbar_init(sfull(i), 1);
+      mbar_init(sempty(i), 8);  // one arrival per epilogue warp
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(512u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  int nact = 0;
+  for (int s = s_beg; s < s_end; ++s) {
+    int sc, sxr, sy, sz;
+    nact += source(lst[s], &sc, &sxr, &sy, &sz) ? 1 : 0;
+  }
+  const int nseg = (nact + kSegOffsets - 1) / kSegOffsets;
+
+  if (tid == 256) {
+    // -------------------------------------------------------- producer --
+    int it = 0, st = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int s = s_beg; s < s_end && ok; ++s) {
+      const int slot = lst[s];
+      int sc, sxr, sy, sz;
+      if (!source(slot, &sc, &sxr, &sy, &sz)) continue;
+      for (int c = 0; c < nchunk; ++c, ++it) {
+        if (it >= kT2Stages && !mbar_wait_ab(empty(st), ph ^ 1u, a.err, 1, abort)) {
+          ok = false;
+          break;
+        }
+        const uint32_t sK = sbase + st * stage;
+        const uint32_t sW = sK + 2 * k_bytes;
+        mbar_expect_tx(full(st), 2 * k_bytes + 2 * w_bytes);
+        bulk_g2s(sK, (const char*)a.kd_img + (((size_t)slot * nchunk + c) * 2) * k_bytes, 2 * k_bytes, full(st));
+        tma_load_5d(sW, &tW0, c * E, sxr, sy, sz, sc, full(st));
+        tma_load_5d(sW + w_bytes, &tW1, c * E, sxr, sy, sz, sc, full(st));
+        if (++st == kT2Stages) st = 0, ph ^= 1u;
+      }
+    }
+  } else if (tid == 288) {
+    // ----------------------------------------------------- MMA issuer --
+    const uint32_t id = idesc(TF32 ? 2u : 1u, (uint32_t)kT2Rows);
+    const uint64_t dK0 = sdesc(sbase), dK1 = sdesc(sbase + stage);
+    const uint64_t dW0 = dK0 + (2 * k_bytes >> 4), dW1 = dK1 + (2 * k_bytes >> 4);
+    int st = 0, done = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int seg = 0; seg < nseg && ok; ++seg) {
+      const int b = seg & 1;
+      if (seg >= 2 && !mbar_wait_ab(sempty(b), ((seg >> 1) - 1) & 1, a.err, 4, abort)) break;
+      tc_fence_after();
+      const uint32_t dacc = tmem + (uint32_t)(b * kT2Rows);
+      const int nit = min(kSegOffsets, nact - done) * nchunk;
+      for (int i = 0; i < nit; ++i) {
+        if (!mbar_wait_ab(full(st), ph, a.err, 2, abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        // A = K^delta planes (M), B = What planes (N): hi*hi, hi*lo, lo*hi
+        issue_chunk<TF32>(dacc, st == 0 ? dK0 : dK1, st == 0 ? dW0 : dW1, k_bytes >> 4, w_bytes >> 4, id, id,
+                          false, i == 0);
+        mma_commit(empty(st));
+        if (++st == kT2Stages) st = 0, ph ^= 1u;
+      }
+      done += kSegOffsets;
+      if (ok) mma_commit(sfull(b));
+    }
+  } else if (warp < 8) {
+    // ------------------------------------------------------ epilogue --
+    // warp w reads TMEM lanes 32 (w % 4) .. (m' rows) and columns
+    // 128 (w / 4) .. of the 256 target rows
+    const int q = warp & 3, half = warp >> 2;
+    float acc[128];
+#pragma unroll
+    for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+    for (int seg = 0; seg < nseg; ++seg) {
+      const int b = seg & 1;
+      bool have = mbar_wait_ab(sfull(b), (seg >> 1) & 1, a.err, 3, abort);
+      have = __all_sync(0xffffffffu, have);
+      if (!have) break;
+      tc_fence_after();
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kT2Rows + 128 * half);
+#pragma unroll
+      for (int j0 = 0; j0 < 128; j0 += 32) {
+        float v[32];
+        tmem_ld32(taddr + j0, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[j0 + i] += v[i];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sempty(b)) : "memory");
+    }
+    // output row of each of the 256 tile rows (x*R + r fastest, then y,
+    // then z), -1 outside the grid: one per epilogue thread, then shared
+    {
+      const int n = tid;
+      const int xr = xr0 + n % bxr;
+      const int yy = y0 + (n / bxr) % a.by;
+      const int zz = z0 + n / (bxr * a.by);
+      int64_t row = -1;
+      if (xr < h * R && yy < h && zz < h) {
+        const int x = xr / R, r = xr % R;
+        row = morton_encode(2 * x + cx, 2 * yy + cy, 2 * zz + cz, a.level) * R + r;
+      }
+      s_row[n] = row;
+    }
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight epilogue warps
+    const int mp = 32 * q + lane;  // m'
+    float* outg = a.out + (size_t)grp * a.part_stride + mp;
+#pragma unroll
+    for (int j = 0; j < 128; ++j) {
+      const int64_t row = s_row[128 * half + j];
+      if (row >= 0) outg[row * dp] = acc[j];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 8)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
 }
 
 __global__ void k_sum_parts(const float4* __restrict__ parts, int groups, int64_t n4, int64_t stride4,
@@ -598,6 +849,24 @@ int m2l_tc_groups(int64_t tiles8, int nsm, int dp) {
 
 // Tile block of the grid layout for R right-hand sides (R a power of two <= 128):
 // bx boxes x R rhs along x, by along y, bz along z, 128 rows in all.
+// 256-row target tile of the transposed M2L: bx x by x bz boxes x R rows.
+bool m2l_t256_block(int R, int* bx, int* by, int* bz) {
+  if (R < 1 || R > 256 || (R & (R - 1))) return false;
+  *bx = R >= 8 ? 1 : 8 / R;
+  const int rem = 256 / (*bx * R);
+  *by = rem >= 8 ? 8 : rem;
+  *bz = rem / *by;
+  return true;
+}
+
+// Offset groups of the transposed M2L: the fewest that occupy three quarters
+// of the SMs (each extra group costs a pass over its partial sums).
+int m2l_t256_groups(int64_t ctas, int nsm) {
+  int g = 1;
+  while (g < 16 && ctas * g * 4 < (int64_t)nsm * 3) g *= 2;
+  return g;
+}
+
 bool m2l_tma_block(int R, int* bx, int* by, int* bz) {
   if (R < 1 || R > 128 || (R & (R - 1))) return false;
   *bx = R >= 8 ? 1 : 8 / R;
@@ -625,14 +894,14 @@ static EncodeTiledFn encode_fn() {
 }
 
 // Tensor map of one What plane in the grid layout of level `level`.
-eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, bool tf32) {
+eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, bool tf32, int rows) {
   auto fn = encode_fn();
   if (!fn) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return EIFMM_ECUDA;
   }
   int bx, by, bz;
-  if (!m2l_tma_block(R, &bx, &by, &bz)) {
+  if (!(rows == 256 ? m2l_t256_block(R, &bx, &by, &bz) : m2l_tma_block(R, &bx, &by, &bz))) {
     set_error("no TMA tile shape for this number of right-hand sides");
     return EIFMM_EUNSUPPORTED;
   }
@@ -760,6 +1029,56 @@ eifmm_status launch_m2l_tma(const M2LTcArgs& a0, const void* map0, const void* m
     EIFMM_CHECK_LAUNCH();
   }
   return EIFMM_OK;
+}
+
+size_t m2l_t256_smem_bytes() { return (size_t)kT2Stages * (2 * 16384 + 2 * kT2Rows * 128) + 1024 + 128 + 8 * kT2Rows; }
+
+eifmm_status launch_m2l_t256(const M2LTcArgs& a0, const void* map0, const void* map1, bool tf32, cudaStream_t s) {
+  M2LTcArgs a = a0;
+  if (a.dp != 128 || !m2l_t256_block(a.R, &a.bx, &a.by, &a.bz)) {
+    set_error("transposed M2L: needs dp = 128 and a tile shape for R");
+    return EIFMM_EUNSUPPORTED;
+  }
+  a.h = 1 << (a.level - 1);
+  const int bxr = a.bx * a.R;
+  const int64_t tiles =
+      (int64_t)((a.h * a.R + bxr - 1) / bxr) * ((a.h + a.by - 1) / a.by) * ((a.h + a.bz - 1) / a.bz);
+  if (a.groups > 1) {
+    a.out = a.part;
+    a.part_stride = a.rows * (int64_t)a.dp;
+  } else {
+    a.out = a.g;
+    a.part_stride = 0;
+  }
+  const size_t sm = m2l_t256_smem_bytes();
+  static bool attr[2] = {false, false};
+  if (!attr[tf32]) {
+    if (tf32)
+      EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_t256<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    else
+      EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_t256<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    attr[tf32] = true;
+  }
+  const unsigned grid = (unsigned)(tiles * 8 * a.groups);
+  const CUtensorMap& m0 = *(const CUtensorMap*)map0;
+  const CUtensorMap& m1 = *(const CUtensorMap*)map1;
+  if (tf32) k_m2l_t256<true><<<grid, kT2Threads, sm, s>>>(m0, m1, a);
+  else k_m2l_t256<false><<<grid, kT2Threads, sm, s>>>(m0, m1, a);
+  EIFMM_CHECK_LAUNCH();
+  if (a.groups > 1) {
+    const int64_t n4 = a.rows * (int64_t)a.dp / 4;
+    k_sum_parts<<<(unsigned)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096), 256, 0, s>>>(
+        (const float4*)a.part, a.groups, n4, a.part_stride / 4, (float4*)a.g);
+    EIFMM_CHECK_LAUNCH();
+  }
+  return EIFMM_OK;
+}
+
+int64_t m2l_t256_ctas(int level, int R) {
+  int bx, by, bz;
+  if (!m2l_t256_block(R, &bx, &by, &bz)) return 0;
+  const int h = 1 << (level - 1), bxr = bx * R;
+  return (int64_t)((h * R + bxr - 1) / bxr) * ((h + by - 1) / by) * ((h + bz - 1) / bz) * 8;
 }
 
 eifmm_status launch_m2l_tc(const M2LTcArgs& a0, bool tf32, cudaStream_t s) {

@@ -31,11 +31,18 @@ constexpr int kMaxDpTc = 320;
 size_t m2l_tc_smem_bytes(int dp, bool tf32);
 int m2l_tc_groups(int64_t tiles8, int nsm, int dp);
 bool m2l_tma_block(int R, int* bx, int* by, int* bz);
+bool m2l_t256_block(int R, int* bx, int* by, int* bz);
+int m2l_t256_groups(int64_t ctas, int nsm);
+int64_t m2l_t256_ctas(int level, int R);  // CTAs of one offset group
+size_t m2l_t256_smem_bytes();
 // Tensor map (a 128-byte CUtensorMap, 64-byte aligned) of one What plane in
 // the per-class grid layout [class][Z][Y][X*R + r][dp].
-eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, bool tf32);
+eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, bool tf32, int rows = 128);
 eifmm_status launch_m2l_tma(const M2LTcArgs& a, const void* map0, const void* map1, bool tf32,
                             cudaStream_t s);
 eifmm_status launch_m2l_tc(const M2LTcArgs& a, bool tf32, cudaStream_t s);
+// Transposed variant (dp = 128): M = 128 (m'), N = 256 target rows per MMA.
+eifmm_status launch_m2l_t256(const M2LTcArgs& a, const void* map0, const void* map1, bool tf32,
+                             cudaStream_t s);
 
 }  // namespace eifmm

@@ -109,7 +109,7 @@ __device__ __forceinline__ void tiled_solve(T* __restrict__ sz, int nb, const T*
     for (int K = 0; K < J; ++K) {
       const T* tk = tJ + (int64_t)K * TL * TL;
       const T* zK = sz + (REV ? (nb - 1 - K) * TL + TL - 1 : K * TL) * kDeltaLd + lane;
-#pragma unroll 4
+#pragma unroll
       for (int k = 0; k < TL; ++k) {
         const T zk = zK[(REV ? -k : k) * kDeltaLd];
         tile_col_update<SH>(acc, tk + k * TL, zk);

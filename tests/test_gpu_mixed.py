@@ -113,15 +113,44 @@ def _coords(k):
     return _CC[k]
 
 
-def test_mixed_m2l_kernel_arithmetic(E, orc, c1m):
+@pytest.mark.parametrize("k", [2, 3])
+def test_mixed_m2l_kernel_arithmetic(E, orc, c1m, k):
     t, lv = c1m["tree"], c1m["lv"]
-    k = 2
     d = lv[k]["d"]
     Wh = E.eifmm_debug_export(t, 1, k, d)
     g = E.eifmm_debug_export(t, 2, k, d)
     gref = _m2l_reference(orc, lv, k, Wh)
     # BF16 hi+lo planes of K^delta (~2^-17 relative), FP32 accumulation
     assert relmax(g, gref) <= 2e-5
+
+
+def test_m2l_transposed_matches_128_row_kernel(E):
+    """The transposed M2L (M = m', N = 256 target rows, segment drains) and
+    the 128-row kernel (M = rows, N = dp, TMEM chains) compute the same g at
+    every level of a depth-5 tree (several tiles per class, offset groups at
+    the coarse levels), to the BF16-split accuracy."""
+    import os
+    n, depth = 150000, 5
+    x = wl.uniform_cube(n, 41)
+    s = wl.sigma_uniform(n, 1, 42)
+    ops = E.eifmm_ops_build("inv_r", 1.0, depth, 1e-4)
+    ops.plan(0)
+    assert ops.error_estimate(depth)[1] > 64  # dp = 128
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    f = torch.zeros(n, dtype=torch.float64, device="cuda")
+    g = {}
+    for kind in ("t256", "128"):
+        if kind == "128":
+            os.environ["EIFMM_M2L_KERNEL"] = "128"
+        try:
+            E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
+            torch.cuda.synchronize()
+            g[kind] = {k: E.eifmm_debug_export(tree, 2, k, ops.error_estimate(k)[1]) for k in range(2, depth + 1)}
+        finally:
+            os.environ.pop("EIFMM_M2L_KERNEL", None)
+    for k in range(2, depth + 1):
+        assert np.isfinite(g["t256"][k]).all()
+        assert relmax(g["t256"][k], g["128"][k]) <= 2e-5, k
 
 
 @pytest.mark.parametrize("eps,tol", [(1e-5, 1e-5), (1e-6, 1e-6), (1e-7, 1e-7)])
