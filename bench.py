@@ -51,6 +51,30 @@ def m2l_pairs(k: int) -> int:
     return sa ** 3 - sb ** 3
 
 
+def near_field_pairs(off: np.ndarray, depth: int) -> int:
+    """Exact source-target pairs of the near field: every target against the
+    points of the 27 leaves around its own, minus the self pairs."""
+    n = 1 << depth
+    cnt = np.diff(off).astype(np.int64)
+    key = np.arange(cnt.size, dtype=np.int64)
+    c = np.zeros((3, cnt.size), dtype=np.int64)
+    for b in range(depth):
+        for a in range(3):
+            c[a] |= ((key >> (3 * b + a)) & 1) << b
+    grid = np.zeros((n + 2, n + 2, n + 2), dtype=np.int64)
+    grid[c[2] + 1, c[1] + 1, c[0] + 1] = cnt
+    nb = sum(grid[1 + dz:n + 1 + dz, 1 + dy:n + 1 + dy, 1 + dx:n + 1 + dx]
+             for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1))
+    own = grid[1:n + 1, 1:n + 1, 1:n + 1]
+    return int((own * nb).sum() - cnt.sum())
+
+
+# one ncu capture of the level-5 k_m2l_t256 launch (dram read + write bytes)
+M2L_T256_TRAFFIC = 37.545728e6 + 0.145408e6
+# nominal special-function rate: 16 results per clock per SM, 152 SMs, 2070 MHz
+SFU_PEAK = 16 * 152 * 2.07e9
+
+
 def peaks() -> dict:
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -273,6 +297,7 @@ def main():
                 "rel_l2_vs_exact": err, "meets_eps": err <= eps, "d": d,
                 "gpu_launches": launches, "steps": steps,
                 "step_ms": [round(statistics.median([t[i] for t in st]), 4) for i in range(8)],
+                "nf_ms": round(statistics.median([t[8] for t in st]), 4),
                 "m2l_ms_per_level": [round(v, 4) for v in m2l]}
             if headline is None and err <= eps and (prec, eps) in (("mixed", 1e-4), ("fp64", 1e-4)):
                 headline = (prec, eps)
@@ -307,14 +332,27 @@ def main():
     achieved = flops / (m2l_ms * 1e-3) / 1e12
     if hp == "mixed":
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk["bf16_tflops"],
-                "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"], "traffic": None,
-                "kernel": "M2L level 5 (tcgen05, BF16 split operands, FP32 accumulate)",
+                "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"],
+                "traffic": M2L_T256_TRAFFIC if dk <= 128 else None,
+                "kernel": "M2L level 5 (k_m2l_t256: tcgen05 M=128 x N=256, BF16 split operands, FP32 accumulate)",
                 "peak_source": pk["source"] + " bf16 burst"}
     else:
         peak64 = 1.25
         roof = {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
                 "frac": achieved / peak64, "traffic": None,
                 "kernel": "M2L level 5 (FP64 FMA)", "peak_source": "nominal FP64 1.25 TFLOP/s"}
+
+    # ---- second bound: the near field, one approximate 1/r per pair ----------
+    _, _, off = tree.export(1)
+    pairs = near_field_pairs(off, DEPTH)
+    nf_ms = hr["nf_ms"]
+    roof_nf = None
+    if nf_ms > 0:
+        roof_nf = {"bound": "alu", "achieved": pairs / (nf_ms * 1e-3), "peak": SFU_PEAK,
+                   "unit": "rsqrt/s", "frac": pairs / (nf_ms * 1e-3) / SFU_PEAK, "traffic": None,
+                   "kernel": f"near field ({'k_p2p32, FP32' if hp == 'mixed' else 'k_p2p64, FP64'}), "
+                             f"{pairs} pairs", "launch_ms": nf_ms,
+                   "peak_source": "nominal: 16 special-function results per clock per SM x 152 SMs x 2070 MHz"}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -335,6 +373,7 @@ def main():
                 "d2h_bytes_per_step": N_POINTS * NRHS * 8},
         "gpu_launches": hr["gpu_launches"],
         "roofline": roof,
+        "roofline_near_field": roof_nf,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "variants": results,

@@ -302,7 +302,8 @@ uint64_t eifmm_kernel_launches(void);
  * the evaluate then waits for its last event).  ms[20]: [0] sigma gather +
  * P2M (step 1), [1] M2M (2), [2] Delta solves (3), [3] M2L (4), [4] L2L (5),
  * [5] Delta^t solve (6), [6] wait for the near field, [7] L2P + sum +
- * un-permute (7), [8] unused; [9 + k] the M2L launch of level k alone. */
+ * un-permute (7), [8] the near-field launch alone (on the library's side
+ * stream); [9 + k] the M2L launch of level k alone. */
 void eifmm_set_timing(int on);
 eifmm_status eifmm_last_step_times(const eifmm_tree* tree, float* ms20);
 

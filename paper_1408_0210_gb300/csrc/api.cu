@@ -68,12 +68,15 @@ static void free_streams(Workspace* ws) {
   if (ws->ev_join) cudaEventDestroy(ws->ev_join);
   for (auto& e : ws->ev_t)
     if (e) cudaEventDestroy(e);
+  for (auto& e : ws->ev_nf)
+    if (e) cudaEventDestroy(e);
   for (auto& e : ws->ev_m2l)
     if (e) cudaEventDestroy(e);
   ws->side = nullptr;
   ws->ev_fork = ws->ev_join = nullptr;
   for (auto& e : ws->ev_t) e = nullptr;
   for (auto& e : ws->ev_m2l) e = nullptr;
+  for (auto& e : ws->ev_nf) e = nullptr;
   dfree(ws->host_sig);
   dfree(ws->host_f);
   ws->host_sig = ws->host_f = nullptr;
@@ -94,6 +97,7 @@ eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec) {
     EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_join, cudaEventDisableTiming));
     for (auto& e : ws.ev_t) EIFMM_CUDA(cudaEventCreate(&e));
     for (auto& e : ws.ev_m2l) EIFMM_CUDA(cudaEventCreate(&e));
+    for (auto& e : ws.ev_nf) EIFMM_CUDA(cudaEventCreate(&e));
   }
   const int tier = (prec == EIFMM_PREC_MIXED) ? ops->tier : -1;
   if (ws.ops_id == (const void*)ops && ws.nrhs == R && ws.prec == prec && ws.tier == tier)
@@ -429,6 +433,7 @@ static eifmm_status evaluate_impl(eifmm_tree* tree, const eifmm_ops* ops, const 
   if (g_timing) {
     EIFMM_CUDA(cudaEventSynchronize(t.ws.ev_t[8]));
     for (int i = 0; i < 8; ++i) cudaEventElapsedTime(&t.ws.step_ms[i], t.ws.ev_t[i], t.ws.ev_t[i + 1]);
+    cudaEventElapsedTime(&t.ws.step_ms[8], t.ws.ev_nf[0], t.ws.ev_nf[1]);
     for (int k = 2; k <= t.depth; ++k)
       cudaEventElapsedTime(&t.ws.step_ms[9 + k], t.ws.ev_m2l[k], t.ws.ev_m2l[k + 1]);
   }

@@ -550,7 +550,9 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   EIFMM_TRY(launch_gather_sigma(sigma, ld_sigma, S, R, ws.sig, ws.sig32, s));
   EIFMM_CUDA(cudaEventRecord(ws.ev_fork, s));
   EIFMM_CUDA(cudaStreamWaitEvent(ws.side, ws.ev_fork, 0));
+  if (timing_enabled()) cudaEventRecord(ws.ev_nf[0], ws.side);
   EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, ws.side, ops->tier >= 1));
+  if (timing_enabled()) cudaEventRecord(ws.ev_nf[1], ws.side);
   EIFMM_CUDA(cudaEventRecord(ws.ev_join, ws.side));
 
   // step 1 (every leaf, empty ones get zeros)

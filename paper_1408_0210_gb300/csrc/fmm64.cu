@@ -339,8 +339,10 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
   // near field on the side stream, concurrent with the far field
   EIFMM_CUDA(cudaEventRecord(ws.ev_fork, s));
   EIFMM_CUDA(cudaStreamWaitEvent(ws.side, ws.ev_fork, 0));
+  if (timing_enabled()) cudaEventRecord(ws.ev_nf[0], ws.side);
   if (near32) EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, ws.side, true));
   else EIFMM_TRY(launch_p2p64(t, kern, ws.sig, R, ws.fnear, ws.side));
+  if (timing_enabled()) cudaEventRecord(ws.ev_nf[1], ws.side);
   EIFMM_CUDA(cudaEventRecord(ws.ev_join, ws.side));
 
   // step 1

@@ -149,6 +149,7 @@ struct Workspace {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_t[10] = {};
   cudaEvent_t ev_m2l[kMaxLevel + 2] = {};
+  cudaEvent_t ev_nf[2] = {};  // the near-field launch on the side stream
   bool evaluated = false;
   float step_ms[20] = {};
 };
