@@ -160,7 +160,7 @@ eifmm_status eifmm_ops_error_estimate(const eifmm_ops* ops, int level,
 eifmm_status eifmm_ops_plan(eifmm_ops* ops, int tier_override, int* tier);
 
 /* Measured choice of the tier (no counterpart in the paper, which computes in
- * FP64): a uniform problem of 8 points per leaf at depth min(depth, 4) is
+ * FP64): a uniform problem of 32 points per leaf at depth min(depth, 4) is
  * evaluated in FP64 and in tiers 0, 1, 2; the cheapest tier whose relative L2
  * difference to FP64 is at most eps/4 is kept, else tier 3.  Allocates and
  * frees its own device memory; synchronises `stream`.  Errors: EINVAL,
@@ -242,15 +242,31 @@ eifmm_status eifmm_tree_sort_static(const double* xyz, int64_t n,
 /* f = sum_j sigma_j K(x_i, y_j) for n_rhs potential vectors.  sigma and f are
  * DEVICE arrays, column-major: sigma[j + r*ld_sigma] (n_src x n_rhs), f[i +
  * r*ld_f] (n_tgt x n_rhs), both FP64 and in the caller's original point
- * order.  The ops must have been built with the tree's depth and L.  The
+ * order.  The ops must cover the tree's levels (ops depth >= tree depth;
+ * levels deeper than the tree are not used) and have the tree's L.  The
  * tree owns the workspace; the first call for a given (ops, n_rhs) allocates
  * it and later calls allocate nothing.  Calls that share a tree must not
- * overlap.  Errors: EINVAL (null, n_rhs < 1 or > 256, ld < n, depth / L
- * mismatch), ENOMEM, ECUDA. */
+ * overlap.  Errors: EINVAL (null, n_rhs < 1 or > 256, ld < n, ops depth
+ * below the tree's, L mismatch), ENOMEM, ECUDA. */
 eifmm_status eifmm_evaluate(eifmm_tree* tree, const eifmm_ops* ops,
                             const double* sigma, int64_t ld_sigma, int n_rhs,
                             double* f, int64_t ld_f, eifmm_precision prec,
                             eifmm_stream stream);
+
+/* Autotuner of the tensor-core M2L (step 4; the paper has no counterpart).
+ * For the mixed path of tiers 0 and 1 it evaluates once with sigma = 0 (which
+ * also sets up the workspace for n_rhs), then times at every level each
+ * applicable M2L variant -- 1 transposed (M = coefficients, N = 256 target
+ * rows), 2 128-row TMA, 3 128-row TMA with a 2-CTA cluster sharing K^delta --
+ * with the offset-group count halved, kept or doubled, against the built-in
+ * rule (variant 0), using CUDA events on `stream`.  The fastest (by at least
+ * 2% over the rule) is kept in the tree for later evaluations with the same
+ * ops, n_rhs and precision.  choice (may be null): int[2 * 11], entries
+ * 2k and 2k+1 = variant and group shift of level k.  Other paths and tiers:
+ * nothing to tune, returns OK with zeros.  Synchronises `stream`.
+ * Errors: as eifmm_evaluate. */
+eifmm_status eifmm_autotune(eifmm_tree* tree, const eifmm_ops* ops, int n_rhs,
+                            eifmm_precision prec, eifmm_stream stream, int* choice);
 
 /* Same computation with HOST sigma and f (pinned memory recommended): the
  * call copies sigma to the device, evaluates, copies f back and synchronises
@@ -260,8 +276,9 @@ eifmm_status eifmm_evaluate_host(eifmm_tree* tree, const eifmm_ops* ops,
                                  int n_rhs, double* f_host, int64_t ld_f,
                                  eifmm_precision prec, eifmm_stream stream);
 
-/* Many independent problems sharing one operator set (same kernel, L and
- * depth): problem p evaluates trees[p] with DEVICE sigma[p] and f[p]
+/* Many independent problems sharing one operator set (same kernel and L;
+ * each tree's depth at most the operators'): problem p evaluates trees[p]
+ * with DEVICE sigma[p] and f[p]
  * (one RHS each, ld = n).  Errors as eifmm_evaluate. */
 eifmm_status eifmm_evaluate_batched(eifmm_tree* const* trees,
                                     const double* const* sigma,
@@ -292,6 +309,14 @@ eifmm_status eifmm_direct_sum(eifmm_kernel kern, const double* tgt_xyz,
                               int64_t ld_sigma, int n_rhs, int exclude_self,
                               const int64_t* tgt_idx, int64_t n_eval,
                               double* f, eifmm_stream stream);
+
+/* Measured arithmetic rates of the current GPU (no counterpart in the
+ * paper): rates[0] FP32 FMA/s, rates[1] approximate reciprocal square roots/s
+ * (rsqrt.approx.ftz.f32), rates[2] FP64 FMA/s, from register loops with 8
+ * independent chains per thread over every SM, best of 3 timed runs.  They
+ * are the roofline denominators of the point kernels and of the FP64 path.
+ * Synchronises `stream`.  Errors: EINVAL (null), ENOMEM, ECUDA. */
+eifmm_status eifmm_measure_rates(eifmm_stream stream, double* rates);
 
 /* Number of kernels this library has launched since it was loaded (all
  * devices, all threads). */

@@ -51,6 +51,11 @@ void free_workspace(Workspace* ws) {
   }
   dfree(ws->lh); dfree(ws->lh32); dfree(ws->sig); dfree(ws->sig32); dfree(ws->m2l_part);
   ws->m2l_part = nullptr;
+  ws->m2l_part_cap = 0;
+  dfree(ws->m2l_part_leaf);
+  ws->m2l_part_leaf = nullptr;
+  ws->m2l_part_leaf_cap = 0;
+  for (int k = 0; k <= kMaxLevel; ++k) ws->m2l_kind[k] = ws->m2l_gshift[k] = 0;
   dfree(ws->fnear); dfree(ws->ffar); dfree(ws->tmp);
   ws->tmp = nullptr;
   ws->lh = nullptr; ws->lh32 = nullptr; ws->sig = nullptr; ws->sig32 = nullptr;
@@ -66,6 +71,11 @@ static void free_streams(Workspace* ws) {
   if (ws->side) cudaStreamDestroy(ws->side);
   if (ws->ev_fork) cudaEventDestroy(ws->ev_fork);
   if (ws->ev_join) cudaEventDestroy(ws->ev_join);
+  if (ws->side2) cudaStreamDestroy(ws->side2);
+  if (ws->ev_fork2) cudaEventDestroy(ws->ev_fork2);
+  if (ws->ev_join2) cudaEventDestroy(ws->ev_join2);
+  for (auto& e : ws->ev_m2le)
+    if (e) cudaEventDestroy(e);
   for (auto& e : ws->ev_t)
     if (e) cudaEventDestroy(e);
   for (auto& e : ws->ev_nf)
@@ -74,6 +84,9 @@ static void free_streams(Workspace* ws) {
     if (e) cudaEventDestroy(e);
   ws->side = nullptr;
   ws->ev_fork = ws->ev_join = nullptr;
+  ws->side2 = nullptr;
+  ws->ev_fork2 = ws->ev_join2 = nullptr;
+  for (auto& e : ws->ev_m2le) e = nullptr;
   for (auto& e : ws->ev_t) e = nullptr;
   for (auto& e : ws->ev_m2l) e = nullptr;
   for (auto& e : ws->ev_nf) e = nullptr;
@@ -95,6 +108,10 @@ eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec) {
     EIFMM_CUDA(cudaStreamCreateWithFlags(&ws.side, cudaStreamNonBlocking));
     EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_fork, cudaEventDisableTiming));
     EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_join, cudaEventDisableTiming));
+    EIFMM_CUDA(cudaStreamCreateWithFlags(&ws.side2, cudaStreamNonBlocking));
+    EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_fork2, cudaEventDisableTiming));
+    EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_join2, cudaEventDisableTiming));
+    for (auto& e : ws.ev_m2le) EIFMM_CUDA(cudaEventCreate(&e));
     for (auto& e : ws.ev_t) EIFMM_CUDA(cudaEventCreate(&e));
     for (auto& e : ws.ev_m2l) EIFMM_CUDA(cudaEventCreate(&e));
     for (auto& e : ws.ev_nf) EIFMM_CUDA(cudaEventCreate(&e));
@@ -407,8 +424,8 @@ static eifmm_status check_eval(const eifmm_tree* tree, const eifmm_ops* ops, int
     return EIFMM_EINVAL;
   }
   const Tree& t = tree->t;
-  if (ops->o.depth != t.depth || ops->o.L != t.L) {
-    set_error("eifmm_evaluate: operators were built for another depth or L");
+  if (ops->o.depth < t.depth || ops->o.L != t.L) {
+    set_error("eifmm_evaluate: operator depth below the tree depth, or another L");
     return EIFMM_EINVAL;
   }
   if (ld_sigma < t.src.n || ld_f < t.tgt.n) {
@@ -435,7 +452,7 @@ static eifmm_status evaluate_impl(eifmm_tree* tree, const eifmm_ops* ops, const 
     for (int i = 0; i < 8; ++i) cudaEventElapsedTime(&t.ws.step_ms[i], t.ws.ev_t[i], t.ws.ev_t[i + 1]);
     cudaEventElapsedTime(&t.ws.step_ms[8], t.ws.ev_nf[0], t.ws.ev_nf[1]);
     for (int k = 2; k <= t.depth; ++k)
-      cudaEventElapsedTime(&t.ws.step_ms[9 + k], t.ws.ev_m2l[k], t.ws.ev_m2l[k + 1]);
+      cudaEventElapsedTime(&t.ws.step_ms[9 + k], t.ws.ev_m2l[k], t.ws.ev_m2le[k]);
   }
   return EIFMM_OK;
 }
@@ -535,6 +552,112 @@ extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_st
   EIFMM_TRY(eifmm_ops_plan(ops, best, nullptr));
   if (tier_out) *tier_out = best;
   return EIFMM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner of the tensor-core M2L (no counterpart in the paper): per level,
+// every applicable variant and offset-group count is timed on this tree with
+// CUDA events and the fastest is kept in the tree's workspace.
+// ---------------------------------------------------------------------------
+extern "C" eifmm_status eifmm_autotune(eifmm_tree* tree, const eifmm_ops* ops, int n_rhs,
+                                       eifmm_precision prec, eifmm_stream stream, int* choice) {
+  if (!tree || !ops) {
+    set_error("eifmm_autotune: null handle");
+    return EIFMM_EINVAL;
+  }
+  Tree& t = tree->t;
+  EIFMM_TRY(check_eval(tree, ops, n_rhs, t.src.n, t.tgt.n, (int)prec));
+  if (choice)
+    for (int k = 0; k <= kMaxLevel; ++k) choice[2 * k] = choice[2 * k + 1] = 0;
+  if (prec != EIFMM_PREC_MIXED || ops->o.tier >= 2) return EIFMM_OK;  // no tensor-core M2L
+  cudaStream_t s = (cudaStream_t)stream;
+  const int R = n_rhs, kap = t.depth;
+  const int64_t ns = t.src.n > 0 ? t.src.n : 1, nt = t.tgt.n > 0 ? t.tgt.n : 1;
+  double *sg = nullptr, *fo = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  eifmm_status rc = EIFMM_OK;
+  do {
+    // one evaluation (sigma = 0) sets up the workspace and the operand planes
+    if ((rc = dalloc(&sg, (size_t)ns * R)) != EIFMM_OK) break;
+    if ((rc = dalloc(&fo, (size_t)nt * R)) != EIFMM_OK) break;
+    cudaMemsetAsync(sg, 0, (size_t)ns * R * sizeof(double), s);
+    if ((rc = evaluate_impl(tree, ops, sg, ns, R, fo, nt, (int)prec, s)) != EIFMM_OK) break;
+    Workspace& ws = t.ws;
+    for (int k = 0; k <= kMaxLevel; ++k) ws.m2l_kind[k] = ws.m2l_gshift[k] = 0;
+    // room for the partial sums of larger group counts, within 1 GiB per
+    // buffer (the leaf level has its own: it runs concurrently)
+    size_t want = ws.m2l_part_cap, want_leaf = ws.m2l_part_leaf_cap;
+    for (int k = 2; k <= kap; ++k) {
+      const size_t per = ((size_t)1 << (3 * k)) * R * ops->o.lv[k].dp;
+      size_t& w = k == kap ? want_leaf : want;
+      for (int g = 2; g <= 16; g *= 2)
+        if (g * per <= ((size_t)1 << 28) && g * per > w) w = g * per;
+    }
+    if (want > ws.m2l_part_cap) {
+      dfree(ws.m2l_part);
+      ws.m2l_part = nullptr;
+      ws.m2l_part_cap = 0;
+      if ((rc = dalloc(&ws.m2l_part, want)) != EIFMM_OK) break;
+      ws.m2l_part_cap = want;
+    }
+    if (want_leaf > ws.m2l_part_leaf_cap) {
+      dfree(ws.m2l_part_leaf);
+      ws.m2l_part_leaf = nullptr;
+      ws.m2l_part_leaf_cap = 0;
+      if ((rc = dalloc(&ws.m2l_part_leaf, want_leaf)) != EIFMM_OK) break;
+      ws.m2l_part_leaf_cap = want_leaf;
+    }
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+      rc = EIFMM_ECUDA;
+      set_error("eifmm_autotune: event creation failed");
+      break;
+    }
+    for (int k = 2; k <= kap && rc == EIFMM_OK; ++k) {
+      float best = 1e30f;
+      int bk = 0, bg = 0;
+      for (int kind = 0; kind <= 3 && rc == EIFMM_OK; ++kind)
+        for (int gs = -1; gs <= 1; ++gs) {
+          if (kind == 0 && gs != 0) continue;  // the built-in rule as it stands
+          eifmm_status r = launch_m2l_level(&t, &ops->o, k, R, kind, gs, s);  // warm-up
+          if (r == EIFMM_EUNSUPPORTED) continue;
+          if (r != EIFMM_OK) {
+            rc = r;
+            break;
+          }
+          float ms[3];
+          for (int rep = 0; rep < 3 && rc == EIFMM_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            rc = launch_m2l_level(&t, &ops->o, k, R, kind, gs, s);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms[rep], e0, e1);
+          }
+          if (rc != EIFMM_OK) break;
+          const float med = ms[0] < ms[1] ? (ms[1] < ms[2] ? ms[1] : (ms[0] < ms[2] ? ms[2] : ms[0]))
+                                          : (ms[0] < ms[2] ? ms[0] : (ms[1] < ms[2] ? ms[2] : ms[1]));
+          if (med < best * 0.98f) {  // a variant must win by 2% to replace the rule
+            best = med;
+            bk = kind;
+            bg = gs;
+          }
+        }
+      ws.m2l_kind[k] = bk;
+      ws.m2l_gshift[k] = bg;
+      if (choice) {
+        choice[2 * k] = bk;
+        choice[2 * k + 1] = bg;
+      }
+    }
+    if (rc == EIFMM_OK && cudaStreamSynchronize(s) != cudaSuccess) {
+      rc = EIFMM_ECUDA;
+      set_error("eifmm_autotune: a timed launch failed");
+    }
+  } while (false);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  dfree(sg);
+  dfree(fo);
+  return rc;
 }
 
 extern "C" eifmm_status eifmm_evaluate(eifmm_tree* tree, const eifmm_ops* ops, const double* sigma,

@@ -462,16 +462,20 @@ eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R) {
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    size_t need = 0;
+    size_t need = 0, need_leaf = 0;
     for (int k = 2; k <= kap; ++k) {
       const int64_t rows = nboxes(k) * R;
       const int64_t tiles = (nboxes(k) / 8 * R + 127) / 128;
+      size_t& nd = k == kap ? need_leaf : need;
       const int G = m2l_tc_groups(tiles * 8, nsm, ops->lv[k].dp);
-      if (G > 1) need = std::max(need, (size_t)G * rows * ops->lv[k].dp);
+      if (G > 1) nd = std::max(nd, (size_t)G * rows * ops->lv[k].dp);
       const int G2 = m2l_t256_groups(m2l_t256_ctas(k, R), nsm);
-      if (G2 > 1) need = std::max(need, (size_t)G2 * rows * ops->lv[k].dp);
+      if (G2 > 1) nd = std::max(nd, (size_t)G2 * rows * ops->lv[k].dp);
     }
     if (need) EIFMM_TRY(dalloc(&ws.m2l_part, need));
+    ws.m2l_part_cap = need;
+    if (need_leaf) EIFMM_TRY(dalloc(&ws.m2l_part_leaf, need_leaf));
+    ws.m2l_part_leaf_cap = need_leaf;
   }
   if (!ws.err) {
     EIFMM_TRY(dalloc(&ws.err, 1));
@@ -527,6 +531,69 @@ static bool use_m2l_t256() {
 
 static void record(Workspace& ws, int i, cudaStream_t s) {
   if (timing_enabled()) cudaEventRecord(ws.ev_t[i], s);
+}
+
+static int sm_count() {
+  int dev = 0, nsm = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  return nsm;
+}
+
+static int shift_groups(int g, int shift) {
+  g = shift >= 0 ? g << shift : g >> -shift;
+  return g < 1 ? 1 : (g > 16 ? 16 : g);
+}
+
+// Step 4 at level k.  kind 0 follows the built-in rule (the transposed kernel
+// where a parity class fills a 256-row tile and dp = 128, else the 128-row
+// TMA kernel, else the cp.async one); 1-3 force a variant (autotuner);
+// gshift scales the offset-group count.  EUNSUPPORTED when the variant does
+// not apply to this level.
+eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, int gshift, cudaStream_t s) {
+  Workspace& ws = t->ws;
+  const bool tf32 = ops->tier == 1;
+  const LevelOps& v = ops->lv[k];
+  if (v.kd_img == nullptr || v.kd_img_tf32 != (int)tf32) {
+    set_error("eifmm_evaluate: tensor-core M2L operands missing for this level (d too large)");
+    return EIFMM_EUNSUPPORTED;
+  }
+  M2LTcArgs a;
+  a.level = k;
+  a.nbox = nboxes(k);
+  a.R = R;
+  a.rows = a.nbox * R;
+  a.dp = v.dp;
+  a.tmem_cols = v.dp <= 128 ? 128 : (v.dp <= 256 ? 256 : 512);
+  a.wa = ws.wa[k];
+  a.kd_img = v.kd_img;
+  a.slot_lists = ops->d_slot_lists;
+  a.g = ws.g32[k];
+  a.err = ws.err;
+  const bool leaf = k == t->depth;
+  a.part = leaf ? ws.m2l_part_leaf : ws.m2l_part;
+  const size_t cap = leaf ? ws.m2l_part_leaf_cap : ws.m2l_part_cap;
+  const int nsm = sm_count();
+  const bool rule = kind == 0;
+  if (rule) {
+    // the transposed kernel where a parity class fills at least one of its
+    // 256-row tiles; the 128-row kernel at the coarse levels
+    kind = (ws.wa_t256[k] && nboxes(k) / 8 * R >= 256 && use_m2l_t256()) ? 1 : (ws.wa_grid[k] ? 2 : 4);
+  }
+  if (kind == 1) {
+    if (!ws.wa_t256[k]) return EIFMM_EUNSUPPORTED;
+    a.groups = shift_groups(m2l_t256_groups(m2l_t256_ctas(k, R), nsm), gshift);
+  } else {
+    // the 128-row TMA kernel reads the per-class grid planes, the cp.async
+    // one the Morton-ordered planes
+    if ((kind == 4) == ws.wa_grid[k]) return EIFMM_EUNSUPPORTED;
+    a.groups = shift_groups(m2l_tc_groups((a.nbox / 8 * R + 127) / 128 * 8, nsm, a.dp), gshift);
+    a.cluster = rule ? 0 : (kind == 3 ? 2 : 1);
+  }
+  if (a.groups > 1 && (size_t)a.groups * a.rows * a.dp > cap) return EIFMM_EUNSUPPORTED;
+  if (kind == 1) return launch_m2l_t256(a, ws.tmap2[k][0], ws.tmap2[k][1], tf32, s);
+  if (kind == 2 || kind == 3) return launch_m2l_tma(a, ws.tmap[k][0], ws.tmap[k][1], tf32, s);
+  return launch_m2l_tc(a, tf32, s);
 }
 
 eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld_sigma, int R,
@@ -603,48 +670,25 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     else EIFMM_TRY((launch_delta_batch<float, float, float, 1>(b, false, s)));
   }
   record(ws, 3, s);
-  // step 4
-  for (int k = 2; k <= kap; ++k) {
-    if (timing_enabled()) cudaEventRecord(ws.ev_m2l[k], s);
-    const LevelOps& v = ops->lv[k];
-    if (v.kd_img == nullptr || v.kd_img_tf32 != (int)tf32) {
-      set_error("eifmm_evaluate: tensor-core M2L operands missing for this level (d too large)");
-      return EIFMM_EUNSUPPORTED;
-    }
-    M2LTcArgs a;
-    a.level = k;
-    a.nbox = nboxes(k);
-    a.R = R;
-    a.rows = a.nbox * R;
-    a.dp = v.dp;
-    a.tmem_cols = v.dp <= 128 ? 128 : (v.dp <= 256 ? 256 : 512);
-    a.wa = ws.wa[k];
-    a.kd_img = v.kd_img;
-    a.slot_lists = ops->d_slot_lists;
-    a.g = ws.g32[k];
-    a.err = ws.err;
-    {
-      int dev = 0, nsm = 148;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      a.groups = m2l_tc_groups((a.nbox / 8 * R + 127) / 128 * 8, nsm, a.dp);
-      a.part = ws.m2l_part;
-    }
-    // the transposed kernel where a parity class fills at least one of its
-    // 256-row tiles; the 128-row kernel at the coarse levels
-    if (ws.wa_t256[k] && nboxes(k) / 8 * R >= 256 && use_m2l_t256()) {
-      int dev = 0, nsm = 148;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      a.groups = m2l_t256_groups(m2l_t256_ctas(k, R), nsm);
-      EIFMM_TRY(launch_m2l_t256(a, ws.tmap2[k][0], ws.tmap2[k][1], tf32, s));
-    } else if (ws.wa_grid[k]) {
-      EIFMM_TRY(launch_m2l_tma(a, ws.tmap[k][0], ws.tmap[k][1], tf32, s));
-    } else {
-      EIFMM_TRY(launch_m2l_tc(a, tf32, s));
-    }
+  // step 4: the levels are independent.  The coarse levels run on a second
+  // stream while the leaf level runs here, so their small grids fill the
+  // SMs the leaf level leaves free; each side has its own partial sums.
+  if (kap > 2) {
+    EIFMM_CUDA(cudaEventRecord(ws.ev_fork2, s));
+    EIFMM_CUDA(cudaStreamWaitEvent(ws.side2, ws.ev_fork2, 0));
   }
-  if (timing_enabled()) cudaEventRecord(ws.ev_m2l[kap + 1], s);
+  if (timing_enabled()) cudaEventRecord(ws.ev_m2l[kap], s);
+  EIFMM_TRY(launch_m2l_level(t, ops, kap, R, ws.m2l_kind[kap], ws.m2l_gshift[kap], s));
+  if (timing_enabled()) cudaEventRecord(ws.ev_m2le[kap], s);
+  for (int k = 2; k < kap; ++k) {
+    if (timing_enabled()) cudaEventRecord(ws.ev_m2l[k], ws.side2);
+    EIFMM_TRY(launch_m2l_level(t, ops, k, R, ws.m2l_kind[k], ws.m2l_gshift[k], ws.side2));
+    if (timing_enabled()) cudaEventRecord(ws.ev_m2le[k], ws.side2);
+  }
+  if (kap > 2) {
+    EIFMM_CUDA(cudaEventRecord(ws.ev_join2, ws.side2));
+    EIFMM_CUDA(cudaStreamWaitEvent(s, ws.ev_join2, 0));
+  }
   record(ws, 4, s);
   // step 5
   for (int k = 3; k <= kap; ++k) {

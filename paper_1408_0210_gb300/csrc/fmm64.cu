@@ -386,8 +386,8 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
     k_m2l64<<<dim3((unsigned)(nb / 8 / M2L_NB * 8), R), TPB, M2L_NB * d * sizeof(double), s>>>(
         k, d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.Wh[k], ws.g[k]);
     EIFMM_CHECK_LAUNCH();
+    if (timing_enabled()) cudaEventRecord(ws.ev_m2le[k], s);
   }
-  if (timing_enabled()) cudaEventRecord(ws.ev_m2l[kap + 1], s);
   record(ws, 4, s);
   // step 5 (l^2 = g^2)
   for (int k = 3; k <= kap; ++k) {

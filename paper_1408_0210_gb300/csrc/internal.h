@@ -133,6 +133,14 @@ struct Workspace {
   alignas(64) unsigned char tmap[kMaxLevel + 1][2][128] = {};  // CUtensorMap per plane
   // 256-row boxes of the transposed M2L (dp = 128)
   bool wa_t256[kMaxLevel + 1] = {};
+  // M2L variant per level set by eifmm_autotune (0: built-in rule, 1:
+  // transposed, 2: 128-row, 3: 128-row with a 2-CTA cluster) and the shift of
+  // its offset-group count (groups << shift, or >> -shift)
+  int m2l_kind[kMaxLevel + 1] = {};
+  int m2l_gshift[kMaxLevel + 1] = {};
+  size_t m2l_part_cap = 0;  // floats in m2l_part (levels below the leaves)
+  float* m2l_part_leaf = nullptr;  // partial sums of the leaf level
+  size_t m2l_part_leaf_cap = 0;
   alignas(64) unsigned char tmap2[kMaxLevel + 1][2][128] = {};
   float* m2l_part = nullptr;    // partial M2L sums of the split offset lists
   int* err = nullptr;           // device error word of bounded waits
@@ -147,8 +155,12 @@ struct Workspace {
   size_t host_cap = 0;
   cudaStream_t side = nullptr;  // near field runs here, concurrent with far
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // step 4: the coarse levels run here, concurrent with the leaf level
+  cudaStream_t side2 = nullptr;
+  cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
   cudaEvent_t ev_t[10] = {};
-  cudaEvent_t ev_m2l[kMaxLevel + 2] = {};
+  cudaEvent_t ev_m2l[kMaxLevel + 2] = {};   // start of the M2L launch of level k
+  cudaEvent_t ev_m2le[kMaxLevel + 2] = {};  // and its end (on the stream that ran it)
   cudaEvent_t ev_nf[2] = {};  // the near-field launch on the side stream
   bool evaluated = false;
   float step_ms[20] = {};
@@ -178,6 +190,7 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma,
 eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R,
                           double* fnear, cudaStream_t s, bool accurate);
 eifmm_status build_kd_image(Ops* ops, bool tf32, cudaStream_t s);
+eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, int gshift, cudaStream_t s);
 eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma,
                         int64_t ld_sigma, int R, double* f, int64_t ld_f,
                         cudaStream_t s);

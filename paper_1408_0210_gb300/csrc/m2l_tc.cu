@@ -1003,7 +1003,7 @@ eifmm_status launch_m2l_tma(const M2LTcArgs& a0, const void* map0, const void* m
   }
   const CUtensorMap& m0 = *(const CUtensorMap*)map0;
   const CUtensorMap& m1 = *(const CUtensorMap*)map1;
-  int cn = m2l_cluster_env();
+  int cn = a0.cluster > 0 ? a0.cluster : m2l_cluster_env();
   while (cn > 1 && tiles < cn) cn >>= 1;
   bool ran = false;
   if (cn > 1) {

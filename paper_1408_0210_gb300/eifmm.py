@@ -25,7 +25,7 @@ EXPORTS = [
     "eifmm_ops_destroy", "eifmm_tree_build", "eifmm_tree_export", "eifmm_tree_destroy",
     "eifmm_evaluate", "eifmm_evaluate_host", "eifmm_evaluate_batched", "eifmm_debug_export",
     "eifmm_set_timing", "eifmm_last_step_times", "eifmm_direct_sum", "eifmm_kernel_launches",
-    "eifmm_tree_sort_static", "eifmm_ops_calibrate",
+    "eifmm_tree_sort_static", "eifmm_ops_calibrate", "eifmm_autotune", "eifmm_measure_rates",
 ]
 
 
@@ -68,6 +68,8 @@ def lib() -> C.CDLL:
         "eifmm_tree_destroy": (None, [vp]),
         "eifmm_evaluate": (i32, [vp, vp, vp, i64, i32, vp, i64, i32, vp]),
         "eifmm_evaluate_host": (i32, [vp, vp, vp, i64, i32, vp, i64, i32, vp]),
+        "eifmm_autotune": (i32, [vp, vp, i32, i32, vp, vp]),
+        "eifmm_measure_rates": (i32, [vp, vp]),
         "eifmm_evaluate_batched": (i32, [vp, vp, vp, i32, vp, i32, vp]),
         "eifmm_debug_export": (i32, [vp, i32, i32, vp, i64]),
         "eifmm_set_timing": (None, [i32]),
@@ -264,6 +266,25 @@ def eifmm_evaluate_batched(trees, sigmas, fs, ops: Ops, prec="fp64", stream=None
     _check(lib().eifmm_evaluate_batched(C.cast(th, C.c_void_p), C.cast(sp, C.c_void_p),
                                         C.cast(fp, C.c_void_p), n, ops.handle, _prec(prec),
                                         _stream(stream)))
+
+
+def eifmm_measure_rates(stream=None) -> dict:
+    """Measured FP32 FMA/s, approximate rsqrt/s and FP64 FMA/s of this GPU."""
+    r = (C.c_double * 3)()
+    _check(lib().eifmm_measure_rates(_stream(stream), C.cast(r, C.c_void_p)))
+    return {"ffma_per_s": r[0], "rsqrt_per_s": r[1], "dfma_per_s": r[2]}
+
+
+M2L_VARIANTS = {0: "rule", 1: "transposed", 2: "128-row", 3: "128-row, 2-CTA cluster"}
+
+
+def eifmm_autotune(tree: Tree, ops: Ops, n_rhs: int = 1, prec="mixed", stream=None) -> dict:
+    """Time the M2L variants per level on this tree and keep the fastest;
+    returns {level: (variant, group shift)}."""
+    ch = (C.c_int * 22)()
+    _check(lib().eifmm_autotune(tree.handle, ops.handle, int(n_rhs), _prec(prec), _stream(stream),
+                                C.cast(ch, C.c_void_p)))
+    return {k: (ch[2 * k], ch[2 * k + 1]) for k in range(2, tree.depth + 1)}
 
 
 def eifmm_debug_export(tree: Tree, what: int, level: int, d: int, R: int = 1):

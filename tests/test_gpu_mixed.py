@@ -153,6 +153,30 @@ def test_m2l_transposed_matches_128_row_kernel(E):
         assert relmax(g["t256"][k], g["128"][k]) <= 2e-5, k
 
 
+def test_autotune_keeps_the_result(E, orc):
+    """The autotuner picks an applicable M2L variant per level; the evaluation
+    with its choice is the same method (another order of the M2L sums)."""
+    n, depth = 150000, 5
+    x = wl.uniform_cube(n, 61)
+    s = wl.sigma_uniform(n, 1, 62)
+    ops = E.eifmm_ops_build("inv_r", 1.0, depth, 1e-4)
+    ops.plan(0)
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    f0 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f0, "mixed")
+    ch = E.eifmm_autotune(tree, ops, 1, "mixed")
+    assert sorted(ch) == [2, 3, 4, 5]
+    assert all(v in E.M2L_VARIANTS and g in (-1, 0, 1) for v, g in ch.values())
+    f1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f1, "mixed")
+    assert rel2(f1.cpu().numpy(), f0.cpu().numpy()) <= 1e-5
+    idx = wl.sample_targets(n, 256, 63)
+    f_exact = orc.direct_sum("inv_r", x, x, s, tgt_idx=idx)[:, 0]
+    assert rel2(f1.cpu().numpy()[idx], f_exact) <= 1e-4
+    # the FP64 path has no tensor-core M2L: nothing to tune
+    assert all(v == (0, 0) for v in E.eifmm_autotune(tree, ops, 1, "fp64").values())
+
+
 @pytest.mark.parametrize("eps,tol", [(1e-5, 1e-5), (1e-6, 1e-6), (1e-7, 1e-7)])
 def test_mixed_tiers_end_to_end(E, orc, eps, tol):
     """Whatever tier the calibration picks, the mixed result meets eps."""
