@@ -178,8 +178,10 @@ static __global__ void __launch_bounds__(256) k_xfer_gemm(XferGemm a) {
     if (more) gload(k0 + 16);
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
-      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
+      // rows m along tx, columns c along ty: a thread's 4 outputs of one
+      // column are 4 consecutive floats of one coefficient row in memory
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][tx * 4]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][kk][ty * 4]);
       const float ar[4] = {a4.x, a4.y, a4.z, a4.w};
       const float br[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
@@ -191,22 +193,28 @@ static __global__ void __launch_bounds__(256) k_xfer_gemm(XferGemm a) {
     __syncthreads();
     buf ^= 1;
   }
+  // float4 stores: 16 lanes write 64 consecutive coefficients of one row
+  const int mb = m0 + tx * 4;
+  if (mb < a.ldk) {
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const int64_t c = c0 + tx * 4 + v;
-    if (c >= a.ncol) continue;
-    const int64_t P = c / a.R;
-    const int r = (int)(c - P * a.R);
-    const int64_t row = a.mode == 0 ? (P * a.R + r) : ((8 * P + i_l2l) * a.R + r);
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int m = m0 + ty * 4 + u;
-      if (m >= a.ldk) continue;
-      const int64_t o = row * a.ldk + m;
+    for (int v = 0; v < 4; ++v) {
+      const int64_t c = c0 + ty * 4 + v;
+      if (c >= a.ncol) continue;
+      const int64_t P = c / a.R;
+      const int r = (int)(c - P * a.R);
+      const int64_t row = a.mode == 0 ? (P * a.R + r) : ((8 * P + i_l2l) * a.R + r);
+      const int64_t o = row * a.ldk + mb;
+      float4 val = make_float4(mb + 0 < a.dk ? acc[0][v] : 0.f, mb + 1 < a.dk ? acc[1][v] : 0.f,
+                               mb + 2 < a.dk ? acc[2][v] : 0.f, mb + 3 < a.dk ? acc[3][v] : 0.f);
       if (a.mode == 0) {
-        a.P8[(int64_t)i_l2l * a.ncol * a.ldk + o] = m < a.dk ? acc[u][v] : 0.f;
+        *reinterpret_cast<float4*>(a.P8 + (int64_t)i_l2l * a.ncol * a.ldk + o) = val;
       } else {
-        a.C[o] = m < a.dk ? a.G[o] + acc[u][v] : 0.f;
+        const float4 g = *reinterpret_cast<const float4*>(a.G + o);
+        val.x = mb + 0 < a.dk ? g.x + val.x : 0.f;
+        val.y = mb + 1 < a.dk ? g.y + val.y : 0.f;
+        val.z = mb + 2 < a.dk ? g.z + val.z : 0.f;
+        val.w = mb + 3 < a.dk ? g.w + val.w : 0.f;
+        *reinterpret_cast<float4*>(a.C + o) = val;
       }
     }
   }
