@@ -228,7 +228,7 @@ void eifmm_tree_destroy(eifmm_tree* tree);
  * caller.  The call synchronises `stream` (it reads back the count of points
  * outside the cube and returns EINVAL if there is any). */
 #define EIFMM_STATIC_SORT_MAX_POINTS 1048576
-#define EIFMM_STATIC_SORT_SCRATCH_BYTES 8913152
+#define EIFMM_STATIC_SORT_SCRATCH_BYTES 8913296
 eifmm_status eifmm_tree_sort_static(const double* xyz, int64_t n,
                                     const double lo[3], double L, int depth,
                                     uint32_t* keys_out, int32_t* perm_out,

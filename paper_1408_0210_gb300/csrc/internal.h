@@ -97,6 +97,7 @@ struct Ops {
 // ------------------------------------------------------------------ tree --
 struct PointSet {
   int64_t n = 0;
+  void* slab = nullptr;         // one device allocation holding every array below
   int32_t* perm = nullptr;      // sorted position -> input index
   uint32_t* keys = nullptr;     // sorted Morton keys
   int32_t* leaf_off = nullptr;  // 8^depth + 1

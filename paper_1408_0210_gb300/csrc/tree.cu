@@ -61,28 +61,82 @@ __global__ void k_rs_count(const uint32_t* __restrict__ keys, int64_t n,
   counts[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// Exclusive scan of `len` counts in one block of 1024 threads.
-__global__ void k_scan_excl(uint32_t* __restrict__ a, int64_t len) {
-  __shared__ uint32_t part[1024];
-  const int t = threadIdx.x;
-  const int64_t chunk = (len + 1023) / 1024;
-  const int64_t b = t * chunk, e = (b + chunk < len) ? b + chunk : len;
-  uint32_t s = 0;
-  for (int64_t i = b; i < e; ++i) s += a[i];
-  part[t] = s;
+// Exclusive scan of the digit-major counts (256 x nblocks entries) in two
+// launches: per-tile totals, then each tile adds the totals of the tiles
+// before it to its own block-wide scan.  A tile is SC_TILE consecutive
+// entries, SC_ITEMS per thread.
+constexpr int SC_THREADS = 1024;
+constexpr int SC_ITEMS = 4;
+constexpr int SC_TILE = SC_THREADS * SC_ITEMS;
+
+inline int64_t scan_tiles(int64_t len) { return (len + SC_TILE - 1) / SC_TILE; }
+
+// Exclusive scan of one value per thread over a block of SC_THREADS threads;
+// *total receives the block's sum.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t ws[SC_THREADS / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();  // ws may still be read by a previous call
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
   __syncthreads();
-  for (int off = 1; off < 1024; off <<= 1) {
-    uint32_t v = (t >= off) ? part[t - off] : 0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
+  if (w == 0) {
+    uint32_t u = ws[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, u, o);
+      if (lane >= o) u += y;
+    }
+    ws[lane] = u;
   }
-  uint32_t run = (t > 0) ? part[t - 1] : 0;
-  for (int64_t i = b; i < e; ++i) {
-    const uint32_t v = a[i];
-    a[i] = run;
-    run += v;
+  __syncthreads();
+  *total = ws[SC_THREADS / 32 - 1];
+  return x - v + (w > 0 ? ws[w - 1] : 0u);
+}
+
+__global__ void __launch_bounds__(SC_THREADS)
+k_scan_totals(const uint32_t* __restrict__ a, int64_t len, uint32_t* __restrict__ part) {
+  const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+  uint32_t s = 0;
+#pragma unroll
+  for (int j = 0; j < SC_ITEMS; ++j)
+    if (base + j < len) s += a[base + j];
+  uint32_t total;
+  block_excl_scan(s, &total);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SC_THREADS)
+k_scan_apply(uint32_t* __restrict__ a, int64_t len, const uint32_t* __restrict__ part) {
+  uint32_t pre = 0;
+  for (int j = threadIdx.x; j < (int)blockIdx.x; j += SC_THREADS) pre += part[j];
+  uint32_t before;
+  block_excl_scan(pre, &before);
+  const int64_t base = (int64_t)blockIdx.x * SC_TILE + (int64_t)threadIdx.x * SC_ITEMS;
+  uint32_t v[SC_ITEMS], s = 0;
+#pragma unroll
+  for (int j = 0; j < SC_ITEMS; ++j) {
+    v[j] = base + j < len ? a[base + j] : 0u;
+    s += v[j];
   }
+  uint32_t total;
+  uint32_t run = before + block_excl_scan(s, &total);
+#pragma unroll
+  for (int j = 0; j < SC_ITEMS; ++j) {
+    if (base + j < len) a[base + j] = run;
+    run += v[j];
+  }
+}
+
+void launch_scan(uint32_t* counts, int64_t len, uint32_t* part, cudaStream_t s) {
+  const unsigned nt = (unsigned)scan_tiles(len);
+  k_scan_totals<<<nt, SC_THREADS, 0, s>>>(counts, len, part);
+  k_scan_apply<<<nt, SC_THREADS, 0, s>>>(counts, len, part);
 }
 
 __global__ void __launch_bounds__(RS_THREADS)
@@ -178,26 +232,39 @@ eifmm_status build_pointset(const double* xyz, int64_t n, const double lo[3],
   ps->n = n;
   const int64_t nleaf = (int64_t)1 << (3 * depth);
   const int64_t nn = n > 0 ? n : 1;
-  EIFMM_TRY(dalloc(&ps->perm, nn));
-  EIFMM_TRY(dalloc(&ps->keys, nn));
-  EIFMM_TRY(dalloc(&ps->leaf_off, nleaf + 1));
-  EIFMM_TRY(dalloc(&ps->nonempty, nleaf));
-  EIFMM_TRY(dalloc(&ps->x, nn));
-  EIFMM_TRY(dalloc(&ps->y, nn));
-  EIFMM_TRY(dalloc(&ps->z, nn));
-  EIFMM_TRY(dalloc(&ps->lx, nn));
-  EIFMM_TRY(dalloc(&ps->ly, nn));
-  EIFMM_TRY(dalloc(&ps->lz, nn));
+  // one slab for the point set, one for the sort's scratch (256-byte aligned parts)
+  auto take = [](size_t& off, size_t bytes) { const size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+  size_t off = 0;
+  const size_t o_perm = take(off, nn * 4), o_keys = take(off, nn * 4), o_loff = take(off, (nleaf + 1) * 4),
+               o_ne = take(off, nleaf * 4), o_x = take(off, nn * 8), o_y = take(off, nn * 8),
+               o_z = take(off, nn * 8), o_lx = take(off, nn * 4), o_ly = take(off, nn * 4),
+               o_lz = take(off, nn * 4);
+  unsigned char* slab = nullptr;
+  EIFMM_TRY(dalloc(&slab, off));
+  ps->slab = slab;
+  ps->perm = (int32_t*)(slab + o_perm);
+  ps->keys = (uint32_t*)(slab + o_keys);
+  ps->leaf_off = (int32_t*)(slab + o_loff);
+  ps->nonempty = (int32_t*)(slab + o_ne);
+  ps->x = (double*)(slab + o_x);
+  ps->y = (double*)(slab + o_y);
+  ps->z = (double*)(slab + o_z);
+  ps->lx = (float*)(slab + o_lx);
+  ps->ly = (float*)(slab + o_ly);
+  ps->lz = (float*)(slab + o_lz);
 
-  uint32_t *k2 = nullptr, *counts = nullptr;
-  int32_t* v2 = nullptr;
-  int* dbad = nullptr;
   const int nblocks = (int)((n + RS_TILE - 1) / RS_TILE);
   const int nb1 = nblocks > 0 ? nblocks : 1;
-  EIFMM_TRY(dalloc(&k2, nn));
-  EIFMM_TRY(dalloc(&v2, nn));
-  EIFMM_TRY(dalloc(&counts, (size_t)256 * nb1));
-  EIFMM_TRY(dalloc(&dbad, 2));
+  size_t soff = 0;
+  const size_t o_k2 = take(soff, nn * 4), o_v2 = take(soff, nn * 4), o_cnt = take(soff, (size_t)256 * nb1 * 4),
+               o_part = take(soff, scan_tiles((int64_t)256 * nb1) * 4), o_bad = take(soff, 2 * sizeof(int));
+  unsigned char* scratch = nullptr;
+  EIFMM_TRY(dalloc(&scratch, soff));
+  uint32_t* k2 = (uint32_t*)(scratch + o_k2);
+  int32_t* v2 = (int32_t*)(scratch + o_v2);
+  uint32_t* counts = (uint32_t*)(scratch + o_cnt);
+  uint32_t* parts = (uint32_t*)(scratch + o_part);
+  int* dbad = (int*)(scratch + o_bad);
   EIFMM_CUDA(cudaMemsetAsync(dbad, 0, 2 * sizeof(int), s));
 
   const double scale = ldexp(1.0, depth) / L;
@@ -214,7 +281,7 @@ eifmm_status build_pointset(const double* xyz, int64_t n, const double lo[3],
     for (int shift = 0; shift < bits; shift += 8) {
       k_rs_count<<<nblocks, RS_THREADS, 0, s>>>(kin, n, shift, counts, nblocks);
       EIFMM_CHECK_LAUNCH();
-      k_scan_excl<<<1, 1024, 0, s>>>(counts, (int64_t)256 * nblocks);
+      launch_scan(counts, (int64_t)256 * nblocks, parts, s);
       EIFMM_CHECK_LAUNCH();
       k_rs_scatter<<<nblocks, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift,
                                                    counts, nblocks);
@@ -241,10 +308,7 @@ eifmm_status build_pointset(const double* xyz, int64_t n, const double lo[3],
   int hb[2] = {0, 0};
   EIFMM_CUDA(cudaMemcpyAsync(hb, dbad, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   EIFMM_CUDA(cudaStreamSynchronize(s));
-  dfree(k2);
-  dfree(v2);
-  dfree(counts);
-  dfree(dbad);
+  dfree(scratch);
   ps->n_nonempty = hb[1];
   if (hb[0] != 0) {
     set_error("eifmm_tree_build: " + std::to_string(hb[0]) +
@@ -255,16 +319,7 @@ eifmm_status build_pointset(const double* xyz, int64_t n, const double lo[3],
 }
 
 void free_pointset(PointSet* ps) {
-  dfree(ps->perm);
-  dfree(ps->keys);
-  dfree(ps->leaf_off);
-  dfree(ps->nonempty);
-  dfree(ps->x);
-  dfree(ps->y);
-  dfree(ps->z);
-  dfree(ps->lx);
-  dfree(ps->ly);
-  dfree(ps->lz);
+  dfree(ps->slab);
   *ps = PointSet();
 }
 
@@ -283,7 +338,8 @@ constexpr int64_t kStaticBlocks = (kStaticMax + RS_TILE - 1) / RS_TILE;
 constexpr size_t kOffKeys = 0;
 constexpr size_t kOffVals = kOffKeys + (size_t)kStaticMax * 4;
 constexpr size_t kOffCounts = kOffVals + (size_t)kStaticMax * 4;
-constexpr size_t kOffBad = kOffCounts + (size_t)256 * kStaticBlocks * 4;
+constexpr size_t kOffParts = kOffCounts + (size_t)256 * kStaticBlocks * 4;
+constexpr size_t kOffBad = kOffParts + (((size_t)256 * kStaticBlocks + SC_TILE - 1) / SC_TILE) * 4 + 16;
 constexpr size_t kStaticBytes = kOffBad + 256;
 static_assert(kStaticBytes == EIFMM_STATIC_SORT_SCRATCH_BYTES, "scratch size of the header");
 
@@ -341,6 +397,7 @@ extern "C" eifmm_status eifmm_tree_sort_static(const double* xyz, int64_t n, con
   uint32_t* k2 = (uint32_t*)(base + kOffKeys);
   int32_t* v2 = (int32_t*)(base + kOffVals);
   uint32_t* counts = (uint32_t*)(base + kOffCounts);
+  uint32_t* parts = (uint32_t*)(base + kOffParts);
   int* bad = (int*)(base + kOffBad);
   // the error counter must start at zero on every call
   EIFMM_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), s));
@@ -358,7 +415,7 @@ extern "C" eifmm_status eifmm_tree_sort_static(const double* xyz, int64_t n, con
     for (int shift = 0; shift < 3 * depth; shift += 8) {
       k_rs_count<<<nblocks, RS_THREADS, 0, s>>>(kin, n, shift, counts, nblocks);
       EIFMM_CHECK_LAUNCH();
-      k_scan_excl<<<1, 1024, 0, s>>>(counts, (int64_t)256 * nblocks);
+      launch_scan(counts, (int64_t)256 * nblocks, parts, s);
       EIFMM_CHECK_LAUNCH();
       k_rs_scatter<<<nblocks, RS_THREADS, 0, s>>>(kin, vin, kout, vout, n, shift, counts, nblocks);
       EIFMM_CHECK_LAUNCH();
