@@ -73,7 +73,8 @@ class _Dump(C.Structure):
 
 class _Level(C.Structure):
     _fields_ = [("d", C.c_int), ("X", C.c_void_p), ("Y", C.c_void_p),
-                ("Gamma", C.c_void_p), ("B", C.c_void_p)]
+                ("Gamma", C.c_void_p), ("B", C.c_void_p), ("r", C.c_int),
+                ("U", C.c_void_p)]
 
 
 def lib():
@@ -104,6 +105,8 @@ def lib():
         L.orc_eifmm.restype = i32
         L.orc_eifmm.argtypes = [i32, dbl, vp, i32, vp, vp, i64, vp, i64, vp, i64,
                                 i32, i32, vp, i64, vp]
+        L.orc_m2l_operators.restype = i64
+        L.orc_m2l_operators.argtypes = [i32, dbl, i32, i32, vp, vp]
         L.orc_interaction_list.restype = i32
         L.orc_interaction_list.argtypes = [i32, i64, vp]
         L.orc_neighbours.restype = i32
@@ -210,6 +213,52 @@ def build_levels(kern, L, depth, eps, d_max=512) -> dict:
             for k in range(2, depth + 1)}
 
 
+def m2l_operators(kern, L, k, level) -> np.ndarray:
+    """K^delta of level k for the 343 offsets (Eq. M2Lstep), [343][d][d];
+    zero for the 27 neighbourhood offsets."""
+    d = level["d"]
+    Y = np.ascontiguousarray(level["Y"], dtype=np.float64)
+    Kd = np.zeros((343, d, d))
+    lib().orc_m2l_operators(_kid(kern), float(L), int(k), int(d), _p(Y), _p(Kd))
+    return Kd
+
+
+FAR_SLOTS = [t for t in range(343)
+             if max(abs(t % 7 - 3), abs((t // 7) % 7 - 3), abs(t // 49 - 3)) > 1]
+
+
+def sarcmp_rank(s, eps) -> tuple:
+    """The two filters of Section 4.2 on singular values s (descending):
+    (i) the values with s_j / s_0 above eps, (ii) the shortest leading run
+    whose sum reaches (1 - eps) of the total.  Returns (r_i, r_ii)."""
+    s = np.asarray(s, dtype=np.float64)
+    r1 = int(np.count_nonzero(s / s[0] > eps))
+    c = np.cumsum(s)
+    r2 = int(np.searchsorted(c, (1.0 - eps) * c[-1], side="left")) + 1
+    return r1, min(r2, len(s))
+
+
+def sarcmp_basis(kern, L, k, level, eps, r=None) -> dict:
+    """First stage of the M2L compression of Section 4.2 for level k.
+
+    K_fat = [K^delta_1 ... K^delta_316] (d x 316 d).  Its truncated SVD
+    (what the bivariate ACA + QR + SVD of the paper computes, taken here
+    directly by a library SVD) gives the basis U (d x r) of kept left
+    singular vectors; r is the larger of the two filters' counts (the kept
+    values satisfy both criteria) unless given.  Keeping only the smaller
+    count misses the configured accuracy (1.7e-4 against the exact sum at
+    eps = 1e-4 on 32,768 uniform points, depth 4, against 1.6e-5 here).
+    For the even kernels of this library K^{-delta} = (K^delta)^t, so U
+    also spans the row space (the symmetric case the paper details)."""
+    Kd = m2l_operators(kern, L, k, level)
+    Kfat = np.hstack([Kd[t] for t in FAR_SLOTS])
+    Uf, s, _ = np.linalg.svd(Kfat, full_matrices=False)
+    r1, r2 = sarcmp_rank(s, eps)
+    if r is None:
+        r = max(r1, r2)
+    return dict(U=np.ascontiguousarray(Uf[:, :r]), r=int(r), s=s, r_i=r1, r_ii=r2)
+
+
 def apply_delta(Gamma, B, v, transpose=False):
     v = np.array(v, dtype=np.float64, copy=True)
     G = np.ascontiguousarray(Gamma, dtype=np.float64)
@@ -234,7 +283,13 @@ def eifmm(kern, L, lo, depth, levels, tgt, src, sigma, exclude_self=True,
         e = levels[k]
         arrs = [np.ascontiguousarray(e[n], dtype=np.float64) for n in ("X", "Y", "Gamma", "B")]
         keep += arrs
-        lv[k] = _Level(e["d"], *[a.ctypes.data for a in arrs])
+        U = e.get("U")
+        if U is not None:
+            U = np.ascontiguousarray(U, dtype=np.float64)
+            assert U.shape[0] == e["d"]
+            keep.append(U)
+        lv[k] = _Level(e["d"], *[a.ctypes.data for a in arrs], 0 if U is None else U.shape[1],
+                       None if U is None else U.ctypes.data)
     f = np.zeros((len(tgt), R), order="F")
     dm = None
     out = {}

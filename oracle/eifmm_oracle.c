@@ -421,6 +421,28 @@ static int in_I0(const double z[3], double l, double L) {
   return m >= 3.0 * l * (1.0 - 1e-12) && m <= (L - l) * (1.0 + 1e-12);
 }
 
+int64_t orc_m2l_operators(int kern, double L, int k, int d, const double* Y, double* Kd) {
+  const double lk = half_width(L, k);
+  int64_t viol = 0;
+  memset(Kd, 0, sizeof(double) * (size_t)(343 * d * d));
+  for (int t = 0; t < 343; ++t) {
+    const int dx = t % 7 - 3, dy = (t / 7) % 7 - 3, dz = t / 49 - 3;
+    if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) continue;
+    const double dl[3] = {2.0 * dx * lk, 2.0 * dy * lk, 2.0 * dz * lk};
+    for (int mp = 0; mp < d; ++mp) {
+      const double* x = Y + 3 * mp;
+      const double xm[3] = {x[0] - dl[0], x[1] - dl[1], x[2] - dl[2]};
+      if (!in_I0(xm, lk, L)) ++viol;
+      for (int l = 0; l < d; ++l) {
+        const double* y = Y + 3 * l;
+        const double ys[3] = {y[0] + dl[0], y[1] + dl[1], y[2] + dl[2]};
+        Kd[((int64_t)t * d + mp) * d + l] = kxy(kern, x, ys);
+      }
+    }
+  }
+  return viol;
+}
+
 int orc_eifmm(int kern, double L, const double lo[3], int depth,
               const orc_level* lv, const double* tgt, int64_t nt,
               const double* src, int64_t ns, const double* sigma,
@@ -533,20 +555,73 @@ int orc_eifmm(int kern, double L, const double lo[3], int depth,
     const int d = lv[k].d;
     const double lk = half_width(L, k);
     double* Kd = (double*)malloc(sizeof(double) * (size_t)(343 * d * d) + 8);
-    for (int t = 0; t < 343; ++t) {
-      const int dx = t % 7 - 3, dy = (t / 7) % 7 - 3, dz = t / 49 - 3;
-      if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) continue;
-      const double dl[3] = {2.0 * dx * lk, 2.0 * dy * lk, 2.0 * dz * lk};
-      for (int mp = 0; mp < d; ++mp) {
-        const double* x = lv[k].Y + 3 * mp;
-        const double xm[3] = {x[0] - dl[0], x[1] - dl[1], x[2] - dl[2]};
-        if (!in_I0(xm, lk, L)) ++viol;
-        for (int l = 0; l < d; ++l) {
-          const double* y = lv[k].Y + 3 * l;
-          const double ys[3] = {y[0] + dl[0], y[1] + dl[1], y[2] + dl[2]};
-          Kd[((int64_t)t * d + mp) * d + l] = kxy(kern, x, ys);
+    viol += orc_m2l_operators(kern, L, k, d, lv[k].Y, Kd);
+    const int r = lv[k].r;
+    if (r > 0) {
+      /* Section 4.2: K^delta ~ U C^delta U^t with C^delta = U^t K^delta U, so
+       * g^I = U sum_J C^delta (U^t What^J). */
+      const double* U = lv[k].U;
+      double* Cd = (double*)malloc(sizeof(double) * (size_t)(343 * r * r) + 8);
+      double* KU = (double*)malloc(sizeof(double) * (size_t)(d * r) + 8);
+      for (int t = 0; t < 343; ++t) {
+        const int dx = t % 7 - 3, dy = (t / 7) % 7 - 3, dz = t / 49 - 3;
+        if (abs(dx) <= 1 && abs(dy) <= 1 && abs(dz) <= 1) continue;
+        const double* K = Kd + (int64_t)t * d * d;
+        for (int mp = 0; mp < d; ++mp) /* K^delta U */
+          for (int q = 0; q < r; ++q) {
+            double s = 0.0;
+            for (int l = 0; l < d; ++l) s += K[(int64_t)mp * d + l] * U[(int64_t)l * r + q];
+            KU[(int64_t)mp * r + q] = s;
+          }
+        for (int qp = 0; qp < r; ++qp) /* U^t (K^delta U) */
+          for (int q = 0; q < r; ++q) {
+            double s = 0.0;
+            for (int mp = 0; mp < d; ++mp) s += U[(int64_t)mp * r + qp] * KU[(int64_t)mp * r + q];
+            Cd[((int64_t)t * r + qp) * r + q] = s;
+          }
+      }
+      double* wt = (double*)malloc(sizeof(double) * (size_t)(nb[k] * R * r) + 8);
+      int64_t J;
+#pragma omp parallel for schedule(static)
+      for (J = 0; J < nb[k] * R; ++J) /* w~ = U^t What */
+        for (int q = 0; q < r; ++q) {
+          double s = 0.0;
+          for (int l = 0; l < d; ++l) s += U[(int64_t)l * r + q] * Wh[k][J * d + l];
+          wt[J * r + q] = s;
+        }
+      int64_t I;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : m2l_pairs)
+      for (I = 0; I < nb[k]; ++I) {
+        int64_t lst[189], ci[3], cj[3];
+        const int n = orc_interaction_list(k, I, lst);
+        demorton3(I, k, ci);
+        m2l_pairs += n;
+        double gt[r];
+        for (int rr = 0; rr < R; ++rr) {
+          for (int qp = 0; qp < r; ++qp) gt[qp] = 0.0;
+          for (int e = 0; e < n; ++e) {
+            const int64_t Jb = lst[e];
+            demorton3(Jb, k, cj);
+            const int t = (int)((cj[0] - ci[0] + 3) + 7 * (cj[1] - ci[1] + 3) + 49 * (cj[2] - ci[2] + 3));
+            for (int qp = 0; qp < r; ++qp) {
+              double s = 0.0;
+              const double* row = Cd + ((int64_t)t * r + qp) * r;
+              for (int q = 0; q < r; ++q) s += row[q] * wt[(Jb * R + rr) * r + q];
+              gt[qp] += s;
+            }
+          }
+          for (int mp = 0; mp < d; ++mp) { /* g = U g~ */
+            double s = 0.0;
+            for (int qp = 0; qp < r; ++qp) s += U[(int64_t)mp * r + qp] * gt[qp];
+            g[k][(I * R + rr) * d + mp] += s;
+          }
         }
       }
+      free(wt);
+      free(KU);
+      free(Cd);
+      free(Kd);
+      continue;
     }
     int64_t I;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : m2l_pairs)

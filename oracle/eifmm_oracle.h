@@ -101,7 +101,21 @@ typedef struct {
   const double* Y;      /* d x 3: y_l^{J_0^k} (= x_l^{J_0^k})          */
   const double* Gamma;  /* d x d row-major, lower triangular          */
   const double* B;      /* d x d row-major, unit lower triangular     */
+  /* Optional M2L compression (Section 4.2, first stage): r > 0 columns of
+   * U (d x r row-major, orthonormal), the kept left singular vectors of
+   * K_fat = [K^delta_1 ... K^delta_316].  Step 4 then applies
+   * C^delta = U^t K^delta U of size r x r between the projections
+   * w~ = U^t What and g = U g~.  r = 0: the full d x d M2L. */
+  int r;
+  const double* U;
 } orc_level;
+
+/* The M2L operators of level k (Eq. M2Lstep): Kd[t][m'][l] =
+ * K(x_{m'}^{J_0^k}, y_l^{J_0^k} + delta_t) for the 343 offsets
+ * t = (dx+3) + 7 (dy+3) + 49 (dz+3), delta_t = 2 l_k (dx, dy, dz); zero for
+ * the 27 offsets of the neighbourhood.  Y (d x 3) holds the interpolation
+ * points.  Returns the count of shifted points outside I_0. */
+int64_t orc_m2l_operators(int kern, double L, int k, int d, const double* Y, double* Kd);
 
 /* Optional intermediate results, canonical layout [box][rhs][m] with the
  * box index in Morton order at its level; any pointer may be NULL. */

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "solve.cuh"
 
 namespace eifmm {
 
@@ -844,6 +845,15 @@ extern "C" eifmm_status eifmm_debug_export(const eifmm_tree* tree, int what, int
     return EIFMM_EINVAL;
   }
   if (ws.W[level] == nullptr && ws.lh == nullptr) return export_mixed(t, o, what, level, out, n);
+  if (what == 1) {
+    // What = Delta W (the evaluation applies K^delta Delta to W instead)
+    DeltaBatch b;
+    b.nlev = 1;
+    b.lv[0] = delta_level(d, delta_ops64(o.lv[level]), false, ws.W[level], d, ws.Wh[level], d, nullptr,
+                          ((int64_t)1 << (3 * level)) * R);
+    EIFMM_TRY((launch_delta_batch<double, double, double, 0>(b, false, 0)));
+    EIFMM_CUDA(cudaDeviceSynchronize());
+  }
   const double* src = what == 0 ? ws.W[level] : what == 1 ? ws.Wh[level] : what == 2 ? ws.g[level]
                      : what == 3 ? ws.l[level] : ws.lh;
   EIFMM_CUDA(cudaMemcpy(out, src, cnt * sizeof(double), cudaMemcpyDeviceToHost));

@@ -371,22 +371,59 @@ __global__ void k_build_img(const double* __restrict__ kdT, int d, int dp, int t
 }
 
 // planes -> FP64 [row][d] (debug export of What)
-__global__ void k_planes_to_f64(const void* __restrict__ planes, int tf32, int64_t nvec, int d, int dp,
-                                int grid_level, int R, double* __restrict__ out) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nvec * d;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v0 = t / d;
-    const int j = (int)(t - v0 * d);
-    const int64_t v = plane_row(v0, grid_level, R);
-    double x;
-    if (tf32) {
-      const float* p = (const float*)planes;
-      x = (double)p[v * dp + j] + (double)p[nvec * dp + v * dp + j];
-    } else {
-      const __nv_bfloat16* p = (const __nv_bfloat16*)planes;
-      x = (double)__bfloat162float(p[v * dp + j]) + (double)__bfloat162float(p[nvec * dp + v * dp + j]);
+// The M2L operand planes of W (hi and lo parts, BF16 or TF32) at every
+// level in one launch; entries j >= d are zero.  One thread per 4
+// consecutive entries (dp is a multiple of 64, so a quad never straddles a
+// row).
+struct PlaneLevel {
+  const float* in;  // [rows][dp]
+  void* out;        // [2][rows][dp] at plane_row order
+  int64_t rows, q0; // q0: first quad of this level in the launch
+  int d, dp, grid_level, R;
+};
+struct PlaneBatch {
+  PlaneLevel lv[kMaxLevel + 1];
+  int nlev = 0;
+  int64_t nq = 0;
+};
+
+template <bool TF32>
+__global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneBatch b) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < b.nq;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int li = 0;
+    while (li + 1 < b.nlev && q >= b.lv[li + 1].q0) ++li;
+    const PlaneLevel& L = b.lv[li];
+    const int64_t e = (q - L.q0) * 4;
+    const int64_t v = e / L.dp;
+    const int j = (int)(e - v * L.dp);
+    float4 x = *reinterpret_cast<const float4*>(L.in + e);
+    if (j + 4 > L.d) {
+      if (j + 0 >= L.d) x.x = 0.f;
+      if (j + 1 >= L.d) x.y = 0.f;
+      if (j + 2 >= L.d) x.z = 0.f;
+      if (j + 3 >= L.d) x.w = 0.f;
     }
-    out[t] = x;
+    const int64_t o = plane_row(v, L.grid_level, L.R) * L.dp + j;
+    const int64_t lo_off = L.rows * L.dp;
+    if (TF32) {
+      const float4 h = make_float4(tf32_rn(x.x), tf32_rn(x.y), tf32_rn(x.z), tf32_rn(x.w));
+      const float4 l = make_float4(tf32_rn(x.x - h.x), tf32_rn(x.y - h.y), tf32_rn(x.z - h.z), tf32_rn(x.w - h.w));
+      float* p = (float*)L.out;
+      *reinterpret_cast<float4*>(p + o) = h;
+      *reinterpret_cast<float4*>(p + lo_off + o) = l;
+    } else {
+      const __nv_bfloat162 h01 = __floats2bfloat162_rn(x.x, x.y), h23 = __floats2bfloat162_rn(x.z, x.w);
+      const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
+      const __nv_bfloat162 l01 = __floats2bfloat162_rn(x.x - f01.x, x.y - f01.y);
+      const __nv_bfloat162 l23 = __floats2bfloat162_rn(x.z - f23.x, x.w - f23.y);
+      __nv_bfloat16* p = (__nv_bfloat16*)L.out;
+      uint2 hv, lv;
+      hv.x = *reinterpret_cast<const uint32_t*>(&h01); hv.y = *reinterpret_cast<const uint32_t*>(&h23);
+      lv.x = *reinterpret_cast<const uint32_t*>(&l01); lv.y = *reinterpret_cast<const uint32_t*>(&l23);
+      *reinterpret_cast<uint2*>(p + o) = hv;
+      *reinterpret_cast<uint2*>(p + lo_off + o) = lv;
+    }
   }
 }
 
@@ -654,20 +691,22 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     EIFMM_TRY(launch_xfer_gemm(x, s));
   }
   record(ws, 2, s);
-  // step 3: What = Delta W (Gamma z = W, then B^t What = z), written as the
-  // two M2L operand planes
+  // step 3: What = Delta W is folded into the M2L operator (K^delta Delta,
+  // built with the operators), so the M2L reads the planes of W itself
   {
-    DeltaBatch b;
+    PlaneBatch b;
     for (int k = 2; k <= kap; ++k) {
       const LevelOps& v = ops->lv[k];
-      const int gl = ws.wa_grid[k] ? k : -1;
-      b.lv[b.nlev++] = tf32 ? delta_level(v.d, delta_ops64(v), false, ws.W32[k], v.dp, nullptr, v.dp, ws.wa[k],
-                                          nboxes(k) * R, gl, R)
-                            : delta_level(v.d, delta_ops32(v), false, ws.W32[k], v.dp, nullptr, v.dp, ws.wa[k],
-                                          nboxes(k) * R, gl, R);
+      PlaneLevel& L = b.lv[b.nlev++];
+      L.in = ws.W32[k]; L.out = ws.wa[k];
+      L.rows = nboxes(k) * R; L.q0 = b.nq;
+      L.d = v.d; L.dp = v.dp; L.grid_level = ws.wa_grid[k] ? k : -1; L.R = R;
+      b.nq += L.rows * v.dp / 4;
     }
-    if (tf32) EIFMM_TRY((launch_delta_batch<double, float, float, 2>(b, false, s)));
-    else EIFMM_TRY((launch_delta_batch<float, float, float, 1>(b, false, s)));
+    const unsigned g = grid_for(b.nq, 256, 152 * 16);
+    if (tf32) k_planes<true><<<g, 256, 0, s>>>(b);
+    else k_planes<false><<<g, 256, 0, s>>>(b);
+    EIFMM_CHECK_LAUNCH();
   }
   record(ws, 3, s);
   // step 4: the levels are independent.  The coarse levels run on a second
@@ -757,8 +796,17 @@ eifmm_status export_mixed(const Tree& t, const Ops& o, int what, int level, doub
   double* tmp = nullptr;
   EIFMM_TRY(dalloc(&tmp, cnt));
   if (what == 1) {
-    k_planes_to_f64<<<grid_for(cnt, 256), 256>>>(ws.wa[level], ws.tier == 1, nvec, v.d, v.dp,
-                                                 ws.wa_grid[level] ? level : -1, ws.nrhs, tmp);
+    // What = Delta W, from the FP32 W of the evaluation (FP64 solves)
+    k_f32_to_f64<<<grid_for(cnt, 256), 256>>>(ws.W32[level], nvec, v.d, v.dp, tmp);
+    EIFMM_CHECK_LAUNCH();
+    DeltaBatch b;
+    b.nlev = 1;
+    b.lv[0] = delta_level(v.d, delta_ops64(v), false, tmp, v.d, tmp, v.d, nullptr, nvec);
+    const eifmm_status rc = launch_delta_batch<double, double, double, 0>(b, false, 0);
+    if (rc != EIFMM_OK) {
+      dfree(tmp);
+      return rc;
+    }
   } else {
     const float* src = what == 0 ? ws.W32[level] : what == 2 ? ws.g32[level] : what == 3 ? ws.l32[level] : ws.lh32;
     k_f32_to_f64<<<grid_for(cnt, 256), 256>>>(src, nvec, v.d, v.dp, tmp);

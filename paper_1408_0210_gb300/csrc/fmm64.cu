@@ -369,14 +369,9 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
     EIFMM_CHECK_LAUNCH();
   }
   record(ws, 2, s);
-  // step 3
-  {
-    DeltaBatch b;
-    for (int k = 2; k <= kap; ++k)
-      b.lv[b.nlev++] = delta_level(ops->lv[k].d, delta_ops64(ops->lv[k]), false, ws.W[k], ops->lv[k].d,
-                                   ws.Wh[k], ops->lv[k].d, nullptr, ((int64_t)1 << (3 * k)) * R);
-    EIFMM_TRY((launch_delta_batch<double, double, double, 0>(b, false, s)));
-  }
+  // step 3: What = Delta W is folded into the M2L operator (kdT holds
+  // K^delta Delta), so step 4 reads W; What itself is formed only when it is
+  // exported
   record(ws, 3, s);
   // step 4
   for (int k = 2; k <= kap; ++k) {
@@ -384,7 +379,7 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
     const int d = ops->lv[k].d;
     const int64_t nb = (int64_t)1 << (3 * k);
     k_m2l64<<<dim3((unsigned)(nb / 8 / M2L_NB * 8), R), TPB, M2L_NB * d * sizeof(double), s>>>(
-        k, d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.Wh[k], ws.g[k]);
+        k, d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.W[k], ws.g[k]);
     EIFMM_CHECK_LAUNCH();
     if (timing_enabled()) cudaEventRecord(ws.ev_m2le[k], s);
   }

@@ -62,7 +62,7 @@ struct LevelOps {
   double* B_rm = nullptr;  // B row-major
   double* m2mT = nullptr;  // [8][q < d_{k+1}][m < d]: (K_M2M^i)^t, levels 2..depth-1
   double* l2lT = nullptr;  // [8][q' < d_{k-1}][m' < d]: (K_L2L^i)^t, levels 3..depth
-  double* kdT = nullptr;   // [343][l < d][m' < d]: K^delta_{m'l}
+  double* kdT = nullptr;   // [343][l < d][m' < d]: (K^delta Delta)_{m'l}, applied to W
   double* m2m = nullptr;   // [8][m < d][q < d_{k+1}]: K_M2M^i row-major
   double* l2l = nullptr;   // [8][m' < d][q' < d_{k-1}]: K_L2L^i row-major
   float* m2m32 = nullptr;

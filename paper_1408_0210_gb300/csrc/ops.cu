@@ -108,6 +108,17 @@ __global__ void k_build_kd(int kern, int d, double lk, const double* __restrict_
   }
 }
 
+// Per-slot transpose of a [slot][d][d] stack: out[s][j][i] = in[s][i][j].
+__global__ void k_transpose_slots(const double* __restrict__ in, int d, double* __restrict__ out) {
+  const int64_t slot = blockIdx.y;
+  const double* a = in + slot * d * d;
+  double* b = out + slot * d * d;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d * d; t += gridDim.x * blockDim.x) {
+    const int i = t / d, j = t - i * d;
+    b[(int64_t)j * d + i] = a[t];
+  }
+}
+
 // Tiles of one lower-triangular solve operator L' (layout in solve.cuh):
 // L'[a][b] = M[p][q] with (p, q) = (a, b), or (dpad-1-a, dpad-1-b) when
 // `rev`; `transpose` reads M[q][p].  Entries beyond d are those of the
@@ -207,6 +218,30 @@ eifmm_status assemble_ops(Ops* ops, cudaStream_t s) {
           src[o], v.d, nb, trans[o], rev[o], v.dt64[o], v.dt32[o], piv[o] >= 0 ? v.piv64[piv[o]] : nullptr,
           piv[o] >= 0 ? v.piv32[piv[o]] : nullptr);
       EIFMM_CHECK_LAUNCH();
+    }
+    // The M2L operator applied to W: K^delta Delta (Steps 3 and 4 together,
+    // g = sum_J K^delta (Delta W^J)).  Row m' of K^delta Delta is Delta^t
+    // applied to row m' of K^delta, so the product comes from the FP64
+    // triangular solves, never from an explicit inverse.  kdT is
+    // overwritten with it, same layout.
+    {
+      double* rows = nullptr;
+      EIFMM_TRY(dalloc(&rows, (size_t)kNumSlots * v.d * v.d));
+      const dim3 tg((v.d * v.d + 255) / 256 < 64 ? (v.d * v.d + 255) / 256 : 64, kNumSlots);
+      k_transpose_slots<<<tg, 256, 0, s>>>(v.kdT, v.d, rows);  // rows[slot][m'][l] = K^delta_{m'l}
+      EIFMM_CHECK_LAUNCH();
+      DeltaBatch b;
+      b.nlev = 1;
+      b.lv[0] = delta_level(v.d, delta_ops64(v), true, rows, v.d, rows, v.d, nullptr,
+                            (int64_t)kNumSlots * v.d);
+      eifmm_status rc = launch_delta_batch<double, double, double, 0>(b, true, s);
+      if (rc == EIFMM_OK) {
+        k_transpose_slots<<<tg, 256, 0, s>>>(rows, v.d, v.kdT);
+        if (cudaGetLastError() != cudaSuccess) rc = EIFMM_ECUDA;
+      }
+      EIFMM_CUDA(cudaStreamSynchronize(s));
+      dfree(rows);
+      if (rc != EIFMM_OK) return rc;
     }
   }
   // slot lists of the 8 parity classes: offsets o in {-2..3} for an even

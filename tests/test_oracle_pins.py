@@ -400,3 +400,112 @@ def test_sphere_points_on_surface():
     x = wl.sphere_surface(1000, 3)
     r = np.linalg.norm(x - 0.5, axis=1)
     assert np.abs(r - 0.5).max() < 1e-12 and (x >= 0).all() and (x <= 1).all()
+
+
+# --------------------------------------------------------------------------
+# M2L compression, Section 4.2 (first stage), and the operator K^delta Delta
+# --------------------------------------------------------------------------
+def _filters_by_definition(s, eps):
+    """The two filters written as the inequalities that define them: (i) j
+    with s_j / s_0 <= eps <= s_{j-1} / s_0 (0-based: the first value at or
+    below eps is s_j, so j values are kept); (ii) the j with
+    sum_{i<=j} s_i >= (1 - eps) sum s >= sum_{i<=j-1} s_i (1-based)."""
+    n = len(s)
+    r1 = n
+    for j in range(1, n):
+        if s[j] / s[0] <= eps <= s[j - 1] / s[0]:
+            r1 = j
+            break
+    tot = math.fsum(s)
+    r2 = n
+    for j in range(1, n + 1):
+        if math.fsum(s[:j]) >= (1 - eps) * tot >= math.fsum(s[:j - 1]):
+            r2 = j
+            break
+    return r1, r2
+
+
+@pytest.mark.parametrize("spec", ["geometric", "plateau", "cliff"])
+def test_sarcmp_filters_match_their_definition(orc, spec):
+    if spec == "geometric":
+        s, eps = 0.5 ** np.arange(40.0), 1e-3
+    elif spec == "plateau":
+        s, eps = np.r_[np.ones(10), 1e-9 * np.ones(5)], 1e-4
+    else:
+        s, eps = np.r_[1.0, 0.5, 0.25, 1e-5, 1e-6, 1e-7, 1e-8], 1e-4
+    assert orc.sarcmp_rank(s, eps) == _filters_by_definition(list(s), eps)
+
+
+@pytest.fixture(scope="module")
+def lv3(orc):
+    return orc.build_levels("inv_r", 1.0, 3, 1e-4)
+
+
+def test_m2l_operators_mirror_symmetry(orc, lv3):
+    """An even kernel gives K^{-delta} = (K^delta)^t: the symmetric case in
+    which one basis U serves both sides of C^delta = U^t K^delta U."""
+    Kd = orc.m2l_operators("inv_r", 1.0, 3, lv3[3])
+    for t in orc.FAR_SLOTS:
+        np.testing.assert_allclose(Kd[342 - t], Kd[t].T, rtol=1e-13, atol=0)
+    assert len(orc.FAR_SLOTS) == 316
+    assert not Kd[171].any()  # delta = 0 is a neighbour offset
+
+
+def test_sarcmp_basis_truncation_error(orc, lv3):
+    """Eckart-Young: projecting K_fat on the r kept left singular vectors
+    leaves exactly the discarded singular values (Frobenius norm)."""
+    b = orc.sarcmp_basis("inv_r", 1.0, 3, lv3[3], 1e-4)
+    U, r, s = b["U"], b["r"], b["s"]
+    Kd = orc.m2l_operators("inv_r", 1.0, 3, lv3[3])
+    Kfat = np.hstack([Kd[t] for t in orc.FAR_SLOTS])
+    np.testing.assert_allclose(U.T @ U, np.eye(r), atol=1e-12)
+    res = np.linalg.norm(Kfat - U @ (U.T @ Kfat)) ** 2
+    assert abs(res - np.sum(s[r:] ** 2)) <= 1e-9 * np.sum(s ** 2)
+    assert r == max(b["r_i"], b["r_ii"]) and 0 < r < lv3[3]["d"]
+
+
+def test_sarcmp_full_rank_is_the_plain_m2l(orc, lv3):
+    """With r = d the basis is orthogonal and U C^delta U^t = K^delta."""
+    x = wl.uniform_cube(3000, 21)
+    s = wl.sigma_uniform(3000, 1, 22)
+    f0 = orc.eifmm("inv_r", 1.0, [0, 0, 0], 3, lv3, x, x, s)
+    lvc = {k: dict(e, U=orc.sarcmp_basis("inv_r", 1.0, k, e, 1e-4, r=e["d"])["U"]) for k, e in lv3.items()}
+    f1 = orc.eifmm("inv_r", 1.0, [0, 0, 0], 3, lvc, x, x, s)
+    assert np.linalg.norm(f1 - f0) <= 1e-11 * np.linalg.norm(f0)
+
+
+def test_sarcmp_meets_the_tolerance(orc, lv3):
+    """The compressed method against the exact sum: within eps, and the
+    truncation is visible (the result moves by more than rounding)."""
+    x = wl.uniform_cube(4096, 1)
+    s = wl.sigma_uniform(4096, 1, 101)
+    f1 = orc.direct_sum("inv_r", x, x, s)
+    f0 = orc.eifmm("inv_r", 1.0, [0, 0, 0], 3, lv3, x, x, s)
+    lvc = {k: dict(e, U=orc.sarcmp_basis("inv_r", 1.0, k, e, 1e-4)["U"]) for k, e in lv3.items()}
+    fc = orc.eifmm("inv_r", 1.0, [0, 0, 0], 3, lvc, x, x, s)
+    assert np.linalg.norm(fc - f1) <= 1e-4 * np.linalg.norm(f1)
+    assert np.linalg.norm(fc - f0) > 1e-9 * np.linalg.norm(f0)
+
+
+def test_m2l_operator_with_delta_folded_in(orc, lv3):
+    """Steps 3-4 as one operator: sum_J K^delta (Delta W^J) equals
+    sum_J (K^delta Delta) W^J, with the rows of K^delta Delta obtained by
+    applying Delta^t (the oracle's own solves) to the rows of K^delta.  The
+    folded operator is also far less sensitive to rounding of its input:
+    W and the operator rounded to FP32 move g by ~1e-7, while What rounded
+    after FP32 solves would not (the ill-conditioned Delta amplifies)."""
+    e = lv3[3]
+    x = wl.uniform_cube(4096, 1)
+    s = wl.sigma_uniform(4096, 1, 101)
+    _, dm = orc.eifmm("inv_r", 1.0, [0, 0, 0], 3, lv3, x, x, s, dump=True)
+    W = dm["W"][3][::8, 0, :]  # multipole coefficients of 64 leaves
+    Kd = orc.m2l_operators("inv_r", 1.0, 3, e)
+    Wh = np.array([orc.apply_delta(e["Gamma"], e["B"], w) for w in W])
+    np.testing.assert_allclose(Wh, dm["What"][3][::8, 0, :], rtol=0, atol=0)
+    for t in (orc.FAR_SLOTS[0], orc.FAR_SLOTS[200]):
+        K = Kd[t]
+        M = np.array([orc.apply_delta(e["Gamma"], e["B"], row, transpose=True) for row in K])
+        g_ref = Wh @ K.T
+        np.testing.assert_allclose(W @ M.T, g_ref, rtol=0, atol=1e-10 * np.abs(g_ref).max())
+        g32 = (W.astype(np.float32) @ M.T.astype(np.float32)).astype(np.float64)
+        assert np.linalg.norm(g32 - g_ref) <= 1e-6 * np.linalg.norm(g_ref)
