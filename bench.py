@@ -314,6 +314,7 @@ def main():
             results[f"{prec}@{eps:g}"] = {
                 "value": N_POINTS * NRHS * ws / (ms * 1e-3), "ms_per_step": ms,
                 "tier": ops[eps].plan() if prec == "mixed" else None,
+                "calibration": ops[eps].calibration() if prec == "mixed" else None,
                 "rel_l2_vs_exact": err, "meets_eps": err <= eps, "d": d,
                 "gpu_launches": launches, "steps": steps,
                 "step_ms": [round(statistics.median([t[i] for t in st]), 4) for i in range(8)],

@@ -168,6 +168,13 @@ eifmm_status eifmm_ops_plan(eifmm_ops* ops, int tier_override, int* tier);
 eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_stream stream,
                                  int* tier);
 
+/* What the last eifmm_ops_calibrate measured: err3[t] is the relative L2
+ * difference of tier t (t = 0, 1, 2) to FP64 on the calibration problem, or
+ * -1 for a tier that was not evaluated (a cheaper one passed first, or its
+ * operands could not be built); *tier the tier kept (-1 before any
+ * calibration).  Either pointer may be NULL.  Errors: EINVAL (null ops). */
+eifmm_status eifmm_ops_calibration(const eifmm_ops* ops, double* err3, int* tier);
+
 void eifmm_ops_destroy(eifmm_ops* ops);
 
 /* ------------------------------------------------------------------------ */

@@ -490,6 +490,8 @@ extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_st
   eifmm_tree* tree = nullptr;
   eifmm_status rc = EIFMM_OK;
   int best = 3;
+  for (double& e : ops->o.calib_err) e = -1.0;
+  ops->o.calib_tier = -1;
   do {
     if ((rc = dalloc(&dx, 3 * n)) != EIFMM_OK) break;
     if ((rc = dalloc(&ds, n)) != EIFMM_OK) break;
@@ -538,6 +540,7 @@ extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_st
       double ne = 0.0;
       for (int64_t i = 0; i < n; ++i) ne += (hm[i] - href[i]) * (hm[i] - href[i]);
       const double err = sqrt(ne / (nref > 0 ? nref : 1.0));
+      ops->o.calib_err[t] = err;
       if (err <= 0.25 * eps) {
         best = t;
         break;
@@ -551,7 +554,19 @@ extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_st
   dfree(fm);
   if (rc != EIFMM_OK) return rc;
   EIFMM_TRY(eifmm_ops_plan(ops, best, nullptr));
+  ops->o.calib_tier = best;
   if (tier_out) *tier_out = best;
+  return EIFMM_OK;
+}
+
+extern "C" eifmm_status eifmm_ops_calibration(const eifmm_ops* ops, double* err3, int* tier) {
+  if (!ops) {
+    set_error("eifmm_ops_calibration: null handle");
+    return EIFMM_EINVAL;
+  }
+  if (err3)
+    for (int t = 0; t < 3; ++t) err3[t] = ops->o.calib_err[t];
+  if (tier) *tier = ops->o.calib_tier;
   return EIFMM_OK;
 }
 

@@ -90,6 +90,8 @@ struct Ops {
   double L = 1.0;
   int depth = 0;
   int tier = 0;        // arithmetic tier of the mixed path
+  double calib_err[3] = {-1.0, -1.0, -1.0};  // last calibration, per tier
+  int calib_tier = -1;
   LevelOps lv[kMaxLevel + 1];
   int* d_slot_lists = nullptr;  // [8][189] slot ids per parity class
 };

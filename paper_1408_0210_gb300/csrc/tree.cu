@@ -28,18 +28,19 @@ __global__ void k_keys(const double* __restrict__ xyz, int64_t n, double lo0,
   if (i >= n) return;
   const double lo[3] = {lo0, lo1, lo2};
   const double hi[3] = {hi0, hi1, hi2};
-  const int64_t nmax = ((int64_t)1 << depth) - 1;
-  int64_t c[3];
+  const int nmax = (1 << depth) - 1;
+  int c[3];
   bool out = false;
+#pragma unroll
   for (int a = 0; a < 3; ++a) {
     const double x = xyz[3 * i + a];
     if (!(x >= lo[a] && x <= hi[a])) out = true;
-    // (x - lo) * scale: a subtraction then a product, never fused.
-    const double t = floor(__dmul_rn(__dsub_rn(x, lo[a]), scale));
-    int64_t v = (int64_t)t;
-    if (!(t >= 0.0)) v = 0;
-    if (v > nmax) v = nmax;
-    c[a] = v;
+    // (x - lo) * scale: a subtraction then a product, never fused.  The
+    // conversion truncates toward zero and clamps to the int range (NaN gives
+    // 0); truncation equals floor wherever the clamp to [0, nmax] leaves the
+    // value unchanged.
+    const int v = __double2int_rz(__dmul_rn(__dsub_rn(x, lo[a]), scale));
+    c[a] = min(max(v, 0), nmax);
   }
   if (out) atomicAdd(bad, 1);
   keys[i] = (uint32_t)morton_encode(c[0], c[1], c[2], depth);
@@ -196,6 +197,8 @@ __global__ void k_leaf_off(const uint32_t* __restrict__ skeys, int64_t n,
   for (int64_t b = prev + 1; b <= cur; ++b) off[b] = (int32_t)p;
 }
 
+// Leaf-centre coordinates lo_a + (2 c + 1) l_kappa of the 2^depth cells
+// per axis are formed once per block in shared memory ([3][2^depth]).
 __global__ void k_gather_points(const double* __restrict__ xyz,
                                 const int32_t* __restrict__ perm,
                                 const uint32_t* __restrict__ skeys, int64_t n,
@@ -204,6 +207,14 @@ __global__ void k_gather_points(const double* __restrict__ xyz,
                                 double* __restrict__ y, double* __restrict__ z,
                                 float* __restrict__ lx, float* __restrict__ ly,
                                 float* __restrict__ lz) {
+  extern __shared__ double s_ctr[];
+  const int nc = 1 << depth;
+  for (int t = threadIdx.x; t < 3 * nc; t += blockDim.x) {
+    const int a = t >> depth, c = t & (nc - 1);
+    const double lo = a == 0 ? lo0 : (a == 1 ? lo1 : lo2);
+    s_ctr[t] = lo + (2.0 * c + 1.0) * lk;
+  }
+  __syncthreads();
   const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int64_t i = perm[p];
@@ -213,9 +224,9 @@ __global__ void k_gather_points(const double* __restrict__ xyz,
   x[p] = px;
   y[p] = py;
   z[p] = pz;
-  lx[p] = (float)(px - (lo0 + (2.0 * c[0] + 1.0) * lk));
-  ly[p] = (float)(py - (lo1 + (2.0 * c[1] + 1.0) * lk));
-  lz[p] = (float)(pz - (lo2 + (2.0 * c[2] + 1.0) * lk));
+  lx[p] = (float)(px - s_ctr[c[0]]);
+  ly[p] = (float)(py - s_ctr[nc + c[1]]);
+  lz[p] = (float)(pz - s_ctr[2 * nc + c[2]]);
 }
 
 __global__ void k_nonempty(const int32_t* __restrict__ off, int64_t nleaf,
@@ -298,7 +309,7 @@ eifmm_status build_pointset(const double* xyz, int64_t n, const double lo[3],
   EIFMM_CHECK_LAUNCH();
   if (n > 0) {
     const double lk = L * ldexp(1.0, -(depth + 1));
-    k_gather_points<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+    k_gather_points<<<(unsigned)((n + 255) / 256), 256, (size_t)3 * sizeof(double) << depth, s>>>(
         xyz, ps->perm, ps->keys, n, lo[0], lo[1], lo[2], lk, depth, ps->x, ps->y,
         ps->z, ps->lx, ps->ly, ps->lz);
     EIFMM_CHECK_LAUNCH();

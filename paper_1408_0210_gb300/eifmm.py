@@ -26,6 +26,7 @@ EXPORTS = [
     "eifmm_evaluate", "eifmm_evaluate_host", "eifmm_evaluate_batched", "eifmm_debug_export",
     "eifmm_set_timing", "eifmm_last_step_times", "eifmm_direct_sum", "eifmm_kernel_launches",
     "eifmm_tree_sort_static", "eifmm_ops_calibrate", "eifmm_autotune", "eifmm_measure_rates",
+    "eifmm_ops_calibration",
 ]
 
 
@@ -78,6 +79,7 @@ def lib() -> C.CDLL:
         "eifmm_kernel_launches": (C.c_uint64, []),
         "eifmm_tree_sort_static": (i32, [vp, i64, vp, dbl, i32, vp, vp, vp, vp]),
         "eifmm_ops_calibrate": (i32, [vp, dbl, vp, vp]),
+        "eifmm_ops_calibration": (i32, [vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -170,6 +172,13 @@ class Ops:
         t = C.c_int()
         _check(lib().eifmm_ops_calibrate(self.handle, float(eps), _stream(stream), C.byref(t)))
         return t.value
+
+    def calibration(self) -> dict:
+        """The last calibration: tier kept and the error of each tier
+        evaluated (None where it was not)."""
+        e, t = (C.c_double * 3)(), C.c_int()
+        _check(lib().eifmm_ops_calibration(self.handle, e, C.byref(t)))
+        return {"tier": t.value, "err": [v if v >= 0 else None for v in e]}
 
     def plan(self, tier_override: int = -1) -> int:
         t = C.c_int()
