@@ -326,8 +326,9 @@ def main():
                 headline = (prec, eps)
     clocks = clk.summary()
 
-    if headline is None:
-        headline = ("fp64", 1e-4)
+    if headline is None:  # no 1e-4 variant met its tolerance: the first one that ran
+        headline = next(((p, e) for p, e in variants if "value" in results.get(f"{p}@{e:g}", {})),
+                        variants[0])
     hp, he = headline
     hr = results[f"{hp}@{he:g}"]
 

@@ -236,6 +236,16 @@ __global__ void k_nonempty(const int32_t* __restrict__ off, int64_t nleaf,
   if (off[b + 1] > off[b]) list[atomicAdd(cnt, 1)] = (int32_t)b;
 }
 
+struct SortScratch {
+  std::mutex m;
+  unsigned char* p = nullptr;
+  size_t cap = 0;
+};
+SortScratch& sort_scratch(int dev) {
+  static SortScratch s[64];
+  return s[dev & 63];
+}
+
 }  // namespace
 
 eifmm_status build_pointset(const double* xyz, int64_t n, const double lo[3],
@@ -269,8 +279,20 @@ eifmm_status build_pointset(const double* xyz, int64_t n, const double lo[3],
   size_t soff = 0;
   const size_t o_k2 = take(soff, nn * 4), o_v2 = take(soff, nn * 4), o_cnt = take(soff, (size_t)256 * nb1 * 4),
                o_part = take(soff, scan_tiles((int64_t)256 * nb1) * 4), o_bad = take(soff, 2 * sizeof(int));
-  unsigned char* scratch = nullptr;
-  EIFMM_TRY(dalloc(&scratch, soff));
+  // The sort's scratch is kept per device between builds (grown on demand,
+  // held until the process exits); builds on one device take turns on it.
+  int dev = 0;
+  EIFMM_CUDA(cudaGetDevice(&dev));
+  SortScratch& sc = sort_scratch(dev);
+  std::unique_lock<std::mutex> hold(sc.m);
+  if (sc.cap < soff) {
+    dfree(sc.p);
+    sc.p = nullptr;
+    sc.cap = 0;
+    EIFMM_TRY(dalloc(&sc.p, soff));
+    sc.cap = soff;
+  }
+  unsigned char* scratch = sc.p;
   uint32_t* k2 = (uint32_t*)(scratch + o_k2);
   int32_t* v2 = (int32_t*)(scratch + o_v2);
   uint32_t* counts = (uint32_t*)(scratch + o_cnt);
@@ -319,7 +341,6 @@ eifmm_status build_pointset(const double* xyz, int64_t n, const double lo[3],
   int hb[2] = {0, 0};
   EIFMM_CUDA(cudaMemcpyAsync(hb, dbad, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
   EIFMM_CUDA(cudaStreamSynchronize(s));
-  dfree(scratch);
   ps->n_nonempty = hb[1];
   if (hb[0] != 0) {
     set_error("eifmm_tree_build: " + std::to_string(hb[0]) +
