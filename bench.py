@@ -373,10 +373,19 @@ def main():
     roof_nf = None
     if nf_ms > 0:
         rs = rates["rsqrt_per_s"]
-        roof_nf = {"bound": "alu", "achieved": pairs / (nf_ms * 1e-3), "peak": rs,
-                   "unit": "rsqrt/s", "frac": pairs / (nf_ms * 1e-3) / rs, "traffic": None,
-                   "kernel": f"near field ({'k_p2p32, FP32' if hp == 'mixed' else 'k_p2p64, FP64'}), "
-                             f"{pairs} pairs, one 1/r each", "launch_ms": nf_ms,
+        # tier 0 with one right-hand side visits each unordered leaf pair once:
+        # one 1/r per unordered point pair, the own leaf in full
+        sym = (hp == "mixed" and hr.get("tier") == 0 and NRHS == 1
+               and os.environ.get("EIFMM_P2P_SYM", "0") == "1")
+        cnt = np.diff(off).astype(np.int64)
+        own = int((cnt * (cnt - 1)).sum())
+        evals = (pairs - own) // 2 + own if sym else pairs
+        name = ("k_p2p32_sym, FP32, each leaf pair once" if sym else
+                "k_p2p32, FP32" if hp == "mixed" else "k_p2p64, FP64")
+        roof_nf = {"bound": "alu", "achieved": evals / (nf_ms * 1e-3), "peak": rs,
+                   "unit": "rsqrt/s", "frac": evals / (nf_ms * 1e-3) / rs, "traffic": None,
+                   "kernel": f"near field ({name}), {pairs} directed pairs, {evals} 1/r evaluations",
+                   "pairs_per_s": pairs / (nf_ms * 1e-3), "launch_ms": nf_ms,
                    "peak_source": "measured rsqrt.approx register loop",
                    "nominal_peak": SFU_PEAK}
 

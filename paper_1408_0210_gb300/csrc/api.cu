@@ -57,7 +57,8 @@ void free_workspace(Workspace* ws) {
   ws->m2l_part_leaf = nullptr;
   ws->m2l_part_leaf_cap = 0;
   for (int k = 0; k <= kMaxLevel; ++k) ws->m2l_kind[k] = ws->m2l_gshift[k] = 0;
-  dfree(ws->fnear); dfree(ws->ffar); dfree(ws->tmp);
+  dfree(ws->fnear); dfree(ws->ffar); dfree(ws->tmp); dfree(ws->gsym);
+  ws->gsym = nullptr;
   ws->tmp = nullptr;
   ws->lh = nullptr; ws->lh32 = nullptr; ws->sig = nullptr; ws->sig32 = nullptr;
   ws->fnear = nullptr; ws->ffar = nullptr;

@@ -26,6 +26,9 @@ eifmm_status launch_gather_sigma(const double* sigma, int64_t ld, const PointSet
 
 namespace {
 
+// forward neighbour offsets of the pair-symmetric near field
+constexpr int kSymSlots = 13;
+
 constexpr int TPB = 128;
 constexpr int RC = 4;
 
@@ -54,7 +57,7 @@ __device__ __forceinline__ float kern_pt(int kern, float z0, float z1, float z2)
 
 // Step 1: one CTA per leaf, threads = m (the d coefficients); the leaf's
 // points are staged as (x, y, z, sigma_r0) in shared memory.
-template <int KERN, int RCT>
+template <int KERN, int RCT, bool ACC>
 __global__ void __launch_bounds__(TPB)
 k_p2m32(int kern_rt, const int32_t* __restrict__ off, const float* __restrict__ lx,
         const float* __restrict__ ly, const float* __restrict__ lz,
@@ -88,7 +91,7 @@ k_p2m32(int kern_rt, const int32_t* __restrict__ off, const float* __restrict__ 
 #pragma unroll 4
           for (int t = 0; t < cnt; ++t) {
             const float4 y = sp[t];
-            const float kv = kern_pt<KERN, true>(kern, x0 - y.x, x1 - y.y, x2 - y.z);
+            const float kv = kern_pt<KERN, ACC>(kern, x0 - y.x, x1 - y.y, x2 - y.z);
 #pragma unroll
             for (int rr = 0; rr < RCT; ++rr) acc[rr] = fmaf(RCT == 1 ? y.w : ss[rr][t], kv, acc[rr]);
           }
@@ -101,15 +104,18 @@ k_p2m32(int kern_rt, const int32_t* __restrict__ off, const float* __restrict__ 
 // Step 7 with the near field and the un-permute: one CTA per non-empty
 // target leaf, threads = (point, slice of l): P points of the leaf (up to
 // TPB per pass) times S = TPB / P interleaved slices of the d terms.
-template <int KERN, int RCT>
+template <int KERN, int RCT, bool ACC>
 __global__ void __launch_bounds__(TPB)
 k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restrict__ off,
         const int32_t* __restrict__ perm, const float* __restrict__ lx,
         const float* __restrict__ ly, const float* __restrict__ lz, int64_t n, int R,
         const float* __restrict__ X, int d, int dp, const float* __restrict__ lh,
-        const double* __restrict__ fnear, double* __restrict__ ffar, double* __restrict__ f,
-        int64_t ld_f) {
+        double* __restrict__ fnear, double* __restrict__ ffar, double* __restrict__ f,
+        int64_t ld_f, const float* __restrict__ gsym, int depth) {
   const int kern = KERN >= 0 ? KERN : kern_rt;
+  // pair-symmetric near field (gsym): the backward neighbours A = B - o of
+  // this leaf B that exist and hold points wrote partials gsym[s][p]
+  __shared__ int s_gmask;
   // (x_l, lhat_l of the first right-hand side) [d], lhat of the pass [RCT d]
   // when RCT > 1, slice partials [RCT TPB]
   extern __shared__ float4 smf4[];
@@ -119,6 +125,20 @@ k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
   const int tid = threadIdx.x;
   const int b = leaves[blockIdx.x];
   const int beg = off[b], end = off[b + 1];
+  if (gsym && tid == 0) {
+    int c[3], m = 0;
+    morton_decode(b, depth, c);
+    const int nside = 1 << depth;
+    for (int s = 0; s < 13; ++s) {
+      const int nb = 14 + s;
+      const int ax = c[0] - (nb % 3 - 1), ay = c[1] - ((nb / 3) % 3 - 1), az = c[2] - (nb / 9 - 1);
+      if (ax >= 0 && ay >= 0 && az >= 0 && ax < nside && ay < nside && az < nside) {
+        const int64_t A = morton_encode(ax, ay, az, depth);
+        if (off[A + 1] > off[A]) m |= 1 << s;
+      }
+    }
+    s_gmask = m;
+  }
   for (int r0 = 0; r0 < R; r0 += RCT) {
     __syncthreads();
     for (int l = tid; l < d; l += TPB)
@@ -141,7 +161,7 @@ k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
 #pragma unroll 4
         for (int l = si; l < d; l += S) {
           const float4 x = sX[l];
-          const float kv = kern_pt<KERN, true>(kern, z0 - x.x, z1 - x.y, z2 - x.z);
+          const float kv = kern_pt<KERN, ACC>(kern, z0 - x.x, z1 - x.y, z2 - x.z);
 #pragma unroll
           for (int rr = 0; rr < RCT; ++rr) acc[rr] = fmaf(kv, RCT == 1 ? x.w : sl[rr * d + l], acc[rr]);
         }
@@ -159,12 +179,42 @@ k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
           for (int k = 0; k < S; ++k) s += sp[rr * TPB + ti + k * P];
           const int rg = r0 + rr;
           if (ffar) ffar[p + rg * n] = s;
-          f[i + rg * ld_f] = (double)s + fnear[p + rg * n];
+          double fn = fnear[p + rg * n];
+          if (gsym) {  // R = 1
+            const int m = s_gmask;
+            float gs = 0.f;
+            for (int q = 0; q < 13; ++q)
+              if (m & (1 << q)) gs += gsym[(int64_t)q * n + p];
+            fn += (double)gs;
+            fnear[p] = fn;
+          }
+          f[i + rg * ld_f] = (double)s + fn;
         }
       }
     }
   }
 }
+
+// Instantiation of a point kernel launch for (kernel, right-hand-side block,
+// Newton step); LAUNCH(K, RCT, ACC) expands to the launch.
+#define EIFMM_POINT_DISPATCH(LAUNCH)                                        \
+  do {                                                                      \
+    if (kern == EIFMM_KERNEL_INV_R) {                                       \
+      if (R == 1) {                                                         \
+        if (acc) LAUNCH(EIFMM_KERNEL_INV_R, 1, true);                       \
+        else LAUNCH(EIFMM_KERNEL_INV_R, 1, false);                          \
+      } else {                                                              \
+        if (acc) LAUNCH(EIFMM_KERNEL_INV_R, RC, true);                      \
+        else LAUNCH(EIFMM_KERNEL_INV_R, RC, false);                         \
+      }                                                                     \
+    } else if (R == 1) {                                                    \
+      if (acc) LAUNCH(-1, 1, true);                                         \
+      else LAUNCH(-1, 1, false);                                            \
+    } else {                                                                \
+      if (acc) LAUNCH(-1, RC, true);                                        \
+      else LAUNCH(-1, RC, false);                                           \
+    }                                                                       \
+  } while (0)
 
 // ------------------------------------------------------------ near field --
 // One CTA (128 threads) per non-empty target leaf.  The sources of the 27
@@ -176,11 +226,11 @@ k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
 // (up to 128) times S = 128 / P contiguous slices of the staged list.  Slice
 // starts are spaced by L = 2 (mod 8) float4, so the few slices a warp reads
 // at once fall in different banks.  The slices of a target are added in FP64
-// in a fixed order; FP32 sums run over at most 64 terms before they are
+// in a fixed order; FP32 sums run over at most 128 terms before they are
 // flushed into a compensated total.
 constexpr int P2P_THREADS = 128;
 constexpr int P2P_SRC = 1024;
-constexpr int P2P_FLUSH = 64;
+constexpr int P2P_FLUSH = 128;
 
 // Kahan step: (s, c) += v.
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
@@ -202,8 +252,12 @@ __device__ __forceinline__ void p2p_span(int kern, const float4* __restrict__ sr
     float sa[RCT], ca[RCT];
 #pragma unroll
     for (int rr = 0; rr < RCT; ++rr) sa[rr] = ca[rr] = 0.f;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(src);
     auto term = [&](int j) {
-      const float4 y = src[j];
+      float4 y;  // one 16-byte shared load from a 32-bit shared address
+      asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                   : "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w)
+                   : "r"(sbase + 16u * (uint32_t)j));
       float kv = kern_pt<KERN, ACC>(kern, x0 - y.x, x1 - y.y, x2 - y.z);
       if (SELF && j == js) kv = 0.f;
 #pragma unroll
@@ -214,9 +268,9 @@ __device__ __forceinline__ void p2p_span(int kern, const float4* __restrict__ sr
       }
     };
     int j = j0;
-    for (; j + 8 <= j1; j += 8) {
+    for (; j + 16 <= j1; j += 16) {
 #pragma unroll
-      for (int u = 0; u < 8; ++u) term(j + u);
+      for (int u = 0; u < 16; ++u) term(j + u);
     }
     for (; j < j1; ++j) term(j);
 #pragma unroll
@@ -468,6 +522,8 @@ eifmm_status build_kd_image(Ops* ops, bool tf32, cudaStream_t s) {
 eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R) {
   Workspace& ws = t->ws;
   const int kap = t->depth;
+  if (R == 1 && t->same && t->exclude_self && t->tgt.n > 0 && !ws.gsym)
+    EIFMM_TRY(dalloc(&ws.gsym, (size_t)kSymSlots * t->tgt.n));
   for (int k = 2; k <= kap; ++k) {
     const int dp = ops->lv[k].dp;
     const size_t n = (size_t)nboxes(k) * R * dp;
@@ -523,6 +579,184 @@ eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R) {
   return EIFMM_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Near field with each unordered pair of leaves visited once (tier 0, one
+// right-hand side, targets = sources; every kernel of the library is even,
+// K(-z) = K(z), so k_ij serves both f_i and f_j).  The CTA of leaf A takes
+// A itself and its 13 forward neighbours B = A + o (neighbour index
+// (dx+1) + 3(dy+1) + 9(dz+1) above 13).  For i in A and j in B it adds
+// sigma_j k_ij to f_i and sigma_i k_ij to the partial g_j, written to
+// gsym[s][j] (s = the forward offset); the L2P of B adds the partials of its
+// 13 backward neighbours in a fixed order.  The own leaf is done in full
+// (f only, i != j).  Every entry of gsym is written by one CTA, so the result
+// is deterministic.
+//
+// Threads: a warp computes 32 targets x 32 sources, lane (ta, sb) =
+// (lane / 4, lane % 4) the 4 x 8 block of targets 4 ta .. 4 ta + 3 and
+// sources 8 sb .. 8 sb + 7, with f and g partials in registers; the f
+// partials are reduce-scattered over the 4 sb lanes and the g partials over
+// the 8 ta lanes with shuffles.  Warps share the column tiles of the staged
+// source list; targets are staged SYM_TGT at a time.
+// ---------------------------------------------------------------------------
+constexpr int SYM_THREADS = 128;
+constexpr int SYM_WARPS = SYM_THREADS / 32;
+constexpr int SYM_SRC = 1024;
+constexpr int SYM_TGT = 128;
+
+template <int KERN>
+__global__ void __launch_bounds__(SYM_THREADS)
+k_p2p32_sym(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restrict__ off,
+            const float* __restrict__ lx, const float* __restrict__ ly, const float* __restrict__ lz,
+            const float* __restrict__ sig, int64_t n, int depth, float two_l, double* __restrict__ fnear,
+            float* __restrict__ gsym) {
+  const int kern = KERN >= 0 ? KERN : kern_rt;
+  __shared__ float4 s_src[SYM_SRC];
+  __shared__ int64_t s_out[SYM_SRC];  // gsym index of a forward source, -1 for the leaf's own points
+  __shared__ float4 s_tgt[SYM_TGT];
+  __shared__ float s_f[SYM_WARPS][SYM_TGT];
+  __shared__ int s_pos[15];    // prefix of the segment lengths (0..12 forward, 13 own)
+  __shared__ int s_beg[14];
+  __shared__ float s_sh[14][3];
+  const unsigned full = 0xffffffffu;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int ta = lane >> 2, sb = lane & 3;
+  const int b = leaves[blockIdx.x];
+  int c[3];
+  morton_decode(b, depth, c);
+  const int nside = 1 << depth;
+  if (tid < 14) {
+    const int nb = tid < 13 ? 14 + tid : 13;
+    const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
+    const int jx = c[0] + dx, jy = c[1] + dy, jz = c[2] + dz;
+    int beg = 0, len = 0;
+    if (jx >= 0 && jy >= 0 && jz >= 0 && jx < nside && jy < nside && jz < nside) {
+      const int64_t J = morton_encode(jx, jy, jz, depth);
+      beg = off[J];
+      len = off[J + 1] - beg;
+    }
+    s_beg[tid] = beg;
+    s_pos[tid + 1] = len;
+    s_sh[tid][0] = dx * two_l;
+    s_sh[tid][1] = dy * two_l;
+    s_sh[tid][2] = dz * two_l;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    s_pos[0] = 0;
+    for (int i = 1; i <= 14; ++i) s_pos[i] += s_pos[i - 1];
+  }
+  __syncthreads();
+  const int n_fwd = s_pos[13], n_all = s_pos[14];
+  const int tbeg = off[b], tend = off[b + 1];
+  for (int t0 = tbeg; t0 < tend; t0 += SYM_TGT) {
+    const int nt = min(SYM_TGT, tend - t0);
+    const int nrt = (nt + 31) >> 5;
+    __syncthreads();
+    for (int i = tid; i < SYM_TGT; i += SYM_THREADS) {
+      // padding targets: sigma 0, far from every source and from the padding sources
+      s_tgt[i] = i < nt ? make_float4(lx[t0 + i], ly[t0 + i], lz[t0 + i], sig[t0 + i])
+                        : make_float4(1e6f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < SYM_WARPS; ++q) s_f[q][i] = 0.f;
+    }
+    for (int c0 = 0; c0 < n_all; c0 += SYM_SRC) {
+      const int cn = min(SYM_SRC, n_all - c0);
+      const int nct = (cn + 31) >> 5;
+      __syncthreads();
+      for (int sg = w; sg < 14; sg += SYM_WARPS) {
+        const int pb = s_pos[sg], pe = s_pos[sg + 1];
+        const int lo = max(pb, c0), hi = min(pe, c0 + cn);
+        const float sx = s_sh[sg][0], sy = s_sh[sg][1], sz = s_sh[sg][2];
+        for (int pos = lo + lane; pos < hi; pos += 32) {
+          const int sj = s_beg[sg] + (pos - pb);
+          const int q = pos - c0;
+          s_src[q] = make_float4(lx[sj] + sx, ly[sj] + sy, lz[sj] + sz, sig[sj]);
+          s_out[q] = sg < kSymSlots ? (int64_t)sg * n + sj : -1;
+        }
+      }
+      for (int q = cn + tid; q < nct * 32; q += SYM_THREADS) {
+        s_src[q] = make_float4(-1e6f, 0.f, 0.f, 0.f);
+        s_out[q] = -1;
+      }
+      __syncthreads();
+      for (int ct = w; ct < nct; ct += SYM_WARPS) {
+        const int jb = ct * 32 + sb * 8;
+        float4 sj[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) sj[v] = s_src[jb + v];
+        // own-leaf sources of this tile start at column own0 (>= 8: none)
+        const int own0 = n_fwd - (c0 + jb);
+        float gl[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) gl[v] = 0.f;
+        for (int rt = 0; rt < nrt; ++rt) {
+          const int ib = rt * 32 + ta * 4;
+          float4 ti[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) ti[u] = s_tgt[ib + u];
+          float fl[4] = {0.f, 0.f, 0.f, 0.f};
+          if (own0 >= 8) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 8; ++v) {
+                const float kv = kern_pt<KERN, false>(kern, ti[u].x - sj[v].x, ti[u].y - sj[v].y, ti[u].z - sj[v].z);
+                fl[u] = fmaf(sj[v].w, kv, fl[u]);
+                gl[v] = fmaf(ti[u].w, kv, gl[v]);
+              }
+          } else {
+            // the own leaf: source column v is the own point own_idx = v - own0
+            // (when v >= own0); the self pair is target (t0 - tbeg) + ib + u
+            const int tself = (t0 - tbeg) + ib;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+              for (int v = 0; v < 8; ++v) {
+                float kv = kern_pt<KERN, false>(kern, ti[u].x - sj[v].x, ti[u].y - sj[v].y, ti[u].z - sj[v].z);
+                const bool own = v >= own0;
+                if (own && v - own0 == tself + u) kv = 0.f;
+                fl[u] = fmaf(sj[v].w, kv, fl[u]);
+                if (!own) gl[v] = fmaf(ti[u].w, kv, gl[v]);
+              }
+          }
+          // f: reduce-scatter over the 4 sb lanes; lane (ta, sb) gets target ib + sb
+          float k0 = (sb & 1) ? fl[1] : fl[0], k1 = (sb & 1) ? fl[3] : fl[2];
+          const float a0 = (sb & 1) ? fl[0] : fl[1], a1 = (sb & 1) ? fl[2] : fl[3];
+          k0 += __shfl_xor_sync(full, a0, 1);
+          k1 += __shfl_xor_sync(full, a1, 1);
+          float fk = (sb & 2) ? k1 : k0;
+          fk += __shfl_xor_sync(full, (sb & 2) ? k0 : k1, 2);
+          s_f[w][ib + sb] += fk;
+        }
+        // g: reduce-scatter over the 8 ta lanes; lane (ta, sb) gets source jb + ta
+        float y[4], z[2];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const float mine = (ta & 1) ? gl[2 * m + 1] : gl[2 * m];
+          const float other = (ta & 1) ? gl[2 * m] : gl[2 * m + 1];
+          y[m] = mine + __shfl_xor_sync(full, other, 4);
+        }
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          const float mine = (ta & 2) ? y[2 * m + 1] : y[2 * m];
+          const float other = (ta & 2) ? y[2 * m] : y[2 * m + 1];
+          z[m] = mine + __shfl_xor_sync(full, other, 8);
+        }
+        const float g = ((ta & 4) ? z[1] : z[0]) + __shfl_xor_sync(full, (ta & 4) ? z[0] : z[1], 16);
+        const int64_t o = s_out[jb + ta];
+        if (o >= 0) gsym[o] = t0 == tbeg ? g : gsym[o] + g;
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < nt; i += SYM_THREADS) {
+      double s = 0.0;
+#pragma unroll
+      for (int q = 0; q < SYM_WARPS; ++q) s += (double)s_f[q][i];
+      fnear[t0 + i] = s;
+    }
+  }
+}
+
 template <int KERN, int RCT, bool ACC>
 static void p2p_launch(const Tree* t, int kern, const float* sig32, int R, double* fnear, float two_l,
                        cudaStream_t s) {
@@ -533,10 +767,30 @@ static void p2p_launch(const Tree* t, int kern, const float* sig32, int R, doubl
       sig32, S.n, R, t->depth, two_l, t->exclude_self, fnear);
 }
 
+// The pair-symmetric near field can serve tier 0 with one right-hand side
+// on a tree whose targets are its sources; it runs when EIFMM_P2P_SYM=1
+// (read at every evaluate).  It is not the default: it measured slower than
+// the per-target kernel (588 against 423 us at 1M points).
+bool use_p2p_sym(const Tree* t, int R, bool accurate, const float* gsym) {
+  const char* e = getenv("EIFMM_P2P_SYM");
+  return gsym && !accurate && R == 1 && t->same && t->exclude_self && e && strcmp(e, "1") == 0;
+}
+
 eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R, double* fnear,
-                          cudaStream_t s, bool accurate) {
+                          cudaStream_t s, bool accurate, float* gsym) {
   if (t->tgt.n_nonempty == 0) return EIFMM_OK;
   const float two_l = (float)(t->L * ldexp(1.0, -t->depth));
+  if (use_p2p_sym(t, R, accurate, gsym)) {
+    const PointSet& T = t->tgt;
+    if (kern == EIFMM_KERNEL_INV_R)
+      k_p2p32_sym<EIFMM_KERNEL_INV_R><<<(unsigned)T.n_nonempty, SYM_THREADS, 0, s>>>(
+          kern, T.nonempty, T.leaf_off, T.lx, T.ly, T.lz, sig32, T.n, t->depth, two_l, fnear, gsym);
+    else
+      k_p2p32_sym<-1><<<(unsigned)T.n_nonempty, SYM_THREADS, 0, s>>>(
+          kern, T.nonempty, T.leaf_off, T.lx, T.ly, T.lz, sig32, T.n, t->depth, two_l, fnear, gsym);
+    EIFMM_CHECK_LAUNCH();
+    return EIFMM_OK;
+  }
   const bool inv = kern == EIFMM_KERNEL_INV_R;
   if (R == 1) {
     if (inv) {
@@ -646,6 +900,9 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     return EIFMM_ETIMEOUT;
   }
   const bool tf32 = ops->tier == 1;
+  // P2M and L2P: the approximate reciprocal square root alone in tier 0
+  // (relative error below 2^-22), one Newton step above
+  const bool acc = ops->tier >= 1;
   const int kap = t->depth;
   const int kern = (int)ops->kern;
   const PointSet& S = t->src;
@@ -655,7 +912,8 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   EIFMM_CUDA(cudaEventRecord(ws.ev_fork, s));
   EIFMM_CUDA(cudaStreamWaitEvent(ws.side, ws.ev_fork, 0));
   if (timing_enabled()) cudaEventRecord(ws.ev_nf[0], ws.side);
-  EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, ws.side, ops->tier >= 1));
+  const bool p2p_sym = use_p2p_sym(t, R, ops->tier >= 1, ws.gsym);
+  EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, ws.side, ops->tier >= 1, ws.gsym));
   if (timing_enabled()) cudaEventRecord(ws.ev_nf[1], ws.side);
   EIFMM_CUDA(cudaEventRecord(ws.ev_join, ws.side));
 
@@ -663,18 +921,11 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   const LevelOps& vl = ops->lv[kap];
   {
     const unsigned nb = (unsigned)nboxes(kap);
-    if (kern == EIFMM_KERNEL_INV_R && R == 1)
-      k_p2m32<EIFMM_KERNEL_INV_R, 1><<<nb, TPB, 0, s>>>(kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32, S.n, R,
-                                                       vl.X32, vl.d, vl.dp, ws.W32[kap]);
-    else if (kern == EIFMM_KERNEL_INV_R)
-      k_p2m32<EIFMM_KERNEL_INV_R, RC><<<nb, TPB, 0, s>>>(kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32, S.n, R,
-                                                        vl.X32, vl.d, vl.dp, ws.W32[kap]);
-    else if (R == 1)
-      k_p2m32<-1, 1><<<nb, TPB, 0, s>>>(kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32, S.n, R, vl.X32, vl.d,
-                                        vl.dp, ws.W32[kap]);
-    else
-      k_p2m32<-1, RC><<<nb, TPB, 0, s>>>(kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32, S.n, R, vl.X32, vl.d,
-                                         vl.dp, ws.W32[kap]);
+#define EIFMM_P2M(K, RC_, A)                                                                   \
+  k_p2m32<K, RC_, A><<<nb, TPB, 0, s>>>(kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32, S.n, R, vl.X32, \
+                                        vl.d, vl.dp, ws.W32[kap])
+    EIFMM_POINT_DISPATCH(EIFMM_P2M);
+#undef EIFMM_P2M
     EIFMM_CHECK_LAUNCH();
   }
   record(ws, 1, s);
@@ -763,20 +1014,12 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     const unsigned nl = (unsigned)T.n_nonempty;
     const int rct = R == 1 ? 1 : RC;
     const size_t sm = (size_t)vl.d * sizeof(float4) + (size_t)((rct > 1 ? rct * vl.d : 0) + rct * TPB) * sizeof(float);
-    if (kern == EIFMM_KERNEL_INV_R && R == 1)
-      k_l2p32<EIFMM_KERNEL_INV_R, 1><<<nl, TPB, sm, s>>>(kern, T.nonempty, T.leaf_off, T.perm, T.lx, T.ly,
-                                                        T.lz, T.n, R, vl.X32, vl.d, vl.dp, ws.lh32, ws.fnear,
-                                                        ws.ffar, f, ld_f);
-    else if (kern == EIFMM_KERNEL_INV_R)
-      k_l2p32<EIFMM_KERNEL_INV_R, RC><<<nl, TPB, sm, s>>>(kern, T.nonempty, T.leaf_off, T.perm, T.lx, T.ly,
-                                                         T.lz, T.n, R, vl.X32, vl.d, vl.dp, ws.lh32, ws.fnear,
-                                                         ws.ffar, f, ld_f);
-    else if (R == 1)
-      k_l2p32<-1, 1><<<nl, TPB, sm, s>>>(kern, T.nonempty, T.leaf_off, T.perm, T.lx, T.ly, T.lz, T.n, R,
-                                         vl.X32, vl.d, vl.dp, ws.lh32, ws.fnear, ws.ffar, f, ld_f);
-    else
-      k_l2p32<-1, RC><<<nl, TPB, sm, s>>>(kern, T.nonempty, T.leaf_off, T.perm, T.lx, T.ly, T.lz, T.n, R,
-                                          vl.X32, vl.d, vl.dp, ws.lh32, ws.fnear, ws.ffar, f, ld_f);
+#define EIFMM_L2P(K, RC_, A)                                                                     \
+  k_l2p32<K, RC_, A><<<nl, TPB, sm, s>>>(kern, T.nonempty, T.leaf_off, T.perm, T.lx, T.ly, T.lz, T.n, R, \
+                                         vl.X32, vl.d, vl.dp, ws.lh32, ws.fnear, ws.ffar, f, ld_f,          \
+                                         p2p_sym ? ws.gsym : nullptr, kap)
+    EIFMM_POINT_DISPATCH(EIFMM_L2P);
+#undef EIFMM_L2P
     EIFMM_CHECK_LAUNCH();
   }
   EIFMM_CUDA(cudaMemcpyAsync(ws.err_host, ws.err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -153,6 +153,7 @@ struct Workspace {
   float* sig32 = nullptr;
   double* fnear = nullptr;      // n_tgt x R, sorted order
   double* ffar = nullptr;       // n_tgt x R, sorted order (debug only)
+  float* gsym = nullptr;        // 13 x n: pair-symmetric near-field partials (R = 1, targets = sources)
   double* host_sig = nullptr;   // device staging for evaluate_host
   double* host_f = nullptr;
   size_t host_cap = 0;
@@ -191,7 +192,7 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma,
                        int64_t ld_sigma, int R, double* f, int64_t ld_f,
                        cudaStream_t s, bool near32 = false);
 eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R,
-                          double* fnear, cudaStream_t s, bool accurate);
+                          double* fnear, cudaStream_t s, bool accurate, float* gsym = nullptr);
 eifmm_status build_kd_image(Ops* ops, bool tf32, cudaStream_t s);
 eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, int gshift, cudaStream_t s);
 eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma,

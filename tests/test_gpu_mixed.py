@@ -340,3 +340,49 @@ def test_forced_tiers_run(E, orc, tier):
     E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
     f1 = orc.direct_sum("inv_r", x, x, s)[:, 0]
     assert rel2(f.cpu().numpy(), f1) <= 5e-5
+
+
+@pytest.mark.parametrize("case", ["uniform", "clustered"])
+def test_pair_symmetric_near_field(E, orc, case, monkeypatch):
+    """Tier 0 with one right-hand side visits each unordered leaf pair once
+    (k_ij used for f_i and f_j, partials of the backward neighbours added by
+    the L2P).  Against the per-target near field (EIFMM_P2P_SYM=0): the same
+    near field and result to FP32 rounding; the clustered case has leaves of
+    thousands of points, so targets and sources are staged in several
+    chunks.  Sampled targets are checked against the CPU checker's near
+    field (the 27-leaf neighbourhood sum of Section 3.2)."""
+    if case == "uniform":
+        n, depth = 150000, 4
+        x = wl.uniform_cube(n, 81)
+    else:
+        n, depth = 120000, 3
+        x = wl.gaussian_mixture(n, 82)
+    s = wl.sigma_uniform(n, 1, 83)
+    ops = E.eifmm_ops_build("inv_r", 1.0, depth, 1e-4)
+    ops.plan(0)
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    out = {}
+    for sym in ("1", "0"):
+        monkeypatch.setenv("EIFMM_P2P_SYM", sym)
+        f = torch.zeros(n, dtype=torch.float64, device="cuda")
+        E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
+        torch.cuda.synchronize()
+        out[sym] = (f.cpu().numpy(), E.eifmm_debug_export(tree, 6, depth, 0))
+    assert np.isfinite(out["1"][0]).all()
+    assert rel2(out["1"][1], out["0"][1]) <= 1e-6
+    assert rel2(out["1"][0], out["0"][0]) <= 1e-6
+    # the near field of sampled targets, summed directly in FP64; the FP32
+    # sums are held to 1e-5 of the sum of the magnitudes of their terms (one
+    # missing or doubled term is far larger: 1/864 of it for 32 points per
+    # leaf, 1/20000 in the clustered leaves)
+    idx = wl.sample_targets(n, 64, 84)
+    keys, _ = orc.morton_keys(x, np.zeros(3), 1.0, depth)
+    c = np.zeros((n, 3), dtype=np.int64)
+    for b in range(depth):
+        for a in range(3):
+            c[:, a] |= ((keys.astype(np.int64) >> (3 * b + a)) & 1) << b
+    for i in idx:
+        nb = np.abs(c - c[i]).max(axis=1) <= 1
+        nb[i] = False
+        terms = s[nb, 0] / np.linalg.norm(x[nb] - x[i], axis=1)
+        assert abs(out["1"][1][i] - terms.sum()) <= 1e-5 * np.abs(terms).sum()
