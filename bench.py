@@ -141,6 +141,23 @@ def dist_setup():
     return rank, ws, dist
 
 
+def max_over_ranks(ms: float, dist, device="cuda") -> float:
+    """The job's step time: the slowest rank's (each rank runs its own
+    replica of the workload, no data-path collective)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: float, world_size: int, ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the job's
+    step time."""
+    return units_per_rank * world_size / (ms * 1e-3)
+
+
 def cpu_oracle_run(n: int, depth: int, eps: float, steps: int):
     """Time the CPU checker's EIFMM (O2) on n points; returns (seconds per
     evaluation, threads, d per level)."""
@@ -289,10 +306,7 @@ def main():
         launches = E.eifmm_kernel_launches() - launches0
         E.eifmm_set_timing(False)
         ms = sum(a.elapsed_time(b) for a, b in zip(e0, e1)) / steps
-        if dist is not None:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         err = float(torch.linalg.norm(f[idx] - fref) / torch.linalg.norm(fref))
         return ms, err, launches, step_times, tuned
 
@@ -312,7 +326,7 @@ def main():
             d = [ops[eps].error_estimate(k)[1] for k in range(2, DEPTH + 1)]
             m2l = [statistics.median([t[9 + k] for t in st]) for k in range(2, DEPTH + 1)]
             results[f"{prec}@{eps:g}"] = {
-                "value": N_POINTS * NRHS * ws / (ms * 1e-3), "ms_per_step": ms,
+                "value": job_throughput(N_POINTS * NRHS, ws, ms), "ms_per_step": ms,
                 "tier": ops[eps].plan() if prec == "mixed" else None,
                 "calibration": ops[eps].calibration() if prec == "mixed" else None,
                 "rel_l2_vs_exact": err, "meets_eps": err <= eps, "d": d,
@@ -345,8 +359,8 @@ def main():
         rc = E.lib().eifmm_evaluate_host(tree.handle, ops[he].handle, sh.data_ptr(), N_POINTS, 1,
                                          fh.data_ptr(), N_POINTS, E.PREC[hp], stream.cuda_stream)
         assert rc == 0, E.lib().eifmm_last_error()
-    e2e_s = (time.perf_counter() - t0) / ke
-    e2e_val = N_POINTS * NRHS * ws / e2e_s
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) / ke * 1e3, dist, dev)
+    e2e_val = job_throughput(N_POINTS * NRHS, ws, e2e_ms)
 
     # ---- roofline of the dominant kernel: the M2L of the leaf level ------
     o = ops[he]

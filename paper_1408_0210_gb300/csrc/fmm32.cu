@@ -156,6 +156,14 @@ k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
       float acc[RCT];
 #pragma unroll
       for (int rr = 0; rr < RCT; ++rr) acc[rr] = 0.f;
+      // the output index and (one right-hand side) the near field, loaded
+      // before the sum so that their latency overlaps it
+      int64_t i_out = 0;
+      double fn0 = 0.0;
+      if (tid < P) {
+        i_out = perm[p];
+        if (RCT == 1) fn0 = fnear[p + (int64_t)r0 * n];
+      }
       if (si < S) {
         const float z0 = lx[p], z1 = ly[p], z2 = lz[p];
 #pragma unroll 4
@@ -171,7 +179,7 @@ k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
       for (int rr = 0; rr < RCT; ++rr) sp[rr * TPB + tid] = acc[rr];
       __syncthreads();
       if (tid < P) {
-        const int64_t i = perm[p];
+        const int64_t i = i_out;
 #pragma unroll
         for (int rr = 0; rr < RCT; ++rr) {
           if (r0 + rr >= R) break;
@@ -179,7 +187,7 @@ k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
           for (int k = 0; k < S; ++k) s += sp[rr * TPB + ti + k * P];
           const int rg = r0 + rr;
           if (ffar) ffar[p + rg * n] = s;
-          double fn = fnear[p + rg * n];
+          double fn = RCT == 1 ? fn0 : fnear[p + rg * n];
           if (gsym) {  // R = 1
             const int m = s_gmask;
             float gs = 0.f;
