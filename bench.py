@@ -206,7 +206,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", default="mixed:1e-4,fp64:1e-4,mixed:1e-7,fp64:1e-7")
+    ap.add_argument("--variants", default="mixed:1e-4,fp64:1e-4,mixed:1e-5,mixed:1e-7,fp64:1e-7")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run this many evaluations of the first variant between "
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off) and exit")

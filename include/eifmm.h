@@ -66,9 +66,15 @@ typedef enum {
  *                    products, FP32 accumulation in several chains), P2M,
  *                    M2M, L2L, L2P, the Delta solves and the near field in
  *                    FP32 on coordinates local to each leaf;
- *            tier 1: M2L with TF32 hi+lo operands, Delta solves in FP64;
- *            tier 2: far field in FP64, near field in FP32 (Kahan sums);
- *            tier 3: FP64 everywhere.
+ *            tier 1: M2L with TF32 hi+lo operands, the Delta^t solve in
+ *                    FP64, one Newton step on every FP32 1/r;
+ *            tier 2: M2L on the FP32 SIMT pipes, each offset's sum in FP32
+ *                    and the offsets added with compensated FP32 sums;
+ *                    FP32 elsewhere with one Newton step on every 1/r;
+ *            tier 3: far field in FP64, near field in FP32 (Kahan sums);
+ *            tier 4: FP64 everywhere.
+ *          In every tier the M2L applies K^delta Delta (built once with
+ *          FP64 solves) to W, so step 3 needs no solve.
  */
 typedef enum { EIFMM_PREC_FP64 = 0, EIFMM_PREC_MIXED = 1 } eifmm_precision;
 
@@ -153,27 +159,28 @@ eifmm_status eifmm_ops_error_estimate(const eifmm_ops* ops, int level,
                                       double* eps_k, int* d_k);
 
 /* Arithmetic tier that EIFMM_PREC_MIXED uses with these operators:
- * 0 = BF16 hi+lo M2L and an FP32 far field, 1 = TF32 hi+lo M2L and FP64
- * Delta solves, 2 = FP64 far field, 3 = FP64 everywhere (near field too).
- * eifmm_ops_load sets it from the built-in error estimate; `tier_override`
- * >= 0 forces a tier. */
+ * 0 = BF16 hi+lo M2L and an FP32 far field, 1 = TF32 hi+lo M2L and the FP64
+ * Delta^t solve, 2 = FP32 SIMT M2L with compensated sums over the offsets, 3 = FP64
+ * far field, 4 = FP64 everywhere (near field too).  eifmm_ops_load sets it
+ * from the built-in error estimate; `tier_override` >= 0 (at most 4) forces
+ * a tier.  Errors: EINVAL (null ops, tier above 4). */
 eifmm_status eifmm_ops_plan(eifmm_ops* ops, int tier_override, int* tier);
 
 /* Measured choice of the tier (no counterpart in the paper, which computes in
  * FP64): a uniform problem of 32 points per leaf at depth min(depth, 4) is
- * evaluated in FP64 and in tiers 0, 1, 2; the cheapest tier whose relative L2
- * difference to FP64 is at most eps/4 is kept, else tier 3.  Allocates and
+ * evaluated in FP64 and in tiers 0, 1, 2, 3; the cheapest tier whose relative
+ * L2 difference to FP64 is at most eps/4 is kept, else tier 4.  Allocates and
  * frees its own device memory; synchronises `stream`.  Errors: EINVAL,
  * ENOMEM, ECUDA. */
 eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_stream stream,
                                  int* tier);
 
-/* What the last eifmm_ops_calibrate measured: err3[t] is the relative L2
- * difference of tier t (t = 0, 1, 2) to FP64 on the calibration problem, or
+/* What the last eifmm_ops_calibrate measured: err4[t] is the relative L2
+ * difference of tier t (t = 0..3) to FP64 on the calibration problem, or
  * -1 for a tier that was not evaluated (a cheaper one passed first, or its
  * operands could not be built); *tier the tier kept (-1 before any
  * calibration).  Either pointer may be NULL.  Errors: EINVAL (null ops). */
-eifmm_status eifmm_ops_calibration(const eifmm_ops* ops, double* err3, int* tier);
+eifmm_status eifmm_ops_calibration(const eifmm_ops* ops, double* err4, int* tier);
 
 void eifmm_ops_destroy(eifmm_ops* ops);
 

@@ -123,7 +123,7 @@ eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec) {
     return EIFMM_OK;
   free_workspace(&ws);
   const int kap = t->depth;
-  const bool fp64_far = (prec == EIFMM_PREC_FP64) || tier >= 2;
+  const bool fp64_far = (prec == EIFMM_PREC_FP64) || tier >= 3;
   if (fp64_far) {
     for (int k = 2; k <= kap; ++k) {
       const size_t n = ((size_t)1 << (3 * k)) * R * ops->lv[k].d;
@@ -198,7 +198,7 @@ static int tier_for_eps(double eps, bool requested) {
   const double f = requested ? 1.0 - 1e-9 : 1.0 / 3.0;
   if (eps >= 1e-5 * f) return 0;
   if (eps >= 1e-6 * f) return 1;
-  return 2;
+  return 3;
 }
 
 extern "C" eifmm_status eifmm_ops_load(eifmm_kernel kern, double L, int depth,
@@ -257,6 +257,7 @@ extern "C" eifmm_status eifmm_ops_load(eifmm_kernel kern, double L, int depth,
   }
   o.tier = tier_for_eps(eps_max > 0.0 ? eps_max : 1e-16, false);
   if (o.tier <= 1) rc = build_kd_image(&o, o.tier == 1, s);
+  else if (o.tier == 2) rc = build_kd32(&o, s);
   if (rc != EIFMM_OK) {
     free_ops(&o);
     delete h;
@@ -330,13 +331,14 @@ extern "C" eifmm_status eifmm_ops_error_estimate(const eifmm_ops* ops, int level
 }
 
 extern "C" eifmm_status eifmm_ops_plan(eifmm_ops* ops, int tier_override, int* tier) {
-  if (!ops || tier_override > 3) {
+  if (!ops || tier_override > 4) {
     set_error("eifmm_ops_plan: invalid handle or tier");
     return EIFMM_EINVAL;
   }
   if (tier_override >= 0) {
     ops->o.tier = tier_override;
     if (tier_override <= 1) EIFMM_TRY(build_kd_image(&ops->o, tier_override == 1, nullptr));
+    else if (tier_override == 2) EIFMM_TRY(build_kd32(&ops->o, nullptr));
   }
   if (tier) *tier = ops->o.tier;
   return EIFMM_OK;
@@ -443,7 +445,7 @@ static eifmm_status evaluate_impl(eifmm_tree* tree, const eifmm_ops* ops, const 
   Tree& t = tree->t;
   EIFMM_TRY(ensure_workspace(&t, &ops->o, n_rhs, prec));
   eifmm_status rc;
-  if (prec == EIFMM_PREC_FP64 || ops->o.tier >= 3)
+  if (prec == EIFMM_PREC_FP64 || ops->o.tier >= 4)
     rc = eval_fp64(&t, &ops->o, sigma, ld_sigma, n_rhs, f, ld_f, s);
   else
     rc = eval_mixed(&t, &ops->o, sigma, ld_sigma, n_rhs, f, ld_f, s);
@@ -462,9 +464,10 @@ static eifmm_status evaluate_impl(eifmm_tree* tree, const eifmm_ops* ops, const 
 
 // ---------------------------------------------------------------------------
 // Measured choice of the mixed-precision tier.  A uniform problem of 32 points
-// per leaf (the near field carries its usual share of the result) is evaluated at depth min(depth, 4) with the operators' own kernel
-// in FP64 and in every mixed tier; the cheapest tier whose relative L2
-// difference to FP64 stays below eps/4 is kept (tier 3: all FP64).
+// per leaf (the near field carries its usual share of the result) is
+// evaluated at depth min(depth, 4) with the operators' own kernel in FP64
+// and in every mixed tier; the cheapest tier whose relative L2
+// difference to FP64 stays below eps/4 is kept (tier 4: all FP64).
 // ---------------------------------------------------------------------------
 extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_stream stream,
                                             int* tier_out) {
@@ -490,7 +493,7 @@ extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_st
   double *dx = nullptr, *ds = nullptr, *fr = nullptr, *fm = nullptr;
   eifmm_tree* tree = nullptr;
   eifmm_status rc = EIFMM_OK;
-  int best = 3;
+  int best = 4;
   for (double& e : ops->o.calib_err) e = -1.0;
   ops->o.calib_tier = -1;
   do {
@@ -516,8 +519,9 @@ extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_st
     }
     double nref = 0.0;
     for (double v : href) nref += v * v;
-    for (int t = 0; t <= 2 && rc == EIFMM_OK; ++t) {
+    for (int t = 0; t <= 3 && rc == EIFMM_OK; ++t) {
       if (t <= 1 && (rc = build_kd_image(&ops->o, t == 1, s)) != EIFMM_OK) break;
+      if (t == 2 && (rc = build_kd32(&ops->o, s)) != EIFMM_OK) break;
       // a tier whose M2L operands could not be built (d too large) is skipped
       bool have_img = true;
       for (int k = 2; k <= depth; ++k)
@@ -560,13 +564,13 @@ extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_st
   return EIFMM_OK;
 }
 
-extern "C" eifmm_status eifmm_ops_calibration(const eifmm_ops* ops, double* err3, int* tier) {
+extern "C" eifmm_status eifmm_ops_calibration(const eifmm_ops* ops, double* err4, int* tier) {
   if (!ops) {
     set_error("eifmm_ops_calibration: null handle");
     return EIFMM_EINVAL;
   }
-  if (err3)
-    for (int t = 0; t < 3; ++t) err3[t] = ops->o.calib_err[t];
+  if (err4)
+    for (int t = 0; t < 4; ++t) err4[t] = ops->o.calib_err[t];
   if (tier) *tier = ops->o.calib_tier;
   return EIFMM_OK;
 }

@@ -1,11 +1,13 @@
 // fmm32.cu -- the mixed-precision EIFMM (Algorithm 3 + near field).
 //
-// Tier 0 (EIM tolerance >= 1e-5): P2M, M2M, the Delta solves, L2L and L2P in
-// FP32 on coordinates local to each leaf; M2L on tcgen05 with BF16 hi + lo
-// operand planes (m2l_tc.cu).  Tier 1 (>= 1e-6): the Delta solves in FP64 and
-// M2L with TF32 hi + lo planes.  Tier 2 (< 1e-6): the FP64 far field of
-// fmm64.cu.  Every tier evaluates the near field here in FP32 with Kahan
-// compensated summation.
+// Tier 0: P2M, M2M, the Delta^t solve, L2L and L2P in FP32 on coordinates
+// local to each leaf; M2L of the folded operator K^delta Delta on tcgen05
+// with BF16 hi + lo operand planes (m2l_tc.cu).  Tier 1: the Delta^t solve
+// in FP64, a Newton step on every 1/r and M2L with TF32 hi + lo planes.
+// Tier 2: the M2L on the FP32 SIMT pipes (compensated sums over the offsets),
+// the Delta^t solve in FP32, a Newton step on every 1/r.  Tier 3: the FP64 far field of fmm64.cu.  Tiers 0-3 evaluate the
+// near field here in FP32 (tiers >= 1 with Kahan compensated summation).
+// The tier is chosen by a measured calibration (api.cu).
 //
 // Far-field arrays: [row = box * R + r][dp] FP32, dp = d rounded up to 64,
 // padding columns zero.
@@ -96,8 +98,8 @@ k_p2m32(int kern_rt, const int32_t* __restrict__ off, const float* __restrict__ 
             for (int rr = 0; rr < RCT; ++rr) acc[rr] = fmaf(RCT == 1 ? y.w : ss[rr][t], kv, acc[rr]);
           }
       }
-      if (m < dp)
-        for (int rr = 0; rr < RCT && r0 + rr < R; ++rr) W[(b * R + r0 + rr) * dp + m] = acc[rr];
+      if (m < dp)  // padding columns are zero
+        for (int rr = 0; rr < RCT && r0 + rr < R; ++rr) W[(b * R + r0 + rr) * dp + m] = m < d ? acc[rr] : 0.f;
     }
   }
 }
@@ -505,6 +507,138 @@ unsigned grid_for(int64_t n, int tpb, unsigned cap = 8192) {
   return (unsigned)(g > cap ? cap : g);
 }
 
+// FP32 copy of the folded M2L operator for the SIMT M2L of tier 2:
+// kd32[slot][l][m'] = (K^delta Delta)_{m' l} for l < d, m' < d, zero for
+// d <= m' < dp (row stride dp).
+__global__ void k_build_kd32(const double* __restrict__ kdT, int d, int dp, float* __restrict__ kd32) {
+  const int64_t slot = blockIdx.y;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)d * dp;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(t / dp), mp = (int)(t - (int64_t)l * dp);
+    kd32[(slot * d + l) * dp + mp] = mp < d ? (float)kdT[(slot * d + l) * d + mp] : 0.f;
+  }
+}
+
+// Step 4 of tier 2 on the SIMT pipes: g^I = sum_J (K^delta Delta) W^J with
+// FP32 products summed in FP32 over the d terms of one offset, and the
+// offsets added with compensated (Kahan) FP32 sums (the plain FP32
+// accumulation of the whole sum, about 30,000 terms, is what limits the
+// tensor-core tiers; FP64 adds would cost 1/64 of the FP32 rate here).
+//
+// A block computes 64 target boxes x 64 rows m': the boxes are 64
+// consecutive parents of one parity class (a 4x4x4 block of the class grid,
+// fewer at level 2), which share the 189 candidate offsets.  Per offset and
+// per chunk of 16 terms l, the 64 source rows (gathered, zero outside the
+// cube) and 16 x 64 operator entries are staged in shared memory; each of
+// the 256 threads accumulates a 4 x 4 block (4 boxes x 4 rows).
+constexpr int M2S_BOX = 64, M2S_ROW = 64, M2S_L = 16, M2S_THREADS = 256;
+
+__global__ void __launch_bounds__(M2S_THREADS, 3)
+k_m2l32s(int level, int d, int dp, int R, const float* __restrict__ kd32, const int* __restrict__ slot_lists,
+         const float* __restrict__ W, float* __restrict__ g, int groups, float* __restrict__ part,
+         int64_t part_stride) {
+  __shared__ __align__(16) float sW[M2S_L][M2S_BOX];  // [l][box]
+  __shared__ __align__(16) float sT[M2S_L][M2S_ROW];  // [l][m']
+  __shared__ int64_t s_src[M2S_BOX];                   // source row offset, -1 outside the cube
+  __shared__ int s_c[M2S_BOX][3];
+  const int tid = threadIdx.x;
+  const int r = blockIdx.z;
+  const int oct = blockIdx.x & 7;
+  const int grp = (int)((blockIdx.x >> 3) % groups);  // offsets [grp, grp+1) * 189 / groups
+  const int64_t per_class = (int64_t)1 << (3 * (level - 1));
+  const int nb = per_class < M2S_BOX ? (int)per_class : M2S_BOX;  // boxes of this block
+  const int64_t p0 = ((blockIdx.x >> 3) / groups) * (int64_t)M2S_BOX;
+  float* const dst = groups > 1 ? part + grp * part_stride : g;
+  const int m0 = blockIdx.y * M2S_ROW;
+  const int n = 1 << level;
+  if (tid < M2S_BOX) {
+    int c[3] = {0, 0, 0};
+    if (tid < nb) morton_decode(8 * (p0 + tid) + oct, level, c);
+    s_c[tid][0] = c[0];
+    s_c[tid][1] = c[1];
+    s_c[tid][2] = c[2];
+  }
+  const int tb = (tid >> 4) * 4, tm = (tid & 15) * 4;  // this thread's 4 boxes and 4 rows
+  float acc[4][4], cmp[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = cmp[i][j] = 0.f;
+  const int* lst = slot_lists + oct * kListLen;
+  // staging roles: box lb, 4 consecutive terms 4 lq of the chunk; operator row
+  // ll, 4 consecutive m' from 4 lm
+  const int lb = tid >> 2, lq = (tid & 3) * 4;
+  const int ll = tid >> 4, lm = (tid & 15) * 4;
+  const int s_end = (grp + 1) * kListLen / groups;
+  for (int s = grp * kListLen / groups; s < s_end; ++s) {
+    const int slot = lst[s];
+    const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+    __syncthreads();  // s_src and the tiles of the previous offset are free
+    if (tid < M2S_BOX) {
+      const int jx = s_c[tid][0] + dx, jy = s_c[tid][1] + dy, jz = s_c[tid][2] + dz;
+      const bool ok = tid < nb && jx >= 0 && jy >= 0 && jz >= 0 && jx < n && jy < n && jz < n;
+      s_src[tid] = ok ? (morton_encode(jx, jy, jz, level) * R + r) * dp : -1;
+    }
+    __syncthreads();
+    const float* K = kd32 + (int64_t)slot * d * dp;
+    float part[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[i][j] = 0.f;
+    // source coefficients (rows of W are dp long, 16-byte aligned, zero
+    // beyond d) and operator entries (rows l >= d do not exist) of the chunk
+    // at l0; the next chunk is loaded while the current one is summed
+    const int64_t so = s_src[lb];
+    auto load_w = [&](int l0) {
+      return (so >= 0 && l0 + lq < dp) ? *reinterpret_cast<const float4*>(W + so + l0 + lq)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    auto load_k = [&](int l0) {
+      return (l0 + ll < d && m0 + lm < dp)
+                 ? __ldg(reinterpret_cast<const float4*>(K + (int64_t)(l0 + ll) * dp + m0 + lm))
+                 : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    float4 wv = load_w(0), kv = load_k(0);
+    for (int l0 = 0; l0 < d; l0 += M2S_L) {
+      sW[lq + 0][lb] = wv.x;
+      sW[lq + 1][lb] = wv.y;
+      sW[lq + 2][lb] = wv.z;
+      sW[lq + 3][lb] = wv.w;
+      *reinterpret_cast<float4*>(&sT[ll][lm]) = kv;
+      __syncthreads();
+      if (l0 + M2S_L < d) {
+        wv = load_w(l0 + M2S_L);
+        kv = load_k(l0 + M2S_L);
+      }
+#pragma unroll
+      for (int u = 0; u < M2S_L; ++u) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&sW[u][tb]);
+        const float4 b4 = *reinterpret_cast<const float4*>(&sT[u][tm]);
+        const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) part[i][j] = fmaf(av[i], bv[j], part[i][j]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) kahan_add(acc[i][j], cmp[i][j], part[i][j]);
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (tb + i >= nb) break;
+    const int64_t I = 8 * (p0 + tb + i) + oct;
+    float* out = dst + (I * R + r) * dp + m0 + tm;
+    if (m0 + tm < dp)
+      *reinterpret_cast<float4*>(out) = make_float4(acc[i][0] - cmp[i][0], acc[i][1] - cmp[i][1],
+                                                    acc[i][2] - cmp[i][2], acc[i][3] - cmp[i][3]);
+  }
+}
+
 }  // namespace
 
 eifmm_status build_kd_image(Ops* ops, bool tf32, cudaStream_t s) {
@@ -524,6 +658,60 @@ eifmm_status build_kd_image(Ops* ops, bool tf32, cudaStream_t s) {
     v.kd_img_tf32 = tf32 ? 1 : 0;
   }
   EIFMM_CUDA(cudaStreamSynchronize(s));
+  return EIFMM_OK;
+}
+
+eifmm_status build_kd32(Ops* ops, cudaStream_t s) {
+  for (int k = 2; k <= ops->depth; ++k) {
+    LevelOps& v = ops->lv[k];
+    if (v.kd32) continue;
+    EIFMM_TRY(dalloc(&v.kd32, (size_t)kNumSlots * v.d * v.dp));
+    k_build_kd32<<<dim3(grid_for((int64_t)v.d * v.dp, 256, 64), kNumSlots), 256, 0, s>>>(v.kdT, v.d, v.dp,
+                                                                                        v.kd32);
+    EIFMM_CHECK_LAUNCH();
+  }
+  EIFMM_CUDA(cudaStreamSynchronize(s));
+  return EIFMM_OK;
+}
+
+// Step 4 of tier 2 at level k (SIMT, FP64 across offsets).
+static int sm_count();
+
+// g = the offset-group partials of the SIMT M2L added in group order with
+// a compensated FP32 sum.
+__global__ void k_sum_groups(const float* __restrict__ part, int groups, int64_t n, int64_t stride,
+                             float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    float s = 0.f, c = 0.f;
+    for (int q = 0; q < groups; ++q) kahan_add(s, c, part[q * stride + i]);
+    out[i] = s - c;
+  }
+}
+
+static eifmm_status launch_m2l_simt(const Tree* t, const Ops* ops, int k, int R, cudaStream_t s) {
+  const LevelOps& v = ops->lv[k];
+  if (!v.kd32) {
+    set_error("eifmm_evaluate: FP32 M2L operator of tier 2 missing");
+    return EIFMM_EUNSUPPORTED;
+  }
+  const Workspace& ws = t->ws;
+  const int64_t per_class = nboxes(k) / 8;
+  const int64_t tiles = (per_class + M2S_BOX - 1) / M2S_BOX;
+  // every block walks its offsets in sequence, so a level with few blocks
+  // splits the offsets into groups (two waves of blocks at least; the leaf
+  // level keeps one group)
+  const int64_t ctas = tiles * 8 * (v.dp / M2S_ROW) * R;
+  const int64_t rows_dp = nboxes(k) * R * v.dp;
+  int G = 1;
+  if (k < t->depth)
+    while (G < 16 && ctas * G < 2 * sm_count() && (size_t)(2 * G) * rows_dp <= ws.m2l_part_cap) G *= 2;
+  k_m2l32s<<<dim3((unsigned)(tiles * 8 * G), (unsigned)(v.dp / M2S_ROW), (unsigned)R), M2S_THREADS, 0, s>>>(
+      k, v.d, v.dp, R, v.kd32, ops->d_slot_lists, ws.W32[k], ws.g32[k], G, ws.m2l_part, rows_dp);
+  EIFMM_CHECK_LAUNCH();
+  if (G > 1) {
+    k_sum_groups<<<grid_for(rows_dp, 256, 4096), 256, 0, s>>>(ws.m2l_part, G, rows_dp, rows_dp, ws.g32[k]);
+    EIFMM_CHECK_LAUNCH();
+  }
   return EIFMM_OK;
 }
 
@@ -897,7 +1085,7 @@ eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, i
 
 eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld_sigma, int R,
                         double* f, int64_t ld_f, cudaStream_t s) {
-  if (ops->tier == 2) return eval_fp64(t, ops, sigma, ld_sigma, R, f, ld_f, s, true);
+  if (ops->tier == 3) return eval_fp64(t, ops, sigma, ld_sigma, R, f, ld_f, s, true);
   Workspace& ws = t->ws;
   if (*ws.err_host != 0) {
     const int code = *ws.err_host;
@@ -952,7 +1140,9 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   record(ws, 2, s);
   // step 3: What = Delta W is folded into the M2L operator (K^delta Delta,
   // built with the operators), so the M2L reads the planes of W itself
-  {
+  // (tier 2 reads W in FP32)
+  const bool simt = ops->tier == 2;
+  if (!simt) {
     PlaneBatch b;
     for (int k = 2; k <= kap; ++k) {
       const LevelOps& v = ops->lv[k];
@@ -975,14 +1165,26 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     EIFMM_CUDA(cudaEventRecord(ws.ev_fork2, s));
     EIFMM_CUDA(cudaStreamWaitEvent(ws.side2, ws.ev_fork2, 0));
   }
+  auto m2l = [&](int k, cudaStream_t st) {
+    return simt ? launch_m2l_simt(t, ops, k, R, st)
+                : launch_m2l_level(t, ops, k, R, ws.m2l_kind[k], ws.m2l_gshift[k], st);
+  };
+  // The SIMT M2L of tier 2 submits the coarse levels first: each of their
+  // few blocks walks all 189 offsets, so they must start early to end
+  // within the leaf level.
+  auto coarse = [&]() -> eifmm_status {
+    for (int k = 2; k < kap; ++k) {
+      if (timing_enabled()) cudaEventRecord(ws.ev_m2l[k], ws.side2);
+      EIFMM_TRY(m2l(k, ws.side2));
+      if (timing_enabled()) cudaEventRecord(ws.ev_m2le[k], ws.side2);
+    }
+    return EIFMM_OK;
+  };
+  if (simt) EIFMM_TRY(coarse());
   if (timing_enabled()) cudaEventRecord(ws.ev_m2l[kap], s);
-  EIFMM_TRY(launch_m2l_level(t, ops, kap, R, ws.m2l_kind[kap], ws.m2l_gshift[kap], s));
+  EIFMM_TRY(m2l(kap, s));
   if (timing_enabled()) cudaEventRecord(ws.ev_m2le[kap], s);
-  for (int k = 2; k < kap; ++k) {
-    if (timing_enabled()) cudaEventRecord(ws.ev_m2l[k], ws.side2);
-    EIFMM_TRY(launch_m2l_level(t, ops, k, R, ws.m2l_kind[k], ws.m2l_gshift[k], ws.side2));
-    if (timing_enabled()) cudaEventRecord(ws.ev_m2le[k], ws.side2);
-  }
+  if (!simt) EIFMM_TRY(coarse());
   if (kap > 2) {
     EIFMM_CUDA(cudaEventRecord(ws.ev_join2, ws.side2));
     EIFMM_CUDA(cudaStreamWaitEvent(s, ws.ev_join2, 0));
@@ -1005,7 +1207,7 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   {
     DeltaBatch b;
     b.nlev = 1;
-    if (tf32) {
+    if (ops->tier == 1) {
       b.lv[0] = delta_level(vl.d, delta_ops64(vl), true, ws.l32[kap], vl.dp, ws.lh32, vl.dp, nullptr,
                             nboxes(kap) * R);
       EIFMM_TRY((launch_delta_batch<double, float, float, 0>(b, true, s)));

@@ -82,6 +82,7 @@ struct LevelOps {
   // (hi, lo) in the K-major 128B-swizzled layout,
   // [slot][chunk of 128 B of l][plane][row m' < dp][128 B].
   void* kd_img = nullptr;
+  float* kd32 = nullptr;   // [343][l < d][m' < dp] FP32 folded operator (SIMT M2L of tier 2)
   int kd_img_tf32 = -1;  // -1 none, 0 BF16 planes, 1 TF32 planes
 };
 
@@ -90,7 +91,7 @@ struct Ops {
   double L = 1.0;
   int depth = 0;
   int tier = 0;        // arithmetic tier of the mixed path
-  double calib_err[3] = {-1.0, -1.0, -1.0};  // last calibration, per tier
+  double calib_err[4] = {-1.0, -1.0, -1.0, -1.0};  // last calibration, per tier
   int calib_tier = -1;
   LevelOps lv[kMaxLevel + 1];
   int* d_slot_lists = nullptr;  // [8][189] slot ids per parity class
@@ -194,6 +195,7 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma,
 eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R,
                           double* fnear, cudaStream_t s, bool accurate, float* gsym = nullptr);
 eifmm_status build_kd_image(Ops* ops, bool tf32, cudaStream_t s);
+eifmm_status build_kd32(Ops* ops, cudaStream_t s);
 eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, int gshift, cudaStream_t s);
 eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma,
                         int64_t ld_sigma, int R, double* f, int64_t ld_f,

@@ -176,7 +176,7 @@ class Ops:
     def calibration(self) -> dict:
         """The last calibration: tier kept and the error of each tier
         evaluated (None where it was not)."""
-        e, t = (C.c_double * 3)(), C.c_int()
+        e, t = (C.c_double * 4)(), C.c_int()
         _check(lib().eifmm_ops_calibration(self.handle, e, C.byref(t)))
         return {"tier": t.value, "err": [v if v >= 0 else None for v in e]}
 

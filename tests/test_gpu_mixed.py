@@ -184,7 +184,7 @@ def test_mixed_tiers_end_to_end(E, orc, eps, tol):
     x = wl.uniform_cube(n, 20)
     s = wl.sigma_uniform(n, 1, 21)
     ops = E.eifmm_ops_build("inv_r", 1.0, depth, eps)
-    assert ops.plan() in (0, 1, 2, 3)
+    assert ops.plan() in (0, 1, 2, 3, 4)
     tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
     f = torch.zeros(n, dtype=torch.float64, device="cuda")
     E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
@@ -327,7 +327,7 @@ def test_sphere_surface_points(E, orc):
         assert rel2(f.cpu().numpy()[idx], f1) <= eps, prec
 
 
-@pytest.mark.parametrize("tier", [0, 1, 2, 3])
+@pytest.mark.parametrize("tier", [0, 1, 2, 3, 4])
 def test_forced_tiers_run(E, orc, tier):
     """Every tier can be forced and stays within its own accuracy class."""
     n, depth, eps = 5000, 3, 1e-5
