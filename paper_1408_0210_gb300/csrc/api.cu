@@ -74,6 +74,10 @@ static void free_streams(Workspace* ws) {
   if (ws->ev_fork) cudaEventDestroy(ws->ev_fork);
   if (ws->ev_join) cudaEventDestroy(ws->ev_join);
   if (ws->side2) cudaStreamDestroy(ws->side2);
+  if (ws->hi) cudaStreamDestroy(ws->hi);
+  if (ws->ev_hi) cudaEventDestroy(ws->ev_hi);
+  ws->hi = nullptr;
+  ws->ev_hi = nullptr;
   if (ws->ev_fork2) cudaEventDestroy(ws->ev_fork2);
   if (ws->ev_join2) cudaEventDestroy(ws->ev_join2);
   for (auto& e : ws->ev_m2le)
@@ -110,7 +114,11 @@ eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec) {
     EIFMM_CUDA(cudaStreamCreateWithFlags(&ws.side, cudaStreamNonBlocking));
     EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_fork, cudaEventDisableTiming));
     EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_join, cudaEventDisableTiming));
-    EIFMM_CUDA(cudaStreamCreateWithFlags(&ws.side2, cudaStreamNonBlocking));
+    int prio_lo = 0, prio_hi = 0;
+    EIFMM_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+    EIFMM_CUDA(cudaStreamCreateWithPriority(&ws.side2, cudaStreamNonBlocking, prio_hi));
+    EIFMM_CUDA(cudaStreamCreateWithPriority(&ws.hi, cudaStreamNonBlocking, prio_hi));
+    EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_hi, cudaEventDisableTiming));
     EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_fork2, cudaEventDisableTiming));
     EIFMM_CUDA(cudaEventCreateWithFlags(&ws.ev_join2, cudaEventDisableTiming));
     for (auto& e : ws.ev_m2le) EIFMM_CUDA(cudaEventCreate(&e));

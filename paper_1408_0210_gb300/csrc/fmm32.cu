@@ -1120,6 +1120,13 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   EIFMM_TRY(launch_gather_sigma(sigma, ld_sigma, S, R, ws.sig, ws.sig32, s));
   EIFMM_CUDA(cudaEventRecord(ws.ev_fork, s));
   EIFMM_CUDA(cudaStreamWaitEvent(ws.side, ws.ev_fork, 0));
+  // the far field continues on the high-priority stream; the caller's stream
+  // waits for it at the end
+  const cudaStream_t caller = s;
+  if (!getenv("EIFMM_NO_PRIORITY")) {
+    EIFMM_CUDA(cudaStreamWaitEvent(ws.hi, ws.ev_fork, 0));
+    s = ws.hi;
+  }
   if (timing_enabled()) cudaEventRecord(ws.ev_nf[0], ws.side);
   const bool p2p_sym = use_p2p_sym(t, R, ops->tier >= 1, ws.gsym);
   EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, ws.side, ops->tier >= 1, ws.gsym));
@@ -1247,6 +1254,10 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   }
   EIFMM_CUDA(cudaMemcpyAsync(ws.err_host, ws.err, sizeof(int), cudaMemcpyDeviceToHost, s));
   record(ws, 8, s);
+  if (s != caller) {
+    EIFMM_CUDA(cudaEventRecord(ws.ev_hi, s));
+    EIFMM_CUDA(cudaStreamWaitEvent(caller, ws.ev_hi, 0));
+  }
   return EIFMM_OK;
 }
 

@@ -163,6 +163,11 @@ struct Workspace {
   // step 4: the coarse levels run here, concurrent with the leaf level
   cudaStream_t side2 = nullptr;
   cudaEvent_t ev_fork2 = nullptr, ev_join2 = nullptr;
+  // the far field of the mixed path runs here at the highest stream priority
+  // (side2 too), so the near field, at the default priority, fills the SMs
+  // it leaves free
+  cudaStream_t hi = nullptr;
+  cudaEvent_t ev_hi = nullptr;
   cudaEvent_t ev_t[10] = {};
   cudaEvent_t ev_m2l[kMaxLevel + 2] = {};   // start of the M2L launch of level k
   cudaEvent_t ev_m2le[kMaxLevel + 2] = {};  // and its end (on the stream that ran it)
