@@ -400,6 +400,8 @@ def main():
                    "unit": "rsqrt/s", "frac": evals / (nf_ms * 1e-3) / rs, "traffic": None,
                    "kernel": f"near field ({name}), {pairs} directed pairs, {evals} 1/r evaluations",
                    "pairs_per_s": pairs / (nf_ms * 1e-3), "launch_ms": nf_ms,
+                   "note": ("the near field runs at the lowest stream priority beside the far field, "
+                            "so launch_ms is its wall span inside the step, not its cost alone"),
                    "peak_source": "measured rsqrt.approx register loop",
                    "nominal_peak": SFU_PEAK}
 
