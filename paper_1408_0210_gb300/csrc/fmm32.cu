@@ -163,7 +163,7 @@ k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
       // before the sum so that their latency overlaps it
       int64_t i_out = 0;
       double fn0 = 0.0;
-      if (tid < P) {
+      if (tid < P && f) {
         i_out = perm[p];
         if (RCT == 1) fn0 = fnear[p + (int64_t)r0 * n];
       }
@@ -190,6 +190,7 @@ k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
           for (int k = 0; k < S; ++k) s += sp[rr * TPB + ti + k * P];
           const int rg = r0 + rr;
           if (ffar) ffar[p + rg * n] = s;
+          if (!f) continue;  // the far field alone; k_combine adds the near field
           double fn = RCT == 1 ? fn0 : fnear[p + rg * n];
           if (gsym) {  // R = 1
             const int m = s_gmask;
@@ -203,6 +204,16 @@ k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
         }
       }
     }
+  }
+}
+
+// f = f_far + f_N in the caller's order, once both are done (the far field
+// no longer waits for the near field before its L2P).
+__global__ void k_combine(const int32_t* __restrict__ perm, int64_t n, int R, const double* __restrict__ ffar,
+                          const double* __restrict__ fnear, double* __restrict__ f, int64_t ld_f) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * R; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / n, p = t - r * n;
+    f[perm[p] + r * ld_f] = ffar[t] + fnear[t];
   }
 }
 
@@ -1238,18 +1249,31 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     }
   }
   record(ws, 6, s);
-  EIFMM_CUDA(cudaStreamWaitEvent(s, ws.ev_join, 0));
-  record(ws, 7, s);
-  if (T.n_nonempty > 0) {
+  // step 7.  The L2P of the far field does not wait for the near field
+  // (which runs at the lower priority and ends last); a short kernel then
+  // adds the two in the caller's order.  The pair-symmetric near field needs
+  // the L2P's per-leaf neighbour test, so it keeps the combined L2P.
+  auto l2p = [&](double* fout) -> eifmm_status {
+    if (T.n_nonempty == 0) return EIFMM_OK;
     const unsigned nl = (unsigned)T.n_nonempty;
     const int rct = R == 1 ? 1 : RC;
     const size_t sm = (size_t)vl.d * sizeof(float4) + (size_t)((rct > 1 ? rct * vl.d : 0) + rct * TPB) * sizeof(float);
 #define EIFMM_L2P(K, RC_, A)                                                                     \
   k_l2p32<K, RC_, A><<<nl, TPB, sm, s>>>(kern, T.nonempty, T.leaf_off, T.perm, T.lx, T.ly, T.lz, T.n, R, \
-                                         vl.X32, vl.d, vl.dp, ws.lh32, ws.fnear, ws.ffar, f, ld_f,          \
+                                         vl.X32, vl.d, vl.dp, ws.lh32, ws.fnear, ws.ffar, fout, ld_f,       \
                                          p2p_sym ? ws.gsym : nullptr, kap)
     EIFMM_POINT_DISPATCH(EIFMM_L2P);
 #undef EIFMM_L2P
+    EIFMM_CHECK_LAUNCH();
+    return EIFMM_OK;
+  };
+  if (!p2p_sym) EIFMM_TRY(l2p(nullptr));
+  EIFMM_CUDA(cudaStreamWaitEvent(s, ws.ev_join, 0));
+  record(ws, 7, s);
+  if (p2p_sym) {
+    EIFMM_TRY(l2p(f));
+  } else if (T.n > 0) {
+    k_combine<<<grid_for(T.n * R, 256, 8192), 256, 0, s>>>(T.perm, T.n, R, ws.ffar, ws.fnear, f, ld_f);
     EIFMM_CHECK_LAUNCH();
   }
   EIFMM_CUDA(cudaMemcpyAsync(ws.err_host, ws.err, sizeof(int), cudaMemcpyDeviceToHost, s));
