@@ -1138,6 +1138,23 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     EIFMM_CUDA(cudaStreamWaitEvent(ws.hi, ws.ev_fork, 0));
     s = ws.hi;
   }
+  // when a step fails after the fork, the caller's stream still waits for
+  // every stream this call may have used, so that no work of the call is
+  // left unordered against the caller's next one
+  struct ForkGuard {
+    Workspace& w;
+    cudaStream_t caller;
+    bool armed = true;
+    ~ForkGuard() {
+      if (!armed) return;
+      cudaEventRecord(w.ev_join, w.side);
+      cudaStreamWaitEvent(caller, w.ev_join, 0);
+      cudaEventRecord(w.ev_join2, w.side2);
+      cudaStreamWaitEvent(caller, w.ev_join2, 0);
+      cudaEventRecord(w.ev_hi, w.hi);
+      cudaStreamWaitEvent(caller, w.ev_hi, 0);
+    }
+  } guard{ws, caller};
   if (timing_enabled()) cudaEventRecord(ws.ev_nf[0], ws.side);
   const bool p2p_sym = use_p2p_sym(t, R, ops->tier >= 1, ws.gsym);
   EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, ws.side, ops->tier >= 1, ws.gsym));
@@ -1282,6 +1299,7 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     EIFMM_CUDA(cudaEventRecord(ws.ev_hi, s));
     EIFMM_CUDA(cudaStreamWaitEvent(caller, ws.ev_hi, 0));
   }
+  guard.armed = false;
   return EIFMM_OK;
 }
 

@@ -386,3 +386,26 @@ def test_pair_symmetric_near_field(E, orc, case, monkeypatch):
         nb[i] = False
         terms = s[nb, 0] / np.linalg.norm(x[nb] - x[i], axis=1)
         assert abs(out["1"][1][i] - terms.sum()) <= 1e-5 * np.abs(terms).sum()
+
+
+def test_stream_layout_does_not_change_the_result(E, monkeypatch):
+    """The far field on the high-priority stream, the near field beside it
+    and the coarse M2L levels on a second stream: every sum has a fixed
+    order, so the result is bitwise the same as with everything on the
+    caller's stream (EIFMM_NO_PRIORITY) and across repeated calls."""
+    n, depth = 200000, 4
+    x = wl.uniform_cube(n, 91)
+    s = wl.sigma_uniform(n, 1, 92)
+    ops = E.eifmm_ops_build("inv_r", 1.0, depth, 1e-4)
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    out = []
+    for env in (None, "1", None):
+        if env is None:
+            monkeypatch.delenv("EIFMM_NO_PRIORITY", raising=False)
+        else:
+            monkeypatch.setenv("EIFMM_NO_PRIORITY", env)
+        f = torch.zeros(n, dtype=torch.float64, device="cuda")
+        E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
+        torch.cuda.synchronize()
+        out.append(f)
+    assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
