@@ -1,6 +1,6 @@
 // rates.cu -- measured per-GPU rates of the arithmetic the point kernels and
 // the FP64 path are bound by (FP32 FMA, the approximate reciprocal square
-// root, FP64 FMA), used as roofline denominators next to the driver-measured
+// root, FP64 FMA), used as roofline denominators next to the measured
 // HBM and BF16 peaks.  Register loops: 8 independent dependency chains per
 // thread, every SM filled, timed with CUDA events; no memory traffic beyond
 // one store per thread.
