@@ -71,7 +71,9 @@ typedef enum {
  *            tier 2: M2L on the FP32 SIMT pipes, each offset's sum in FP32
  *                    and the offsets added with compensated FP32 sums;
  *                    FP32 elsewhere with one Newton step on every 1/r;
- *            tier 3: far field in FP64, near field in FP32 (Kahan sums);
+ *            tier 3: far field in FP64 (its M2L in FP32 pairs, hi + lo,
+ *                    with exact product splits: about 46 bits), near
+ *                    field in FP32 (Kahan sums);
  *            tier 4: FP64 everywhere.
  *          In every tier the M2L applies K^delta Delta (built once with
  *          FP64 solves) to W, so step 3 needs no solve.

@@ -4,6 +4,8 @@
 // These kernels are the FP64 reference path on the GPU (and the baseline the
 // mixed-precision path is measured against): one thread per output entry,
 // operands staged in shared memory, operators read coalesced along m.
+#include <cstdlib>
+
 #include "internal.h"
 #include "transfer.cuh"
 #include "solve.cuh"
@@ -150,6 +152,115 @@ k_m2l64(int level, int d, int R, const double* __restrict__ kdT,
   }
 }
 
+
+// Step 4 of the mixed path's tier 3 (FP64 far field) with the FP64 numbers
+// carried as unevaluated sums of two FP32 numbers (hi + lo, about 46
+// significant bits) on the FP32 pipes, which run 72 times faster than the
+// FP64 ones on this GPU.  Each product hi_a hi_b is split exactly with an
+// FMA (p + e), the cross terms hi_a lo_b + lo_a hi_b are added in FP32, and
+// the running sum is an FP32 pair updated with an error-free two-sum.
+// Inputs and output are the FP64 arrays of the FP64 path; the split into
+// pairs happens while the tiles are staged.  Tile: 64 target boxes of one
+// parity class x 64 rows m', 4 x 4 per thread, terms l in chunks of 16.
+constexpr int DF_BOX = 64, DF_ROW = 64, DF_L = 16, DF_THREADS = 256;
+
+__device__ __forceinline__ void df_split(double x, float& h, float& l) {
+  h = (float)x;
+  l = (float)(x - (double)h);
+}
+
+__global__ void __launch_bounds__(DF_THREADS, 2)
+k_m2l_df(int level, int d, int R, const double* __restrict__ kdT, const int* __restrict__ slot_lists,
+         const double* __restrict__ W, double* __restrict__ g) {
+  __shared__ __align__(16) float sWh[DF_L][DF_BOX], sWl[DF_L][DF_BOX];  // [l][box]
+  __shared__ __align__(16) float sTh[DF_L][DF_ROW], sTl[DF_L][DF_ROW];  // [l][m']
+  __shared__ int64_t s_src[DF_BOX];
+  __shared__ int s_c[DF_BOX][3];
+  const int tid = threadIdx.x;
+  const int r = blockIdx.z;
+  const int oct = blockIdx.x & 7;
+  const int64_t per_class = (int64_t)1 << (3 * (level - 1));
+  const int nb = per_class < DF_BOX ? (int)per_class : DF_BOX;
+  const int64_t p0 = (blockIdx.x >> 3) * (int64_t)DF_BOX;
+  const int m0 = blockIdx.y * DF_ROW;
+  const int n = 1 << level;
+  if (tid < DF_BOX) {
+    int c[3] = {0, 0, 0};
+    if (tid < nb) morton_decode(8 * (p0 + tid) + oct, level, c);
+    s_c[tid][0] = c[0];
+    s_c[tid][1] = c[1];
+    s_c[tid][2] = c[2];
+  }
+  const int tb = (tid >> 4) * 4, tm = (tid & 15) * 4;
+  float ah[4][4], al[4][4];  // running sums of boxes tb.. x rows tm..
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) ah[i][j] = al[i][j] = 0.f;
+  const int* lst = slot_lists + oct * kListLen;
+  const int lb = tid >> 2, lq = (tid & 3) * 4;   // staging: box lb, terms lq..lq+3
+  const int ll = tid >> 4, lm = (tid & 15) * 4;  // staging: term ll, rows lm..lm+3
+  for (int s = 0; s < kListLen; ++s) {
+    const int slot = lst[s];
+    const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+    __syncthreads();
+    if (tid < DF_BOX) {
+      const int jx = s_c[tid][0] + dx, jy = s_c[tid][1] + dy, jz = s_c[tid][2] + dz;
+      const bool ok = tid < nb && jx >= 0 && jy >= 0 && jz >= 0 && jx < n && jy < n && jz < n;
+      s_src[tid] = ok ? (morton_encode(jx, jy, jz, level) * R + r) * d : -1;
+    }
+    __syncthreads();
+    const double* K = kdT + (int64_t)slot * d * d;
+    const int64_t so = s_src[lb];
+    for (int l0 = 0; l0 < d; l0 += DF_L) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int l = l0 + lq + q;
+        const double w = (so >= 0 && l < d) ? W[so + l] : 0.0;
+        df_split(w, sWh[lq + q][lb], sWl[lq + q][lb]);
+        const int lk = l0 + ll, mp = m0 + lm + q;
+        const double kv = (lk < d && mp < d) ? __ldg(K + (int64_t)lk * d + mp) : 0.0;
+        df_split(kv, sTh[ll][lm + q], sTl[ll][lm + q]);
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int u = 0; u < DF_L; ++u) {
+        const float4 wh = *reinterpret_cast<const float4*>(&sWh[u][tb]);
+        const float4 wl = *reinterpret_cast<const float4*>(&sWl[u][tb]);
+        const float4 th = *reinterpret_cast<const float4*>(&sTh[u][tm]);
+        const float4 tl = *reinterpret_cast<const float4*>(&sTl[u][tm]);
+        const float whv[4] = {wh.x, wh.y, wh.z, wh.w}, wlv[4] = {wl.x, wl.y, wl.z, wl.w};
+        const float thv[4] = {th.x, th.y, th.z, th.w}, tlv[4] = {tl.x, tl.y, tl.z, tl.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            // explicit roundings: no contraction may merge the product into
+            // the two-sum
+            const float p = __fmul_rn(whv[i], thv[j]);
+            const float e = fmaf(whv[i], thv[j], -p);
+            const float c = fmaf(whv[i], tlv[j], __fmul_rn(wlv[i], thv[j]));
+            const float sum = __fadd_rn(ah[i][j], p);
+            const float bb = __fsub_rn(sum, ah[i][j]);
+            const float err = __fadd_rn(__fsub_rn(ah[i][j], __fsub_rn(sum, bb)), __fsub_rn(p, bb));
+            al[i][j] += err + (e + c);
+            ah[i][j] = sum;
+          }
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (tb + i >= nb) break;
+    const int64_t I = 8 * (p0 + tb + i) + oct;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int mp = m0 + tm + j;
+      if (mp < d) g[(I * R + r) * d + mp] = (double)ah[i][j] + (double)al[i][j];
+    }
+  }
+}
 
 // Step 7 + sum + un-permute: f(x_i) = sum_l' K(x_i - c_I, y_l'^{I_0}) lhat_l'
 // + f_N(x_i), written to the caller's original order.
@@ -378,8 +489,13 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
     if (timing_enabled()) cudaEventRecord(ws.ev_m2l[k], s);
     const int d = ops->lv[k].d;
     const int64_t nb = (int64_t)1 << (3 * k);
-    k_m2l64<<<dim3((unsigned)(nb / 8 / M2L_NB * 8), R), TPB, M2L_NB * d * sizeof(double), s>>>(
-        k, d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.W[k], ws.g[k]);
+    if (near32 && !getenv("EIFMM_M2L_FP64"))  // tier 3 of the mixed path: FP32 pairs
+      k_m2l_df<<<dim3((unsigned)(((nb / 8 + DF_BOX - 1) / DF_BOX) * 8), (unsigned)((d + DF_ROW - 1) / DF_ROW),
+                      (unsigned)R), DF_THREADS, 0, s>>>(k, d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.W[k],
+                                                        ws.g[k]);
+    else
+      k_m2l64<<<dim3((unsigned)(nb / 8 / M2L_NB * 8), R), TPB, M2L_NB * d * sizeof(double), s>>>(
+          k, d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.W[k], ws.g[k]);
     EIFMM_CHECK_LAUNCH();
     if (timing_enabled()) cudaEventRecord(ws.ev_m2le[k], s);
   }

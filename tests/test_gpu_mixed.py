@@ -409,3 +409,27 @@ def test_stream_layout_does_not_change_the_result(E, monkeypatch):
         torch.cuda.synchronize()
         out.append(f)
     assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
+
+
+def test_tier3_pair_arithmetic_m2l(E, monkeypatch):
+    """Tier 3 (FP64 far field) runs its M2L on FP32 pairs (hi + lo, exact
+    product splits, two-sum accumulation); against the FP64 M2L
+    (EIFMM_M2L_FP64) every level's g agrees to about 1e-12."""
+    n, depth, eps = 60000, 4, 1e-6
+    x = wl.uniform_cube(n, 93)
+    s = wl.sigma_uniform(n, 1, 94)
+    ops = E.eifmm_ops_build("inv_r", 1.0, depth, eps)
+    ops.plan(3)
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    g = {}
+    for env in ("0", "1"):
+        if env == "1":
+            monkeypatch.setenv("EIFMM_M2L_FP64", "1")
+        else:
+            monkeypatch.delenv("EIFMM_M2L_FP64", raising=False)
+        f = torch.zeros(n, dtype=torch.float64, device="cuda")
+        E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
+        torch.cuda.synchronize()
+        g[env] = {k: E.eifmm_debug_export(tree, 2, k, ops.error_estimate(k)[1]) for k in range(2, depth + 1)}
+    for k in range(2, depth + 1):
+        assert relmax(g["0"][k], g["1"][k]) <= 1e-11, k
