@@ -74,7 +74,8 @@ typedef enum {
  *            tier 3: far field in FP64 (its M2L in FP32 pairs, hi + lo,
  *                    with exact product splits: about 46 bits), near
  *                    field in FP32 (Kahan sums);
- *            tier 4: FP64 everywhere.
+ *            tier 4: FP64 everywhere (near field too) but the M2L, which
+ *                    runs in FP32 pairs as in tier 3.
  *          In every tier the M2L applies K^delta Delta (built once with
  *          FP64 solves) to W, so step 3 needs no solve.
  */
@@ -162,8 +163,9 @@ eifmm_status eifmm_ops_error_estimate(const eifmm_ops* ops, int level,
 
 /* Arithmetic tier that EIFMM_PREC_MIXED uses with these operators:
  * 0 = BF16 hi+lo M2L and an FP32 far field, 1 = TF32 hi+lo M2L and the FP64
- * Delta^t solve, 2 = FP32 SIMT M2L with compensated sums over the offsets, 3 = FP64
- * far field, 4 = FP64 everywhere (near field too).  eifmm_ops_load sets it
+ * Delta^t solve, 2 = FP32 SIMT M2L with compensated sums over the offsets,
+ * 3 = FP64 far field (M2L in FP32 pairs), 4 = FP64 everywhere, the near
+ * field too (M2L in FP32 pairs).  eifmm_ops_load sets it
  * from the built-in error estimate; `tier_override` >= 0 (at most 4) forces
  * a tier.  Errors: EINVAL (null ops, tier above 4). */
 eifmm_status eifmm_ops_plan(eifmm_ops* ops, int tier_override, int* tier);

@@ -453,8 +453,10 @@ static eifmm_status evaluate_impl(eifmm_tree* tree, const eifmm_ops* ops, const 
   Tree& t = tree->t;
   EIFMM_TRY(ensure_workspace(&t, &ops->o, n_rhs, prec));
   eifmm_status rc;
-  if (prec == EIFMM_PREC_FP64 || ops->o.tier >= 4)
+  if (prec == EIFMM_PREC_FP64)
     rc = eval_fp64(&t, &ops->o, sigma, ld_sigma, n_rhs, f, ld_f, s);
+  else if (ops->o.tier >= 4)  // FP64 everywhere, the M2L in FP32 pairs
+    rc = eval_fp64(&t, &ops->o, sigma, ld_sigma, n_rhs, f, ld_f, s, false, true);
   else
     rc = eval_mixed(&t, &ops->o, sigma, ld_sigma, n_rhs, f, ld_f, s);
   if (rc != EIFMM_OK) return rc;
@@ -475,7 +477,8 @@ static eifmm_status evaluate_impl(eifmm_tree* tree, const eifmm_ops* ops, const 
 // per leaf (the near field carries its usual share of the result) is
 // evaluated at depth min(depth, 4) with the operators' own kernel in FP64
 // and in every mixed tier; the cheapest tier whose relative L2
-// difference to FP64 stays below eps/4 is kept (tier 4: all FP64).
+// difference to FP64 stays below eps/4 is kept (else tier 4: FP64
+// throughout, the M2L in FP32 pairs).
 // ---------------------------------------------------------------------------
 extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_stream stream,
                                             int* tier_out) {

@@ -1109,7 +1109,7 @@ eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, i
 
 eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld_sigma, int R,
                         double* f, int64_t ld_f, cudaStream_t s) {
-  if (ops->tier == 3) return eval_fp64(t, ops, sigma, ld_sigma, R, f, ld_f, s, true);
+  if (ops->tier == 3) return eval_fp64(t, ops, sigma, ld_sigma, R, f, ld_f, s, true, true);
   Workspace& ws = t->ws;
   if (*ws.err_host != 0) {
     const int code = *ws.err_host;

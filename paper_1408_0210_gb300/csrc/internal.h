@@ -196,7 +196,8 @@ void free_ops(Ops* ops);
 
 eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma,
                        int64_t ld_sigma, int R, double* f, int64_t ld_f,
-                       cudaStream_t s, bool near32 = false);
+                       cudaStream_t s, bool near32 = false,
+                       bool pair_m2l = false);
 eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R,
                           double* fnear, cudaStream_t s, bool accurate, float* gsym = nullptr);
 eifmm_status build_kd_image(Ops* ops, bool tf32, cudaStream_t s);

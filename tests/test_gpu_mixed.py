@@ -414,7 +414,10 @@ def test_stream_layout_does_not_change_the_result(E, monkeypatch):
 def test_tier3_pair_arithmetic_m2l(E, monkeypatch):
     """Tier 3 (FP64 far field) runs its M2L on FP32 pairs (hi + lo, exact
     product splits, two-sum accumulation); against the FP64 M2L
-    (EIFMM_M2L_FP64) every level's g agrees to about 1e-12."""
+    (EIFMM_M2L_FP64) every level's g agrees to 1e-10 of its largest entry:
+    a pair holds about 48 bits and a product loses the lo x lo term and the
+    rounding of the FP32 cross terms (about 2^-47 relative), over some
+    30,000 terms whose magnitudes exceed the result's (measured 1.6e-11)."""
     n, depth, eps = 60000, 4, 1e-6
     x = wl.uniform_cube(n, 93)
     s = wl.sigma_uniform(n, 1, 94)
@@ -432,4 +435,4 @@ def test_tier3_pair_arithmetic_m2l(E, monkeypatch):
         torch.cuda.synchronize()
         g[env] = {k: E.eifmm_debug_export(tree, 2, k, ops.error_estimate(k)[1]) for k in range(2, depth + 1)}
     for k in range(2, depth + 1):
-        assert relmax(g["0"][k], g["1"][k]) <= 1e-11, k
+        assert relmax(g["0"][k], g["1"][k]) <= 1e-10, k
