@@ -212,17 +212,27 @@ k_m2l_df(int level, int d, int R, const double* __restrict__ kdT, const int* __r
     __syncthreads();
     const double* K = kdT + (int64_t)slot * d * d;
     const int64_t so = s_src[lb];
-    for (int l0 = 0; l0 < d; l0 += DF_L) {
+    // the FP64 entries of the next chunk are loaded while the current one is
+    // summed
+    double wq[4], kq[4];
+    auto load = [&](int l0) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int l = l0 + lq + q;
-        const double w = (so >= 0 && l < d) ? W[so + l] : 0.0;
-        df_split(w, sWh[lq + q][lb], sWl[lq + q][lb]);
+        wq[q] = (so >= 0 && l < d) ? W[so + l] : 0.0;
         const int lk = l0 + ll, mp = m0 + lm + q;
-        const double kv = (lk < d && mp < d) ? __ldg(K + (int64_t)lk * d + mp) : 0.0;
-        df_split(kv, sTh[ll][lm + q], sTl[ll][lm + q]);
+        kq[q] = (lk < d && mp < d) ? __ldg(K + (int64_t)lk * d + mp) : 0.0;
+      }
+    };
+    load(0);
+    for (int l0 = 0; l0 < d; l0 += DF_L) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        df_split(wq[q], sWh[lq + q][lb], sWl[lq + q][lb]);
+        df_split(kq[q], sTh[ll][lm + q], sTl[ll][lm + q]);
       }
       __syncthreads();
+      if (l0 + DF_L < d) load(l0 + DF_L);
 #pragma unroll 4
       for (int u = 0; u < DF_L; ++u) {
         const float4 wh = *reinterpret_cast<const float4*>(&sWh[u][tb]);
