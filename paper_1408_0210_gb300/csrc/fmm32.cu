@@ -582,7 +582,11 @@ k_m2l32s(int level, int d, int dp, int R, const float* __restrict__ kd32, const 
     s_c[tid][1] = c[1];
     s_c[tid][2] = c[2];
   }
-  const int tb = (tid >> 4) * 4, tm = (tid & 15) * 4;  // this thread's 4 boxes and 4 rows
+  // this thread's 4 rows and 4 boxes; the rows come from the warp index, so
+  // a warp whose 8 rows all lie at or beyond d (the padding of the last row
+  // tile) skips the sums
+  const int tm = (tid >> 4) * 4, tb = (tid & 15) * 4;
+  const bool rows_live = m0 + (tid >> 5) * 8 < d;
   float acc[4][4], cmp[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -636,7 +640,7 @@ k_m2l32s(int level, int d, int dp, int R, const float* __restrict__ kd32, const 
         kv = load_k(l0 + M2S_L);
       }
 #pragma unroll
-      for (int u = 0; u < M2S_L; ++u) {
+      for (int u = 0; u < M2S_L && rows_live; ++u) {
         const float4 a4 = *reinterpret_cast<const float4*>(&sW[u][tb]);
         const float4 b4 = *reinterpret_cast<const float4*>(&sT[u][tm]);
         const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};

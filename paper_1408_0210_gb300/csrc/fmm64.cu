@@ -191,7 +191,10 @@ k_m2l_df(int level, int d, int R, const double* __restrict__ kdT, const int* __r
     s_c[tid][1] = c[1];
     s_c[tid][2] = c[2];
   }
-  const int tb = (tid >> 4) * 4, tm = (tid & 15) * 4;
+  // rows from the warp index: a warp whose 8 rows all lie at or beyond d
+  // (the padding of the last row tile) skips the sums
+  const int tm = (tid >> 4) * 4, tb = (tid & 15) * 4;
+  const bool rows_live = m0 + (tid >> 5) * 8 < d;
   float ah[4][4], al[4][4];  // running sums of boxes tb.. x rows tm..
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -234,7 +237,7 @@ k_m2l_df(int level, int d, int R, const double* __restrict__ kdT, const int* __r
       __syncthreads();
       if (l0 + DF_L < d) load(l0 + DF_L);
 #pragma unroll 4
-      for (int u = 0; u < DF_L; ++u) {
+      for (int u = 0; u < DF_L && rows_live; ++u) {
         const float4 wh = *reinterpret_cast<const float4*>(&sWh[u][tb]);
         const float4 wl = *reinterpret_cast<const float4*>(&sWl[u][tb]);
         const float4 th = *reinterpret_cast<const float4*>(&sTh[u][tm]);
