@@ -995,7 +995,7 @@ static void p2p_launch(const Tree* t, int kern, const float* sig32, int R, doubl
 // on a tree whose targets are its sources; it runs when EIFMM_P2P_SYM=1
 // (read at every evaluate).  It is not the default: it measured slower than
 // the per-target kernel (588 against 423 us at 1M points).
-bool use_p2p_sym(const Tree* t, int R, bool accurate, const float* gsym) {
+static bool use_p2p_sym(const Tree* t, int R, bool accurate, const float* gsym) {
   const char* e = getenv("EIFMM_P2P_SYM");
   return gsym && !accurate && R == 1 && t->same && t->exclude_self && e && strcmp(e, "1") == 0;
 }
