@@ -436,3 +436,20 @@ def test_tier3_pair_arithmetic_m2l(E, monkeypatch):
         g[env] = {k: E.eifmm_debug_export(tree, 2, k, ops.error_estimate(k)[1]) for k in range(2, depth + 1)}
     for k in range(2, depth + 1):
         assert relmax(g["0"][k], g["1"][k]) <= 1e-10, k
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-5, 1e-7])
+def test_calibration_report_is_consistent(E, eps):
+    """eifmm_ops_calibration reports what the calibration measured: the
+    kept tier is the planned one, every cheaper tier that was evaluated
+    missed eps/4, and the kept one (below 4) met it."""
+    ops = E.eifmm_ops_build("inv_r", 1.0, 3, eps)
+    rep = ops.calibration()
+    assert rep["tier"] == ops.plan()
+    err = rep["err"]
+    assert len(err) == 4
+    for t in range(rep["tier"]):
+        if t < 4 and err[t] is not None:
+            assert err[t] > eps / 4, (t, err)
+    if rep["tier"] < 4:
+        assert err[rep["tier"]] is not None and err[rep["tier"]] <= eps / 4
