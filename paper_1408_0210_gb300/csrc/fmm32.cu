@@ -104,9 +104,11 @@ k_p2m32(int kern_rt, const int32_t* __restrict__ off, const float* __restrict__ 
     }
   }
 }
-// Step 7 with the near field and the un-permute: one CTA per non-empty
-// target leaf, threads = (point, slice of l): P points of the leaf (up to
-// TPB per pass) times S = TPB / P interleaved slices of the d terms.
+// Step 7: one CTA per non-empty target leaf, threads = (point, slice of l):
+// P points of the leaf (up to TPB per pass) times S = TPB / P interleaved
+// slices of the d terms.  It writes the far field (ffar, leaf order); with
+// f non-null it also adds the near field (and the pair-symmetric partials,
+// gsym) and writes f in the caller's order, otherwise k_combine does that.
 template <int KERN, int RCT, bool ACC>
 __global__ void __launch_bounds__(TPB)
 k_l2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restrict__ off,
