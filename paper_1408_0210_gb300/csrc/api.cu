@@ -13,6 +13,7 @@
 namespace eifmm {
 
 static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint64_t> g_ops_uid{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static thread_local std::string g_err;
@@ -63,6 +64,7 @@ void free_workspace(Workspace* ws) {
   ws->lh = nullptr; ws->lh32 = nullptr; ws->sig = nullptr; ws->sig32 = nullptr;
   ws->fnear = nullptr; ws->ffar = nullptr;
   ws->ops_id = nullptr;
+  ws->ops_uid = 0;
   ws->nrhs = 0;
   ws->prec = -1;
   ws->tier = -1;
@@ -127,7 +129,8 @@ eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec) {
     for (auto& e : ws.ev_nf) EIFMM_CUDA(cudaEventCreate(&e));
   }
   const int tier = (prec == EIFMM_PREC_MIXED) ? ops->tier : -1;
-  if (ws.ops_id == (const void*)ops && ws.nrhs == R && ws.prec == prec && ws.tier == tier)
+  if (ws.ops_id == (const void*)ops && ws.ops_uid == ops->uid && ws.nrhs == R &&
+      ws.prec == prec && ws.tier == tier)
     return EIFMM_OK;
   free_workspace(&ws);
   const int kap = t->depth;
@@ -155,6 +158,7 @@ eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec) {
   EIFMM_TRY(dalloc(&ws.fnear, (size_t)(t->tgt.n > 0 ? t->tgt.n : 1) * R));
   EIFMM_TRY(dalloc(&ws.ffar, (size_t)(t->tgt.n > 0 ? t->tgt.n : 1) * R));
   ws.ops_id = ops;
+  ws.ops_uid = ops->uid;
   ws.nrhs = R;
   ws.prec = prec;
   ws.tier = tier;
@@ -234,6 +238,7 @@ extern "C" eifmm_status eifmm_ops_load(eifmm_kernel kern, double L, int depth,
   o.kern = kern;
   o.L = L;
   o.depth = depth;
+  o.uid = g_ops_uid.fetch_add(1, std::memory_order_relaxed) + 1;
   double eps_max = 0.0;
   cudaStream_t s = nullptr;
   eifmm_status rc = EIFMM_OK;
@@ -248,11 +253,11 @@ extern "C" eifmm_status eifmm_ops_load(eifmm_kernel kern, double L, int depth,
     if ((rc = dalloc(&v.Y, 3 * e.d)) != EIFMM_OK) break;
     if ((rc = dalloc(&v.G_rm, (size_t)e.d * e.d)) != EIFMM_OK) break;
     if ((rc = dalloc(&v.B_rm, (size_t)e.d * e.d)) != EIFMM_OK) break;
-    cudaMemcpy(v.X, e.X, 3 * e.d * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(v.Y, e.Y, 3 * e.d * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(v.G_rm, e.Gamma, (size_t)e.d * e.d * sizeof(double), cudaMemcpyHostToDevice);
-    if (cudaMemcpy(v.B_rm, e.B, (size_t)e.d * e.d * sizeof(double), cudaMemcpyHostToDevice) !=
-        cudaSuccess) {
+    const size_t dd = (size_t)e.d * e.d * sizeof(double);
+    if (cudaMemcpy(v.X, e.X, 3 * e.d * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(v.Y, e.Y, 3 * e.d * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(v.G_rm, e.Gamma, dd, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(v.B_rm, e.B, dd, cudaMemcpyHostToDevice) != cudaSuccess) {
       set_error("eifmm_ops_load: upload failed");
       rc = EIFMM_ECUDA;
     }
@@ -512,8 +517,12 @@ extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_st
     if ((rc = dalloc(&ds, n)) != EIFMM_OK) break;
     if ((rc = dalloc(&fr, n)) != EIFMM_OK) break;
     if ((rc = dalloc(&fm, n)) != EIFMM_OK) break;
-    cudaMemcpy(dx, hx.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(ds, hs.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    if (cudaMemcpy(dx, hx.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(ds, hs.data(), n * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+      rc = EIFMM_ECUDA;
+      set_error("eifmm_ops_calibrate: upload failed");
+      break;
+    }
     const double lo[3] = {0.0, 0.0, 0.0};
     if ((rc = eifmm_tree_build(dx, n, dx, n, lo, L, depth, 1, stream, &tree)) != EIFMM_OK) break;
     // a view of the operators restricted to the calibration depth

@@ -93,6 +93,8 @@ struct Ops {
   int tier = 0;        // arithmetic tier of the mixed path
   double calib_err[4] = {-1.0, -1.0, -1.0, -1.0};  // last calibration, per tier
   int calib_tier = -1;
+  uint64_t uid = 0;    // unique per loaded operator set: workspaces are keyed on it, not
+                       // on the handle's address, which a later load may reuse
   LevelOps lv[kMaxLevel + 1];
   int* d_slot_lists = nullptr;  // [8][189] slot ids per parity class
 };
@@ -116,6 +118,7 @@ struct PointSet {
 
 struct Workspace {
   const void* ops_id = nullptr;
+  uint64_t ops_uid = 0;
   int nrhs = 0;
   int prec = -1;
   int tier = -1;

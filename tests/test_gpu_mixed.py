@@ -453,3 +453,32 @@ def test_calibration_report_is_consistent(E, eps):
             assert err[t] > eps / 4, (t, err)
     if rep["tier"] < 4:
         assert err[rep["tier"]] is not None and err[rep["tier"]] <= eps / 4
+
+
+def test_workspace_follows_a_new_operator_set(E):
+    """A tree evaluated with an operator set that is then destroyed, and
+    evaluated again with a new set of other ranks d (whose handle may sit at
+    the freed address), sizes its workspace for the new set: the result is
+    bitwise that of a fresh tree."""
+    import gc
+    n, depth = 4096, 3
+    x = wl.uniform_cube(n, 95)
+    s = dev(wl.sigma_uniform(n, 1, 96)[:, 0])
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    f = torch.zeros(n, dtype=torch.float64, device="cuda")
+    a = E.eifmm_ops_build("inv_r", 1.0, depth, 1e-3)
+    a.plan(0)
+    d_a = [a.error_estimate(k)[1] for k in range(2, depth + 1)]
+    E.eifmm_evaluate(tree, a, s, f, "mixed")
+    torch.cuda.synchronize()
+    del a
+    gc.collect()
+    b = E.eifmm_ops_build("inv_r", 1.0, depth, 1e-5)
+    b.plan(0)
+    assert [b.error_estimate(k)[1] for k in range(2, depth + 1)] != d_a
+    E.eifmm_evaluate(tree, b, s, f, "mixed")
+    fresh = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    f2 = torch.zeros(n, dtype=torch.float64, device="cuda")
+    E.eifmm_evaluate(fresh, b, s, f2, "mixed")
+    torch.cuda.synchronize()
+    assert torch.equal(f, f2)
