@@ -296,8 +296,15 @@ eifmm_status eifmm_evaluate_host(eifmm_tree* tree, const eifmm_ops* ops,
 
 /* Many independent problems sharing one operator set (same kernel and L;
  * each tree's depth at most the operators'): problem p evaluates trees[p]
- * with DEVICE sigma[p] and f[p]
- * (one RHS each, ld = n).  Errors as eifmm_evaluate. */
+ * with DEVICE sigma[p] and f[p] (one RHS each, ld = n).  The first call
+ * evaluates the problems one after another on `stream` and records them into
+ * a CUDA graph; a later call with the same trees, arrays, operators,
+ * precision, tier and stream replays that graph with one launch.  The
+ * library keeps one such graph per process (a call with other arguments
+ * records a new one; destroying one of its trees or its operators drops
+ * it).  The legacy default stream (NULL) is never captured: every call on it
+ * evaluates directly.  Calls from several host threads are serialised.
+ * Errors as eifmm_evaluate. */
 eifmm_status eifmm_evaluate_batched(eifmm_tree* const* trees,
                                     const double* const* sigma,
                                     double* const* f, int n_problems,

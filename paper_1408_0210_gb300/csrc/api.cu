@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -757,11 +758,13 @@ struct BatchGraph {
   cudaStream_t stream = nullptr;
 };
 BatchGraph g_batch;
+std::mutex g_batch_mu;  // guards g_batch
 }  // namespace
 
 // A graph refers to the workspaces of its trees and operators: drop it when
 // one of them is destroyed.
 static void invalidate_batch(const void* h) {
+  std::lock_guard<std::mutex> lock(g_batch_mu);
   if (!g_batch.exec) return;
   for (const void* k : g_batch.key)
     if (k == h) {
@@ -788,6 +791,7 @@ extern "C" eifmm_status eifmm_evaluate_batched(eifmm_tree* const* trees, const d
     EIFMM_TRY(check_eval(trees[p], ops, 1, trees[p]->t.src.n, trees[p]->t.tgt.n, (int)prec));
   }
   cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lock(g_batch_mu);
   std::vector<const void*> key;
   key.push_back(ops);
   key.push_back((const void*)(intptr_t)prec);
