@@ -151,6 +151,24 @@ def test_interaction_list_brute_force(orc, level):
     assert total == {2: 3096, 3: 53352}[level]
 
 
+def test_list_sizes_match_the_separable_count(orc):
+    """Section 3.3 lists at full levels against a closed form: per dimension
+    a box at index i has the children of its parent's neighbours,
+    [2(i//2) - 2, 2(i//2) + 3] clipped to the grid, of which its own
+    neighbours [i - 1, i + 1] are excluded, so the number of (I, J) pairs of a
+    level is (sum of the first counts)^3 - (sum of the second)^3, and the near
+    (leaf, neighbour) pairs are (3n - 2)^3."""
+    for k in (2, 3, 4, 5):
+        n = 1 << k
+        sa = sum(min(n - 1, 2 * (i // 2) + 3) - max(0, 2 * (i // 2) - 2) + 1 for i in range(n))
+        sb = sum(min(n - 1, i + 1) - max(0, i - 1) + 1 for i in range(n))
+        got = sum(len(orc.interaction_list(k, I)) for I in range(8 ** k))
+        assert got == sa ** 3 - sb ** 3
+        assert sum(len(orc.neighbours(k, I)) for I in range(8 ** k)) == (3 * n - 2) ** 3
+    # all far-field levels of a full depth-5 tree: 6,039,504 M2L pairs
+    assert sum(len(orc.interaction_list(k, I)) for k in (2, 3, 4, 5) for I in range(8 ** k)) == 6039504
+
+
 def test_lists_tile_every_leaf_exactly_once(orc):
     kap = 3
     nleaf = 8 ** kap
