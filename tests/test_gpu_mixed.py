@@ -482,3 +482,40 @@ def test_workspace_follows_a_new_operator_set(E):
     E.eifmm_evaluate(fresh, b, s, f2, "mixed")
     torch.cuda.synchronize()
     assert torch.equal(f, f2)
+
+
+@pytest.mark.parametrize("tier", [0, 1, 2, 3, 4])
+def test_mixed_degenerate_inputs(E, orc, tier):
+    """Each forced tier on the degenerate trees: every point in one leaf
+    (3000 points: the near field alone, several source chunks and target
+    passes), a single point (f = 0 exactly), two far-apart points (the far
+    field alone), and targets without sources (f = 0 exactly)."""
+    eps = 1e-4
+    ops = E.eifmm_ops_build("inv_r", 1.0, 2, eps)
+    ops.plan(tier)
+    x = 0.01 * wl.uniform_cube(3000, 1)
+    s = wl.sigma_uniform(3000, 1, 2)[:, 0]
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, 2, True)
+    f = torch.zeros(3000, dtype=torch.float64, device="cuda")
+    E.eifmm_evaluate(tree, ops, dev(s), f, "mixed")
+    torch.cuda.synchronize()
+    assert rel2(f.cpu().numpy(), orc.direct_sum("inv_r", x, x, s)[:, 0]) <= eps
+    x1 = np.array([[0.3, 0.6, 0.9]])
+    t1 = E.eifmm_tree_build(dev(x1), None, (0, 0, 0), 1.0, 2, True)
+    f1 = torch.ones(1, dtype=torch.float64, device="cuda")
+    E.eifmm_evaluate(t1, ops, dev(np.array([2.0])), f1, "mixed")
+    torch.cuda.synchronize()
+    assert f1.item() == 0.0
+    x2 = np.array([[0.05, 0.05, 0.05], [0.95, 0.95, 0.95]])
+    s2 = np.array([1.0, -2.0])
+    t2 = E.eifmm_tree_build(dev(x2), None, (0, 0, 0), 1.0, 2, True)
+    f2 = torch.zeros(2, dtype=torch.float64, device="cuda")
+    E.eifmm_evaluate(t2, ops, dev(s2), f2, "mixed")
+    torch.cuda.synchronize()
+    assert rel2(f2.cpu().numpy(), orc.direct_sum("inv_r", x2, x2, s2)[:, 0]) <= eps
+    src = torch.zeros((0, 3), dtype=torch.float64, device="cuda")
+    t3 = E.eifmm_tree_build(src, dev(wl.uniform_cube(100, 3)), (0, 0, 0), 1.0, 2, False)
+    f3 = torch.ones(100, dtype=torch.float64, device="cuda")
+    E.eifmm_evaluate(t3, ops, torch.zeros(0, dtype=torch.float64, device="cuda"), f3, "mixed")
+    torch.cuda.synchronize()
+    assert bool((f3 == 0).all())
