@@ -317,9 +317,9 @@ eifmm_status eifmm_evaluate_batched(eifmm_tree* const* trees,
  *   what = 0 W (step 1-2), 1 What (step 3), 2 g (step 4), 3 l (step 5),
  *          4 lhat (step 6, level = depth), 5 f_far, 6 f_near (n_tgt x n_rhs
  *          column-major, original target order).
- * `n` is the capacity of `out` in doubles.  The operator set of that
- * evaluation must not have been destroyed since.  Synchronous.  Errors: EINVAL
- * when nothing was evaluated, the level is out of range or n is too small. */
+ * `n` is the capacity of `out` in doubles.  Synchronous.  Errors: EINVAL
+ * when nothing was evaluated, the level is out of range, n is too small, or
+ * (what 0-4) the operator set of that evaluation has been destroyed since. */
 eifmm_status eifmm_debug_export(const eifmm_tree* tree, int what, int level,
                                 double* out, int64_t n);
 

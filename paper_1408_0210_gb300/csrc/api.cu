@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <mutex>
+#include <set>
 #include <vector>
 
 #include "internal.h"
@@ -15,6 +16,13 @@ namespace eifmm {
 
 static std::atomic<uint64_t> g_launches{0};
 static std::atomic<uint64_t> g_ops_uid{0};
+// ids of the operator sets not yet destroyed
+static std::mutex g_live_mu;
+static std::set<uint64_t> g_live_ops;
+static bool ops_alive(uint64_t uid) {
+  std::lock_guard<std::mutex> lock(g_live_mu);
+  return g_live_ops.count(uid) != 0;
+}
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 static thread_local std::string g_err;
@@ -277,6 +285,10 @@ extern "C" eifmm_status eifmm_ops_load(eifmm_kernel kern, double L, int depth,
     delete h;
     return rc;
   }
+  {
+    std::lock_guard<std::mutex> lock(g_live_mu);
+    g_live_ops.insert(o.uid);
+  }
   *out = h;
   return EIFMM_OK;
 }
@@ -362,6 +374,10 @@ static void invalidate_batch(const void* h);
 
 extern "C" void eifmm_ops_destroy(eifmm_ops* ops) {
   if (!ops) return;
+  {
+    std::lock_guard<std::mutex> lock(g_live_mu);
+    g_live_ops.erase(ops->o.uid);
+  }
   invalidate_batch(ops);
   free_ops(&ops->o);
   delete ops;
@@ -861,7 +877,6 @@ extern "C" eifmm_status eifmm_debug_export(const eifmm_tree* tree, int what, int
   }
   const Tree& t = tree->t;
   const Workspace& ws = t.ws;
-  const Ops& o = reinterpret_cast<const eifmm_ops*>(ws.ops_id)->o;
   const int R = ws.nrhs;
   EIFMM_CUDA(cudaDeviceSynchronize());
   if (what == 5 || what == 6) {
@@ -882,6 +897,11 @@ extern "C" eifmm_status eifmm_debug_export(const eifmm_tree* tree, int what, int
     set_error("eifmm_debug_export: invalid `what` or level");
     return EIFMM_EINVAL;
   }
+  if (!ops_alive(ws.ops_uid)) {
+    set_error("eifmm_debug_export: the operators of the last evaluation were destroyed");
+    return EIFMM_EINVAL;
+  }
+  const Ops& o = reinterpret_cast<const eifmm_ops*>(ws.ops_id)->o;
   const int d = o.lv[level].d;
   const int64_t cnt = ((int64_t)1 << (3 * level)) * R * d;
   if (n < cnt) {

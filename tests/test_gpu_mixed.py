@@ -473,6 +473,10 @@ def test_workspace_follows_a_new_operator_set(E):
     torch.cuda.synchronize()
     del a
     gc.collect()
+    with pytest.raises(E.EifmmError, match="destroyed"):
+        E.eifmm_debug_export(tree, 0, 2, d_a[0])
+    f_far = E.eifmm_debug_export(tree, 5, depth, 0)  # still held by the tree
+    assert f_far.shape == (n, 1) and np.isfinite(f_far).all()
     b = E.eifmm_ops_build("inv_r", 1.0, depth, 1e-5)
     b.plan(0)
     assert [b.error_estimate(k)[1] for k in range(2, depth + 1)] != d_a
