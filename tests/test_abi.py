@@ -70,6 +70,21 @@ def test_argument_validation_without_device(E):
     assert L.eifmm_ops_build(0, 1.0, 3, -1.0, 100, None, C.byref(h)) == 1
     assert L.eifmm_evaluate(None, None, None, 0, 1, None, 0, 0, None) == 1
     assert L.eifmm_debug_export(None, 0, 2, None, 0) == 1
+    # every other entry point rejects a null handle or output before any device work
+    e, dk = C.c_double(), C.c_int()
+    assert L.eifmm_ops_error_estimate(None, 2, C.byref(e), C.byref(dk)) == 1
+    assert L.eifmm_ops_plan(None, 0, None) == 1
+    assert L.eifmm_ops_calibrate(None, 1e-4, None, None) == 1
+    assert L.eifmm_ops_calibration(None, None, None) == 1
+    assert L.eifmm_tree_export(None, 0, None, None, None) == 1
+    assert L.eifmm_evaluate_host(None, None, None, 0, 1, None, 0, 0, None) == 1
+    assert L.eifmm_evaluate_batched(None, None, None, 0, None, 0, None) == 1
+    assert L.eifmm_autotune(None, None, 1, 1, None, None) == 1
+    assert L.eifmm_last_step_times(None, None) == 1
+    assert L.eifmm_measure_rates(None, None) == 1
+    assert L.eifmm_direct_sum(0, None, 0, None, 0, None, 0, 1, 0, None, 0, None, None) == 1
+    L.eifmm_ops_destroy(None)
+    L.eifmm_tree_destroy(None)
 
 
 def test_binding_refuses_missing_library(tmp_path, monkeypatch):
