@@ -351,9 +351,12 @@ uint64_t eifmm_kernel_launches(void);
 /* Device times (ms) of the last evaluate on this tree, recorded with CUDA
  * events on the launching stream when timing is on (eifmm_set_timing(1);
  * the evaluate then waits for its last event).  ms[20]: [0] sigma gather +
- * P2M (step 1), [1] M2M (2), [2] Delta solves (3), [3] M2L (4), [4] L2L (5),
- * [5] Delta^t solve (6), [6] wait for the near field, [7] L2P + sum +
- * un-permute (7), [8] the near-field launch alone (on the library's side
+ * P2M (step 1), [1] M2M (2), [2] step 3 (Delta is folded into the M2L
+ * operator: nothing in the FP64 path, the hi/lo operand planes of W in the
+ * tensor-core tiers), [3] M2L (4), [4] L2L (5), [5] Delta^t solve (6);
+ * mixed path: [6] L2P of the far field + wait for the near field, [7] sum +
+ * un-permute; FP64 path: [6] wait for the near field, [7] L2P + sum +
+ * un-permute (7); [8] the near-field launch alone (on the library's side
  * stream); [9 + k] the M2L launch of level k alone. */
 void eifmm_set_timing(int on);
 eifmm_status eifmm_last_step_times(const eifmm_tree* tree, float* ms20);
