@@ -922,6 +922,16 @@ eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, boo
   return EIFMM_OK;
 }
 
+// One-time launch setup (the shared-memory limit of a kernel, whether its
+// clusters can be placed) belongs to one device's context, so it is
+// remembered per device.
+constexpr int kMaxDevices = 64;
+static int current_device() {
+  int d = 0;
+  cudaGetDevice(&d);
+  return d;
+}
+
 // Cluster size of the TMA M2L (B multicast): EIFMM_M2L_CLUSTER = 1, 2 or 4
 // (default 2).
 static int m2l_cluster_env() {
@@ -937,7 +947,11 @@ template <bool TF32, int CN>
 static eifmm_status launch_m2l_tma_cn(const CUtensorMap& m0, const CUtensorMap& m1, const M2LTcArgs& a,
                                       unsigned grid, size_t sm, cudaStream_t s, bool* ran) {
   auto kfn = k_m2l_tma<TF32, CN>;
-  static int state = 0;  // 0 unknown, 1 usable, -1 clusters of CN cannot be placed
+  // per device: 0 unknown, 1 usable, -1 clusters of CN cannot be placed
+  static int state_by_dev[kMaxDevices] = {};
+  const int dev = current_device();
+  int state_here = 0;
+  int& state = dev < kMaxDevices ? state_by_dev[dev] : state_here;
   if (state == 0) {
     EIFMM_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     state = 1;
@@ -1051,13 +1065,14 @@ eifmm_status launch_m2l_t256(const M2LTcArgs& a0, const void* map0, const void* 
     a.part_stride = 0;
   }
   const size_t sm = m2l_t256_smem_bytes();
-  static bool attr[2] = {false, false};
-  if (!attr[tf32]) {
+  static bool attr[kMaxDevices][2] = {};
+  const int dev = current_device();
+  if (dev >= kMaxDevices || !attr[dev][tf32]) {
     if (tf32)
       EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_t256<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     else
       EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_t256<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr[tf32] = true;
+    if (dev < kMaxDevices) attr[dev][tf32] = true;
   }
   const unsigned grid = (unsigned)(tiles * 8 * a.groups);
   const CUtensorMap& m0 = *(const CUtensorMap*)map0;
@@ -1087,13 +1102,14 @@ eifmm_status launch_m2l_tc(const M2LTcArgs& a0, bool tf32, cudaStream_t s) {
   a.chains = a.dp <= 128 ? 4 : (a.dp <= 256 ? 2 : 1);
   a.tmem_cols = 512;
   const size_t sm = m2l_tc_smem_bytes(a.dp, tf32);
-  static bool attr[2] = {false, false};
-  if (!attr[tf32]) {
+  static bool attr[kMaxDevices][2] = {};
+  const int dev = current_device();
+  if (dev >= kMaxDevices || !attr[dev][tf32]) {
     if (tf32)
       EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     else
       EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr[tf32] = true;
+    if (dev < kMaxDevices) attr[dev][tf32] = true;
   }
   const int64_t tiles = (a.nbox / 8 * a.R + kRows - 1) / kRows;
   if (a.groups > 1) {
