@@ -1,0 +1,25 @@
+"""Host-side work counts of bench.py, against the checker: the M2L pair
+counts behind the tensor-core roofline and the near-field pair count behind
+the reciprocal-square-root roofline, on a uniform and a clustered tree."""
+import numpy as np
+import pytest
+
+import bench
+from paper_1408_0210_gb300 import workloads as wl
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_m2l_pairs_equal_the_lists(orc, k):
+    assert bench.m2l_pairs(k) == sum(len(orc.interaction_list(k, I)) for I in range(8 ** k))
+
+
+@pytest.mark.parametrize("points,depth", [("uniform", 3), ("mixture", 4)])
+def test_near_field_pairs_by_brute_force(orc, points, depth):
+    x = wl.uniform_cube(3000, 61) if points == "uniform" else wl.gaussian_mixture(3000, 62)
+    keys, outside = orc.morton_keys(x, [0.0, 0.0, 0.0], 1.0, depth)
+    assert outside == 0
+    _, off = orc.sort_leaves(keys, depth)
+    cnt = np.diff(off)
+    want = sum(int(cnt[I]) * sum(int(cnt[J]) for J in orc.neighbours(depth, I))
+               for I in range(8 ** depth) if cnt[I]) - len(x)
+    assert bench.near_field_pairs(off, depth) == want
