@@ -23,3 +23,20 @@ def test_near_field_pairs_by_brute_force(orc, points, depth):
     want = sum(int(cnt[I]) * sum(int(cnt[J]) for J in orc.neighbours(depth, I))
                for I in range(8 ** depth) if cnt[I]) - len(x)
     assert bench.near_field_pairs(off, depth) == want
+
+
+def test_clock_summary_parses_the_sampler_lines():
+    """The clock record of the timed region: median SM clock under load, the
+    maximum, and which throttle reasons were ever active."""
+    c = bench.ClockSampler(0)
+    c.out = "\n".join([
+        "0, 1965, 2070, 610.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 900.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 1500, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "garbage line",
+    ])
+    s = c.summary()
+    assert s["samples"] == 3 and s["sm_max_mhz"] == 2070.0
+    assert s["sm_mhz"] == 1965.0 and s["reasons"] == ["sw_power_cap"]
+    c.out = ""
+    assert c.summary() is None
