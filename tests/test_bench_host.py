@@ -40,3 +40,14 @@ def test_clock_summary_parses_the_sampler_lines():
     assert s["sm_mhz"] == 1965.0 and s["reasons"] == ["sw_power_cap"]
     c.out = ""
     assert c.summary() is None
+
+
+def test_peaks_measured_or_fallback(tmp_path, monkeypatch):
+    """Roofline denominators: the measured file when present, else the
+    recipe's fallback (6.8 TB/s, 1.9 PFLOP/s burst), labelled as such."""
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    p = bench.peaks()
+    assert p["source"] == "fallback" and p["hbm_gbs"] == 6800.0 and p["bf16_tflops"] == 1900.0
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6696.5, "bf16_tflops": 1930.6}')
+    p = bench.peaks()
+    assert p["source"] == "measured" and p["hbm_gbs"] == 6696.5
