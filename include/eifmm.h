@@ -275,7 +275,7 @@ eifmm_status eifmm_evaluate(eifmm_tree* tree, const eifmm_ops* ops,
  * For the mixed path of tiers 0 and 1 it evaluates once with sigma = 0 (which
  * also sets up the workspace for n_rhs), then times at every level each
  * applicable M2L variant -- 1 transposed (M = coefficients, N = 256 target
- * rows), 2 128-row TMA, 3 128-row TMA with a 2-CTA cluster sharing K^delta --
+ * rows), 2 128-row TMA --
  * with the offset-group count halved, kept or doubled, against the built-in
  * rule (variant 0), using CUDA events on `stream`.  The fastest (by at least
  * 2% over the rule) is kept in the tree for later evaluations with the same

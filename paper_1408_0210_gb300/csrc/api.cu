@@ -673,7 +673,7 @@ extern "C" eifmm_status eifmm_autotune(eifmm_tree* tree, const eifmm_ops* ops, i
     for (int k = 2; k <= kap && rc == EIFMM_OK; ++k) {
       float best = 1e30f;
       int bk = 0, bg = 0;
-      for (int kind = 0; kind <= 3 && rc == EIFMM_OK; ++kind)
+      for (int kind = 0; kind <= 2 && rc == EIFMM_OK; ++kind)
         for (int gs = -1; gs <= 1; ++gs) {
           if (kind == 0 && gs != 0) continue;  // the built-in rule as it stands
           eifmm_status r = launch_m2l_level(&t, &ops->o, k, R, kind, gs, s);  // warm-up

@@ -1105,11 +1105,10 @@ eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, i
     // one the Morton-ordered planes
     if ((kind == 4) == ws.wa_grid[k]) return EIFMM_EUNSUPPORTED;
     a.groups = shift_groups(m2l_tc_groups((a.nbox / 8 * R + 127) / 128 * 8, nsm, a.dp), gshift);
-    a.cluster = rule ? 0 : (kind == 3 ? 2 : 1);
   }
   if (a.groups > 1 && (size_t)a.groups * a.rows * a.dp > cap) return EIFMM_EUNSUPPORTED;
   if (kind == 1) return launch_m2l_t256(a, ws.tmap2[k][0], ws.tmap2[k][1], tf32, s);
-  if (kind == 2 || kind == 3) return launch_m2l_tma(a, ws.tmap[k][0], ws.tmap[k][1], tf32, s);
+  if (kind == 2) return launch_m2l_tma(a, ws.tmap[k][0], ws.tmap[k][1], tf32, s);
   return launch_m2l_tc(a, tf32, s);
 }
 

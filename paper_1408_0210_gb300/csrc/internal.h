@@ -141,8 +141,8 @@ struct Workspace {
   // 256-row boxes of the transposed M2L (dp = 128)
   bool wa_t256[kMaxLevel + 1] = {};
   // M2L variant per level set by eifmm_autotune (0: built-in rule, 1:
-  // transposed, 2: 128-row, 3: 128-row with a 2-CTA cluster) and the shift of
-  // its offset-group count (groups << shift, or >> -shift)
+  // transposed, 2: 128-row) and the shift of its offset-group count
+  // (groups << shift, or >> -shift)
   int m2l_kind[kMaxLevel + 1] = {};
   int m2l_gshift[kMaxLevel + 1] = {};
   size_t m2l_part_cap = 0;  // floats in m2l_part (levels below the leaves)

@@ -349,34 +349,6 @@ k_m2l_tc(M2LTcArgs a) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)a.tmem_cols));
 }
 
-// Multicast forms (thread-block clusters): the bulk copy lands at the same
-// CTA-relative offset in every CTA of `mask` and signals the mbarrier at the
-// same offset in each; the commit arrives on the mbarrier of every CTA of
-// `mask`.
-__device__ __forceinline__ void bulk_g2s_mc(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar,
-                                            uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
-      "%4;" ::"r"(dst),
-      "l"(src), "r"(bytes), "r"(mbar), "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit_mc(uint32_t mbar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          mbar),
-      "h"(mask)
-      : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             int c3, int c4, uint32_t mbar) {
   asm volatile(
@@ -391,14 +363,9 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
 // the 128 source rows of a tile for one offset form a regular box of that
 // grid: one 5-D TMA tile load per plane brings them in, zero-filled outside
 // the cube.  Warp 4 produces (TMA for A, bulk copy for B), warp 5 issues the
-// MMAs, warps 0-3 drain the accumulators.
-//
-// CN > 1: a cluster of CN CTAs with the same parity class and offset group
-// and consecutive tiles walks the same offsets; each CTA copies 1/CN of the
-// K^delta image of a stage and multicasts it to all of them, so B is read
-// from L2 once per cluster.  A stage's `empty` barrier then collects the
-// commits of all CN CTAs' MMAs before any of them refills it.
-template <bool TF32, int CN>
+// MMAs, warps 0-3 drain the accumulators.  CTAs that share an offset read
+// the same K^delta image; they find it in L2.
+template <bool TF32>
 __global__ void __launch_bounds__(192, 1)
 k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1, M2LTcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -421,12 +388,9 @@ k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
 
   const int h = a.h, R = a.R;
   const int bxr = a.bx * R;  // merged (x, r) rows of the tile
-  const int rank = CN > 1 ? (int)cluster_rank() : 0;
-  const uint16_t cmask = (uint16_t)((1u << CN) - 1);
-  const int qb = blockIdx.x / CN;
-  const int oct = qb % 8;
-  const int grp = (qb / 8) % a.groups;
-  int tile = (qb / (8 * a.groups)) * CN + rank;  // tiles past the grid load zeros and store nothing
+  const int oct = blockIdx.x % 8;
+  const int grp = (blockIdx.x / 8) % a.groups;
+  int tile = blockIdx.x / (8 * a.groups);
   const int ntx = (h * R + bxr - 1) / bxr, nty = (h + a.by - 1) / a.by;
   const int tx = tile % ntx;
   tile /= ntx;
@@ -449,7 +413,7 @@ k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
   if (tid == 0) {
     for (int i = 0; i < kMaxStages; ++i) {
       mbar_init(full(i), 1);
-      mbar_init(empty(i), CN);
+      mbar_init(empty(i), 1);
     }
     mbar_init(done_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -462,14 +426,12 @@ k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (CN > 1) cluster_sync();  // every peer's barriers exist before the first multicast
   const uint32_t tmem = *tslot;
-  // number of offsets walked (same count in every thread; with CN > 1 the
-  // whole group, so that all CTAs of the cluster walk the same sequence)
+  // number of offsets walked (the same count in every thread)
   int nact = 0;
   for (int s = s_beg; s < s_end; ++s) {
     int sc, sxr, sy, sz;
-    nact += (CN > 1 || source(lst[s], &sc, &sxr, &sy, &sz)) ? 1 : 0;
+    nact += source(lst[s], &sc, &sxr, &sy, &sz) ? 1 : 0;
   }
   const int nit = nact * nchunk;
   bool ok = true;
@@ -481,7 +443,7 @@ k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
     for (int s = s_beg; s < s_end && ok; ++s) {
       const int slot = lst[s];
       int sc, sxr, sy, sz;
-      if (!source(slot, &sc, &sxr, &sy, &sz) && CN == 1) continue;
+      if (!source(slot, &sc, &sxr, &sy, &sz)) continue;
       for (int c = 0; c < nchunk && ok; ++c, ++it) {
         if (it >= S && !mbar_wait(empty(pst), pph ^ 1u, a.err, 1)) {
           ok = false;
@@ -494,12 +456,7 @@ k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
         tma_load_5d(sA, &tA0, c * E, sxr, sy, sz, sc, full(st));
         tma_load_5d(sA + a_bytes, &tA1, c * E, sxr, sy, sz, sc, full(st));
         const char* src = (const char*)a.kd_img + (((size_t)slot * nchunk + c) * 2) * b_bytes;
-        if (CN == 1) {
-          bulk_g2s(sA + 2 * a_bytes, src, 2 * b_bytes, full(st));
-        } else {
-          const uint32_t piece = 2 * b_bytes / CN;
-          bulk_g2s_mc(sA + 2 * a_bytes + rank * piece, src + rank * piece, piece, full(st), cmask);
-        }
+        bulk_g2s(sA + 2 * a_bytes, src, 2 * b_bytes, full(st));
       }
     }
   } else if (tid == 160) {
@@ -523,8 +480,7 @@ k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
       const uint64_t da = st == 0 ? dA0 : (st == 1 ? dA1 : dA2);
       const uint64_t db = st == 0 ? dB0 : (st == 1 ? dB1 : dB2);
       issue_chunk<TF32>(dacc, da, db, a_bytes >> 4, b_bytes >> 4, id_lo, id_hi, dp > 256, first);
-      if (CN == 1) mma_commit(empty(st));
-      else mma_commit_mc(empty(st), cmask);
+      mma_commit(empty(st));
       if (++st == S) st = 0, ph ^= 1u;
       if (++c == nchunk) {
         c = 0;
@@ -568,9 +524,6 @@ k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
   }
   tc_fence_before();
   __syncthreads();
-  // no CTA of the cluster leaves while a peer's copies or commits may still
-  // target its shared memory
-  if (CN > 1) cluster_sync();
   if (tid >= 128 && tid < 160)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)a.tmem_cols));
 }
@@ -922,76 +875,13 @@ eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, boo
   return EIFMM_OK;
 }
 
-// One-time launch setup (the shared-memory limit of a kernel, whether its
-// clusters can be placed) belongs to one device's context, so it is
-// remembered per device.
+// One-time launch setup (the shared-memory limit of a kernel) belongs to one
+// device's context, so it is remembered per device.
 constexpr int kMaxDevices = 64;
 static int current_device() {
   int d = 0;
   cudaGetDevice(&d);
   return d;
-}
-
-// Cluster size of the TMA M2L (B multicast): EIFMM_M2L_CLUSTER = 1, 2 or 4
-// (default 2).
-static int m2l_cluster_env() {
-  static const int cn = [] {
-    const char* e = getenv("EIFMM_M2L_CLUSTER");
-    const int v = e ? atoi(e) : 2;
-    return (v == 1 || v == 2 || v == 4) ? v : 2;
-  }();
-  return cn;
-}
-
-template <bool TF32, int CN>
-static eifmm_status launch_m2l_tma_cn(const CUtensorMap& m0, const CUtensorMap& m1, const M2LTcArgs& a,
-                                      unsigned grid, size_t sm, cudaStream_t s, bool* ran) {
-  auto kfn = k_m2l_tma<TF32, CN>;
-  // per device: 0 unknown, 1 usable, -1 clusters of CN cannot be placed
-  static int state_by_dev[kMaxDevices] = {};
-  const int dev = current_device();
-  int state_here = 0;
-  int& state = dev < kMaxDevices ? state_by_dev[dev] : state_here;
-  if (state == 0) {
-    EIFMM_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    state = 1;
-    if (CN > 1) {
-      cudaLaunchConfig_t q = {};
-      q.gridDim = dim3(CN * 64);
-      q.blockDim = dim3(192);
-      q.dynamicSmemBytes = sm;
-      cudaLaunchAttribute at;
-      at.id = cudaLaunchAttributeClusterDimension;
-      at.val.clusterDim.x = CN;
-      at.val.clusterDim.y = 1;
-      at.val.clusterDim.z = 1;
-      q.attrs = &at;
-      q.numAttrs = 1;
-      int nc = 0;
-      if (cudaOccupancyMaxActiveClusters(&nc, kfn, &q) != cudaSuccess || nc < 1) {
-        cudaGetLastError();
-        state = -1;
-      }
-    }
-  }
-  *ran = false;
-  if (state < 0) return EIFMM_OK;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(192);
-  cfg.dynamicSmemBytes = sm;
-  cfg.stream = s;
-  cudaLaunchAttribute at;
-  at.id = cudaLaunchAttributeClusterDimension;
-  at.val.clusterDim.x = CN;
-  at.val.clusterDim.y = 1;
-  at.val.clusterDim.z = 1;
-  cfg.attrs = &at;
-  cfg.numAttrs = 1;
-  EIFMM_CUDA(cudaLaunchKernelEx(&cfg, kfn, m0, m1, a));
-  EIFMM_CHECK_LAUNCH();
-  *ran = true;
-  return EIFMM_OK;
 }
 
 eifmm_status launch_m2l_tma(const M2LTcArgs& a0, const void* map0, const void* map1, bool tf32,
@@ -1015,27 +905,21 @@ eifmm_status launch_m2l_tma(const M2LTcArgs& a0, const void* map0, const void* m
     a.out = a.g;
     a.part_stride = 0;
   }
+  static bool attr[kMaxDevices][2] = {};
+  const int dev = current_device();
+  if (dev >= kMaxDevices || !attr[dev][tf32]) {
+    if (tf32)
+      EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    else
+      EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    if (dev < kMaxDevices) attr[dev][tf32] = true;
+  }
+  const unsigned grid = (unsigned)(tiles * 8 * a.groups);
   const CUtensorMap& m0 = *(const CUtensorMap*)map0;
   const CUtensorMap& m1 = *(const CUtensorMap*)map1;
-  int cn = a0.cluster > 0 ? a0.cluster : m2l_cluster_env();
-  while (cn > 1 && tiles < cn) cn >>= 1;
-  bool ran = false;
-  if (cn > 1) {
-    const int64_t tiles_pad = (tiles + cn - 1) / cn * cn;
-    const unsigned grid = (unsigned)(tiles_pad * 8 * a.groups);
-    if (cn == 4) {
-      if (tf32) EIFMM_TRY((launch_m2l_tma_cn<true, 4>(m0, m1, a, grid, sm, s, &ran)));
-      else EIFMM_TRY((launch_m2l_tma_cn<false, 4>(m0, m1, a, grid, sm, s, &ran)));
-    } else {
-      if (tf32) EIFMM_TRY((launch_m2l_tma_cn<true, 2>(m0, m1, a, grid, sm, s, &ran)));
-      else EIFMM_TRY((launch_m2l_tma_cn<false, 2>(m0, m1, a, grid, sm, s, &ran)));
-    }
-  }
-  if (!ran) {
-    const unsigned grid = (unsigned)(tiles * 8 * a.groups);
-    if (tf32) EIFMM_TRY((launch_m2l_tma_cn<true, 1>(m0, m1, a, grid, sm, s, &ran)));
-    else EIFMM_TRY((launch_m2l_tma_cn<false, 1>(m0, m1, a, grid, sm, s, &ran)));
-  }
+  if (tf32) k_m2l_tma<true><<<grid, 192, sm, s>>>(m0, m1, a);
+  else k_m2l_tma<false><<<grid, 192, sm, s>>>(m0, m1, a);
+  EIFMM_CHECK_LAUNCH();
   if (a.groups > 1) {
     const int64_t n4 = a.rows * (int64_t)a.dp / 4;
     k_sum_parts<<<(unsigned)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096), 256, 0, s>>>(

@@ -25,7 +25,6 @@ struct M2LTcArgs {
   int chains = 1;        // accumulators in TMEM (round-robin over offsets)
   int h = 0;             // TMA variant: boxes per axis per parity class
   int bx = 0, by = 0, bz = 0;  // TMA variant: tile block
-  int cluster = 0;             // TMA variant: CTAs sharing K^delta (0: default)
 };
 
 constexpr int kMaxDpTc = 320;

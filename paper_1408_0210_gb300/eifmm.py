@@ -284,7 +284,7 @@ def eifmm_measure_rates(stream=None) -> dict:
     return {"ffma_per_s": r[0], "rsqrt_per_s": r[1], "dfma_per_s": r[2]}
 
 
-M2L_VARIANTS = {0: "rule", 1: "transposed", 2: "128-row", 3: "128-row, 2-CTA cluster"}
+M2L_VARIANTS = {0: "rule", 1: "transposed", 2: "128-row"}
 
 
 def eifmm_autotune(tree: Tree, ops: Ops, n_rhs: int = 1, prec="mixed", stream=None) -> dict:
