@@ -29,6 +29,24 @@ def test_direct_sum_hand_example(orc):
     np.testing.assert_allclose(f, g["f"], rtol=1e-15, atol=0)
 
 
+def test_kernels_hand_values(orc):
+    """Every transcendental kernel branch of the oracle against its closed form
+    at points worked out by hand (tests/golden/kernels_hand.json; written by
+    make_kernels_hand.py from those closed forms alone).  The anisotropic
+    kernel is checked with the same |z| along each axis, so the 0.01 weight
+    on the second component is pinned to that axis."""
+    g = json.load(open(os.path.join(GOLD, "kernels_hand.json")))
+    seen = set()
+    for c in g["cases"]:
+        v = orc.kernel(c["kernel"], np.array([c["z"]]))[0]
+        assert abs(v - c["k"]) <= 1e-15 * abs(c["k"]), (c["kernel"], c["z"], v, c["k"])
+        seen.add(c["kernel"])
+    assert seen == {"config3", "exp_r2", "cos20r_r", "sqrt_r2p1"}
+    # a weight on another axis would change the value by orders of magnitude
+    by_z = {tuple(c["z"]): c["k"] for c in g["cases"] if c["kernel"] == "config3"}
+    assert by_z[(0.0, 10.0, 0.0)] > 9 * by_z[(10.0, 0.0, 0.0)]
+
+
 def test_direct_sum_closed_forms(orc):
     x = wl.uniform_cube(700, 11)
     y = wl.uniform_cube(500, 12)
