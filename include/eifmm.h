@@ -221,12 +221,12 @@ void eifmm_tree_destroy(eifmm_tree* tree);
 
 /* Morton bin/sort of one point set that allocates no memory at all.
  *
- * The paper has no counterpart: this entry point exists for callers that
- * cannot call cudaMalloc -- code recorded into a CUDA graph under a capture
- * mode that forbids allocation, programs whose device memory is owned by
- * another allocator (a framework's caching pool that would be bypassed or
- * starved by a raw cudaMalloc), and latency-bound loops that cannot afford
- * the implicit device synchronisation of cudaMalloc/cudaFree.
+ * The paper has no counterpart.  This entry point serves callers that cannot
+ * call cudaMalloc: programs whose device memory belongs to another allocator
+ * (a framework's caching pool, which a raw cudaMalloc would bypass and could
+ * starve of memory), programs that run inside a device-memory budget fixed
+ * when they start, and loops that cannot pay for the implicit device-wide
+ * synchronisation of cudaMalloc and cudaFree.
  *
  * It computes what eifmm_tree_build computes for the sources (same keys,
  * same stable permutation, same leaf offsets) into caller-owned DEVICE
@@ -241,10 +241,12 @@ void eifmm_tree_destroy(eifmm_tree* tree);
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
  * before any stream capture.  All calls share the one array and it keeps
- * the last call's contents: calls that overlap on the GPU (concurrent
- * streams, several host threads) race on it and must be serialised by the
- * caller.  The call synchronises `stream` (it reads back the count of points
- * outside the cube and returns EINVAL if there is any). */
+ * the last call's contents (the call clears the part that must start at
+ * zero): calls that overlap on the GPU (concurrent streams, several host
+ * threads) race on it and must be serialised by the caller.  The call
+ * waits for `stream`: it copies the count of points outside the cube to
+ * the host, synchronises the stream and returns EINVAL if the count is not
+ * zero. */
 #define EIFMM_STATIC_SORT_MAX_POINTS 1048576
 #define EIFMM_STATIC_SORT_SCRATCH_BYTES 8913296
 eifmm_status eifmm_tree_sort_static(const double* xyz, int64_t n,

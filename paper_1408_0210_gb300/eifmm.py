@@ -229,12 +229,49 @@ class Tree:
         return keys, perm, off
 
 
+def check_points(xyz, name: str = "xyz") -> None:
+    """Raise ValueError unless xyz is a contiguous float64 (n, 3) CUDA tensor
+    on the current device: the library reads 24 bytes per point from the
+    current device's memory."""
+    import torch
+    if not isinstance(xyz, torch.Tensor):
+        raise ValueError(f"{name}: a torch tensor is required")
+    if xyz.dtype != torch.float64:
+        raise ValueError(f"{name}: dtype must be float64, not {xyz.dtype}")
+    if xyz.dim() != 2 or xyz.shape[1] != 3:
+        raise ValueError(f"{name}: shape must be (n, 3), not {tuple(xyz.shape)}")
+    if not xyz.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous (row-major n x 3)")
+    if not xyz.is_cuda:
+        raise ValueError(f"{name}: must be a CUDA tensor")
+    if xyz.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: on {xyz.device}, but the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+
+
+def check_int32_out(t, min_len: int, device, name: str) -> None:
+    """Raise ValueError unless t is a contiguous int32 CUDA tensor on `device`
+    with at least min_len elements (the library writes that many)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: a torch tensor is required")
+    if t.dtype != torch.int32:
+        raise ValueError(f"{name}: dtype must be int32, not {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if t.numel() < min_len:
+        raise ValueError(f"{name}: needs at least {min_len} elements, has {t.numel()}")
+    if not t.is_cuda or t.device != device:
+        raise ValueError(f"{name}: must be a CUDA tensor on {device}, not {t.device}")
+
+
 def eifmm_tree_build(src_xyz, tgt_xyz=None, lo=(0.0, 0.0, 0.0), L: float = 1.0, depth: int = 3,
                      exclude_self: bool = True, stream=None) -> Tree:
-    """src_xyz / tgt_xyz: CUDA float64 tensors of shape (n, 3), contiguous."""
+    """src_xyz / tgt_xyz: CUDA float64 tensors of shape (n, 3), contiguous,
+    on the current device."""
     tgt = src_xyz if tgt_xyz is None else tgt_xyz
-    for t in (src_xyz, tgt):
-        assert t.is_cuda and t.dtype.is_floating_point and t.is_contiguous() and t.shape[-1] == 3
+    check_points(src_xyz, "src_xyz")
+    check_points(tgt, "tgt_xyz")
     lo = np.ascontiguousarray(lo, dtype=np.float64)
     h = C.c_void_p()
     _check(lib().eifmm_tree_build(_p(src_xyz), src_xyz.shape[0], _p(tgt), tgt.shape[0], _p(lo),
@@ -246,11 +283,21 @@ def eifmm_tree_build(src_xyz, tgt_xyz=None, lo=(0.0, 0.0, 0.0), L: float = 1.0, 
 def eifmm_evaluate(tree: Tree, ops: Ops, sigma, f, prec="fp64", stream=None) -> None:
     """sigma (n_src, R) and f (n_tgt, R): CUDA float64 tensors, column-major
     (use ``t.T.contiguous().T`` or allocate as ``torch.empty(R, n).T``)."""
+    import torch
+    for name, t, n in (("sigma", sigma, tree.n_src), ("f", f, tree.n_tgt)):
+        if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
+            raise ValueError(f"{name}: a float64 CUDA tensor is required")
+        if t.dim() not in (1, 2) or t.shape[0] != n:
+            raise ValueError(f"{name}: needs {n} rows, has shape {tuple(t.shape)}")
     R = 1 if sigma.dim() == 1 else sigma.shape[1]
+    if (1 if f.dim() == 1 else f.shape[1]) != R:
+        raise ValueError("sigma and f need the same number of columns")
     ld_s = sigma.shape[0] if sigma.dim() == 1 or R == 1 else sigma.stride(1)
     ld_f = f.shape[0] if f.dim() == 1 or R == 1 else f.stride(1)
-    if R > 1:
-        assert sigma.stride(0) == 1 and f.stride(0) == 1, "sigma and f must be column-major"
+    if (sigma.dim() == 1 or R == 1) and not (sigma.is_contiguous() and f.is_contiguous()):
+        raise ValueError("sigma and f must be contiguous")
+    if R > 1 and not (sigma.stride(0) == 1 and f.stride(0) == 1):
+        raise ValueError("sigma and f must be column-major")
     _check(lib().eifmm_evaluate(tree.handle, ops.handle, _p(sigma), ld_s, R, _p(f), ld_f,
                                 _prec(prec), _stream(stream)))
 
@@ -341,10 +388,19 @@ def eifmm_tree_sort_static(xyz, lo=(0.0, 0.0, 0.0), L: float = 1.0, depth: int =
                            keys=None, perm=None, leaf_off=None, stream=None):
     """Allocation-free bin/sort into caller-owned CUDA tensors (created here
     when not given): returns (keys uint32 as int32 bits, perm int32,
-    leaf_off int32)."""
+    leaf_off int32).  xyz: contiguous float64 (n, 3) CUDA tensor on the
+    current device; keys and perm: int32, at least n entries; leaf_off:
+    int32, at least 8^depth + 1 entries; all on xyz's device.  Invalid
+    arguments raise ValueError before anything runs on the GPU."""
     import torch
+    check_points(xyz, "xyz")
+    if not (2 <= int(depth) <= 10):
+        raise ValueError(f"depth must lie in [2, 10], not {depth}")
     n = xyz.shape[0]
     dev = xyz.device
+    for name, t, need in (("keys", keys, n), ("perm", perm, n), ("leaf_off", leaf_off, (1 << (3 * depth)) + 1)):
+        if t is not None:
+            check_int32_out(t, need, dev, name)
     if keys is None:
         keys = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
     if perm is None:

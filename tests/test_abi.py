@@ -95,3 +95,35 @@ def test_binding_refuses_missing_library(tmp_path, monkeypatch):
     with pytest.raises(RuntimeError, match="missing"):
         E.lib()
     importlib.reload(E)
+
+
+def test_binding_rejects_bad_tensors_before_any_launch(E):
+    """The binding checks dtype, shape, contiguity, device and output sizes of
+    the static sort and the tree build before it calls the library: a float32
+    or wrongly shaped array would make the kernels read past the buffer."""
+    torch = pytest.importorskip("torch")
+    n0 = E.eifmm_kernel_launches()
+    bad = [
+        (torch.zeros((10, 3), dtype=torch.float32), "float64"),
+        (torch.zeros((10, 4), dtype=torch.float64), "shape"),
+        (torch.zeros((3, 10), dtype=torch.float64).T, "contiguous"),
+        (torch.zeros((10, 6), dtype=torch.float64)[:, :3], "contiguous"),
+        (torch.zeros((10, 3), dtype=torch.float64), "CUDA"),
+        (np.zeros((10, 3)), "torch tensor"),
+    ]
+    for x, msg in bad:
+        with pytest.raises(ValueError, match=msg):
+            E.eifmm_tree_sort_static(x, (0, 0, 0), 1.0, 3)
+        with pytest.raises(ValueError, match=msg):
+            E.eifmm_tree_build(x, None, (0, 0, 0), 1.0, 3, True)
+    # output arrays: dtype, length and device, checked on their own
+    dev = torch.device("cpu")
+    with pytest.raises(ValueError, match="int32"):
+        E.check_int32_out(torch.zeros(10, dtype=torch.int64), 10, dev, "keys")
+    with pytest.raises(ValueError, match="at least 513"):
+        E.check_int32_out(torch.zeros(512, dtype=torch.int32), 513, dev, "leaf_off")
+    with pytest.raises(ValueError, match="contiguous"):
+        E.check_int32_out(torch.zeros(40, dtype=torch.int32)[::2], 10, dev, "perm")
+    with pytest.raises(ValueError, match="CUDA"):
+        E.check_int32_out(torch.zeros(10, dtype=torch.int32), 10, dev, "perm")
+    assert E.eifmm_kernel_launches() == n0

@@ -1,10 +1,10 @@
 """The allocation-free bin/sort (eifmm_tree_sort_static) against the regular
 tree build.
 
-Some callers cannot allocate device memory (graph capture that forbids it,
-memory owned by another allocator, loops that cannot afford cudaMalloc's
-synchronisation); this entry point sorts into caller-owned arrays with a
-static scratch array of the library.  Two calls in a row must reproduce the
+Some callers cannot allocate device memory (their memory is owned by another
+allocator, or fixed in a budget when they start, or their loops cannot pay
+for cudaMalloc's device-wide synchronisation); this entry point sorts into
+caller-owned arrays with a static scratch array of the library.  Two calls in a row must reproduce the
 regular entry point bit for bit (integer work), and the second call must not
 see anything left over by the first.  The file is named to be collected last.
 """
