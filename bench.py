@@ -158,14 +158,16 @@ def job_throughput(units_per_rank: float, world_size: int, ms: float) -> float:
     return units_per_rank * world_size / (ms * 1e-3)
 
 
-def cpu_oracle_run(n: int, depth: int, eps: float, steps: int):
-    """Time the CPU checker's EIFMM (O2) on n points; returns (seconds per
-    evaluation, threads, d per level)."""
+def cpu_oracle_run(n: int, depth: int, eps: float, steps: int, warmup: int = 0):
+    """Time the CPU checker's EIFMM (O2) on n points after `warmup` untimed
+    evaluations; returns (seconds per evaluation, threads, d per level)."""
     import oracle
     from paper_1408_0210_gb300 import workloads as wl
     x = wl.uniform_cube(n, 2)
     s = wl.sigma_uniform(n, NRHS, 102)
     lv = oracle.build_levels("inv_r", 1.0, depth, eps)
+    for _ in range(warmup):
+        oracle.eifmm("inv_r", 1.0, [0, 0, 0], depth, lv, x, x, s)
     times = []
     for _ in range(steps):
         t0 = time.perf_counter()
@@ -176,6 +178,8 @@ def cpu_oracle_run(n: int, depth: int, eps: float, steps: int):
 
 # the bounded CPU sample: 131,072 points at depth 4 keeps 32 points per leaf
 CPU_SAMPLE_N, CPU_SAMPLE_DEPTH = 1 << 17, 4
+CPU_SAMPLE_WORKLOAD = (f"uniform cube N={CPU_SAMPLE_N} (bounded sample of the N={N_POINTS} workload), "
+                       f"K=1/r, depth {CPU_SAMPLE_DEPTH} (32 points/leaf as in the workload), {NRHS} RHS")
 
 
 def reference_arm(args):
@@ -183,16 +187,15 @@ def reference_arm(args):
     if rank != 0:
         return
     eps = EPS_LIST[0]
-    for _ in range(max(args.warmup, 0)):
-        pass
-    sec, threads, ds = cpu_oracle_run(CPU_SAMPLE_N, CPU_SAMPLE_DEPTH, eps, max(1, args.steps))
+    sec, threads, ds = cpu_oracle_run(CPU_SAMPLE_N, CPU_SAMPLE_DEPTH, eps, max(1, args.steps),
+                                      max(args.warmup, 0))
     value = CPU_SAMPLE_N * NRHS / sec
     sample = (f"CPU EIFMM (plain FP64 C + OpenMP) on {CPU_SAMPLE_N} uniform points at depth "
               f"{CPU_SAMPLE_DEPTH} (32 points/leaf as in the workload), eps={eps:g}, d={ds}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "eps": eps},
+            "data": "synthetic", "config": {"workload": CPU_SAMPLE_WORKLOAD, "eps": eps},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -413,6 +416,8 @@ def main():
                    "peak_source": "measured rsqrt.approx register loop",
                    "nominal_peak": SFU_PEAK}
 
+    acc_ref = {"kind": "exact FP64 sum of Eq. (1) on the GPU (eifmm_direct_sum), self pair excluded",
+               "targets": SAMPLE_TARGETS}
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         sec, threads, ds = cpu_oracle_run(CPU_SAMPLE_N, CPU_SAMPLE_DEPTH, he, 1)
@@ -420,6 +425,14 @@ def main():
                "kind": "oracle",
                "sample": f"CPU EIFMM (plain FP64 C + OpenMP) on {CPU_SAMPLE_N} uniform points, "
                          f"depth {CPU_SAMPLE_DEPTH} (32 points/leaf), eps={he:g}, d={ds}"}
+        # the accuracy reference itself (the GPU exact sum) against the CPU
+        # oracle's exact sum O1 on the first 256 sampled targets
+        import oracle
+        i256 = idx[:256].cpu().numpy()
+        o1 = oracle.direct_sum("inv_r", x, x, s, exclude_self=True, tgt_idx=i256)[:, 0]
+        g1 = fref[:256].cpu().numpy()
+        acc_ref["max_rel_diff_vs_cpu_oracle_exact_sum"] = float(np.max(np.abs(g1 - o1)) / np.max(np.abs(o1)))
+        acc_ref["oracle_targets"] = 256
 
     line = {
         "metric": METRIC, "value": hr["value"], "unit": UNIT, "n_gpus": ws,
@@ -431,6 +444,7 @@ def main():
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": N_POINTS * NRHS * 8,
                 "d2h_bytes_per_step": N_POINTS * NRHS * 8},
         "gpu_launches": hr["gpu_launches"],
+        "accuracy_reference": acc_ref,
         "roofline": roof,
         "roofline_near_field": roof_nf,
         "measured_rates": rates,

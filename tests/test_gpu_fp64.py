@@ -253,25 +253,6 @@ def test_fp64_degenerate_inputs(E, orc):
         E.eifmm_evaluate(t3, ops, dev(np.array([1.0, -2.0])), f2, "fp64")
 
 
-def test_fp64_full_size_1m_depth5(E, orc):
-    """The 1M-point, depth-5 workload: the GPU FP64 path against the CPU
-    EIFMM element by element and against the exact sum on sampled targets."""
-    n, depth, eps = 1 << 20, 5, 1e-4
-    x = wl.uniform_cube(n, 2)
-    s = wl.sigma_uniform(n, 1, 102)
-    ops = E.eifmm_ops_build("inv_r", 1.0, depth, eps)
-    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
-    f = torch.zeros(n, dtype=torch.float64, device="cuda")
-    E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "fp64")
-    fg = f.cpu().numpy()
-    idx = wl.sample_targets(n, 400, 55)
-    f1 = orc.direct_sum("inv_r", x, x, s, tgt_idx=idx)[:, 0]
-    assert rel2(fg[idx], f1) <= eps
-    lv = _levels(orc, "inv_r", depth, eps)
-    f2 = orc.eifmm("inv_r", 1.0, [0, 0, 0], depth, lv, x, x, s)[:, 0]
-    assert relmax(fg, f2) <= 1e-12
-
-
 def test_direct_sum_matches_checker(E, orc):
     x = wl.uniform_cube(5000, 90)
     y = wl.gaussian_mixture(7000, 91)
