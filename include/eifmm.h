@@ -66,8 +66,11 @@ typedef enum {
  *                    products, FP32 accumulation in several chains), P2M,
  *                    M2M, L2L, L2P, the Delta solves and the near field in
  *                    FP32 on coordinates local to each leaf;
- *            tier 1: M2L with TF32 hi+lo operands, the Delta^t solve in
- *                    FP64, one Newton step on every FP32 1/r;
+ *            tier 1: M2L on tcgen05 with FP16 hi+lo operands (a power-of-
+ *                    two scale per level for W and per coefficient for the
+ *                    operator), each offset's FP32 accumulator drained from
+ *                    tensor memory into round-to-nearest FP32 sums; FP32
+ *                    elsewhere with one Newton step on every 1/r;
  *            tier 2: M2L on the FP32 SIMT pipes, each offset's sum in FP32
  *                    and the offsets added with compensated FP32 sums;
  *                    FP32 elsewhere with one Newton step on every 1/r;
@@ -162,8 +165,8 @@ eifmm_status eifmm_ops_error_estimate(const eifmm_ops* ops, int level,
                                       double* eps_k, int* d_k);
 
 /* Arithmetic tier that EIFMM_PREC_MIXED uses with these operators:
- * 0 = BF16 hi+lo M2L and an FP32 far field, 1 = TF32 hi+lo M2L and the FP64
- * Delta^t solve, 2 = FP32 SIMT M2L with compensated sums over the offsets,
+ * 0 = BF16 hi+lo M2L and an FP32 far field, 1 = FP16 hi+lo M2L with per-offset
+ * drains, 2 = FP32 SIMT M2L with compensated sums over the offsets,
  * 3 = FP64 far field (M2L in FP32 pairs), 4 = FP64 everywhere, the near
  * field too (M2L in FP32 pairs).  eifmm_ops_load sets it
  * from the built-in error estimate; `tier_override` >= 0 (at most 4) forces

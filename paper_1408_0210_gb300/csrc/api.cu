@@ -67,8 +67,9 @@ void free_workspace(Workspace* ws) {
   ws->m2l_part_leaf = nullptr;
   ws->m2l_part_leaf_cap = 0;
   for (int k = 0; k <= kMaxLevel; ++k) ws->m2l_kind[k] = ws->m2l_gshift[k] = 0;
-  dfree(ws->fnear); dfree(ws->ffar); dfree(ws->tmp); dfree(ws->gsym);
+  dfree(ws->fnear); dfree(ws->ffar); dfree(ws->tmp); dfree(ws->gsym); dfree(ws->wmax);
   ws->gsym = nullptr;
+  ws->wmax = nullptr;
   ws->tmp = nullptr;
   ws->lh = nullptr; ws->lh32 = nullptr; ws->sig = nullptr; ws->sig32 = nullptr;
   ws->fnear = nullptr; ws->ffar = nullptr;
@@ -278,7 +279,7 @@ extern "C" eifmm_status eifmm_ops_load(eifmm_kernel kern, double L, int depth,
     return rc;
   }
   o.tier = tier_for_eps(eps_max > 0.0 ? eps_max : 1e-16, false);
-  if (o.tier <= 1) rc = build_kd_image(&o, o.tier == 1, s);
+  if (o.tier <= 1) rc = build_kd_image(&o, o.tier == 1 ? kPlaneF16 : kPlaneBF16, s);
   else if (o.tier == 2) rc = build_kd32(&o, s);
   if (rc != EIFMM_OK) {
     free_ops(&o);
@@ -363,7 +364,7 @@ extern "C" eifmm_status eifmm_ops_plan(eifmm_ops* ops, int tier_override, int* t
   }
   if (tier_override >= 0) {
     ops->o.tier = tier_override;
-    if (tier_override <= 1) EIFMM_TRY(build_kd_image(&ops->o, tier_override == 1, nullptr));
+    if (tier_override <= 1) EIFMM_TRY(build_kd_image(&ops->o, tier_override == 1 ? kPlaneF16 : kPlaneBF16, nullptr));
     else if (tier_override == 2) EIFMM_TRY(build_kd32(&ops->o, nullptr));
   }
   if (tier) *tier = ops->o.tier;
@@ -557,12 +558,13 @@ extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_st
     double nref = 0.0;
     for (double v : href) nref += v * v;
     for (int t = 0; t <= 3 && rc == EIFMM_OK; ++t) {
-      if (t <= 1 && (rc = build_kd_image(&ops->o, t == 1, s)) != EIFMM_OK) break;
+      if (t <= 1 && (rc = build_kd_image(&ops->o, t == 1 ? kPlaneF16 : kPlaneBF16, s)) != EIFMM_OK) break;
       if (t == 2 && (rc = build_kd32(&ops->o, s)) != EIFMM_OK) break;
-      // a tier whose M2L operands could not be built (d too large) is skipped
+      // tier 0 needs its M2L operand image at every level (d too large: the
+      // tier is skipped); tier 1 runs the SIMT M2L where it has none
       bool have_img = true;
       for (int k = 2; k <= depth; ++k)
-        if (t <= 1 && ops->o.lv[k].kd_img == nullptr) have_img = false;
+        if (t == 0 && ops->o.lv[k].kd_img == nullptr) have_img = false;
       if (!have_img) continue;
       view.o = ops->o;
       view.o.depth = depth;

@@ -2,8 +2,10 @@
 //
 // Tier 0: P2M, M2M, the Delta^t solve, L2L and L2P in FP32 on coordinates
 // local to each leaf; M2L of the folded operator K^delta Delta on tcgen05
-// with BF16 hi + lo operand planes (m2l_tc.cu).  Tier 1: the Delta^t solve
-// in FP64, a Newton step on every 1/r and M2L with TF32 hi + lo planes.
+// with BF16 hi + lo operand planes (m2l_tc.cu).  Tier 1: a Newton step on
+// every 1/r and M2L with scaled FP16 hi + lo planes, each offset's tensor-
+// core accumulator drained into round-to-nearest FP32 sums (levels without
+// an FP16 tile use the tier-2 SIMT M2L).
 // Tier 2: the M2L on the FP32 SIMT pipes (compensated sums over the offsets),
 // the Delta^t solve in FP32, a Newton step on every 1/r.  Tier 3: the FP64 far field of fmm64.cu.  Tiers 0-3 evaluate the
 // near field here in FP32 (tiers >= 1 with Kahan compensated summation).
@@ -422,12 +424,229 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
   }
 }
 
+// ------------------------------------------- near field, packed pairs ----
+// The near field of 1/r with one right-hand side on the packed FP32 pipes.
+// Every FP32 add, multiply and FMA of a source-target interaction runs as a
+// The distance r2 of two sources at once is 3 packed differences and 3
+// packed multiply-adds (sub/mul/fma.rn.f32x2); 1/r and the sum run on each
+// half in place.  An interaction then issues 3 packed FP32 instructions per
+// pair, one approximate reciprocal square root (16 per clock per SM: the
+// bound), one FMA and one broadcast shared load.  The sources are staged as
+// SoA pairs, which puts both halves of a packed operand in one register
+// pair straight from shared memory:
+//   float4 [2q]     = (x_2q, x_2q+1, y_2q, y_2q+1)
+//   float4 [2q + 1] = (z_2q, z_2q+1, sigma_2q, sigma_2q+1)
+// in the frame of the target leaf.  The staged list is the 26 other
+// neighbour leaves, padded to a multiple of 16 sources, then the leaf
+// itself; a pad source sits far away (X2_FAR) with sigma = 0 and adds an
+// exact zero.  Threads = (target t, slice s) as in k_p2p32, one pass of P
+// targets (S = 128 / P slices) per leaf of up to 128 points; slice s holds
+// L pairs (a multiple of 8) and is followed by one unused pair, so the
+// slices a warp reads at once start in different banks.  Only the 8-pair
+// blocks that reach the leaf itself test for the self pair, whose sigma is
+// replaced by 0 (and its zero distance by 1).  Each
+// half keeps its own FP32 sum over 64 pairs; the sums are then flushed
+// (tier 0: FP32 Kahan totals; ACC: compensated per term and FP64 totals).
+// A chunk of X2_SRC sources is np <= 512 pairs; S slices of
+// L <= np / S + 7 pairs plus one gap each take at most 512 + 9 S <= 800.
+constexpr int X2_SRC = 1024;          // sources per chunk of the staged list
+constexpr int X2_MAXS = 32;           // slices per pass
+constexpr int X2_PAIRS = X2_SRC / 2 + 9 * X2_MAXS;  // staged pairs, gaps included
+constexpr float X2_FAR = 1.0e4f;
+
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void up2(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
+// r2 of the staged pair e[0..1] against the target (X, Y, Z), and sigma of
+// the pair.
+__device__ __forceinline__ void x2_r2(const ulonglong2* e, uint64_t X, uint64_t Y, uint64_t Z, uint64_t& r2,
+                                      uint64_t& sg) {
+  const ulonglong2 v0 = e[0], v1 = e[1];
+  const uint64_t xa = v0.x, ya = v0.y, za = v1.x;
+  sg = v1.y;
+  uint64_t dx, dy, dz;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(xa), "l"(X));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(ya), "l"(Y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(za), "l"(Z));
+  asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(r2) : "l"(dx));
+  asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(r2) : "l"(dy));
+  asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(r2) : "l"(dz));
+}
+
+// sum (+)= sigma / r for one half: 1/r is the approximate reciprocal square
+// root, with one Newton step y (1.5 - 0.5 r2 y^2) and a Kahan step when
+// ACC.  Scalar: the halves of r2 and sigma are read in place from their
+// register pairs, so nothing is packed.
+template <bool ACC>
+__device__ __forceinline__ void x2_term(float r2, float sg, float& sa, float& ca) {
+  float y = rsqrt_approx(r2);
+  if (ACC) {
+    y = y * fmaf(-0.5f * r2, y * y, 1.5f);
+    kahan_add(sa, ca, sg * y);
+  } else {
+    sa = fmaf(sg, y, sa);
+  }
+}
+
+template <bool ACC>
+__global__ void __launch_bounds__(P2P_THREADS)
+k_p2p32x2(const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff, const float* __restrict__ tlx,
+          const float* __restrict__ tly, const float* __restrict__ tlz, int64_t nt,
+          const int32_t* __restrict__ soff, const float* __restrict__ slx, const float* __restrict__ sly,
+          const float* __restrict__ slz, const float* __restrict__ sig, int depth, float two_l,
+          int exclude_self, double* __restrict__ fnear) {
+  __shared__ __align__(16) float4 s_pair[2 * X2_PAIRS];
+  __shared__ double s_red[P2P_THREADS];
+  __shared__ int s_pos[28];      // logical start of each segment, then the end
+  __shared__ int s_len[27];      // sources of each segment
+  __shared__ int s_beg[27];
+  __shared__ float s_sh[27][3];
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const int b = leaves[blockIdx.x];
+  int c[3];
+  morton_decode(b, depth, c);
+  const int n = 1 << depth;
+  if (tid < 27) {
+    const int nb = tid < 13 ? tid : (tid < 26 ? tid + 1 : 13);
+    const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
+    const int jx = c[0] + dx, jy = c[1] + dy, jz = c[2] + dz;
+    int beg = 0, len = 0;
+    if (jx >= 0 && jy >= 0 && jz >= 0 && jx < n && jy < n && jz < n) {
+      const int64_t J = morton_encode(jx, jy, jz, depth);
+      beg = soff[J];
+      len = soff[J + 1] - beg;
+    }
+    s_beg[tid] = beg;
+    s_len[tid] = len;
+    s_sh[tid][0] = dx * two_l;
+    s_sh[tid][1] = dy * two_l;
+    s_sh[tid][2] = dz * two_l;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    // logical positions: the other leaves from 0, the leaf itself from the
+    // next multiple of 16 (the gap holds pads)
+    int q = 0;
+    for (int i = 0; i < 26; ++i) s_pos[i] = q, q += s_len[i];
+    s_pos[26] = (q + 15) & ~15;
+    s_pos[27] = s_pos[26] + s_len[26];
+  }
+  __syncthreads();
+  const int n_other = s_pos[26], n_log = s_pos[27];
+  const int beg = toff[b], end = toff[b + 1];
+  for (int t0 = beg, P = 0; t0 < end; t0 += P) {
+    P = min(P2P_THREADS, end - t0);
+    const int S = min(P2P_THREADS / P, X2_MAXS);
+    const int ti = tid % P, si = tid / P;
+    const bool act = si < S;
+    const int p = t0 + (act ? ti : 0);
+    const float x0 = tlx[p], x1 = tly[p], x2 = tlz[p];
+    const uint64_t X = pk2(x0, x0), Y = pk2(x1, x1), Z = pk2(x2, x2);
+    // logical position of the self pair
+    const int js = exclude_self ? n_other + (p - beg) : -1;
+    float th0 = 0.f, tc0 = 0.f, th1 = 0.f, tc1 = 0.f;  // tier 0: FP32 Kahan totals per half
+    double td = 0.0;                                   // ACC: FP64 total
+    for (int c0 = 0; c0 < n_log; c0 += X2_SRC) {
+      const int cn = min(X2_SRC, n_log - c0);
+      const int np = (cn + 1) >> 1;
+      const int L = ((np + S - 1) / S + 7) & ~7;  // pairs per slice
+      const int used = S * (L + 1);
+      __syncthreads();
+      // pads everywhere, then the sources over them
+      for (int q = tid; q < used; q += P2P_THREADS) {
+        s_pair[2 * q] = make_float4(X2_FAR, X2_FAR, X2_FAR, X2_FAR);
+        s_pair[2 * q + 1] = make_float4(X2_FAR, X2_FAR, 0.f, 0.f);
+      }
+      __syncthreads();
+      for (int sg = w; sg < 27; sg += P2P_THREADS / 32) {
+        const int pb = s_pos[sg];
+        const int lo = max(pb, c0), hi = min(pb + s_len[sg], c0 + cn);
+        const float sx = s_sh[sg][0], sy = s_sh[sg][1], sz = s_sh[sg][2];
+        for (int pos = lo + lane; pos < hi; pos += 32) {
+          const int sj = s_beg[sg] + (pos - pb);
+          const int lp = pos - c0, q = lp >> 1, h = lp & 1;
+          float* e = (float*)&s_pair[2 * (q + q / L)];
+          e[h] = slx[sj] + sx;
+          e[2 + h] = sly[sj] + sy;
+          e[4 + h] = slz[sj] + sz;
+          e[6 + h] = sig[sj];
+        }
+      }
+      __syncthreads();
+      if (act) {
+        const int qs = js - c0 >= 0 && js - c0 < cn ? (js - c0) >> 1 : -1, hs = (js - c0) & 1;
+        const int qown = max(0, n_other - c0) >> 1;  // first pair of the leaf itself
+        const int qb = si * L;
+        float sl = 0.f, sh = 0.f, cl = 0.f, ch = 0.f;  // per half: sum, Kahan term
+        int cnt = 0;
+        for (int q8 = qb; q8 < qb + L; q8 += 8) {
+          const ulonglong2* a0 = reinterpret_cast<const ulonglong2*>(s_pair) + 2 * (q8 + si);
+          if (q8 + 8 <= qown || qs < 0) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              uint64_t r2, sg;
+              x2_r2(a0 + 2 * u, X, Y, Z, r2, sg);
+              float rl, rh, gl, gh;
+              up2(r2, rl, rh);
+              up2(sg, gl, gh);
+              x2_term<ACC>(rl, gl, sl, cl);
+              x2_term<ACC>(rh, gh, sh, ch);
+            }
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              uint64_t r2, sg;
+              x2_r2(a0 + 2 * u, X, Y, Z, r2, sg);
+              float rl, rh, gl, gh;
+              up2(r2, rl, rh);
+              up2(sg, gl, gh);
+              if (q8 + u == qs) {  // the self pair: sigma 0 at distance 1
+                if (hs) rh = 1.f, gh = 0.f;
+                else rl = 1.f, gl = 0.f;
+              }
+              x2_term<ACC>(rl, gl, sl, cl);
+              x2_term<ACC>(rh, gh, sh, ch);
+            }
+          }
+          if (++cnt == 8 || q8 + 8 >= qb + L) {  // flush every 64 pairs
+            cnt = 0;
+            if (ACC) {
+              td += ((double)sl - (double)cl) + ((double)sh - (double)ch);
+            } else {
+              kahan_add(th0, tc0, sl);
+              kahan_add(th1, tc1, sh);
+            }
+            sl = sh = cl = ch = 0.f;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (!ACC) td = ((double)th0 - (double)tc0) + ((double)th1 - (double)tc1);
+    s_red[tid] = act ? td : 0.0;
+    __syncthreads();
+    if (tid < P) {
+      double s = 0.0;
+      for (int k = 0; k < S; ++k) s += s_red[ti + k * P];
+      fnear[p] = s;
+    }
+  }
+}
+
 // --------------------------------------------------- operator images ----
 // K^delta (kdT[slot][l][m'] FP64) -> two planes in the swizzled image used
 // by the tensor-core M2L: byte offset of row n, 16-byte unit j inside the
 // 128-byte chunk: (n / 8) * 1024 + (n % 8) * 128 + ((j ^ (n % 8)) * 16).
-__global__ void k_build_img(const double* __restrict__ kdT, int d, int dp, int tf32,
-                            unsigned char* __restrict__ img) {
+// fmt: PlaneFmt; FP16 rows are scaled by kscale[m'] (a power of two).
+__global__ void k_build_img(const double* __restrict__ kdT, int d, int dp, int fmt,
+                            const float* __restrict__ kscale, unsigned char* __restrict__ img) {
+  const bool tf32 = fmt == kPlaneTF32;
   const int esz = tf32 ? 4 : 2;
   const int E = 128 / esz;  // elements per chunk
   const int nchunk = dp / E;
@@ -445,7 +664,13 @@ __global__ void k_build_img(const double* __restrict__ kdT, int d, int dp, int t
     for (int e = 0; e < per; ++e) {
       const int l = c * E + j * per + e;
       const double v = (l < d && nrow < d) ? kdT[((int64_t)slot * d + l) * d + nrow] : 0.0;
-      if (tf32) {
+      if (fmt == kPlaneF16) {
+        const double vs = v * (double)kscale[nrow];
+        const __half hi = __double2half(vs);
+        const __half lo = __double2half(vs - (double)__half2float(hi));
+        ((__half*)(base0 + off))[e] = hi;
+        ((__half*)(base1 + off))[e] = lo;
+      } else if (tf32) {
         const float hi = tf32_rn((float)v);
         const float lo = tf32_rn((float)(v - (double)hi));
         ((float*)(base0 + off))[e] = hi;
@@ -460,6 +685,49 @@ __global__ void k_build_img(const double* __restrict__ kdT, int d, int dp, int t
   }
 }
 
+// Power-of-two scale of row m' of the FP16 operator image: its largest
+// entry over the 316 far offsets and every l lands in [2^14, 2^15).  One
+// block per row.
+__global__ void k_kd_rowscale(const double* __restrict__ kdT, int d, int dp, float* __restrict__ kscale) {
+  const int row = blockIdx.x;
+  __shared__ float red[256];
+  float m = 0.f;
+  if (row < d)
+    for (int64_t t = threadIdx.x; t < (int64_t)kNumSlots * d; t += blockDim.x) {
+      const int slot = (int)(t / d), l = (int)(t - (int64_t)slot * d);
+      const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+      if (max(abs(dx), max(abs(dy), abs(dz))) < 2) continue;  // near offsets: not M2L
+      m = fmaxf(m, (float)fabs(kdT[((int64_t)slot * d + l) * d + row]));
+    }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + w]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) kscale[row] = f16_plane_scale(red[0]);
+}
+
+// wmax[k] = bits of max |W| over level k (levels lo..hi, one launch; wmax
+// zeroed before): non-negative floats order like their bit patterns.
+struct AbsMaxBatch {
+  const float* w[kMaxLevel + 1];
+  int64_t n[kMaxLevel + 1];
+  int lo = 0, hi = -1;
+};
+__global__ void __launch_bounds__(256) k_absmax(const __grid_constant__ AbsMaxBatch b, uint32_t* __restrict__ wmax) {
+  for (int k = b.lo; k <= b.hi; ++k) {
+    float m = 0.f;
+    const int64_t n4 = b.n[k] / 4;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+      const float4 v = reinterpret_cast<const float4*>(b.w[k])[i];
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(&wmax[k], __float_as_uint(m));
+  }
+}
+
 // planes -> FP64 [row][d] (debug export of What)
 // The M2L operand planes of W (hi and lo parts, BF16 or TF32) at every
 // level in one launch; entries j >= d are zero.  One thread per 4
@@ -469,16 +737,20 @@ struct PlaneLevel {
   const float* in;  // [rows][dp]
   void* out;        // [2][rows][dp] at plane_row order
   int64_t rows, q0; // q0: first quad of this level in the launch
-  int d, dp, grid_level, R;
+  int d, dp, grid_level, R, level;
 };
 struct PlaneBatch {
   PlaneLevel lv[kMaxLevel + 1];
   int nlev = 0;
   int64_t nq = 0;
+  const uint32_t* wmax = nullptr;  // FP16: bits of max |W| per level
 };
 
-template <bool TF32>
+// FMT: PlaneFmt.  FP16 planes hold W s_W = hi + lo with the level's scale
+// s_W = f16_plane_scale(max |W|).
+template <int FMT>
 __global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneBatch b) {
+  constexpr bool TF32 = FMT == kPlaneTF32;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < b.nq;
        q += (int64_t)gridDim.x * blockDim.x) {
     int li = 0;
@@ -502,6 +774,19 @@ __global__ void __launch_bounds__(256) k_planes(const __grid_constant__ PlaneBat
       float* p = (float*)L.out;
       *reinterpret_cast<float4*>(p + o) = h;
       *reinterpret_cast<float4*>(p + lo_off + o) = l;
+    } else if (FMT == kPlaneF16) {
+      const float sw = f16_plane_scale(__uint_as_float(b.wmax[L.level]));
+      x.x *= sw; x.y *= sw; x.z *= sw; x.w *= sw;  // exact: a power of two
+      const __half2 h01 = __floats2half2_rn(x.x, x.y), h23 = __floats2half2_rn(x.z, x.w);
+      const float2 f01 = __half22float2(h01), f23 = __half22float2(h23);
+      const __half2 l01 = __floats2half2_rn(x.x - f01.x, x.y - f01.y);
+      const __half2 l23 = __floats2half2_rn(x.z - f23.x, x.w - f23.y);
+      __half* p = (__half*)L.out;
+      uint2 hv, lv;
+      hv.x = *reinterpret_cast<const uint32_t*>(&h01); hv.y = *reinterpret_cast<const uint32_t*>(&h23);
+      lv.x = *reinterpret_cast<const uint32_t*>(&l01); lv.y = *reinterpret_cast<const uint32_t*>(&l23);
+      *reinterpret_cast<uint2*>(p + o) = hv;
+      *reinterpret_cast<uint2*>(p + lo_off + o) = lv;
     } else {
       const __nv_bfloat162 h01 = __floats2bfloat162_rn(x.x, x.y), h23 = __floats2bfloat162_rn(x.z, x.w);
       const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
@@ -671,22 +956,32 @@ k_m2l32s(int level, int d, int dp, int R, const float* __restrict__ kd32, const 
 
 }  // namespace
 
-eifmm_status build_kd_image(Ops* ops, bool tf32, cudaStream_t s) {
+eifmm_status build_kd_image(Ops* ops, int fmt, cudaStream_t s) {
+  const bool tf32 = fmt == kPlaneTF32;
   for (int k = 2; k <= ops->depth; ++k) {
     LevelOps& v = ops->lv[k];
-    if (v.kd_img_tf32 == (int)tf32) continue;
+    if (v.kd_img_fmt == fmt) continue;
     dfree(v.kd_img);
     v.kd_img = nullptr;
-    v.kd_img_tf32 = -1;
-    if (v.dp > kMaxDpTc) continue;  // the SIMT path serves these levels
+    v.kd_img_fmt = -1;
+    // the SIMT path serves larger levels (FP16: the drains hold dp <= 256)
+    if (v.dp > (fmt == kPlaneF16 ? 256 : kMaxDpTc)) continue;
+    if (fmt == kPlaneF16 && !v.kscale) {
+      EIFMM_TRY(dalloc(&v.kscale, (size_t)v.dp));
+      k_kd_rowscale<<<v.dp, 256, 0, s>>>(v.kdT, v.d, v.dp, v.kscale);
+      EIFMM_CHECK_LAUNCH();
+    }
     const size_t bytes = (size_t)kNumSlots * 2 * v.dp * (size_t)(v.dp * (tf32 ? 4 : 2));
     EIFMM_TRY(dmalloc(&v.kd_img, bytes));
     const int nchunk = v.dp * (tf32 ? 4 : 2) / 128;
     k_build_img<<<dim3(grid_for((int64_t)nchunk * v.dp * 8, 256, 64), kNumSlots), 256, 0, s>>>(
-        v.kdT, v.d, v.dp, tf32 ? 1 : 0, (unsigned char*)v.kd_img);
+        v.kdT, v.d, v.dp, fmt, v.kscale, (unsigned char*)v.kd_img);
     EIFMM_CHECK_LAUNCH();
-    v.kd_img_tf32 = tf32 ? 1 : 0;
+    v.kd_img_fmt = fmt;
   }
+  // tier 1 falls back to the SIMT M2L where it has no FP16 tile (dp above
+  // 256, or a right-hand-side count without a tile shape)
+  if (fmt == kPlaneF16) EIFMM_TRY(build_kd32(ops, s));
   EIFMM_CUDA(cudaStreamSynchronize(s));
   return EIFMM_OK;
 }
@@ -759,19 +1054,19 @@ eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R) {
     else EIFMM_TRY(dalloc(&ws.l32[k], n));
     EIFMM_TRY(dmalloc(&ws.wa[k], 2 * n * 4));
     // TMA-tiled M2L when the rhs count has a tile shape: planes on the
-    // per-class grid, one tensor map per plane
+    // per-class grid, one tensor map per plane (tier 0: BF16, tier 1: FP16)
     int bx, by, bz;
     ws.wa_grid[k] = false;
-    const bool tf32 = ops->tier == 1;
+    ws.wa_t256[k] = false;
+    const int fmt = ops->tier == 1 ? kPlaneF16 : kPlaneBF16;
     if (ops->tier <= 1 && ops->lv[k].dp <= kMaxDpTc && m2l_tma_block(R, &bx, &by, &bz)) {
-      const size_t plane = n * (tf32 ? 4 : 2);
-      EIFMM_TRY(make_plane_map(ws.tmap[k][0], ws.wa[k], k, R, dp, tf32));
-      EIFMM_TRY(make_plane_map(ws.tmap[k][1], (char*)ws.wa[k] + plane, k, R, dp, tf32));
+      const size_t plane = n * 2;
+      EIFMM_TRY(make_plane_map(ws.tmap[k][0], ws.wa[k], k, R, dp, fmt));
+      EIFMM_TRY(make_plane_map(ws.tmap[k][1], (char*)ws.wa[k] + plane, k, R, dp, fmt));
       ws.wa_grid[k] = true;
-      ws.wa_t256[k] = false;
-      if (dp == 128 && m2l_t256_block(R, &bx, &by, &bz)) {
-        EIFMM_TRY(make_plane_map(ws.tmap2[k][0], ws.wa[k], k, R, dp, tf32, 256));
-        EIFMM_TRY(make_plane_map(ws.tmap2[k][1], (char*)ws.wa[k] + plane, k, R, dp, tf32, 256));
+      if (fmt == kPlaneBF16 && dp == 128 && m2l_t256_block(R, &bx, &by, &bz)) {
+        EIFMM_TRY(make_plane_map(ws.tmap2[k][0], ws.wa[k], k, R, dp, fmt, 256));
+        EIFMM_TRY(make_plane_map(ws.tmap2[k][1], (char*)ws.wa[k] + plane, k, R, dp, fmt, 256));
         ws.wa_t256[k] = true;
       }
     }
@@ -790,12 +1085,15 @@ eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R) {
       if (G > 1) nd = std::max(nd, (size_t)G * rows * ops->lv[k].dp);
       const int G2 = m2l_t256_groups(m2l_t256_ctas(k, R), nsm);
       if (G2 > 1) nd = std::max(nd, (size_t)G2 * rows * ops->lv[k].dp);
+      const int G3 = ops->tier == 1 ? m2l_h16_groups(m2l_tma_ctas(k, R), nsm) : 1;
+      if (G3 > 1) nd = std::max(nd, (size_t)G3 * rows * ops->lv[k].dp);
     }
     if (need) EIFMM_TRY(dalloc(&ws.m2l_part, need));
     ws.m2l_part_cap = need;
     if (need_leaf) EIFMM_TRY(dalloc(&ws.m2l_part_leaf, need_leaf));
     ws.m2l_part_leaf_cap = need_leaf;
   }
+  if (!ws.wmax) EIFMM_TRY(dalloc(&ws.wmax, (size_t)kMaxLevel + 1));
   if (!ws.err) {
     EIFMM_TRY(dalloc(&ws.err, 1));
     EIFMM_CUDA(cudaMemset(ws.err, 0, sizeof(int)));
@@ -988,6 +1286,12 @@ static void p2p_launch(const Tree* t, int kern, const float* sig32, int R, doubl
                        cudaStream_t s) {
   const PointSet& T = t->tgt;
   const PointSet& S = t->src;
+  if (KERN == EIFMM_KERNEL_INV_R && RCT == 1) {  // 1/r, one right-hand side: packed pairs
+    k_p2p32x2<ACC><<<(unsigned)T.n_nonempty, P2P_THREADS, 0, s>>>(
+        T.nonempty, T.leaf_off, T.lx, T.ly, T.lz, T.n, S.leaf_off, S.lx, S.ly, S.lz, sig32, t->depth, two_l,
+        t->exclude_self, fnear);
+    return;
+  }
   k_p2p32<KERN, RCT, ACC><<<(unsigned)T.n_nonempty, P2P_THREADS, 0, s>>>(
       kern, T.nonempty, T.leaf_off, T.lx, T.ly, T.lz, T.n, S.leaf_off, S.lx, S.ly, S.lz,
       sig32, S.n, R, t->depth, two_l, t->exclude_self, fnear);
@@ -1069,9 +1373,16 @@ static int shift_groups(int g, int shift) {
 // not apply to this level.
 eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, int gshift, cudaStream_t s) {
   Workspace& ws = t->ws;
-  const bool tf32 = ops->tier == 1;
+  const bool tf32 = false;
+  const int fmt = ops->tier == 1 ? kPlaneF16 : kPlaneBF16;
   const LevelOps& v = ops->lv[k];
-  if (v.kd_img == nullptr || v.kd_img_tf32 != (int)tf32) {
+  if (ops->tier == 1 && (v.kd_img == nullptr || !ws.wa_grid[k])) {
+    // no FP16 tile for this level (dp above 256 or no tile shape for R): the
+    // SIMT M2L with its compensated sums serves it
+    if (kind != 0) return EIFMM_EUNSUPPORTED;
+    return launch_m2l_simt(t, ops, k, R, s);
+  }
+  if (v.kd_img == nullptr || v.kd_img_fmt != fmt) {
     set_error("eifmm_evaluate: tensor-core M2L operands missing for this level (d too large)");
     return EIFMM_EUNSUPPORTED;
   }
@@ -1091,6 +1402,12 @@ eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, i
   a.part = leaf ? ws.m2l_part_leaf : ws.m2l_part;
   const size_t cap = leaf ? ws.m2l_part_leaf_cap : ws.m2l_part_cap;
   const int nsm = sm_count();
+  if (ops->tier == 1) {  // FP16 planes, per-offset drains: one variant
+    if (kind != 0) return EIFMM_EUNSUPPORTED;
+    a.groups = shift_groups(m2l_h16_groups(m2l_tma_ctas(k, R), nsm), gshift);
+    if (a.groups > 1 && (size_t)a.groups * a.rows * a.dp > cap) return EIFMM_EUNSUPPORTED;
+    return launch_m2l_h16(a, ws.tmap[k][0], ws.tmap[k][1], ws.wmax, v.kscale, s);
+  }
   const bool rule = kind == 0;
   if (rule) {
     // the transposed kernel where a parity class fills at least one of its
@@ -1124,7 +1441,6 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
               std::to_string(code) + ")");
     return EIFMM_ETIMEOUT;
   }
-  const bool tf32 = ops->tier == 1;
   // P2M and L2P: the approximate reciprocal square root alone in tier 0
   // (relative error below 2^-22), one Newton step above
   const bool acc = ops->tier >= 1;
@@ -1197,17 +1513,30 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   const bool simt = ops->tier == 2;
   if (!simt) {
     PlaneBatch b;
+    AbsMaxBatch mb;
+    mb.lo = 2;
+    mb.hi = kap;
     for (int k = 2; k <= kap; ++k) {
       const LevelOps& v = ops->lv[k];
       PlaneLevel& L = b.lv[b.nlev++];
       L.in = ws.W32[k]; L.out = ws.wa[k];
       L.rows = nboxes(k) * R; L.q0 = b.nq;
-      L.d = v.d; L.dp = v.dp; L.grid_level = ws.wa_grid[k] ? k : -1; L.R = R;
+      L.d = v.d; L.dp = v.dp; L.grid_level = ws.wa_grid[k] ? k : -1; L.R = R; L.level = k;
       b.nq += L.rows * v.dp / 4;
+      mb.w[k] = ws.W32[k];
+      mb.n[k] = L.rows * v.dp;
     }
     const unsigned g = grid_for(b.nq, 256, 152 * 16);
-    if (tf32) k_planes<true><<<g, 256, 0, s>>>(b);
-    else k_planes<false><<<g, 256, 0, s>>>(b);
+    if (ops->tier == 1) {
+      // the FP16 planes need the largest |W| of every level first
+      EIFMM_CUDA(cudaMemsetAsync(ws.wmax, 0, (kMaxLevel + 1) * sizeof(uint32_t), s));
+      k_absmax<<<152 * 4, 256, 0, s>>>(mb, ws.wmax);
+      EIFMM_CHECK_LAUNCH();
+      b.wmax = ws.wmax;
+      k_planes<kPlaneF16><<<g, 256, 0, s>>>(b);
+    } else {
+      k_planes<kPlaneBF16><<<g, 256, 0, s>>>(b);
+    }
     EIFMM_CHECK_LAUNCH();
   }
   record(ws, 3, s);
@@ -1260,15 +1589,9 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   {
     DeltaBatch b;
     b.nlev = 1;
-    if (ops->tier == 1) {
-      b.lv[0] = delta_level(vl.d, delta_ops64(vl), true, ws.l32[kap], vl.dp, ws.lh32, vl.dp, nullptr,
-                            nboxes(kap) * R);
-      EIFMM_TRY((launch_delta_batch<double, float, float, 0>(b, true, s)));
-    } else {
-      b.lv[0] = delta_level(vl.d, delta_ops32(vl), true, ws.l32[kap], vl.dp, ws.lh32, vl.dp, nullptr,
-                            nboxes(kap) * R);
-      EIFMM_TRY((launch_delta_batch<float, float, float, 0>(b, true, s)));
-    }
+    b.lv[0] = delta_level(vl.d, delta_ops32(vl), true, ws.l32[kap], vl.dp, ws.lh32, vl.dp, nullptr,
+                          nboxes(kap) * R);
+    EIFMM_TRY((launch_delta_batch<float, float, float, 0>(b, true, s)));
   }
   record(ws, 6, s);
   // step 7.  The L2P of the far field does not wait for the near field

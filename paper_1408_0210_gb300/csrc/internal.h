@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <string>
@@ -83,7 +84,8 @@ struct LevelOps {
   // [slot][chunk of 128 B of l][plane][row m' < dp][128 B].
   void* kd_img = nullptr;
   float* kd32 = nullptr;   // [343][l < d][m' < dp] FP32 folded operator (SIMT M2L of tier 2)
-  int kd_img_tf32 = -1;  // -1 none, 0 BF16 planes, 1 TF32 planes
+  int kd_img_fmt = -1;     // -1 none, else the PlaneFmt of the image
+  float* kscale = nullptr; // [dp] power-of-two scale of row m' (FP16 image)
 };
 
 struct Ops {
@@ -150,6 +152,7 @@ struct Workspace {
   size_t m2l_part_leaf_cap = 0;
   alignas(64) unsigned char tmap2[kMaxLevel + 1][2][128] = {};
   float* m2l_part = nullptr;    // partial M2L sums of the split offset lists
+  uint32_t* wmax = nullptr;     // [kMaxLevel + 1] bits of max |W| per level (FP16 planes)
   int* err = nullptr;           // device error word of bounded waits
   int* err_host = nullptr;      // pinned copy, read at the next call
   void* tmp = nullptr;          // intermediate of the two Delta sweeps
@@ -203,7 +206,9 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma,
                        bool pair_m2l = false);
 eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R,
                           double* fnear, cudaStream_t s, bool accurate, float* gsym = nullptr);
-eifmm_status build_kd_image(Ops* ops, bool tf32, cudaStream_t s);
+// Element format of the tensor-core M2L operand planes.
+enum PlaneFmt { kPlaneBF16 = 0, kPlaneTF32 = 1, kPlaneF16 = 2 };
+eifmm_status build_kd_image(Ops* ops, int fmt, cudaStream_t s);
 eifmm_status build_kd32(Ops* ops, cudaStream_t s);
 eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, int gshift, cudaStream_t s);
 eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma,

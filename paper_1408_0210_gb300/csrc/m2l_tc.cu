@@ -756,6 +756,195 @@ k_m2l_t256(const __grid_constant__ CUtensorMap tW0, const __grid_constant__ CUte
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
 }
 
+// ---------------------------------------------------------------------------
+// FP16 M2L with per-offset drains (tier 1): M = 128 target rows, N = DP
+// coefficients m', K = l; operands are FP16 hi + lo planes, 3 products.
+// FP16 keeps 11 significant bits per plane against BF16's 8, so the split
+// operand holds about 22 bits; its narrow exponent range is met by scaling:
+// W of a level by a power of two s_W (its largest entry near 2^14) and row
+// m' of K^delta Delta by a power of two s_m' (common to all offsets), both
+// undone exactly in the epilogue.  The tensor core's FP32 accumulation
+// chain is cut after every offset: the 3 x K products of one offset go to
+// one of two TMEM accumulators while the eight drain warps read the other
+// with tcgen05.ld and add it, in round-to-nearest FP32, to running sums in
+// registers.  Warp 8 produces (two 5-D TMA loads of the W planes and one
+// bulk copy of the K^delta image per stage), warp 9 issues the MMAs; warp w
+// < 8 drains TMEM lanes 32 (w % 4) (tile rows) and columns DP/2 (w / 4).
+// ---------------------------------------------------------------------------
+constexpr int kH16Threads = 320;
+constexpr int kH16Stages = 2;
+
+template <int DP>
+__global__ void __launch_bounds__(kH16Threads, 1)
+k_m2l_h16(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUtensorMap tA1, M2LTcArgs a,
+          const uint32_t* __restrict__ wmax, const float* __restrict__ kscale) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int E = 64;                 // FP16 elements per 128-byte chunk
+  constexpr int NCH = DP / E;           // chunks of l per offset
+  constexpr int HALF = DP / 2;          // columns per drain warp
+  constexpr uint32_t a_bytes = 16384u;  // 128 rows x 128 B per plane
+  constexpr uint32_t b_bytes = DP * 128u;
+  constexpr uint32_t stage = 2 * a_bytes + 2 * b_bytes;
+  constexpr uint32_t tcols = 2 * DP <= 128 ? 128 : (2 * DP <= 256 ? 256 : 512);
+  uint64_t* bars = (uint64_t*)(smem + kH16Stages * stage);  // full[2] empty[2] afull[2] aempty[2]
+  uint32_t* tslot = (uint32_t*)(bars + 8);
+  volatile int* abort = (volatile int*)(tslot + 1);
+  float* s_inv = (float*)(bars + 9);  // [DP] 1 / (s_W s_m')
+  const uint32_t sbase = smem_u32(smem);
+  auto full = [&](int st) { return smem_u32(&bars[st]); };
+  auto empty = [&](int st) { return smem_u32(&bars[2 + st]); };
+  auto afull = [&](int b) { return smem_u32(&bars[4 + b]); };
+  auto aempty = [&](int b) { return smem_u32(&bars[6 + b]); };
+
+  const int h = a.h, R = a.R;
+  const int bxr = a.bx * R;
+  const int oct = blockIdx.x % 8;
+  const int grp = (blockIdx.x / 8) % a.groups;
+  int tile = blockIdx.x / (8 * a.groups);
+  const int ntx = (h * R + bxr - 1) / bxr, nty = (h + a.by - 1) / a.by;
+  const int tx = tile % ntx;
+  tile /= ntx;
+  const int ty = tile % nty, tz = tile / nty;
+  const int xr0 = tx * bxr, y0 = ty * a.by, z0 = tz * a.bz;
+  const int cx = oct & 1, cy = (oct >> 1) & 1, cz = (oct >> 2) & 1;
+  const int s_beg = grp * kListLen / a.groups, s_end = (grp + 1) * kListLen / a.groups;
+  const int* lst = a.slot_lists + oct * kListLen;
+
+  auto source = [&](int slot, int* sc, int* sxr, int* sy, int* sz) {
+    const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+    *sc = ((cx + dx) & 1) | (((cy + dy) & 1) << 1) | (((cz + dz) & 1) << 2);
+    *sxr = xr0 + ((cx + dx) >> 1) * R;
+    *sy = y0 + ((cy + dy) >> 1);
+    *sz = z0 + ((cz + dz) >> 1);
+    return *sxr < h * R && *sxr + bxr > 0 && *sy < h && *sy + a.by > 0 && *sz < h && *sz + a.bz > 0;
+  };
+
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(full(i), 1);
+      mbar_init(empty(i), 1);
+      mbar_init(afull(i), 1);
+      mbar_init(aempty(i), 8);  // one arrival per drain warp
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  {
+    const float sw = f16_plane_scale(__uint_as_float(wmax[a.level]));
+    for (int j = tid; j < DP; j += kH16Threads) s_inv[j] = 1.0f / (sw * kscale[j]);  // powers of two
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  int nact = 0;
+  for (int s = s_beg; s < s_end; ++s) {
+    int sc, sxr, sy, sz;
+    nact += source(lst[s], &sc, &sxr, &sy, &sz) ? 1 : 0;
+  }
+
+  if (tid == 256) {
+    // -------------------------------------------------------- producer --
+    int it = 0, st = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int s = s_beg; s < s_end && ok; ++s) {
+      const int slot = lst[s];
+      int sc, sxr, sy, sz;
+      if (!source(slot, &sc, &sxr, &sy, &sz)) continue;
+      for (int c = 0; c < NCH; ++c, ++it) {
+        if (it >= kH16Stages && !mbar_wait_ab(empty(st), ph ^ 1u, a.err, 1, abort)) {
+          ok = false;
+          break;
+        }
+        const uint32_t sA = sbase + st * stage;
+        mbar_expect_tx(full(st), 2 * a_bytes + 2 * b_bytes);
+        tma_load_5d(sA, &tA0, c * E, sxr, sy, sz, sc, full(st));
+        tma_load_5d(sA + a_bytes, &tA1, c * E, sxr, sy, sz, sc, full(st));
+        bulk_g2s(sA + 2 * a_bytes, (const char*)a.kd_img + (((size_t)slot * NCH + c) * 2) * b_bytes,
+                 2 * b_bytes, full(st));
+        if (++st == kH16Stages) st = 0, ph ^= 1u;
+      }
+    }
+  } else if (tid == 288) {
+    // ----------------------------------------------------- MMA issuer --
+    const uint32_t id = idesc(0u /* F16 */, (uint32_t)DP);
+    const uint64_t dA0 = sdesc(sbase), dA1 = sdesc(sbase + stage);
+    const uint64_t dB0 = dA0 + (2 * a_bytes >> 4), dB1 = dA1 + (2 * a_bytes >> 4);
+    int st = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int e = 0; e < nact && ok; ++e) {
+      const int b = e & 1;
+      if (e >= 2 && !mbar_wait_ab(aempty(b), ((e >> 1) - 1) & 1, a.err, 4, abort)) break;
+      tc_fence_after();
+      const uint32_t dacc = tmem + (uint32_t)(b * DP);
+      for (int c = 0; c < NCH; ++c) {
+        if (!mbar_wait_ab(full(st), ph, a.err, 2, abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        issue_chunk<false>(dacc, st == 0 ? dA0 : dA1, st == 0 ? dB0 : dB1, a_bytes >> 4, b_bytes >> 4, id, id,
+                           false, c == 0);
+        mma_commit(empty(st));
+        if (++st == kH16Stages) st = 0, ph ^= 1u;
+      }
+      if (ok) mma_commit(afull(b));
+    }
+  } else if (warp < 8) {
+    // ------------------------------------------------------- drains --
+    const int q = warp & 3, hf = warp >> 2;
+    float acc[HALF];
+#pragma unroll
+    for (int j = 0; j < HALF; ++j) acc[j] = 0.f;
+    for (int e = 0; e < nact; ++e) {
+      const int b = e & 1;
+      bool have = mbar_wait_ab(afull(b), (e >> 1) & 1, a.err, 3, abort);
+      have = __all_sync(0xffffffffu, have);
+      if (!have) break;
+      tc_fence_after();
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * DP + HALF * hf);
+#pragma unroll
+      for (int j0 = 0; j0 < HALF; j0 += 32) {
+        float v[32];
+        tmem_ld32(taddr + j0, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) acc[j0 + i] += v[i];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(aempty(b)) : "memory");
+    }
+    // tile row 32 q + lane: (x R + r fastest, then y, then z)
+    const int t = 32 * q + lane;
+    const int xr = xr0 + t % bxr;
+    const int yy = y0 + (t / bxr) % a.by;
+    const int zz = z0 + t / (bxr * a.by);
+    if (xr < h * R && yy < h && zz < h) {
+      const int x = xr / R, r = xr % R;
+      const int64_t I = morton_encode(2 * x + cx, 2 * yy + cy, 2 * zz + cz, a.level);
+      float* out = a.out + (size_t)grp * a.part_stride + (size_t)(I * R + r) * DP + HALF * hf;
+      const float* inv = s_inv + HALF * hf;
+#pragma unroll
+      for (int j = 0; j < HALF; j += 4)
+        *reinterpret_cast<float4*>(out + j) =
+            make_float4(acc[j] * inv[j], acc[j + 1] * inv[j + 1], acc[j + 2] * inv[j + 2], acc[j + 3] * inv[j + 3]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 8)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+}
+
 __global__ void k_sum_parts(const float4* __restrict__ parts, int groups, int64_t n4, int64_t stride4,
                             float4* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
@@ -847,7 +1036,7 @@ static EncodeTiledFn encode_fn() {
 }
 
 // Tensor map of one What plane in the grid layout of level `level`.
-eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, bool tf32, int rows) {
+eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, int fmt, int rows) {
   auto fn = encode_fn();
   if (!fn) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
@@ -858,13 +1047,16 @@ eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, boo
     set_error("no TMA tile shape for this number of right-hand sides");
     return EIFMM_EUNSUPPORTED;
   }
+  const bool tf32 = fmt == kPlaneTF32;
   const int esz = tf32 ? 4 : 2;
   const uint64_t h = (uint64_t)1 << (level - 1);
   cuuint64_t dims[5] = {(cuuint64_t)dp, h * R, h, h, 8};
   cuuint64_t strides[4] = {(cuuint64_t)dp * esz, h * R * dp * esz, h * h * R * dp * esz, h * h * h * R * dp * esz};
   cuuint32_t box[5] = {(cuuint32_t)(128 / esz), (cuuint32_t)(bx * R), (cuuint32_t)by, (cuuint32_t)bz, 1};
   cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-  const CUresult r = fn((CUtensorMap*)map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+  const CUtensorMapDataType dt = tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : (fmt == kPlaneF16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  const CUresult r = fn((CUtensorMap*)map, dt,
                         5, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -963,6 +1155,77 @@ eifmm_status launch_m2l_t256(const M2LTcArgs& a0, const void* map0, const void* 
   const CUtensorMap& m1 = *(const CUtensorMap*)map1;
   if (tf32) k_m2l_t256<true><<<grid, kT2Threads, sm, s>>>(m0, m1, a);
   else k_m2l_t256<false><<<grid, kT2Threads, sm, s>>>(m0, m1, a);
+  EIFMM_CHECK_LAUNCH();
+  if (a.groups > 1) {
+    const int64_t n4 = a.rows * (int64_t)a.dp / 4;
+    k_sum_parts<<<(unsigned)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096), 256, 0, s>>>(
+        (const float4*)a.part, a.groups, n4, a.part_stride / 4, (float4*)a.g);
+    EIFMM_CHECK_LAUNCH();
+  }
+  return EIFMM_OK;
+}
+
+size_t m2l_h16_smem_bytes(int dp) {
+  return (size_t)kH16Stages * (2 * 16384 + 2 * (size_t)dp * 128) + 1024 + 128 + 4 * (size_t)dp;
+}
+
+int64_t m2l_tma_ctas(int level, int R) {
+  int bx, by, bz;
+  if (!m2l_tma_block(R, &bx, &by, &bz)) return 0;
+  const int h = 1 << (level - 1), bxr = bx * R;
+  return (int64_t)((h * R + bxr - 1) / bxr) * ((h + by - 1) / by) * ((h + bz - 1) / bz) * 8;
+}
+
+// Offset groups of the FP16 M2L: the fewest that fill one wave of the SMs
+// (its per-offset drains need no extra chains for accuracy).
+int m2l_h16_groups(int64_t ctas, int nsm) {
+  int g = 1;
+  while (g < 16 && ctas * g < nsm) g *= 2;
+  return g;
+}
+
+eifmm_status launch_m2l_h16(const M2LTcArgs& a0, const void* map0, const void* map1, const uint32_t* wmax,
+                            const float* kscale, cudaStream_t s) {
+  M2LTcArgs a = a0;
+  if (!(a.dp == 64 || a.dp == 128 || a.dp == 192 || a.dp == 256) || !m2l_tma_block(a.R, &a.bx, &a.by, &a.bz)) {
+    set_error("FP16 M2L: needs dp in {64, 128, 192, 256} and a tile shape for R");
+    return EIFMM_EUNSUPPORTED;
+  }
+  a.h = 1 << (a.level - 1);
+  const int bxr = a.bx * a.R;
+  const int64_t tiles =
+      (int64_t)((a.h * a.R + bxr - 1) / bxr) * ((a.h + a.by - 1) / a.by) * ((a.h + a.bz - 1) / a.bz);
+  if (a.groups > 1) {
+    a.out = a.part;
+    a.part_stride = a.rows * (int64_t)a.dp;
+  } else {
+    a.out = a.g;
+    a.part_stride = 0;
+  }
+  const size_t sm = m2l_h16_smem_bytes(a.dp);
+  const int di = a.dp / 64 - 1;
+  static bool attr[kMaxDevices][4] = {};
+  const int dev = current_device();
+  if (dev >= kMaxDevices || !attr[dev][di]) {
+    cudaError_t e = cudaSuccess;
+    switch (a.dp) {
+      case 64: e = cudaFuncSetAttribute(k_m2l_h16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024); break;
+      case 128: e = cudaFuncSetAttribute(k_m2l_h16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024); break;
+      case 192: e = cudaFuncSetAttribute(k_m2l_h16<192>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024); break;
+      default: e = cudaFuncSetAttribute(k_m2l_h16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024); break;
+    }
+    EIFMM_CUDA(e);
+    if (dev < kMaxDevices) attr[dev][di] = true;
+  }
+  const unsigned grid = (unsigned)(tiles * 8 * a.groups);
+  const CUtensorMap& m0 = *(const CUtensorMap*)map0;
+  const CUtensorMap& m1 = *(const CUtensorMap*)map1;
+  switch (a.dp) {
+    case 64: k_m2l_h16<64><<<grid, kH16Threads, sm, s>>>(m0, m1, a, wmax, kscale); break;
+    case 128: k_m2l_h16<128><<<grid, kH16Threads, sm, s>>>(m0, m1, a, wmax, kscale); break;
+    case 192: k_m2l_h16<192><<<grid, kH16Threads, sm, s>>>(m0, m1, a, wmax, kscale); break;
+    default: k_m2l_h16<256><<<grid, kH16Threads, sm, s>>>(m0, m1, a, wmax, kscale); break;
+  }
   EIFMM_CHECK_LAUNCH();
   if (a.groups > 1) {
     const int64_t n4 = a.rows * (int64_t)a.dp / 4;

@@ -1,5 +1,7 @@
 // m2l_tc.h -- launcher of the tensor-core M2L (step 4 of Algorithm 3).
 #pragma once
+#include <cmath>
+
 #include "internal.h"
 
 namespace eifmm {
@@ -37,10 +39,31 @@ int64_t m2l_t256_ctas(int level, int R);  // CTAs of one offset group
 size_t m2l_t256_smem_bytes();
 // Tensor map (a 128-byte CUtensorMap, 64-byte aligned) of one What plane in
 // the per-class grid layout [class][Z][Y][X*R + r][dp].
-eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, bool tf32, int rows = 128);
+eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, int fmt, int rows = 128);
 eifmm_status launch_m2l_tma(const M2LTcArgs& a, const void* map0, const void* map1, bool tf32,
                             cudaStream_t s);
 eifmm_status launch_m2l_tc(const M2LTcArgs& a, bool tf32, cudaStream_t s);
+// FP16 hi + lo planes, per-offset drains (dp in {64, 128, 192, 256}): W
+// planes scaled by f16_plane_scale(max |W| of the level) (wmax: the bits of
+// that maximum per level), K^delta Delta rows by kscale[m'].
+size_t m2l_h16_smem_bytes(int dp);
+int64_t m2l_tma_ctas(int level, int R);   // CTAs of one offset group, 128-row tiles
+int m2l_h16_groups(int64_t ctas, int nsm);
+eifmm_status launch_m2l_h16(const M2LTcArgs& a, const void* map0, const void* map1, const uint32_t* wmax,
+                            const float* kscale, cudaStream_t s);
+
+// Power of two s with maxabs * s in [2^14, 2^15): the scale of an FP16
+// operand plane whose largest magnitude is maxabs (1 when maxabs is 0).  The
+// split x s = hi + lo then keeps hi and lo in FP16's normal range for every
+// entry within 2^-24 of the largest.
+__host__ __device__ inline float f16_plane_scale(float maxabs) {
+  if (!(maxabs > 0.0f) || maxabs > 3.0e38f) return 1.0f;
+  int e = 0;
+  frexpf(maxabs, &e);  // maxabs = m 2^e, m in [0.5, 1)
+  e = 15 - e;
+  e = e < -100 ? -100 : (e > 100 ? 100 : e);
+  return ldexpf(1.0f, e);
+}
 // Transposed variant (dp = 128): M = 128 (m'), N = 256 target rows per MMA.
 eifmm_status launch_m2l_t256(const M2LTcArgs& a, const void* map0, const void* map1, bool tf32,
                              cudaStream_t s);

@@ -275,6 +275,7 @@ void free_ops(Ops* ops) {
     for (int o = 0; o < 2; ++o) { dfree(v.piv64[o]); dfree(v.piv32[o]); }
     dfree(v.X32);
     dfree(v.kd_img);
+    dfree(v.kscale);
     dfree(v.kd32);
     v = LevelOps();
   }
