@@ -220,7 +220,31 @@ eifmm_status eifmm_tree_export(const eifmm_tree* tree, int which,
                                uint32_t* keys, int32_t* perm,
                                int64_t* leaf_off);
 
+/* Frees the tree and its workspace.  Evaluations of this tree that were
+ * enqueued on the caller's streams must have finished (synchronise those
+ * streams first); the library waits for its own streams of the tree. */
 void eifmm_tree_destroy(eifmm_tree* tree);
+
+/* Per-tree choices among equivalent kernels (no counterpart in the paper;
+ * for comparisons and tests: every default is the fastest measured).
+ *   M2L_128ROW: 1 runs the 128-row tensor-core M2L (M = target rows) where
+ *     the transposed one (M = coefficients, N = 256 target rows) would run;
+ *   P2P_PAIR_SYMMETRIC: 1 makes the tier-0 near field of one right-hand
+ *     side with targets = sources visit each unordered leaf pair once;
+ *   SINGLE_STREAM: 1 runs the whole evaluate on the caller's stream instead
+ *     of the near field, far field and coarse M2L levels on streams of their
+ *     own (the result is bitwise the same);
+ *   M2L_FP64: 1 runs the FP64 M2L instead of the FP32-pair one in tiers 3
+ *     and 4.
+ * The option holds for later evaluations of this tree.  Errors: EINVAL
+ * (null tree, unknown option, value other than 0 or 1). */
+typedef enum {
+  EIFMM_OPT_M2L_128ROW = 0,
+  EIFMM_OPT_P2P_PAIR_SYMMETRIC = 1,
+  EIFMM_OPT_SINGLE_STREAM = 2,
+  EIFMM_OPT_M2L_FP64 = 3
+} eifmm_option;
+eifmm_status eifmm_tree_set_option(eifmm_tree* tree, eifmm_option opt, int value);
 
 /* Morton bin/sort of one point set that allocates no memory at all.
  *

@@ -444,12 +444,25 @@ extern "C" eifmm_status eifmm_tree_export(const eifmm_tree* tree, int which, uin
 extern "C" void eifmm_tree_destroy(eifmm_tree* tree) {
   if (!tree) return;
   invalidate_batch(tree);
-  cudaDeviceSynchronize();
+  // the library's own streams of this tree finish first; work on the
+  // caller's streams is the caller's to finish (see the header)
+  Workspace& ws = tree->t.ws;
+  for (cudaStream_t st : {ws.side, ws.side2, ws.hi})
+    if (st) cudaStreamSynchronize(st);
   free_workspace(&tree->t.ws);
   free_streams(&tree->t.ws);
   free_pointset(&tree->t.src);
   if (!tree->t.same) free_pointset(&tree->t.tgt);
   delete tree;
+}
+
+extern "C" eifmm_status eifmm_tree_set_option(eifmm_tree* tree, eifmm_option opt, int value) {
+  if (!tree || (int)opt < 0 || (int)opt >= kNumOptions || (value != 0 && value != 1)) {
+    set_error("eifmm_tree_set_option: null tree, unknown option or value other than 0 or 1");
+    return EIFMM_EINVAL;
+  }
+  tree->t.opt[(int)opt] = value;
+  return EIFMM_OK;
 }
 
 static eifmm_status check_eval(const eifmm_tree* tree, const eifmm_ops* ops, int n_rhs,

@@ -424,35 +424,33 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
   }
 }
 
-// ------------------------------------------- near field, packed pairs ----
-// The near field of 1/r with one right-hand side on the packed FP32 pipes.
-// Every FP32 add, multiply and FMA of a source-target interaction runs as a
-// The distance r2 of two sources at once is 3 packed differences and 3
-// packed multiply-adds (sub/mul/fma.rn.f32x2); 1/r and the sum run on each
-// half in place.  An interaction then issues 3 packed FP32 instructions per
-// pair, one approximate reciprocal square root (16 per clock per SM: the
-// bound), one FMA and one broadcast shared load.  The sources are staged as
-// SoA pairs, which puts both halves of a packed operand in one register
-// pair straight from shared memory:
-//   float4 [2q]     = (x_2q, x_2q+1, y_2q, y_2q+1)
-//   float4 [2q + 1] = (z_2q, z_2q+1, sigma_2q, sigma_2q+1)
-// in the frame of the target leaf.  The staged list is the 26 other
-// neighbour leaves, padded to a multiple of 16 sources, then the leaf
-// itself; a pad source sits far away (X2_FAR) with sigma = 0 and adds an
-// exact zero.  Threads = (target t, slice s) as in k_p2p32, one pass of P
-// targets (S = 128 / P slices) per leaf of up to 128 points; slice s holds
-// L pairs (a multiple of 8) and is followed by one unused pair, so the
-// slices a warp reads at once start in different banks.  Only the 8-pair
-// blocks that reach the leaf itself test for the self pair, whose sigma is
-// replaced by 0 (and its zero distance by 1).  Each
-// half keeps its own FP32 sum over 64 pairs; the sums are then flushed
-// (tier 0: FP32 Kahan totals; ACC: compensated per term and FP64 totals).
-// A chunk of X2_SRC sources is np <= 512 pairs; S slices of
-// L <= np / S + 7 pairs plus one gap each take at most 512 + 9 S <= 800.
-constexpr int X2_SRC = 1024;          // sources per chunk of the staged list
-constexpr int X2_MAXS = 32;           // slices per pass
-constexpr int X2_PAIRS = X2_SRC / 2 + 9 * X2_MAXS;  // staged pairs, gaps included
-constexpr float X2_FAR = 1.0e4f;
+// -------------------------------------- near field, packed distances ----
+// The near field of 1/r with one right-hand side.  One CTA (128 threads)
+// per non-empty target leaf.  The sources of the 27 neighbour leaves are
+// staged in shared memory in chunks of NF_SRC, in the frame of the target
+// leaf, as SoA pairs:
+//   pair q: ulonglong2 [2q] = (x_2q, x_2q+1 | y_2q, y_2q+1),
+//           ulonglong2 [2q + 1] = (z_2q, z_2q+1 | sigma_2q, sigma_2q+1),
+// the 26 other leaves first, then the leaf itself from the next even
+// position; a pad source (far away, sigma = 0, an exact zero) fills an odd
+// end.  Threads = (target t, slice s), thread = t + P s: P targets of the
+// pass times S = min(128 / P, 32) contiguous slices of about np / S pairs;
+// the passes take 128 targets while that many remain, else 32 while more
+// than 32 remain, then the rest, so that the lanes stay busy.  Per pair of
+// sources the distance is 3 packed differences and 3 packed multiply-adds
+// (sub/mul/fma.rn.f32x2, operands straight from the shared loads); 1/r is
+// the approximate reciprocal square root on each half, with a Newton step
+// and Kahan sums when ACC.  Each half keeps its own FP32 sum over the slice
+// (at most 256 pairs) before a compensated flush.  Only the pairs of the leaf
+// itself test for the self pair, whose sigma is replaced by 0 (and its zero
+// distance by 1).  The slices of a target are added in FP64 in a fixed
+// order.  Staging costs about as much as the arithmetic of one target per
+// source, so its bookkeeping is kept to a warp scan and two pad writes.
+constexpr int NF_THREADS = 128;
+constexpr int NF_SRC = 1024;               // sources per chunk
+constexpr int NF_MAXS = 32;                // slices per pass
+constexpr float NF_FAR = 1.0e4f;
+constexpr size_t NF_SMEM = NF_SRC * sizeof(ulonglong2);  // NF_SRC / 2 pairs of 32 bytes
 
 __device__ __forceinline__ uint64_t pk2(float lo, float hi) {
   uint64_t r;
@@ -463,28 +461,24 @@ __device__ __forceinline__ void up2(uint64_t v, float& lo, float& hi) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
-// r2 of the staged pair e[0..1] against the target (X, Y, Z), and sigma of
-// the pair.
-__device__ __forceinline__ void x2_r2(const ulonglong2* e, uint64_t X, uint64_t Y, uint64_t Z, uint64_t& r2,
+// r2 of the staged pair e[0..1] against the target (X, Y, Z) (packed), and
+// the pair's sigma.
+__device__ __forceinline__ void nf_r2(const ulonglong2* e, uint64_t X, uint64_t Y, uint64_t Z, uint64_t& r2,
                                       uint64_t& sg) {
   const ulonglong2 v0 = e[0], v1 = e[1];
-  const uint64_t xa = v0.x, ya = v0.y, za = v1.x;
   sg = v1.y;
   uint64_t dx, dy, dz;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(xa), "l"(X));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(ya), "l"(Y));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(za), "l"(Z));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(v0.x), "l"(X));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(v0.y), "l"(Y));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(v1.x), "l"(Z));
   asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(r2) : "l"(dx));
   asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(r2) : "l"(dy));
   asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(r2) : "l"(dz));
 }
 
-// sum (+)= sigma / r for one half: 1/r is the approximate reciprocal square
-// root, with one Newton step y (1.5 - 0.5 r2 y^2) and a Kahan step when
-// ACC.  Scalar: the halves of r2 and sigma are read in place from their
-// register pairs, so nothing is packed.
+// sum (+)= sigma / r for one half.
 template <bool ACC>
-__device__ __forceinline__ void x2_term(float r2, float sg, float& sa, float& ca) {
+__device__ __forceinline__ void nf_term(float r2, float sg, float& sa, float& ca) {
   float y = rsqrt_approx(r2);
   if (ACC) {
     y = y * fmaf(-0.5f * r2, y * y, 1.5f);
@@ -494,141 +488,146 @@ __device__ __forceinline__ void x2_term(float r2, float sg, float& sa, float& ca
   }
 }
 
+// Pairs [qa, qe) of the staged list; SELF: pair qs, half hs is the target
+// itself.
+template <bool ACC, bool SELF>
+__device__ __forceinline__ void nf_span(const ulonglong2* s_pair, int qa, int qe, int qs, int hs, uint64_t X,
+                                        uint64_t Y, uint64_t Z, float& sl, float& sh, float& cl, float& ch) {
+#pragma unroll 8
+  for (int q = qa; q < qe; ++q) {
+    uint64_t r2, sg;
+    nf_r2(s_pair + 2 * q, X, Y, Z, r2, sg);
+    float rl, rh, gl, gh;
+    up2(r2, rl, rh);
+    up2(sg, gl, gh);
+    if (SELF && q == qs) {  // the self pair: sigma 0 at distance 1
+      if (hs) rh = 1.f, gh = 0.f;
+      else rl = 1.f, gl = 0.f;
+    }
+    nf_term<ACC>(rl, gl, sl, cl);
+    nf_term<ACC>(rh, gh, sh, ch);
+  }
+}
+
 template <bool ACC>
-__global__ void __launch_bounds__(P2P_THREADS)
-k_p2p32x2(const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff, const float* __restrict__ tlx,
-          const float* __restrict__ tly, const float* __restrict__ tlz, int64_t nt,
-          const int32_t* __restrict__ soff, const float* __restrict__ slx, const float* __restrict__ sly,
-          const float* __restrict__ slz, const float* __restrict__ sig, int depth, float two_l,
-          int exclude_self, double* __restrict__ fnear) {
-  __shared__ __align__(16) float4 s_pair[2 * X2_PAIRS];
-  __shared__ double s_red[P2P_THREADS];
-  __shared__ int s_pos[28];      // logical start of each segment, then the end
-  __shared__ int s_len[27];      // sources of each segment
+__global__ void __launch_bounds__(NF_THREADS)
+k_p2p32x(const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff, const float* __restrict__ tlx,
+         const float* __restrict__ tly, const float* __restrict__ tlz, const int32_t* __restrict__ soff,
+         const float* __restrict__ slx, const float* __restrict__ sly, const float* __restrict__ slz,
+         const float* __restrict__ sig, int depth, float two_l, int exclude_self, double* __restrict__ fnear) {
+  extern __shared__ __align__(16) ulonglong2 s_pair[];  // [NF_SRC]: NF_SRC / 2 pairs
+  __shared__ double s_red[NF_THREADS];
+  __shared__ int s_pos[28];  // logical start of each segment, then the end
+  __shared__ int s_len[27];
   __shared__ int s_beg[27];
   __shared__ float s_sh[27][3];
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const int b = leaves[blockIdx.x];
-  int c[3];
-  morton_decode(b, depth, c);
-  const int n = 1 << depth;
-  if (tid < 27) {
-    const int nb = tid < 13 ? tid : (tid < 26 ? tid + 1 : 13);
-    const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
-    const int jx = c[0] + dx, jy = c[1] + dy, jz = c[2] + dz;
+  if (w == 0) {
+    // segment `lane`: 0..25 the neighbours other than the leaf, 26 itself
+    int c[3];
+    morton_decode(b, depth, c);
+    const int n = 1 << depth;
     int beg = 0, len = 0;
-    if (jx >= 0 && jy >= 0 && jz >= 0 && jx < n && jy < n && jz < n) {
-      const int64_t J = morton_encode(jx, jy, jz, depth);
-      beg = soff[J];
-      len = soff[J + 1] - beg;
+    if (lane < 27) {
+      const int nb = lane < 13 ? lane : (lane < 26 ? lane + 1 : 13);
+      const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = nb / 9 - 1;
+      const int jx = c[0] + dx, jy = c[1] + dy, jz = c[2] + dz;
+      if (jx >= 0 && jy >= 0 && jz >= 0 && jx < n && jy < n && jz < n) {
+        const int64_t J = morton_encode(jx, jy, jz, depth);
+        beg = soff[J];
+        len = soff[J + 1] - beg;
+      }
+      s_beg[lane] = beg;
+      s_len[lane] = len;
+      s_sh[lane][0] = dx * two_l;
+      s_sh[lane][1] = dy * two_l;
+      s_sh[lane][2] = dz * two_l;
     }
-    s_beg[tid] = beg;
-    s_len[tid] = len;
-    s_sh[tid][0] = dx * two_l;
-    s_sh[tid][1] = dy * two_l;
-    s_sh[tid][2] = dz * two_l;
+    // exclusive scan of the lengths of segments 0..25; the leaf itself
+    // starts at the next even position
+    int x = lane < 26 ? len : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const int other = __shfl_sync(0xffffffffu, x, 25);
+    const int own = __shfl_sync(0xffffffffu, len, 26);
+    if (lane < 26) s_pos[lane] = x - len;
+    if (lane == 26) s_pos[26] = (other + 1) & ~1;
+    if (lane == 27) s_pos[27] = ((other + 1) & ~1) + own;
   }
   __syncthreads();
-  if (tid == 0) {
-    // logical positions: the other leaves from 0, the leaf itself from the
-    // next multiple of 16 (the gap holds pads)
-    int q = 0;
-    for (int i = 0; i < 26; ++i) s_pos[i] = q, q += s_len[i];
-    s_pos[26] = (q + 15) & ~15;
-    s_pos[27] = s_pos[26] + s_len[26];
-  }
-  __syncthreads();
+  const int n_real_other = s_pos[25] + s_len[25];
   const int n_other = s_pos[26], n_log = s_pos[27];
   const int beg = toff[b], end = toff[b + 1];
+  int staged_c0 = -1;
   for (int t0 = beg, P = 0; t0 < end; t0 += P) {
-    P = min(P2P_THREADS, end - t0);
-    const int S = min(P2P_THREADS / P, X2_MAXS);
+    const int m = end - t0;
+    P = m >= NF_THREADS ? NF_THREADS : (m > 32 ? 32 : m);
+    const int S = min(NF_THREADS / P, NF_MAXS);
     const int ti = tid % P, si = tid / P;
     const bool act = si < S;
     const int p = t0 + (act ? ti : 0);
     const float x0 = tlx[p], x1 = tly[p], x2 = tlz[p];
     const uint64_t X = pk2(x0, x0), Y = pk2(x1, x1), Z = pk2(x2, x2);
-    // logical position of the self pair
-    const int js = exclude_self ? n_other + (p - beg) : -1;
-    float th0 = 0.f, tc0 = 0.f, th1 = 0.f, tc1 = 0.f;  // tier 0: FP32 Kahan totals per half
-    double td = 0.0;                                   // ACC: FP64 total
-    for (int c0 = 0; c0 < n_log; c0 += X2_SRC) {
-      const int cn = min(X2_SRC, n_log - c0);
+    const int js = exclude_self ? n_other + (p - beg) : -1;  // logical position of the self pair
+    float th0 = 0.f, tc0 = 0.f, th1 = 0.f, tc1 = 0.f;      // tier 0: FP32 Kahan totals per half
+    double td = 0.0;                                       // ACC: FP64 total
+    for (int c0 = 0; c0 < n_log; c0 += NF_SRC) {
+      const int cn = min(NF_SRC, n_log - c0);
       const int np = (cn + 1) >> 1;
-      const int L = ((np + S - 1) / S + 7) & ~7;  // pairs per slice
-      const int used = S * (L + 1);
-      __syncthreads();
-      // pads everywhere, then the sources over them
-      for (int q = tid; q < used; q += P2P_THREADS) {
-        s_pair[2 * q] = make_float4(X2_FAR, X2_FAR, X2_FAR, X2_FAR);
-        s_pair[2 * q + 1] = make_float4(X2_FAR, X2_FAR, 0.f, 0.f);
-      }
-      __syncthreads();
-      for (int sg = w; sg < 27; sg += P2P_THREADS / 32) {
-        const int pb = s_pos[sg];
-        const int lo = max(pb, c0), hi = min(pb + s_len[sg], c0 + cn);
-        const float sx = s_sh[sg][0], sy = s_sh[sg][1], sz = s_sh[sg][2];
-        for (int pos = lo + lane; pos < hi; pos += 32) {
-          const int sj = s_beg[sg] + (pos - pb);
-          const int lp = pos - c0, q = lp >> 1, h = lp & 1;
-          float* e = (float*)&s_pair[2 * (q + q / L)];
-          e[h] = slx[sj] + sx;
-          e[2 + h] = sly[sj] + sy;
-          e[4 + h] = slz[sj] + sz;
-          e[6 + h] = sig[sj];
+      if (staged_c0 != c0) {
+        __syncthreads();
+        for (int sg = w; sg < 27; sg += NF_THREADS / 32) {
+          const int pb = s_pos[sg];
+          const int lo = max(pb, c0), hi = min(pb + s_len[sg], c0 + cn);
+          const float sx = s_sh[sg][0], sy = s_sh[sg][1], sz = s_sh[sg][2];
+          const int sb = s_beg[sg] - pb;
+          for (int pos = lo + lane; pos < hi; pos += 32) {
+            const int sj = sb + pos;
+            const int lp = pos - c0;
+            float* e = reinterpret_cast<float*>(&s_pair[2 * (lp >> 1)]) + (lp & 1);
+            e[0] = slx[sj] + sx;
+            e[2] = sly[sj] + sy;
+            e[4] = slz[sj] + sz;
+            e[6] = sig[sj];
+          }
         }
+        // pads at an odd end of the other leaves and of the chunk
+        if (tid < 2) {
+          const int g = tid == 0 ? n_real_other : c0 + cn;
+          if ((g & 1) && g >= c0 && g < c0 + 2 * np && (tid == 1 || g < n_other)) {
+            float* e = reinterpret_cast<float*>(&s_pair[2 * ((g - c0) >> 1)]) + 1;
+            e[0] = NF_FAR;
+            e[2] = NF_FAR;
+            e[4] = NF_FAR;
+            e[6] = 0.f;
+          }
+        }
+        __syncthreads();
+        staged_c0 = c0;
       }
-      __syncthreads();
       if (act) {
-        const int qs = js - c0 >= 0 && js - c0 < cn ? (js - c0) >> 1 : -1, hs = (js - c0) & 1;
+        const int L = (np + S - 1) / S;
+        const int qb = min(np, si * L), qe = min(np, qb + L);
         const int qown = max(0, n_other - c0) >> 1;  // first pair of the leaf itself
-        const int qb = si * L;
-        float sl = 0.f, sh = 0.f, cl = 0.f, ch = 0.f;  // per half: sum, Kahan term
-        int cnt = 0;
-        for (int q8 = qb; q8 < qb + L; q8 += 8) {
-          const ulonglong2* a0 = reinterpret_cast<const ulonglong2*>(s_pair) + 2 * (q8 + si);
-          if (q8 + 8 <= qown || qs < 0) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              uint64_t r2, sg;
-              x2_r2(a0 + 2 * u, X, Y, Z, r2, sg);
-              float rl, rh, gl, gh;
-              up2(r2, rl, rh);
-              up2(sg, gl, gh);
-              x2_term<ACC>(rl, gl, sl, cl);
-              x2_term<ACC>(rh, gh, sh, ch);
-            }
-          } else {
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              uint64_t r2, sg;
-              x2_r2(a0 + 2 * u, X, Y, Z, r2, sg);
-              float rl, rh, gl, gh;
-              up2(r2, rl, rh);
-              up2(sg, gl, gh);
-              if (q8 + u == qs) {  // the self pair: sigma 0 at distance 1
-                if (hs) rh = 1.f, gh = 0.f;
-                else rl = 1.f, gl = 0.f;
-              }
-              x2_term<ACC>(rl, gl, sl, cl);
-              x2_term<ACC>(rh, gh, sh, ch);
-            }
-          }
-          if (++cnt == 8 || q8 + 8 >= qb + L) {  // flush every 64 pairs
-            cnt = 0;
-            if (ACC) {
-              td += ((double)sl - (double)cl) + ((double)sh - (double)ch);
-            } else {
-              kahan_add(th0, tc0, sl);
-              kahan_add(th1, tc1, sh);
-            }
-            sl = sh = cl = ch = 0.f;
-          }
+        const int qs = js - c0 >= 0 && js - c0 < cn ? (js - c0) >> 1 : -1, hs = (js - c0) & 1;
+        const int qm = qs < 0 ? qe : max(qb, min(qe, qown));
+        float sl = 0.f, sh = 0.f, cl = 0.f, ch = 0.f;
+        nf_span<ACC, false>(s_pair, qb, qm, -1, 0, X, Y, Z, sl, sh, cl, ch);
+        nf_span<ACC, true>(s_pair, qm, qe, qs, hs, X, Y, Z, sl, sh, cl, ch);
+        if (ACC) {
+          td += ((double)sl - (double)cl) + ((double)sh - (double)ch);
+        } else {
+          kahan_add(th0, tc0, sl);
+          kahan_add(th1, tc1, sh);
         }
       }
     }
-    __syncthreads();
     if (!ACC) td = ((double)th0 - (double)tc0) + ((double)th1 - (double)tc1);
+    __syncthreads();
     s_red[tid] = act ? td : 0.0;
     __syncthreads();
     if (tid < P) {
@@ -1286,9 +1285,16 @@ static void p2p_launch(const Tree* t, int kern, const float* sig32, int R, doubl
                        cudaStream_t s) {
   const PointSet& T = t->tgt;
   const PointSet& S = t->src;
-  if (KERN == EIFMM_KERNEL_INV_R && RCT == 1) {  // 1/r, one right-hand side: packed pairs
-    k_p2p32x2<ACC><<<(unsigned)T.n_nonempty, P2P_THREADS, 0, s>>>(
-        T.nonempty, T.leaf_off, T.lx, T.ly, T.lz, T.n, S.leaf_off, S.lx, S.ly, S.lz, sig32, t->depth, two_l,
+  if (KERN == EIFMM_KERNEL_INV_R && RCT == 1) {  // 1/r, one right-hand side: packed distances
+    static bool attr[64][2] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 64 || !attr[dev][ACC]) {
+      cudaFuncSetAttribute(k_p2p32x<ACC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)NF_SMEM);
+      if (dev < 64) attr[dev][ACC] = true;
+    }
+    k_p2p32x<ACC><<<(unsigned)T.n_nonempty, NF_THREADS, NF_SMEM, s>>>(
+        T.nonempty, T.leaf_off, T.lx, T.ly, T.lz, S.leaf_off, S.lx, S.ly, S.lz, sig32, t->depth, two_l,
         t->exclude_self, fnear);
     return;
   }
@@ -1298,12 +1304,12 @@ static void p2p_launch(const Tree* t, int kern, const float* sig32, int R, doubl
 }
 
 // The pair-symmetric near field can serve tier 0 with one right-hand side
-// on a tree whose targets are its sources; it runs when EIFMM_P2P_SYM=1
+// on a tree whose targets are its sources; it runs when the tree's option
+// EIFMM_OPT_P2P_PAIR_SYMMETRIC is on
 // (read at every evaluate).  It is not the default: it measured slower than
 // the per-target kernel (588 against 423 us at 1M points).
 static bool use_p2p_sym(const Tree* t, int R, bool accurate, const float* gsym) {
-  const char* e = getenv("EIFMM_P2P_SYM");
-  return gsym && !accurate && R == 1 && t->same && t->exclude_self && e && strcmp(e, "1") == 0;
+  return gsym && !accurate && R == 1 && t->same && t->exclude_self && t->opt[EIFMM_OPT_P2P_PAIR_SYMMETRIC];
 }
 
 eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R, double* fnear,
@@ -1341,13 +1347,6 @@ eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R, do
   }
   EIFMM_CHECK_LAUNCH();
   return EIFMM_OK;
-}
-
-// The transposed M2L serves dp = 128 unless EIFMM_M2L_KERNEL=128 asks for the
-// 128-row kernel (read at every evaluate, for comparisons).
-static bool use_m2l_t256() {
-  const char* e = getenv("EIFMM_M2L_KERNEL");
-  return !(e && strcmp(e, "128") == 0);
 }
 
 static void record(Workspace& ws, int i, cudaStream_t s) {
@@ -1412,7 +1411,8 @@ eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, i
   if (rule) {
     // the transposed kernel where a parity class fills at least one of its
     // 256-row tiles; the 128-row kernel at the coarse levels
-    kind = (ws.wa_t256[k] && nboxes(k) / 8 * R >= 256 && use_m2l_t256()) ? 1 : (ws.wa_grid[k] ? 2 : 4);
+    kind = (ws.wa_t256[k] && nboxes(k) / 8 * R >= 256 && !t->opt[EIFMM_OPT_M2L_128ROW]) ? 1
+                                                                                         : (ws.wa_grid[k] ? 2 : 4);
   }
   if (kind == 1) {
     if (!ws.wa_t256[k]) return EIFMM_EUNSUPPORTED;
@@ -1455,7 +1455,7 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   // the far field continues on the high-priority stream; the caller's stream
   // waits for it at the end
   const cudaStream_t caller = s;
-  if (!getenv("EIFMM_NO_PRIORITY")) {
+  if (!t->opt[EIFMM_OPT_SINGLE_STREAM]) {
     EIFMM_CUDA(cudaStreamWaitEvent(ws.hi, ws.ev_fork, 0));
     s = ws.hi;
   }

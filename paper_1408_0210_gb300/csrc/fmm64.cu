@@ -502,7 +502,7 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
     if (timing_enabled()) cudaEventRecord(ws.ev_m2l[k], s);
     const int d = ops->lv[k].d;
     const int64_t nb = (int64_t)1 << (3 * k);
-    if (pair_m2l && !getenv("EIFMM_M2L_FP64"))  // tiers 3 and 4 of the mixed path: FP32 pairs
+    if (pair_m2l && !t->opt[EIFMM_OPT_M2L_FP64])  // tiers 3 and 4 of the mixed path: FP32 pairs
       k_m2l_df<<<dim3((unsigned)(((nb / 8 + DF_BOX - 1) / DF_BOX) * 8), (unsigned)((d + DF_ROW - 1) / DF_ROW),
                       (unsigned)R), DF_THREADS, 0, s>>>(k, d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.W[k],
                                                         ws.g[k]);

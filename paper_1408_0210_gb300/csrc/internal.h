@@ -182,6 +182,8 @@ struct Workspace {
   float step_ms[20] = {};
 };
 
+constexpr int kNumOptions = 4;  // eifmm_option
+
 struct Tree {
   int depth = 0;
   double lo[3] = {0, 0, 0};
@@ -190,6 +192,7 @@ struct Tree {
   bool same = false;  // targets are the sources
   PointSet src, tgt;  // tgt aliases src when `same`
   Workspace ws;
+  int opt[kNumOptions] = {};  // eifmm_option values (all 0 by default)
 };
 
 // ------------------------------------------------------------ launchers --

@@ -980,10 +980,7 @@ int m2l_tc_groups(int64_t tiles8, int nsm, int dp) {
   // by k_sum_parts): at least two waves of CTAs, and at least 16 FP32
   // accumulation chains per output together with the in-CTA chains.
   const int chains = dp <= 128 ? 4 : (dp <= 256 ? 2 : 1);
-  static const int gmin = [] {
-    const char* e = getenv("EIFMM_M2L_MIN_CHAINS");
-    return e ? atoi(e) : 16;
-  }();
+  constexpr int gmin = 16;
   int g = 1;
   while (g < 16 && (tiles8 * g < 2 * nsm || chains * g < gmin)) g *= 2;
   return g;

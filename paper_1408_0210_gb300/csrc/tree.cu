@@ -188,13 +188,20 @@ k_rs_scatter(const uint32_t* __restrict__ kin, const int32_t* __restrict__ vin,
   }
 }
 
+// off[b] = first sorted position whose key is at least b (b = 0..nleaf;
+// off[nleaf] = n): one thread per leaf, a binary search over the sorted
+// keys, so runs of empty leaves cost no more than full ones.
 __global__ void k_leaf_off(const uint32_t* __restrict__ skeys, int64_t n,
                            int64_t nleaf, int32_t* __restrict__ off) {
-  const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (p > n) return;
-  const int64_t prev = (p == 0) ? -1 : (int64_t)skeys[p - 1];
-  const int64_t cur = (p == n) ? nleaf : (int64_t)skeys[p];
-  for (int64_t b = prev + 1; b <= cur; ++b) off[b] = (int32_t)p;
+  const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b > nleaf) return;
+  int64_t lo = 0, hi = n;  // the answer lies in [lo, hi]
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)__ldg(skeys + mid) < b) lo = mid + 1;
+    else hi = mid;
+  }
+  off[b] = (int32_t)lo;
 }
 
 // Leaf-centre coordinates lo_a + (2 c + 1) l_kappa of the 2^depth cells
@@ -327,7 +334,7 @@ eifmm_status build_pointset(const double* xyz, int64_t n, const double lo[3],
       EIFMM_CUDA(cudaMemcpyAsync(ps->perm, vin, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     }
   }
-  k_leaf_off<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(ps->keys, n, nleaf, ps->leaf_off);
+  k_leaf_off<<<(unsigned)((nleaf + 1 + 255) / 256), 256, 0, s>>>(ps->keys, n, nleaf, ps->leaf_off);
   EIFMM_CHECK_LAUNCH();
   if (n > 0) {
     const double lk = L * ldexp(1.0, -(depth + 1));
@@ -459,7 +466,7 @@ extern "C" eifmm_status eifmm_tree_sort_static(const double* xyz, int64_t n, con
       EIFMM_CUDA(cudaMemcpyAsync(perm_out, vin, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     }
   }
-  k_leaf_off<<<(unsigned)((n + 1 + 255) / 256), 256, 0, s>>>(keys_out, n, nleaf, leaf_off_out);
+  k_leaf_off<<<(unsigned)((nleaf + 1 + 255) / 256), 256, 0, s>>>(keys_out, n, nleaf, leaf_off_out);
   EIFMM_CHECK_LAUNCH();
   int hbad = 0;
   EIFMM_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));

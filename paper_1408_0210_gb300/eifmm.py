@@ -26,8 +26,9 @@ EXPORTS = [
     "eifmm_evaluate", "eifmm_evaluate_host", "eifmm_evaluate_batched", "eifmm_debug_export",
     "eifmm_set_timing", "eifmm_last_step_times", "eifmm_direct_sum", "eifmm_kernel_launches",
     "eifmm_tree_sort_static", "eifmm_ops_calibrate", "eifmm_autotune", "eifmm_measure_rates",
-    "eifmm_ops_calibration",
+    "eifmm_ops_calibration", "eifmm_tree_set_option",
 ]
+OPTIONS = {"m2l_128row": 0, "p2p_pair_symmetric": 1, "single_stream": 2, "m2l_fp64": 3}
 
 
 class EifmmError(RuntimeError):
@@ -80,6 +81,7 @@ def lib() -> C.CDLL:
         "eifmm_tree_sort_static": (i32, [vp, i64, vp, dbl, i32, vp, vp, vp, vp]),
         "eifmm_ops_calibrate": (i32, [vp, dbl, vp, vp]),
         "eifmm_ops_calibration": (i32, [vp, vp, vp]),
+        "eifmm_tree_set_option": (i32, [vp, i32, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -219,6 +221,10 @@ class Tree:
         if getattr(self, "handle", None) and _lib is not None:
             _lib.eifmm_tree_destroy(self.handle)
             self.handle = None
+
+    def set_option(self, name: str, value: bool) -> None:
+        """eifmm_tree_set_option: one of OPTIONS, on (1) or off (0)."""
+        _check(lib().eifmm_tree_set_option(self.handle, OPTIONS[name], int(bool(value))))
 
     def export(self, which: int = 0):
         n = self.n_src if which == 0 else self.n_tgt

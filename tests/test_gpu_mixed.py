@@ -129,7 +129,6 @@ def test_m2l_transposed_matches_128_row_kernel(E):
     the 128-row kernel (M = rows, N = dp, TMEM chains) compute the same g at
     every level of a depth-5 tree (several tiles per class, offset groups at
     the coarse levels), to the BF16-split accuracy."""
-    import os
     n, depth = 150000, 5
     x = wl.uniform_cube(n, 41)
     s = wl.sigma_uniform(n, 1, 42)
@@ -140,14 +139,10 @@ def test_m2l_transposed_matches_128_row_kernel(E):
     f = torch.zeros(n, dtype=torch.float64, device="cuda")
     g = {}
     for kind in ("t256", "128"):
-        if kind == "128":
-            os.environ["EIFMM_M2L_KERNEL"] = "128"
-        try:
-            E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
-            torch.cuda.synchronize()
-            g[kind] = {k: E.eifmm_debug_export(tree, 2, k, ops.error_estimate(k)[1]) for k in range(2, depth + 1)}
-        finally:
-            os.environ.pop("EIFMM_M2L_KERNEL", None)
+        tree.set_option("m2l_128row", kind == "128")
+        E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
+        torch.cuda.synchronize()
+        g[kind] = {k: E.eifmm_debug_export(tree, 2, k, ops.error_estimate(k)[1]) for k in range(2, depth + 1)}
     for k in range(2, depth + 1):
         assert np.isfinite(g["t256"][k]).all()
         assert relmax(g["t256"][k], g["128"][k]) <= 2e-5, k
@@ -343,10 +338,10 @@ def test_forced_tiers_run(E, orc, tier):
 
 
 @pytest.mark.parametrize("case", ["uniform", "clustered"])
-def test_pair_symmetric_near_field(E, orc, case, monkeypatch):
+def test_pair_symmetric_near_field(E, orc, case):
     """Tier 0 with one right-hand side visits each unordered leaf pair once
     (k_ij used for f_i and f_j, partials of the backward neighbours added by
-    the L2P).  Against the per-target near field (EIFMM_P2P_SYM=0): the same
+    the L2P).  Against the per-target near field (option off): the same
     near field and result to FP32 rounding; the clustered case has leaves of
     thousands of points, so targets and sources are staged in several
     chunks.  Sampled targets are checked against the CPU checker's near
@@ -363,7 +358,7 @@ def test_pair_symmetric_near_field(E, orc, case, monkeypatch):
     tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
     out = {}
     for sym in ("1", "0"):
-        monkeypatch.setenv("EIFMM_P2P_SYM", sym)
+        tree.set_option("p2p_pair_symmetric", sym == "1")
         f = torch.zeros(n, dtype=torch.float64, device="cuda")
         E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
         torch.cuda.synchronize()
@@ -388,22 +383,19 @@ def test_pair_symmetric_near_field(E, orc, case, monkeypatch):
         assert abs(out["1"][1][i] - terms.sum()) <= 1e-5 * np.abs(terms).sum()
 
 
-def test_stream_layout_does_not_change_the_result(E, monkeypatch):
+def test_stream_layout_does_not_change_the_result(E):
     """The far field on the high-priority stream, the near field beside it
     and the coarse M2L levels on a second stream: every sum has a fixed
     order, so the result is bitwise the same as with everything on the
-    caller's stream (EIFMM_NO_PRIORITY) and across repeated calls."""
+    caller's stream (option single_stream) and across repeated calls."""
     n, depth = 200000, 4
     x = wl.uniform_cube(n, 91)
     s = wl.sigma_uniform(n, 1, 92)
     ops = E.eifmm_ops_build("inv_r", 1.0, depth, 1e-4)
     tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
     out = []
-    for env in (None, "1", None):
-        if env is None:
-            monkeypatch.delenv("EIFMM_NO_PRIORITY", raising=False)
-        else:
-            monkeypatch.setenv("EIFMM_NO_PRIORITY", env)
+    for single in (False, True, False):
+        tree.set_option("single_stream", single)
         f = torch.zeros(n, dtype=torch.float64, device="cuda")
         E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
         torch.cuda.synchronize()
@@ -411,10 +403,10 @@ def test_stream_layout_does_not_change_the_result(E, monkeypatch):
     assert torch.equal(out[0], out[1]) and torch.equal(out[0], out[2])
 
 
-def test_tier3_pair_arithmetic_m2l(E, monkeypatch):
+def test_tier3_pair_arithmetic_m2l(E):
     """Tier 3 (FP64 far field) runs its M2L on FP32 pairs (hi + lo, exact
     product splits, two-sum accumulation); against the FP64 M2L
-    (EIFMM_M2L_FP64) every level's g agrees to 1e-10 of its largest entry:
+    (option m2l_fp64) every level's g agrees to 1e-10 of its largest entry:
     a pair holds about 48 bits and a product loses the lo x lo term and the
     rounding of the FP32 cross terms (about 2^-47 relative), over some
     30,000 terms whose magnitudes exceed the result's (measured 1.6e-11)."""
@@ -426,10 +418,7 @@ def test_tier3_pair_arithmetic_m2l(E, monkeypatch):
     tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
     g = {}
     for env in ("0", "1"):
-        if env == "1":
-            monkeypatch.setenv("EIFMM_M2L_FP64", "1")
-        else:
-            monkeypatch.delenv("EIFMM_M2L_FP64", raising=False)
+        tree.set_option("m2l_fp64", env == "1")
         f = torch.zeros(n, dtype=torch.float64, device="cuda")
         E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
         torch.cuda.synchronize()
