@@ -337,7 +337,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variants", default="mixed:1e-4,fp64:1e-4,mixed:1e-5,mixed:1e-7,fp64:1e-7")
+    ap.add_argument("--variants", default="mixed:1e-4,fp64:1e-4,mixed:1e-5,mixed:1e-6,mixed+c:1e-6,fp64:1e-6,fp64+c:1e-6,mixed:1e-7,fp64:1e-7")
     ap.add_argument("--workloads", default="c1,c3,c4a,c4b,c5,sphere",
                     help="other benchmark workloads to time after the headline ('' for none)")
     ap.add_argument("--profile-steps", type=int, default=0,
@@ -384,35 +384,42 @@ def main():
     fref = E.eifmm_direct_sum("inv_r", xd, xd, sd, True, idx, stream)[:, 0]
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
+    # a variant: path (fp64 / mixed), EIM tolerance, and "+c" for the M2L
+    # compression of Section 4.2 (its own operator set: the FP64 far field
+    # runs the compressed M2L)
     variants = []
     for v in args.variants.split(","):
-        prec, eps = v.split(":")
-        variants.append((prec, float(eps)))
+        name, eps = v.split(":")
+        variants.append((name, float(eps)))
     ops = {}
     ops_err = {}
-    for _, eps in variants:
-        if eps not in ops and eps not in ops_err:
+    for name, eps in variants:
+        key = (eps, name.endswith("+c"))
+        if key not in ops and key not in ops_err:
             try:
-                ops[eps] = E.eifmm_ops_build("inv_r", 1.0, DEPTH, eps, 512, stream)
+                ops[key] = E.eifmm_ops_build("inv_r", 1.0, DEPTH, eps, 512, stream)
+                if key[1]:
+                    ops[key].compress(eps, stream)
             except E.EifmmError as e:
-                ops_err[eps] = str(e)
+                ops_err[key] = str(e)
 
     if args.profile_steps > 0:
-        prec, eps = variants[0]
+        name, eps = variants[0]
+        prec, o = name.split("+")[0], ops[(eps, name.endswith("+c"))]
         if prec == "mixed":
-            E.eifmm_autotune(tree, ops[eps], NRHS, prec, stream)
+            E.eifmm_autotune(tree, o, NRHS, prec, stream)
         for _ in range(max(args.warmup, 1)):
-            E.eifmm_evaluate(tree, ops[eps], sd, f, prec, stream)
+            E.eifmm_evaluate(tree, o, sd, f, prec, stream)
         torch.cuda.synchronize()
         torch.cuda.profiler.start()
         for _ in range(args.profile_steps):
-            E.eifmm_evaluate(tree, ops[eps], sd, f, prec, stream)
+            E.eifmm_evaluate(tree, o, sd, f, prec, stream)
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         return
 
-    def run_variant(prec, eps, steps, warmup, timing=False):
-        o = ops[eps]
+    def run_variant(name, eps, steps, warmup, timing=False):
+        prec, o = name.split("+")[0], ops[(eps, name.endswith("+c"))]
         tuned = None
         if prec == "mixed":
             # the M2L autotuner (setup, like the tree build): per-level variant
@@ -446,22 +453,25 @@ def main():
     results = {}
     headline = None
     with ClockSampler(torch.cuda.current_device()) as clk:
-        for prec, eps in variants:
-            if eps in ops_err:
-                results[f"{prec}@{eps:g}"] = {"unavailable": ops_err[eps]}
+        for name, eps in variants:
+            prec, key = name.split("+")[0], (eps, name.endswith("+c"))
+            if key in ops_err:
+                results[f"{name}@{eps:g}"] = {"unavailable": ops_err[key]}
                 continue
             try:
                 steps = args.steps if (prec == "mixed" or eps >= 1e-5) else max(3, args.steps // 3)
-                ms, err, launches, st, tuned = run_variant(prec, eps, steps, args.warmup, timing=True)
+                ms, err, launches, st, tuned = run_variant(name, eps, steps, args.warmup, timing=True)
             except E.EifmmError as e:
-                results[f"{prec}@{eps:g}"] = {"unavailable": str(e)}
+                results[f"{name}@{eps:g}"] = {"unavailable": str(e)}
                 continue
-            d = [ops[eps].error_estimate(k)[1] for k in range(2, DEPTH + 1)]
+            o = ops[key]
+            d = [o.error_estimate(k)[1] for k in range(2, DEPTH + 1)]
             m2l = [statistics.median([t[9 + k] for t in st]) for k in range(2, DEPTH + 1)]
-            results[f"{prec}@{eps:g}"] = {
+            results[f"{name}@{eps:g}"] = {
                 "value": job_throughput(N_POINTS * NRHS, ws, ms), "ms_per_step": ms,
-                "tier": ops[eps].plan() if prec == "mixed" else None,
-                "calibration": ops[eps].calibration() if prec == "mixed" else None,
+                "tier": o.plan() if prec == "mixed" else None,
+                "calibration": o.calibration() if prec == "mixed" else None,
+                "m2l_rank": ({str(k): o.basis(k)["r"] for k in range(2, DEPTH + 1)} if key[1] else None),
                 "rel_l2_vs_exact": err, "meets_eps": err <= eps, "d": d,
                 "gpu_launches": launches, "steps": steps,
                 "step_ms": [round(statistics.median([t[i] for t in st]), 4) for i in range(8)],
@@ -469,8 +479,8 @@ def main():
                 "m2l_autotune": ({str(k): [E.M2L_VARIANTS[v], g] for k, (v, g) in tuned.items()}
                                  if tuned else None),
                 "m2l_ms_per_level": [round(v, 4) for v in m2l]}
-            if headline is None and err <= eps and (prec, eps) in (("mixed", 1e-4), ("fp64", 1e-4)):
-                headline = (prec, eps)
+            if headline is None and err <= eps and (name, eps) in (("mixed", 1e-4), ("fp64", 1e-4)):
+                headline = (name, eps)
         names = [w for w in args.workloads.split(",") if w]
         workloads = run_workloads(names, stream, flush, dist) if names else {}
     clocks = clk.summary()
@@ -485,20 +495,20 @@ def main():
     sh = torch.from_numpy(np.ascontiguousarray(s[:, 0])).pin_memory()
     fh = torch.zeros(N_POINTS, dtype=torch.float64).pin_memory()
     for _ in range(2):
-        E.lib().eifmm_evaluate_host(tree.handle, ops[he].handle, sh.data_ptr(), N_POINTS, 1,
+        E.lib().eifmm_evaluate_host(tree.handle, ops[(he, False)].handle, sh.data_ptr(), N_POINTS, 1,
                                     fh.data_ptr(), N_POINTS, E.PREC[hp], stream.cuda_stream)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ke = max(3, args.steps // 2)
     for _ in range(ke):
-        rc = E.lib().eifmm_evaluate_host(tree.handle, ops[he].handle, sh.data_ptr(), N_POINTS, 1,
+        rc = E.lib().eifmm_evaluate_host(tree.handle, ops[(he, False)].handle, sh.data_ptr(), N_POINTS, 1,
                                          fh.data_ptr(), N_POINTS, E.PREC[hp], stream.cuda_stream)
         assert rc == 0, E.lib().eifmm_last_error()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) / ke * 1e3, dist, dev)
     e2e_val = job_throughput(N_POINTS * NRHS, ws, e2e_ms)
 
     # ---- roofline of the dominant kernel: the M2L of the leaf level ------
-    o = ops[he]
+    o = ops[(he, False)]
     dk = o.error_estimate(DEPTH)[1]
     flops = 2.0 * dk * dk * m2l_pairs(DEPTH) * NRHS
     m2l_ms = hr["m2l_ms_per_level"][-1]

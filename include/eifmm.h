@@ -189,6 +189,30 @@ eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_stream stream
  * calibration).  Either pointer may be NULL.  Errors: EINVAL (null ops). */
 eifmm_status eifmm_ops_calibration(const eifmm_ops* ops, double* err4, int* tier);
 
+/* M2L compression, first stage of Section 4.2, for the FP64 far field (the
+ * FP64 path and the mixed tiers 3 and 4; the folded FP32 and tensor-core
+ * tiers keep the full operators).  Per level, K_fat = [K^delta_1 ...
+ * K^delta_316] (the unfolded M2L matrices of the far offsets); its leading
+ * left singular vectors U (d x r) come from the eigen-decomposition of
+ * K_fat K_fat^t in FP64, and r keeps what both filters of Section 4.2 keep:
+ * the singular values with s_j / s_0 > eps, and the shortest leading run
+ * whose sum reaches (1 - eps) of the total.  C^delta = U^t K^delta U (r x r)
+ * replaces K^delta: step 4 becomes w~ = U^t What (What = Delta W by the FP64
+ * solves), g~ = sum_J C^delta w~, g = U g~.  eps = 0 removes the
+ * compression.  ranks (may be NULL): int[11], entry k = r of level k (0
+ * outside 2..depth).  Synchronises `stream`.  Errors: EINVAL (null, eps
+ * outside [0, 1), all-zero operators), ENOMEM, ECUDA. */
+eifmm_status eifmm_ops_compress(eifmm_ops* ops, double eps, eifmm_stream stream,
+                                int* ranks);
+
+/* The compression basis of `level` (no counterpart in the paper; for
+ * checks): U (HOST, d x r row-major, may be NULL), *d, *r (0 when the level
+ * is not compressed), info (may be NULL): double[4] = {count of filter (i),
+ * count of filter (ii), s_{r-1} / s_0, s_r / s_0}.  Synchronous.  Errors:
+ * EINVAL (null handle, level outside [2, depth]), ECUDA. */
+eifmm_status eifmm_ops_basis(const eifmm_ops* ops, int level, double* U, int* d,
+                             int* r, double* info);
+
 void eifmm_ops_destroy(eifmm_ops* ops);
 
 /* ------------------------------------------------------------------------ */
@@ -235,14 +259,19 @@ void eifmm_tree_destroy(eifmm_tree* tree);
  *     of the near field, far field and coarse M2L levels on streams of their
  *     own (the result is bitwise the same);
  *   M2L_FP64: 1 runs the FP64 M2L instead of the FP32-pair one in tiers 3
- *     and 4.
+ *     and 4;
+ *   M2L_STREAM_K: 1 runs the leaf-level transposed M2L as one CTA per SM
+ *     over equal shares of the (tile, offset) work, split tiles added by a
+ *     fix-up kernel, instead of one CTA per tile (measured slower at 2^20
+ *     points: 384 against 369 us).
  * The option holds for later evaluations of this tree.  Errors: EINVAL
  * (null tree, unknown option, value other than 0 or 1). */
 typedef enum {
   EIFMM_OPT_M2L_128ROW = 0,
   EIFMM_OPT_P2P_PAIR_SYMMETRIC = 1,
   EIFMM_OPT_SINGLE_STREAM = 2,
-  EIFMM_OPT_M2L_FP64 = 3
+  EIFMM_OPT_M2L_FP64 = 3,
+  EIFMM_OPT_M2L_STREAM_K = 4
 } eifmm_option;
 eifmm_status eifmm_tree_set_option(eifmm_tree* tree, eifmm_option opt, int value);
 
@@ -323,11 +352,14 @@ eifmm_status eifmm_evaluate_host(eifmm_tree* tree, const eifmm_ops* ops,
                                  int n_rhs, double* f_host, int64_t ld_f,
                                  eifmm_precision prec, eifmm_stream stream);
 
-/* Many independent problems sharing one operator set (same kernel and L;
- * each tree's depth at most the operators'): problem p evaluates trees[p]
- * with DEVICE sigma[p] and f[p] (one RHS each, ld = n).  The first call
- * evaluates the problems one after another on `stream` and records them into
- * a CUDA graph; a later call with the same trees, arrays, operators,
+/* Many independent problems sharing one operator set (the paper's
+ * many-query setting, Section 1; same kernel and L; each tree's depth at
+ * most the operators'): problem p evaluates trees[p] with DEVICE sigma[p]
+ * and f[p] (one RHS each, ld = n).  The problems run on 8 parallel branches
+ * (problem p on branch p mod 8) that fork from and join into `stream`, so
+ * the launches of small, uneven problems overlap.  The first call evaluates
+ * them directly and records them into a CUDA graph; a later call with the
+ * same trees, arrays, operators,
  * precision, tier and stream replays that graph with one launch.  The
  * library keeps one such graph per process (a call with other arguments
  * records a new one; destroying one of its trees or its operators drops
@@ -372,6 +404,17 @@ eifmm_status eifmm_direct_sum(eifmm_kernel kern, const double* tgt_xyz,
  * are the roofline denominators of the point kernels and of the FP64 path.
  * Synchronises `stream`.  Errors: EINVAL (null), ENOMEM, ECUDA. */
 eifmm_status eifmm_measure_rates(eifmm_stream stream, double* rates);
+
+/* Self-test of failure detection (no counterpart in the paper).  Every wait
+ * of the library's tensor-core kernels on an mbarrier is bounded (about 2 s
+ * of clock cycles); when one runs out the kernel records a code in a device
+ * error word, gives up its work, and the next evaluate returns ETIMEOUT.
+ * This call runs that same bounded wait, with `limit_cycles`, on an mbarrier
+ * that nothing completes, in a kernel that holds no copy, MMA or tensor
+ * memory: it returns ETIMEOUT with *code (may be NULL) = 7, the code the
+ * waiting kernel recorded, and leaves the context usable.  Synchronous.
+ * Errors: EINVAL (negative limit), ENOMEM, ECUDA. */
+eifmm_status eifmm_wait_selftest(int64_t limit_cycles, int* code);
 
 /* Number of kernels this library has launched since it was loaded (all
  * devices, all threads). */

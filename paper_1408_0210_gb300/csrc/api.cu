@@ -67,6 +67,7 @@ void free_workspace(Workspace* ws) {
   ws->m2l_part_leaf = nullptr;
   ws->m2l_part_leaf_cap = 0;
   for (int k = 0; k <= kMaxLevel; ++k) ws->m2l_kind[k] = ws->m2l_gshift[k] = 0;
+  free_sk_plan(&ws->sk);
   dfree(ws->fnear); dfree(ws->ffar); dfree(ws->tmp); dfree(ws->gsym); dfree(ws->wmax);
   ws->gsym = nullptr;
   ws->wmax = nullptr;
@@ -616,6 +617,44 @@ extern "C" eifmm_status eifmm_ops_calibrate(eifmm_ops* ops, double eps, eifmm_st
   return EIFMM_OK;
 }
 
+extern "C" eifmm_status eifmm_wait_selftest(int64_t limit_cycles, int* code) {
+  if (limit_cycles < 0) {
+    set_error("eifmm_wait_selftest: negative limit");
+    return EIFMM_EINVAL;
+  }
+  return wait_selftest((long long)limit_cycles, code);
+}
+
+extern "C" eifmm_status eifmm_ops_compress(eifmm_ops* ops, double eps, eifmm_stream stream, int* ranks) {
+  if (!ops || !(eps >= 0.0) || eps >= 1.0) {
+    set_error("eifmm_ops_compress: null handle or eps outside [0, 1)");
+    return EIFMM_EINVAL;
+  }
+  EIFMM_TRY(compress_ops(&ops->o, eps, (cudaStream_t)stream));
+  if (ranks)
+    for (int k = 0; k <= kMaxLevel; ++k) ranks[k] = (k >= 2 && k <= ops->o.depth) ? ops->o.lv[k].r : 0;
+  return EIFMM_OK;
+}
+
+extern "C" eifmm_status eifmm_ops_basis(const eifmm_ops* ops, int level, double* U, int* d, int* r,
+                                        double* info) {
+  if (!ops || level < 2 || level > ops->o.depth) {
+    set_error("eifmm_ops_basis: null handle or level outside [2, depth]");
+    return EIFMM_EINVAL;
+  }
+  const LevelOps& v = ops->o.lv[level];
+  if (d) *d = v.d;
+  if (r) *r = v.r;
+  if (info) {
+    info[0] = v.r_i;
+    info[1] = v.r_ii;
+    info[2] = v.s_kept;
+    info[3] = v.s_next;
+  }
+  if (U && v.r > 0) EIFMM_CUDA(cudaMemcpy(U, v.U, (size_t)v.d * v.r * sizeof(double), cudaMemcpyDeviceToHost));
+  return EIFMM_OK;
+}
+
 extern "C" eifmm_status eifmm_ops_calibration(const eifmm_ops* ops, double* err4, int* tier) {
   if (!ops) {
     set_error("eifmm_ops_calibration: null handle");
@@ -688,7 +727,7 @@ extern "C" eifmm_status eifmm_autotune(eifmm_tree* tree, const eifmm_ops* ops, i
     for (int k = 2; k <= kap && rc == EIFMM_OK; ++k) {
       float best = 1e30f;
       int bk = 0, bg = 0;
-      for (int kind = 0; kind <= 2 && rc == EIFMM_OK; ++kind)
+      for (int kind = 0; kind <= 3 && rc == EIFMM_OK; ++kind)
         for (int gs = -1; gs <= 1; ++gs) {
           if (kind == 0 && gs != 0) continue;  // the built-in rule as it stands
           eifmm_status r = launch_m2l_level(&t, &ops->o, k, R, kind, gs, s);  // warm-up
@@ -781,12 +820,20 @@ extern "C" eifmm_status eifmm_evaluate_host(eifmm_tree* tree, const eifmm_ops* o
 
 // The batch is recorded once into a CUDA graph (after one direct pass that
 // sizes every workspace) and replayed by a single cudaGraphLaunch while the
-// same trees, operators, precision and array pointers are passed again.
+// same trees, operators, precision and array pointers are passed again.  The
+// problems run on kBranches parallel branches (problem p on branch p mod
+// kBranches), each tree on its own workspace and streams and the operators
+// only read, so the many small launches of uneven problems overlap instead
+// of following one another.
+constexpr int kBranches = 8;
 namespace {
 struct BatchGraph {
   std::vector<const void*> key;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t stream = nullptr;
+  int dev = -1;  // device of the branch streams
+  cudaStream_t br[kBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBranches] = {};
 };
 BatchGraph g_batch;
 std::mutex g_batch_mu;  // guards g_batch
@@ -838,12 +885,45 @@ extern "C" eifmm_status eifmm_evaluate_batched(eifmm_tree* const* trees, const d
     for (int p = 0; p < n_problems; ++p) trees[p]->t.ws.evaluated = true;
     return EIFMM_OK;
   }
-  // direct pass (sizes the workspaces; also the result of this call)
-  for (int p = 0; p < n_problems; ++p) {
-    if (trees[p]->t.tgt.n == 0) continue;
-    EIFMM_TRY(evaluate_impl(trees[p], ops, sigma[p], trees[p]->t.src.n, 1, f[p], trees[p]->t.tgt.n,
-                            (int)prec, s));
+  // the branch streams of this device
+  int dev = 0;
+  EIFMM_CUDA(cudaGetDevice(&dev));
+  if (g_batch.dev != dev) {
+    for (int b = 0; b < kBranches; ++b) {
+      if (g_batch.br[b]) cudaStreamDestroy(g_batch.br[b]);
+      if (g_batch.join[b]) cudaEventDestroy(g_batch.join[b]);
+      g_batch.br[b] = nullptr;
+      g_batch.join[b] = nullptr;
+    }
+    if (g_batch.fork) cudaEventDestroy(g_batch.fork);
+    g_batch.fork = nullptr;
+    g_batch.dev = -1;
+    EIFMM_CUDA(cudaEventCreateWithFlags(&g_batch.fork, cudaEventDisableTiming));
+    for (int b = 0; b < kBranches; ++b) {
+      EIFMM_CUDA(cudaStreamCreateWithFlags(&g_batch.br[b], cudaStreamNonBlocking));
+      EIFMM_CUDA(cudaEventCreateWithFlags(&g_batch.join[b], cudaEventDisableTiming));
+    }
+    g_batch.dev = dev;
   }
+  // every problem on its branch; the branches fork from and join into s
+  auto run_all = [&]() -> eifmm_status {
+    const int K = n_problems < kBranches ? (n_problems > 0 ? n_problems : 1) : kBranches;
+    EIFMM_CUDA(cudaEventRecord(g_batch.fork, s));
+    for (int b = 0; b < K; ++b) EIFMM_CUDA(cudaStreamWaitEvent(g_batch.br[b], g_batch.fork, 0));
+    eifmm_status rc = EIFMM_OK;
+    for (int p = 0; p < n_problems && rc == EIFMM_OK; ++p) {
+      if (trees[p]->t.tgt.n == 0) continue;
+      rc = evaluate_impl(trees[p], ops, sigma[p], trees[p]->t.src.n, 1, f[p], trees[p]->t.tgt.n, (int)prec,
+                         g_batch.br[p % K]);
+    }
+    for (int b = 0; b < K; ++b) {  // joined also after a failure
+      cudaEventRecord(g_batch.join[b], g_batch.br[b]);
+      cudaStreamWaitEvent(s, g_batch.join[b], 0);
+    }
+    return rc;
+  };
+  // direct pass (sizes the workspaces; also the result of this call)
+  EIFMM_TRY(run_all());
   if (g_timing || s == nullptr) return EIFMM_OK;  // the legacy stream cannot be captured
   if (g_batch.exec) {
     cudaGraphExecDestroy(g_batch.exec);
@@ -853,12 +933,7 @@ extern "C" eifmm_status eifmm_evaluate_batched(eifmm_tree* const* trees, const d
   EIFMM_CUDA(cudaStreamSynchronize(s));
   cudaGraph_t graph = nullptr;
   EIFMM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  eifmm_status rc = EIFMM_OK;
-  for (int p = 0; p < n_problems && rc == EIFMM_OK; ++p) {
-    if (trees[p]->t.tgt.n == 0) continue;
-    rc = evaluate_impl(trees[p], ops, sigma[p], trees[p]->t.src.n, 1, f[p], trees[p]->t.tgt.n,
-                       (int)prec, s);
-  }
+  eifmm_status rc = run_all();
   cudaError_t e = cudaStreamEndCapture(s, &graph);
   if (rc != EIFMM_OK) {
     if (graph) cudaGraphDestroy(graph);

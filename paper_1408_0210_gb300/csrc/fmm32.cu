@@ -1087,6 +1087,11 @@ eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R) {
       const int G3 = ops->tier == 1 ? m2l_h16_groups(m2l_tma_ctas(k, R), nsm) : 1;
       if (G3 > 1) nd = std::max(nd, (size_t)G3 * rows * ops->lv[k].dp);
     }
+    // the stream-K form of the leaf level of tier 0 (an autotuner variant
+    // and a tree option) when its transposed tiles fill less than two waves
+    // of the SMs
+    if (ops->tier == 0 && ws.wa_t256[kap] && nboxes(kap) / 8 * R >= 256 && m2l_t256_ctas(kap, R) < 2 * nsm)
+      EIFMM_TRY(build_sk_plan(kap, R, nsm, &ws.sk));
     if (need) EIFMM_TRY(dalloc(&ws.m2l_part, need));
     ws.m2l_part_cap = need;
     if (need_leaf) EIFMM_TRY(dalloc(&ws.m2l_part_leaf, need_leaf));
@@ -1413,6 +1418,11 @@ eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, i
     // 256-row tiles; the 128-row kernel at the coarse levels
     kind = (ws.wa_t256[k] && nboxes(k) / 8 * R >= 256 && !t->opt[EIFMM_OPT_M2L_128ROW]) ? 1
                                                                                          : (ws.wa_grid[k] ? 2 : 4);
+    if (kind == 1 && leaf && ws.sk.tu && t->opt[EIFMM_OPT_M2L_STREAM_K]) kind = 3;
+  }
+  if (kind == 3) {  // stream-K: one CTA per SM, no offset groups
+    if (!leaf || !ws.sk.tu || !ws.wa_t256[k] || gshift != 0) return EIFMM_EUNSUPPORTED;
+    return launch_m2l_t256s(a, ws.tmap2[k][0], ws.tmap2[k][1], ws.sk, s);
   }
   if (kind == 1) {
     if (!ws.wa_t256[k]) return EIFMM_EUNSUPPORTED;

@@ -450,6 +450,26 @@ static void record(Workspace& ws, int i, cudaStream_t s) {
   if (timing_enabled()) cudaEventRecord(ws.ev_t[i], s);
 }
 
+// Step 4 of level k on FP64 arrays [box R + r][d]: the operator stack kdT
+// ([343][l][m'], d x d) applied by FP32-pair arithmetic or in FP64.
+eifmm_status launch_m2l_df(int level, int d, int R, const double* kdT, const int* slot_lists, const double* W,
+                           double* g, cudaStream_t s) {
+  const int64_t nb = (int64_t)1 << (3 * level);
+  k_m2l_df<<<dim3((unsigned)(((nb / 8 + DF_BOX - 1) / DF_BOX) * 8), (unsigned)((d + DF_ROW - 1) / DF_ROW),
+                  (unsigned)R), DF_THREADS, 0, s>>>(level, d, R, kdT, slot_lists, W, g);
+  EIFMM_CHECK_LAUNCH();
+  return EIFMM_OK;
+}
+
+eifmm_status launch_m2l64(int level, int d, int R, const double* kdT, const int* slot_lists, const double* W,
+                          double* g, cudaStream_t s) {
+  const int64_t nb = (int64_t)1 << (3 * level);
+  k_m2l64<<<dim3((unsigned)(nb / 8 / M2L_NB * 8), R), TPB, M2L_NB * d * sizeof(double), s>>>(
+      level, d, R, kdT, slot_lists, W, g);
+  EIFMM_CHECK_LAUNCH();
+  return EIFMM_OK;
+}
+
 eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_sigma, int R,
                        double* f, int64_t ld_f, cudaStream_t s, bool near32, bool pair_m2l) {
   Workspace& ws = t->ws;
@@ -497,19 +517,16 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
   // K^delta Delta), so step 4 reads W; What itself is formed only when it is
   // exported
   record(ws, 3, s);
-  // step 4
+  // step 4 (the compressed operators of Section 4.2 when they are built)
   for (int k = 2; k <= kap; ++k) {
     if (timing_enabled()) cudaEventRecord(ws.ev_m2l[k], s);
-    const int d = ops->lv[k].d;
-    const int64_t nb = (int64_t)1 << (3 * k);
-    if (pair_m2l && !t->opt[EIFMM_OPT_M2L_FP64])  // tiers 3 and 4 of the mixed path: FP32 pairs
-      k_m2l_df<<<dim3((unsigned)(((nb / 8 + DF_BOX - 1) / DF_BOX) * 8), (unsigned)((d + DF_ROW - 1) / DF_ROW),
-                      (unsigned)R), DF_THREADS, 0, s>>>(k, d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.W[k],
-                                                        ws.g[k]);
+    const bool pair = pair_m2l && !t->opt[EIFMM_OPT_M2L_FP64];  // tiers 3 and 4: FP32 pairs
+    if (ops->compressed && ops->lv[k].r > 0)
+      EIFMM_TRY(m2l_compressed(ws, ops, k, R, pair, s));
+    else if (pair)
+      EIFMM_TRY(launch_m2l_df(k, ops->lv[k].d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.W[k], ws.g[k], s));
     else
-      k_m2l64<<<dim3((unsigned)(nb / 8 / M2L_NB * 8), R), TPB, M2L_NB * d * sizeof(double), s>>>(
-          k, d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.W[k], ws.g[k]);
-    EIFMM_CHECK_LAUNCH();
+      EIFMM_TRY(launch_m2l64(k, ops->lv[k].d, R, ops->lv[k].kdT, ops->d_slot_lists, ws.W[k], ws.g[k], s));
     if (timing_enabled()) cudaEventRecord(ws.ev_m2le[k], s);
   }
   record(ws, 4, s);

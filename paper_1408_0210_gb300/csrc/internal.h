@@ -84,6 +84,11 @@ struct LevelOps {
   // [slot][chunk of 128 B of l][plane][row m' < dp][128 B].
   void* kd_img = nullptr;
   float* kd32 = nullptr;   // [343][l < d][m' < dp] FP32 folded operator (SIMT M2L of tier 2)
+  // M2L compression (Section 4.2, first stage), FP64 far field only
+  double* U = nullptr;     // d x r row-major: the kept left singular vectors of K_fat
+  double* Ct = nullptr;    // [343][l < r][m' < r]: C^delta_{m'l} = (U^t K^delta U)_{m'l}
+  int r = 0, r_i = 0, r_ii = 0;     // kept rank and the counts of the two filters
+  double s_kept = 0.0, s_next = 0.0;  // last kept and first dropped singular value / s_0
   int kd_img_fmt = -1;     // -1 none, else the PlaneFmt of the image
   float* kscale = nullptr; // [dp] power-of-two scale of row m' (FP16 image)
 };
@@ -95,6 +100,8 @@ struct Ops {
   int tier = 0;        // arithmetic tier of the mixed path
   double calib_err[4] = {-1.0, -1.0, -1.0, -1.0};  // last calibration, per tier
   int calib_tier = -1;
+  bool compressed = false;  // the FP64 far field runs the compressed M2L
+  double compress_eps = 0.0;
   uint64_t uid = 0;    // unique per loaded operator set: workspaces are keyed on it, not
                        // on the handle's address, which a later load may reuse
   LevelOps lv[kMaxLevel + 1];
@@ -117,6 +124,18 @@ struct PointSet {
   float* ly = nullptr;
   float* lz = nullptr;
 };
+
+// Device arrays of the stream-K plan of the leaf-level tensor-core M2L.
+struct SkPlanDev {
+  int* tu = nullptr;        // [ntiles + 1] units (active offsets) before each tile
+  int* fix_t = nullptr;     // split tiles
+  int* fix_b = nullptr;     // [nfix + 1] their first slot in fix_slot
+  int* fix_slot = nullptr;  // partial slots, CTA order
+  float* part = nullptr;    // [2 nctas][256][128] partial tiles
+  int ntiles = 0, tpc = 0, nctas = 0, nfix = 0;
+};
+void free_sk_plan(SkPlanDev* p);
+eifmm_status wait_selftest(long long limit, int* code);  // m2l_tc.cu
 
 struct Workspace {
   const void* ops_id = nullptr;
@@ -143,8 +162,8 @@ struct Workspace {
   // 256-row boxes of the transposed M2L (dp = 128)
   bool wa_t256[kMaxLevel + 1] = {};
   // M2L variant per level set by eifmm_autotune (0: built-in rule, 1:
-  // transposed, 2: 128-row) and the shift of its offset-group count
-  // (groups << shift, or >> -shift)
+  // transposed, 2: 128-row, 3: transposed stream-K) and the shift of its
+  // offset-group count (groups << shift, or >> -shift)
   int m2l_kind[kMaxLevel + 1] = {};
   int m2l_gshift[kMaxLevel + 1] = {};
   size_t m2l_part_cap = 0;  // floats in m2l_part (levels below the leaves)
@@ -153,6 +172,7 @@ struct Workspace {
   alignas(64) unsigned char tmap2[kMaxLevel + 1][2][128] = {};
   float* m2l_part = nullptr;    // partial M2L sums of the split offset lists
   uint32_t* wmax = nullptr;     // [kMaxLevel + 1] bits of max |W| per level (FP16 planes)
+  SkPlanDev sk;                 // stream-K plan of the leaf level (tier 0), when it pays
   int* err = nullptr;           // device error word of bounded waits
   int* err_host = nullptr;      // pinned copy, read at the next call
   void* tmp = nullptr;          // intermediate of the two Delta sweeps
@@ -182,7 +202,7 @@ struct Workspace {
   float step_ms[20] = {};
 };
 
-constexpr int kNumOptions = 4;  // eifmm_option
+constexpr int kNumOptions = 5;  // eifmm_option
 
 struct Tree {
   int depth = 0;
@@ -213,11 +233,17 @@ eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R,
 enum PlaneFmt { kPlaneBF16 = 0, kPlaneTF32 = 1, kPlaneF16 = 2 };
 eifmm_status build_kd_image(Ops* ops, int fmt, cudaStream_t s);
 eifmm_status build_kd32(Ops* ops, cudaStream_t s);
+// M2L compression (sarcmp.cu): eps <= 0 removes it.
+eifmm_status compress_ops(Ops* ops, double eps, cudaStream_t s);
+void free_compression(LevelOps& v);
 eifmm_status launch_m2l_level(Tree* t, const Ops* ops, int k, int R, int kind, int gshift, cudaStream_t s);
 eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma,
                         int64_t ld_sigma, int R, double* f, int64_t ld_f,
                         cudaStream_t s);
 eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec);
+// Step 4 of level k with the compressed operators (sarcmp.cu) on the FP64
+// far field; pair: FP32-pair arithmetic, else FP64.
+eifmm_status m2l_compressed(Workspace& ws, const Ops* ops, int k, int R, bool pair, cudaStream_t s);
 void free_workspace(Workspace* ws);
 bool timing_enabled();
 

@@ -23,6 +23,10 @@
 #include <cuda.h>
 #include <stdlib.h>
 
+#include <algorithm>
+#include <cstdlib>
+#include <vector>
+
 #include "internal.h"
 #include "m2l_tc.h"
 
@@ -52,16 +56,30 @@ __device__ __forceinline__ uint32_t mbar_try(uint32_t a, uint32_t parity) {
       : "memory");
   return ok;
 }
-// Bounded wait; returns false (and records `code`) on time-out.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err, int code) {
+// Bounded wait; returns false (and records `code`) after `limit` cycles.
+__device__ __forceinline__ bool mbar_wait_lim(uint32_t a, uint32_t parity, int* err, int code, long long limit) {
   const long long t0 = clock64();
   while (!mbar_try(a, parity)) {
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       atomicExch(err, code);
       return false;
     }
   }
   return true;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, int* err, int code) {
+  return mbar_wait_lim(a, parity, err, code, kWaitCycles);
+}
+
+// The producer's last act: every copy it issued has landed (each stage's
+// last fill completed its phase) before the CTA may exit, also after an
+// abort.  it = fills issued so far, ring of `stages`.  Bounded like every
+// wait.
+__device__ __forceinline__ void drain_fills(int it, int stages, const uint64_t* bars_full, int* err) {
+  for (int k = 0; k < stages && k < it; ++k) {
+    const int i = it - 1 - k;  // a recent fill
+    mbar_wait(smem_u32(&bars_full[i % stages]), (uint32_t)((i / stages) & 1), err, 5);
+  }
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
@@ -459,6 +477,7 @@ k_m2l_tma(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
         bulk_g2s(sA + 2 * a_bytes, src, 2 * b_bytes, full(st));
       }
     }
+    drain_fills(it, S, bars, a.err);
   } else if (tid == 160) {
     // ----------------------------------------------------- MMA issuer --
     const uint32_t id_lo = idesc(TF32 ? 2u : 1u, dp > 256 ? 256u : (uint32_t)dp);
@@ -672,6 +691,7 @@ k_m2l_t256(const __grid_constant__ CUtensorMap tW0, const __grid_constant__ CUte
         if (++st == kT2Stages) st = 0, ph ^= 1u;
       }
     }
+    drain_fills(it, kT2Stages, bars, a.err);
   } else if (tid == 288) {
     // ----------------------------------------------------- MMA issuer --
     const uint32_t id = idesc(TF32 ? 2u : 1u, (uint32_t)kT2Rows);
@@ -754,6 +774,284 @@ k_m2l_t256(const __grid_constant__ CUtensorMap tW0, const __grid_constant__ CUte
   __syncthreads();
   if (warp == 8)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
+}
+
+// ---------------------------------------------------------------------------
+// Stream-K form of the transposed M2L for one level: exactly one CTA per SM.
+// The work is the sequence of (tile, active offset) units over all tiles
+// (tile t: parity class t / tpc, tile t % tpc of that class; tu[t] = units
+// before tile t); CTA c takes units [c U / N, (c + 1) U / N).  Its pieces
+// (the part of one tile inside its range) run through the same producer /
+// MMA / segment-drain pipeline as k_m2l_t256, the rings and the TMEM
+// buffers continuing from one piece to the next.  A piece that covers its
+// whole tile writes g; any other writes a partial tile (256 rows x 128 m') to
+// slot 2c (the CTA's first piece) or 2c + 1 (its last), and k_sk_fixup adds
+// the partials of each split tile in CTA order.  No CTA waits on another.
+// ---------------------------------------------------------------------------
+struct SkPlan {
+  const int* tu;      // [ntiles + 1] units before each tile
+  int ntiles, tpc;    // tiles, tiles per parity class
+  int nctas;
+  float* part;        // [2 nctas][256][128] partial tiles
+};
+
+template <bool TF32>
+__global__ void __launch_bounds__(kT2Threads, 1)
+k_m2l_t256s(const __grid_constant__ CUtensorMap tW0, const __grid_constant__ CUtensorMap tW1, M2LTcArgs a,
+            SkPlan sk) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int esz = TF32 ? 4 : 2;
+  const int E = 128 / esz;
+  const int dp = a.dp;  // 128
+  const int nchunk = dp * esz / 128;
+  const uint32_t k_bytes = 128u * 128u;
+  const uint32_t w_bytes = kT2Rows * 128u;
+  const uint32_t stage = 2 * k_bytes + 2 * w_bytes;
+  uint64_t* bars = (uint64_t*)(smem + kT2Stages * stage);  // full[2] empty[2] sfull[2] sempty[2]
+  uint32_t* tslot = (uint32_t*)(bars + 8);
+  volatile int* abort = (volatile int*)(tslot + 1);
+  int64_t* s_row = (int64_t*)(bars + 9);  // [256] output rows of the current tile
+  const uint32_t sbase = smem_u32(smem);
+  auto full = [&](int st) { return smem_u32(&bars[st]); };
+  auto empty = [&](int st) { return smem_u32(&bars[2 + st]); };
+  auto sfull = [&](int b) { return smem_u32(&bars[4 + b]); };
+  auto sempty = [&](int b) { return smem_u32(&bars[6 + b]); };
+
+  const int h = a.h, R = a.R;
+  const int bxr = a.bx * R;
+  const int ntx = (h * R + bxr - 1) / bxr, nty = (h + a.by - 1) / a.by;
+  const int c = blockIdx.x;
+  const int U = sk.tu[sk.ntiles];
+  const int u0 = (int)((int64_t)c * U / sk.nctas), u1 = (int)((int64_t)(c + 1) * U / sk.nctas);
+  int t_first = 0;  // the tile holding unit u0: the last t with tu[t] <= u0
+  {
+    int lo = 0, hi = sk.ntiles - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (sk.tu[mid] <= u0) lo = mid;
+      else hi = mid - 1;
+    }
+    t_first = lo;
+  }
+  // geometry of tile t: parity class, first (x r, y, z) of its block
+  struct Geo {
+    int oct, cx, cy, cz, xr0, y0, z0;
+  };
+  auto geo = [&](int t) {
+    Geo g;
+    g.oct = t / sk.tpc;
+    int tile = t % sk.tpc;
+    const int tx = tile % ntx;
+    tile /= ntx;
+    const int ty = tile % nty, tz = tile / nty;
+    g.xr0 = tx * bxr;
+    g.y0 = ty * a.by;
+    g.z0 = tz * a.bz;
+    g.cx = g.oct & 1;
+    g.cy = (g.oct >> 1) & 1;
+    g.cz = (g.oct >> 2) & 1;
+    return g;
+  };
+  auto source = [&](const Geo& g, int slot, int* sc, int* sxr, int* sy, int* sz) {
+    const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+    *sc = ((g.cx + dx) & 1) | (((g.cy + dy) & 1) << 1) | (((g.cz + dz) & 1) << 2);
+    *sxr = g.xr0 + ((g.cx + dx) >> 1) * R;
+    *sy = g.y0 + ((g.cy + dy) >> 1);
+    *sz = g.z0 + ((g.cz + dz) >> 1);
+    return *sxr < h * R && *sxr + bxr > 0 && *sy < h && *sy + a.by > 0 && *sz < h && *sz + a.bz > 0;
+  };
+
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(full(i), 1);
+      mbar_init(empty(i), 1);
+      mbar_init(sfull(i), 1);
+      mbar_init(sempty(i), 8);  // one arrival per epilogue warp
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 8) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(512u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  if (tid == 256) {
+    // -------------------------------------------------------- producer --
+    int it = 0, st = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int t = t_first; t < sk.ntiles && sk.tu[t] < u1 && ok; ++t) {
+      const int lo = max(u0, sk.tu[t]) - sk.tu[t], hi = min(u1, sk.tu[t + 1]) - sk.tu[t];
+      const Geo g = geo(t);
+      const int* lst = a.slot_lists + g.oct * kListLen;
+      int ai = 0;  // index among the tile's active offsets
+      for (int s = 0; s < kListLen && ai < hi && ok; ++s) {
+        const int slot = lst[s];
+        int sc, sxr, sy, sz;
+        if (!source(g, slot, &sc, &sxr, &sy, &sz)) continue;
+        if (ai++ < lo) continue;
+        for (int cc = 0; cc < nchunk; ++cc, ++it) {
+          if (it >= kT2Stages && !mbar_wait_ab(empty(st), ph ^ 1u, a.err, 1, abort)) {
+            ok = false;
+            break;
+          }
+          const uint32_t sK = sbase + st * stage;
+          const uint32_t sW = sK + 2 * k_bytes;
+          mbar_expect_tx(full(st), 2 * k_bytes + 2 * w_bytes);
+          bulk_g2s(sK, (const char*)a.kd_img + (((size_t)slot * nchunk + cc) * 2) * k_bytes, 2 * k_bytes, full(st));
+          tma_load_5d(sW, &tW0, cc * E, sxr, sy, sz, sc, full(st));
+          tma_load_5d(sW + w_bytes, &tW1, cc * E, sxr, sy, sz, sc, full(st));
+          if (++st == kT2Stages) st = 0, ph ^= 1u;
+        }
+      }
+    }
+    drain_fills(it, kT2Stages, bars, a.err);
+  } else if (tid == 288) {
+    // ----------------------------------------------------- MMA issuer --
+    const uint32_t id = idesc(TF32 ? 2u : 1u, (uint32_t)kT2Rows);
+    const uint64_t dK0 = sdesc(sbase), dK1 = sdesc(sbase + stage);
+    const uint64_t dW0 = dK0 + (2 * k_bytes >> 4), dW1 = dK1 + (2 * k_bytes >> 4);
+    int st = 0, seg = 0;
+    uint32_t ph = 0;
+    bool ok = true;
+    for (int t = t_first; t < sk.ntiles && sk.tu[t] < u1 && ok; ++t) {
+      const int n_here = min(u1, sk.tu[t + 1]) - max(u0, sk.tu[t]);
+      for (int done = 0; done < n_here && ok; done += kSegOffsets, ++seg) {
+        const int b = seg & 1;
+        if (seg >= 2 && !mbar_wait_ab(sempty(b), ((seg >> 1) - 1) & 1, a.err, 4, abort)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dacc = tmem + (uint32_t)(b * kT2Rows);
+        const int nit = min(kSegOffsets, n_here - done) * nchunk;
+        for (int i = 0; i < nit; ++i) {
+          if (!mbar_wait_ab(full(st), ph, a.err, 2, abort)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          issue_chunk<TF32>(dacc, st == 0 ? dK0 : dK1, st == 0 ? dW0 : dW1, k_bytes >> 4, w_bytes >> 4, id, id,
+                            false, i == 0);
+          mma_commit(empty(st));
+          if (++st == kT2Stages) st = 0, ph ^= 1u;
+        }
+        if (ok) mma_commit(sfull(b));
+      }
+    }
+  } else if (warp < 8) {
+    // ------------------------------------------------------ epilogue --
+    const int q = warp & 3, half = warp >> 2;
+    const int mp = 32 * q + lane;  // m'
+    // every epilogue warp runs through every piece and both named barriers of
+    // each, whatever a wait returns, so that the barriers always match
+    int seg = 0;
+    bool have = true;
+    for (int t = t_first; t < sk.ntiles && sk.tu[t] < u1; ++t) {
+      const int lo = max(u0, sk.tu[t]) - sk.tu[t], hi = min(u1, sk.tu[t + 1]) - sk.tu[t];
+      const int n_here = hi - lo;
+      if (n_here <= 0) continue;  // a tile without units: the fix-up writes its zeros
+      float acc[128];
+#pragma unroll
+      for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+      for (int done = 0; done < n_here; done += kSegOffsets, ++seg) {
+        const int b = seg & 1;
+        if (have) have = mbar_wait_ab(sfull(b), (seg >> 1) & 1, a.err, 3, abort);
+        have = __all_sync(0xffffffffu, have);
+        if (!have) continue;
+        tc_fence_after();
+        const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * kT2Rows + 128 * half);
+#pragma unroll
+        for (int j0 = 0; j0 < 128; j0 += 32) {
+          float v[32];
+          tmem_ld32(taddr + j0, v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[j0 + i] += v[i];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sempty(b)) : "memory");
+      }
+      const bool whole = lo == 0 && hi == sk.tu[t + 1] - sk.tu[t];
+      asm volatile("bar.sync 1, 256;" ::: "memory");  // the previous tile's rows are read
+      {
+        const Geo g = geo(t);
+        const int n = tid;
+        const int xr = g.xr0 + n % bxr;
+        const int yy = g.y0 + (n / bxr) % a.by;
+        const int zz = g.z0 + n / (bxr * a.by);
+        int64_t row = -1;
+        if (xr < h * R && yy < h && zz < h) {
+          const int x = xr / R, r = xr % R;
+          row = morton_encode(2 * x + g.cx, 2 * yy + g.cy, 2 * zz + g.cz, a.level) * R + r;
+        }
+        s_row[n] = row;
+      }
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (!have) continue;
+      if (whole) {
+        float* outg = a.g + mp;
+#pragma unroll
+        for (int j = 0; j < 128; ++j) {
+          const int64_t row = s_row[128 * half + j];
+          if (row >= 0) outg[row * dp] = acc[j];
+        }
+      } else {
+        // slot 2c for the CTA's first piece, 2c + 1 for any later one
+        float* slot = sk.part + ((size_t)(2 * c + (t == t_first ? 0 : 1)) * kT2Rows) * 128 + mp;
+#pragma unroll
+        for (int j = 0; j < 128; ++j) slot[(size_t)(128 * half + j) * 128] = acc[j];
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 8)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
+}
+
+// The split tiles of the stream-K M2L: tile fix_t[i] is the sum, in CTA
+// order, of the partial slots fix_slot[fix_b[i] .. fix_b[i + 1]) (none: a
+// tile without active offsets, g = 0).  One block per split tile, thread n
+// = tile row n.
+__global__ void __launch_bounds__(256)
+k_sk_fixup(M2LTcArgs a, SkPlan sk, const int* __restrict__ fix_t, const int* __restrict__ fix_b,
+           const int* __restrict__ fix_slot) {
+  const int i = blockIdx.x, n = threadIdx.x;
+  const int t = fix_t[i];
+  const int h = a.h, R = a.R, bxr = a.bx * R;
+  const int ntx = (h * R + bxr - 1) / bxr, nty = (h + a.by - 1) / a.by;
+  const int oct = t / sk.tpc;
+  int tile = t % sk.tpc;
+  const int tx = tile % ntx;
+  tile /= ntx;
+  const int ty = tile % nty, tz = tile / nty;
+  const int xr = tx * bxr + n % bxr;
+  const int yy = ty * a.by + (n / bxr) % a.by;
+  const int zz = tz * a.bz + n / (bxr * a.by);
+  if (!(xr < h * R && yy < h && zz < h)) return;
+  const int x = xr / R, r = xr % R;
+  const int64_t row = morton_encode(2 * x + (oct & 1), 2 * yy + ((oct >> 1) & 1), 2 * zz + ((oct >> 2) & 1), a.level) * R + r;
+  float4* out = reinterpret_cast<float4*>(a.g + row * a.dp);
+  for (int j = 0; j < 32; ++j) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = fix_b[i]; k < fix_b[i + 1]; ++k) {
+      const float4 p = reinterpret_cast<const float4*>(sk.part + ((size_t)fix_slot[k] * kT2Rows + n) * 128)[j];
+      v.x += p.x;
+      v.y += p.y;
+      v.z += p.z;
+      v.w += p.w;
+    }
+    out[j] = v;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -873,6 +1171,7 @@ k_m2l_h16(const __grid_constant__ CUtensorMap tA0, const __grid_constant__ CUten
         if (++st == kH16Stages) st = 0, ph ^= 1u;
       }
     }
+    drain_fills(it, kH16Stages, bars, a.err);
   } else if (tid == 288) {
     // ----------------------------------------------------- MMA issuer --
     const uint32_t id = idesc(0u /* F16 */, (uint32_t)DP);
@@ -962,7 +1261,44 @@ __global__ void k_sum_parts(const float4* __restrict__ parts, int groups, int64_
   }
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that
+// nothing completes, with the wait routine of the kernels above and a
+// limit of `limit` cycles; it records code 7 and returns.  No copy, MMA or
+// tensor memory is involved, so giving up leaves nothing in flight.
+__global__ void k_wait_selftest(long long limit, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait_lim(smem_u32(&bar), 0, err, 7, limit);
+  }
+}
+
 }  // namespace
+
+eifmm_status wait_selftest(long long limit, int* code) {
+  int* err = nullptr;
+  EIFMM_TRY(dalloc(&err, 1));
+  eifmm_status rc = EIFMM_OK;
+  int h = 0;
+  if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess) rc = EIFMM_ECUDA;
+  if (rc == EIFMM_OK) {
+    k_wait_selftest<<<1, 32>>>(limit, err);
+    count_launch();
+    if (cudaGetLastError() != cudaSuccess || cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      set_error("eifmm_wait_selftest: launch failed");
+      rc = EIFMM_ECUDA;
+    }
+  }
+  dfree(err);
+  if (rc != EIFMM_OK) return rc;
+  if (code) *code = h;
+  if (h != 0) {
+    set_error("eifmm_wait_selftest: the bounded wait gave up (code " + std::to_string(h) + ")");
+    return EIFMM_ETIMEOUT;
+  }
+  return EIFMM_OK;
+}
 
 int m2l_tc_stages(int dp) {
   const size_t stage = 2 * 16384 + 2 * (size_t)dp * 128;
@@ -1228,6 +1564,120 @@ eifmm_status launch_m2l_h16(const M2LTcArgs& a0, const void* map0, const void* m
     const int64_t n4 = a.rows * (int64_t)a.dp / 4;
     k_sum_parts<<<(unsigned)((n4 + 255) / 256 < 4096 ? (n4 + 255) / 256 : 4096), 256, 0, s>>>(
         (const float4*)a.part, a.groups, n4, a.part_stride / 4, (float4*)a.g);
+    EIFMM_CHECK_LAUNCH();
+  }
+  return EIFMM_OK;
+}
+
+// Host plan of the stream-K M2L at `level` for R right-hand sides on nsm
+// CTAs: the units of every tile (its active offsets: the candidate offsets
+// of its parity class whose source block meets the class grid, the test the
+// kernels make), the CTA ranges, and the split tiles with the slots of their
+// partials in CTA order.  Uploaded once into device arrays owned by `p`.
+eifmm_status build_sk_plan(int level, int R, int nsm, SkPlanDev* p) {
+  int bx, by, bz;
+  if (!m2l_t256_block(R, &bx, &by, &bz) || nsm < 1) return EIFMM_EUNSUPPORTED;
+  const int h = 1 << (level - 1), bxr = bx * R;
+  const int ntx = (h * R + bxr - 1) / bxr, nty = (h + by - 1) / by, ntz = (h + bz - 1) / bz;
+  const int tpc = ntx * nty * ntz, ntiles = 8 * tpc;
+  std::vector<int> tu(ntiles + 1, 0);
+  for (int t = 0; t < ntiles; ++t) {
+    const int oct = t / tpc;
+    int tile = t % tpc;
+    const int tx = tile % ntx;
+    tile /= ntx;
+    const int ty = tile % nty, tz = tile / nty;
+    const int xr0 = tx * bxr, y0 = ty * by, z0 = tz * bz;
+    const int cx = oct & 1, cy = (oct >> 1) & 1, cz = (oct >> 2) & 1;
+    int n = 0;
+    for (int slot = 0; slot < kNumSlots; ++slot) {
+      const int dx = slot % 7 - 3, dy = (slot / 7) % 7 - 3, dz = slot / 49 - 3;
+      // the candidate offsets of the class: the parent's neighbours' children
+      // that are not neighbours of the box
+      if (((cx + dx) >> 1) < -1 || ((cx + dx) >> 1) > 1 || ((cy + dy) >> 1) < -1 || ((cy + dy) >> 1) > 1 ||
+          ((cz + dz) >> 1) < -1 || ((cz + dz) >> 1) > 1)
+        continue;
+      if (std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz))) < 2) continue;
+      const int sxr = xr0 + ((cx + dx) >> 1) * R, sy = y0 + ((cy + dy) >> 1), sz = z0 + ((cz + dz) >> 1);
+      if (sxr < h * R && sxr + bxr > 0 && sy < h && sy + by > 0 && sz < h && sz + bz > 0) ++n;
+    }
+    tu[t + 1] = tu[t] + n;
+  }
+  const int U = tu[ntiles];
+  const int nctas = std::max(1, std::min(nsm, U));
+  // pieces of every CTA; a tile is split unless one CTA covers it whole
+  std::vector<std::vector<int>> slots(ntiles);
+  std::vector<char> whole(ntiles, 0);
+  for (int c = 0; c < nctas; ++c) {
+    const int u0 = (int)((int64_t)c * U / nctas), u1 = (int)((int64_t)(c + 1) * U / nctas);
+    int t_first = (int)(std::upper_bound(tu.begin(), tu.begin() + ntiles, u0) - tu.begin()) - 1;
+    for (int t = t_first; t < ntiles && tu[t] < u1; ++t) {
+      const int lo = std::max(u0, tu[t]) - tu[t], hi = std::min(u1, tu[t + 1]) - tu[t];
+      if (hi <= lo) continue;
+      if (lo == 0 && hi == tu[t + 1] - tu[t]) whole[t] = 1;
+      else slots[t].push_back(2 * c + (t == t_first ? 0 : 1));
+    }
+  }
+  std::vector<int> fix_t, fix_b(1, 0), fix_slot;
+  for (int t = 0; t < ntiles; ++t) {
+    if (whole[t]) continue;  // tiles without units have no pieces: g = 0 from the fix-up
+    fix_t.push_back(t);
+    for (int sl : slots[t]) fix_slot.push_back(sl);
+    fix_b.push_back((int)fix_slot.size());
+  }
+  p->ntiles = ntiles;
+  p->tpc = tpc;
+  p->nctas = nctas;
+  p->nfix = (int)fix_t.size();
+  auto up = [](int** d, const std::vector<int>& v) -> eifmm_status {
+    EIFMM_TRY(dalloc(d, v.size() > 0 ? v.size() : 1));
+    if (!v.empty()) EIFMM_CUDA(cudaMemcpy(*d, v.data(), v.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return EIFMM_OK;
+  };
+  EIFMM_TRY(up(&p->tu, tu));
+  EIFMM_TRY(up(&p->fix_t, fix_t));
+  EIFMM_TRY(up(&p->fix_b, fix_b));
+  EIFMM_TRY(up(&p->fix_slot, fix_slot));
+  EIFMM_TRY(dalloc(&p->part, (size_t)2 * nctas * kT2Rows * 128));
+  return EIFMM_OK;
+}
+
+void free_sk_plan(SkPlanDev* p) {
+  dfree(p->tu);
+  dfree(p->fix_t);
+  dfree(p->fix_b);
+  dfree(p->fix_slot);
+  dfree(p->part);
+  *p = SkPlanDev();
+}
+
+eifmm_status launch_m2l_t256s(const M2LTcArgs& a0, const void* map0, const void* map1, const SkPlanDev& p,
+                              cudaStream_t s) {
+  M2LTcArgs a = a0;
+  if (a.dp != 128 || !m2l_t256_block(a.R, &a.bx, &a.by, &a.bz) || !p.tu) {
+    set_error("stream-K M2L: needs dp = 128, a tile shape for R and a plan");
+    return EIFMM_EUNSUPPORTED;
+  }
+  a.h = 1 << (a.level - 1);
+  const size_t sm = m2l_t256_smem_bytes();
+  static bool attr[kMaxDevices] = {};
+  const int dev = current_device();
+  if (dev >= kMaxDevices || !attr[dev]) {
+    EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_t256s<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    if (dev < kMaxDevices) attr[dev] = true;
+  }
+  SkPlan sk;
+  sk.tu = p.tu;
+  sk.ntiles = p.ntiles;
+  sk.tpc = p.tpc;
+  sk.nctas = p.nctas;
+  sk.part = p.part;
+  const CUtensorMap& m0 = *(const CUtensorMap*)map0;
+  const CUtensorMap& m1 = *(const CUtensorMap*)map1;
+  k_m2l_t256s<false><<<(unsigned)p.nctas, kT2Threads, sm, s>>>(m0, m1, a, sk);
+  EIFMM_CHECK_LAUNCH();
+  if (p.nfix > 0) {
+    k_sk_fixup<<<(unsigned)p.nfix, 256, 0, s>>>(a, sk, p.fix_t, p.fix_b, p.fix_slot);
     EIFMM_CHECK_LAUNCH();
   }
   return EIFMM_OK;

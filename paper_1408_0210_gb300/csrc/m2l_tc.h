@@ -43,6 +43,13 @@ eifmm_status make_plane_map(void* map, void* base, int level, int R, int dp, int
 eifmm_status launch_m2l_tma(const M2LTcArgs& a, const void* map0, const void* map1, bool tf32,
                             cudaStream_t s);
 eifmm_status launch_m2l_tc(const M2LTcArgs& a, bool tf32, cudaStream_t s);
+// Stream-K transposed M2L (dp = 128): one CTA per SM over (tile, offset)
+// units, split tiles summed by a fix-up kernel (plan: SkPlanDev).
+eifmm_status build_sk_plan(int level, int R, int nsm, SkPlanDev* p);
+void free_sk_plan(SkPlanDev* p);
+eifmm_status launch_m2l_t256s(const M2LTcArgs& a, const void* map0, const void* map1, const SkPlanDev& p,
+                              cudaStream_t s);
+
 // FP16 hi + lo planes, per-offset drains (dp in {64, 128, 192, 256}): W
 // planes scaled by f16_plane_scale(max |W| of the level) (wmax: the bits of
 // that maximum per level), K^delta Delta rows by kscale[m'].

@@ -276,6 +276,8 @@ void free_ops(Ops* ops) {
     dfree(v.X32);
     dfree(v.kd_img);
     dfree(v.kscale);
+    dfree(v.U);
+    dfree(v.Ct);
     dfree(v.kd32);
     v = LevelOps();
   }

@@ -26,9 +26,11 @@ EXPORTS = [
     "eifmm_evaluate", "eifmm_evaluate_host", "eifmm_evaluate_batched", "eifmm_debug_export",
     "eifmm_set_timing", "eifmm_last_step_times", "eifmm_direct_sum", "eifmm_kernel_launches",
     "eifmm_tree_sort_static", "eifmm_ops_calibrate", "eifmm_autotune", "eifmm_measure_rates",
-    "eifmm_ops_calibration", "eifmm_tree_set_option",
+    "eifmm_ops_calibration", "eifmm_tree_set_option", "eifmm_ops_compress", "eifmm_ops_basis",
+    "eifmm_wait_selftest",
 ]
-OPTIONS = {"m2l_128row": 0, "p2p_pair_symmetric": 1, "single_stream": 2, "m2l_fp64": 3}
+OPTIONS = {"m2l_128row": 0, "p2p_pair_symmetric": 1, "single_stream": 2, "m2l_fp64": 3,
+           "m2l_stream_k": 4}
 
 
 class EifmmError(RuntimeError):
@@ -82,6 +84,9 @@ def lib() -> C.CDLL:
         "eifmm_ops_calibrate": (i32, [vp, dbl, vp, vp]),
         "eifmm_ops_calibration": (i32, [vp, vp, vp]),
         "eifmm_tree_set_option": (i32, [vp, i32, i32]),
+        "eifmm_ops_compress": (i32, [vp, dbl, vp, vp]),
+        "eifmm_wait_selftest": (i32, [i64, vp]),
+        "eifmm_ops_basis": (i32, [vp, i32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -181,6 +186,25 @@ class Ops:
         e, t = (C.c_double * 4)(), C.c_int()
         _check(lib().eifmm_ops_calibration(self.handle, e, C.byref(t)))
         return {"tier": t.value, "err": [v if v >= 0 else None for v in e]}
+
+    def compress(self, eps: float, stream=None) -> dict:
+        """eifmm_ops_compress: the M2L compression of Section 4.2 for the FP64
+        far field (eps = 0 removes it); returns {level: rank}."""
+        rk = (C.c_int * 11)()
+        _check(lib().eifmm_ops_compress(self.handle, float(eps), _stream(stream), C.cast(rk, C.c_void_p)))
+        return {k: rk[k] for k in range(2, self.depth + 1)}
+
+    def basis(self, level: int) -> dict:
+        """eifmm_ops_basis: U (d x r), the two filter counts and the singular
+        values around the cut (relative to s_0)."""
+        d, r = C.c_int(), C.c_int()
+        info = (C.c_double * 4)()
+        _check(lib().eifmm_ops_basis(self.handle, level, None, C.byref(d), C.byref(r), C.cast(info, C.c_void_p)))
+        U = np.zeros((d.value, r.value))
+        if r.value > 0:
+            _check(lib().eifmm_ops_basis(self.handle, level, _p(U), None, None, None))
+        return {"U": U, "d": d.value, "r": r.value, "r_i": int(info[0]), "r_ii": int(info[1]),
+                "s_kept": info[2], "s_next": info[3]}
 
     def plan(self, tier_override: int = -1) -> int:
         t = C.c_int()
@@ -337,7 +361,7 @@ def eifmm_measure_rates(stream=None) -> dict:
     return {"ffma_per_s": r[0], "rsqrt_per_s": r[1], "dfma_per_s": r[2]}
 
 
-M2L_VARIANTS = {0: "rule", 1: "transposed", 2: "128-row"}
+M2L_VARIANTS = {0: "rule", 1: "transposed", 2: "128-row", 3: "transposed stream-K"}
 
 
 def eifmm_autotune(tree: Tree, ops: Ops, n_rhs: int = 1, prec="mixed", stream=None) -> dict:
@@ -381,6 +405,14 @@ def eifmm_direct_sum(kern, tgt_xyz, src_xyz, sigma, exclude_self=True, tgt_idx=N
                                   src_xyz.shape[0], _p(sigma), ld, R, int(bool(exclude_self)),
                                   _p(tgt_idx), n_eval, _p(f), _stream(stream)))
     return f
+
+
+def eifmm_wait_selftest(limit_cycles: int) -> tuple[int, int]:
+    """Runs the library's bounded device wait on a barrier nothing completes;
+    returns (status, code): (4 = ETIMEOUT, 7) when the wait gave up."""
+    code = C.c_int(-1)
+    st = lib().eifmm_wait_selftest(int(limit_cycles), C.byref(code))
+    return st, code.value
 
 
 def eifmm_kernel_launches() -> int:

@@ -148,6 +148,34 @@ def test_m2l_transposed_matches_128_row_kernel(E):
         assert relmax(g["t256"][k], g["128"][k]) <= 2e-5, k
 
 
+def test_stream_k_leaf_m2l_matches_per_tile_form(E):
+    """The leaf-level transposed M2L in stream-K form (one CTA per SM over
+    equal shares of the (tile, offset) units, split tiles added by the
+    fix-up kernel in CTA order) against one CTA per tile: the same g at the
+    leaf level to the FP32 rounding of another grouping of the segment sums
+    (each grouping lies about 2e-6 of max |g| from the exact sum in the
+    accumulation study of the design notes, so two differ by up to twice
+    that), and the same g bit for bit above it (those levels do not
+    change)."""
+    n, depth = 300000, 5
+    x = wl.uniform_cube(n, 43)
+    s = wl.sigma_uniform(n, 1, 44)
+    ops = E.eifmm_ops_build("inv_r", 1.0, depth, 1e-4)
+    ops.plan(0)
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    g = {}
+    for off in (False, True):
+        tree.set_option("m2l_stream_k", not off)
+        f = torch.zeros(n, dtype=torch.float64, device="cuda")
+        E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
+        torch.cuda.synchronize()
+        g[off] = {k: E.eifmm_debug_export(tree, 2, k, ops.error_estimate(k)[1]) for k in range(2, depth + 1)}
+    assert np.isfinite(g[False][depth]).all()
+    assert relmax(g[False][depth], g[True][depth]) <= 5e-6
+    for k in range(2, depth):
+        np.testing.assert_array_equal(g[False][k], g[True][k])
+
+
 def test_autotune_keeps_the_result(E, orc):
     """The autotuner picks an applicable M2L variant per level; the evaluation
     with its choice is the same method (another order of the M2L sums)."""
@@ -512,3 +540,23 @@ def test_mixed_degenerate_inputs(E, orc, tier):
     E.eifmm_evaluate(t3, ops, torch.zeros(0, dtype=torch.float64, device="cuda"), f3, "mixed")
     torch.cuda.synchronize()
     assert bool((f3 == 0).all())
+
+
+def test_bounded_wait_times_out_and_the_context_survives(E, orc):
+    """Failure detection without a GPU fault: the library's bounded wait, on
+    an mbarrier that nothing completes and with a limit of about a
+    millisecond, gives up, records its code and returns ETIMEOUT; the
+    context stays usable, and an evaluation right after it is correct."""
+    st, code = E.eifmm_wait_selftest(2_000_000)
+    assert (st, code) == (4, 7)
+    assert E.lib().eifmm_last_error().decode().startswith("eifmm_wait_selftest")
+    n, depth = 3000, 3
+    x = wl.uniform_cube(n, 61)
+    s = wl.sigma_uniform(n, 1, 62)
+    ops = E.eifmm_ops_build("inv_r", 1.0, depth, 1e-4)
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    f = torch.zeros(n, dtype=torch.float64, device="cuda")
+    E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
+    f1 = orc.direct_sum("inv_r", x, x, s)[:, 0]
+    assert rel2(f.cpu().numpy(), f1) <= 1e-4
+

@@ -92,7 +92,7 @@ def test_two_rank_spatial_plan_against_brute_force(orc, depth, m):
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         port = s.getsockname()[1]
-    with mp.Manager() as man:
+    with mp.get_context("spawn").Manager() as man:
         out = man.dict()
         mp.spawn(_rank, args=(2, port, depth, m, counts, out), nprocs=2, join=True)
         res = dict(out)
