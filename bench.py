@@ -212,6 +212,8 @@ WORKLOADS = {
     "c3": ("8-Gaussian mixture N=1048576 (std 0.05, centres U[0.2,0.8]^3, clipped), "
            "K=exp(-r)/r + 1/sqrt(r1^2+0.01 r2^2+r3^2+1e-3), depth 5, eps 1e-6, 1 RHS, mixed"),
     "c4a": "uniform cube N=262144, K=1/r, depth 5, eps 1e-6, 64 RHS, mixed",
+    "c4a+c": ("uniform cube N=262144, K=1/r, depth 5, eps 1e-6, 64 RHS, mixed, M2L compressed "
+              "(Section 4.2 first stage)"),
     "c4b": ("32 problems, N log-uniform in [16384, 262144], own uniform points and trees "
             "(depth clamp(ceil(log8(N/32)), 3, 5)), one operator set, K=1/r, eps 1e-6, "
             "one graph launch, mixed"),
@@ -263,20 +265,24 @@ def run_workloads(names, stream, flush, dist):
     for name in names:
         r = {"workload": WORKLOADS[name]}
         try:
-            if name in ("c1", "c3", "c4a", "c5", "sphere"):
+            if name in ("c1", "c3", "c4a", "c4a+c", "c5", "sphere"):
                 kern, n, depth, eps, R, prec, steps, warmup = {
                     "c1": ("inv_r", 4096, 3, 1e-6, 1, "fp64", 10, 3),
                     "c3": ("config3", 1 << 20, 5, 1e-6, 1, "mixed", 3, 3),
                     "c4a": ("inv_r", 262144, 5, 1e-6, 64, "mixed", 1, 1),
+                    "c4a+c": ("inv_r", 262144, 5, 1e-6, 64, "mixed", 1, 1),
                     "c5": ("inv_r", 1 << 24, 7, 1e-5, 8, "mixed", 2, 3),
                     "sphere": ("inv_r", 992046, 7, 1e-4, 1, "mixed", 5, 3),
                 }[name]
                 x = {"c1": lambda: wl.uniform_cube(n, 1), "c3": lambda: wl.gaussian_mixture(n, 3),
-                     "c4a": lambda: wl.uniform_cube(n, 4), "c5": lambda: wl.uniform_cube(n, 5),
+                     "c4a": lambda: wl.uniform_cube(n, 4), "c4a+c": lambda: wl.uniform_cube(n, 4),
+                     "c5": lambda: wl.uniform_cube(n, 5),
                      "sphere": lambda: wl.sphere_surface(n, 6)}[name]()
                 s = (wl.sigma_normal(n, R, 105) if name == "c5" else
-                     wl.sigma_uniform(n, R, {"c1": 101, "c3": 103, "c4a": 104, "sphere": 106}[name]))
+                     wl.sigma_uniform(n, R, {"c1": 101, "c3": 103, "c4a": 104, "c4a+c": 104, "sphere": 106}[name]))
                 ops = E.eifmm_ops_build(kern, 1.0, depth, eps, 512, stream)
+                if name.endswith("+c"):
+                    r["m2l_rank"] = ops.compress(eps, stream)
                 tree = E.eifmm_tree_build(torch.from_numpy(x).to(dev), None, (0, 0, 0), 1.0, depth, True, stream)
                 sd = cols(s) if R > 1 else torch.from_numpy(np.ascontiguousarray(s[:, 0])).to(dev)
                 f = (torch.zeros(R, n, dtype=torch.float64, device=dev).T if R > 1
@@ -338,7 +344,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variants", default="mixed:1e-4,fp64:1e-4,mixed:1e-5,mixed:1e-6,mixed+c:1e-6,fp64:1e-6,fp64+c:1e-6,mixed:1e-7,fp64:1e-7")
-    ap.add_argument("--workloads", default="c1,c3,c4a,c4b,c5,sphere",
+    ap.add_argument("--workloads", default="c1,c3,c4a,c4a+c,c4b,c5,sphere",
                     help="other benchmark workloads to time after the headline ('' for none)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run this many evaluations of the first variant between "
