@@ -346,6 +346,10 @@ def main():
     ap.add_argument("--variants", default="mixed:1e-4,fp64:1e-4,mixed:1e-5,mixed:1e-6,mixed+c:1e-6,fp64:1e-6,fp64+c:1e-6,mixed:1e-7,fp64:1e-7")
     ap.add_argument("--workloads", default="c1,c3,c4a,c4a+c,c4b,c5,sphere",
                     help="other benchmark workloads to time after the headline ('' for none)")
+    ap.add_argument("--tree-option", action="append", default=[],
+                    help="name=0|1: eifmm_tree_set_option on the workload's tree (for comparisons)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the built-in M2L and near-field rules (with --tree-option, to compare kernels)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run this many evaluations of the first variant between "
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off) and exit")
@@ -373,6 +377,9 @@ def main():
     sd = torch.from_numpy(np.ascontiguousarray(s[:, 0])).to(dev)
     f = torch.zeros(N_POINTS, dtype=torch.float64, device=dev)
     tree = E.eifmm_tree_build(xd, None, (0, 0, 0), 1.0, DEPTH, True, stream)
+    for opt in args.tree_option:
+        name, val = opt.split("=")
+        tree.set_option(name, val not in ("0", "false", "False"))
     # the tree build (step a0, outside the timed evaluate as in the paper),
     # timed on its own: device events around a few rebuilds
     tb = []
@@ -412,7 +419,7 @@ def main():
     if args.profile_steps > 0:
         name, eps = variants[0]
         prec, o = name.split("+")[0], ops[(eps, name.endswith("+c"))]
-        if prec == "mixed":
+        if prec == "mixed" and not args.no_autotune:
             E.eifmm_autotune(tree, o, NRHS, prec, stream)
         for _ in range(max(args.warmup, 1)):
             E.eifmm_evaluate(tree, o, sd, f, prec, stream)
@@ -427,7 +434,7 @@ def main():
     def run_variant(name, eps, steps, warmup, timing=False):
         prec, o = name.split("+")[0], ops[(eps, name.endswith("+c"))]
         tuned = None
-        if prec == "mixed":
+        if prec == "mixed" and not args.no_autotune:
             # the M2L autotuner (setup, like the tree build): per-level variant
             tuned = E.eifmm_autotune(tree, o, NRHS, prec, stream)
         for _ in range(warmup):
@@ -484,6 +491,7 @@ def main():
                 "nf_ms": round(statistics.median([t[8] for t in st]), 4),
                 "m2l_autotune": ({str(k): [E.M2L_VARIANTS[v], g] for k, (v, g) in tuned.items()}
                                  if tuned else None),
+                "p2p_pair_symmetric": tree.p2p_pair_symmetric if tuned else None,
                 "m2l_ms_per_level": [round(v, 4) for v in m2l]}
             if headline is None and err <= eps and (name, eps) in (("mixed", 1e-4), ("fp64", 1e-4)):
                 headline = (name, eps)

@@ -333,12 +333,16 @@ eifmm_status eifmm_evaluate(eifmm_tree* tree, const eifmm_ops* ops,
  * For the mixed path of tiers 0 and 1 it evaluates once with sigma = 0 (which
  * also sets up the workspace for n_rhs), then times at every level each
  * applicable M2L variant -- 1 transposed (M = coefficients, N = 256 target
- * rows), 2 128-row TMA --
+ * rows), 2 128-row TMA, 3 transposed in stream-K form (leaf level) --
  * with the offset-group count halved, kept or doubled, against the built-in
  * rule (variant 0), using CUDA events on `stream`.  The fastest (by at least
  * 2% over the rule) is kept in the tree for later evaluations with the same
- * ops, n_rhs and precision.  choice (may be null): int[2 * 11], entries
- * 2k and 2k+1 = variant and group shift of level k.  Other paths and tiers:
+ * ops, n_rhs and precision.  For tier 0 with one right-hand side on a tree
+ * whose targets are its sources it also times the near field (Section 3.2)
+ * per target against its pair-symmetric form and keeps the faster (the
+ * latter must win by 2%).  choice (may be null): int[2 * 11], entries 2k
+ * and 2k+1 = variant and group shift of level k >= 2; entry 0 = 1 when the
+ * pair-symmetric near field was kept.  Other paths and tiers:
  * nothing to tune, returns OK with zeros.  Synchronises `stream`.
  * Errors: as eifmm_evaluate. */
 eifmm_status eifmm_autotune(eifmm_tree* tree, const eifmm_ops* ops, int n_rhs,

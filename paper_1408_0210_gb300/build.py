@@ -63,7 +63,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
         objs = list(ex.map(compile_one, srcs))
     if force or not os.path.exists(OUT) or any(os.path.getmtime(o) > os.path.getmtime(OUT) for o in objs):
         tmp = OUT + ".tmp"
-        r = subprocess.run([cc, ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs], capture_output=True, text=True)
+        r = subprocess.run([cc, ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs, "-lcublas"],
+                           capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
         os.replace(tmp, OUT)

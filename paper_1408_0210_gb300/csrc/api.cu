@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 #include <set>
@@ -67,6 +68,7 @@ void free_workspace(Workspace* ws) {
   ws->m2l_part_leaf = nullptr;
   ws->m2l_part_leaf_cap = 0;
   for (int k = 0; k <= kMaxLevel; ++k) ws->m2l_kind[k] = ws->m2l_gshift[k] = 0;
+  ws->p2p_sym = 0;
   free_sk_plan(&ws->sk);
   dfree(ws->fnear); dfree(ws->ffar); dfree(ws->tmp); dfree(ws->gsym); dfree(ws->wmax);
   ws->gsym = nullptr;
@@ -696,6 +698,7 @@ extern "C" eifmm_status eifmm_autotune(eifmm_tree* tree, const eifmm_ops* ops, i
     if ((rc = evaluate_impl(tree, ops, sg, ns, R, fo, nt, (int)prec, s)) != EIFMM_OK) break;
     Workspace& ws = t.ws;
     for (int k = 0; k <= kMaxLevel; ++k) ws.m2l_kind[k] = ws.m2l_gshift[k] = 0;
+    ws.p2p_sym = 0;
     // room for the partial sums of larger group counts, within 1 GiB per
     // buffer (the leaf level has its own: it runs concurrently)
     size_t want = ws.m2l_part_cap, want_leaf = ws.m2l_part_leaf_cap;
@@ -759,6 +762,27 @@ extern "C" eifmm_status eifmm_autotune(eifmm_tree* tree, const eifmm_ops* ops, i
         choice[2 * k] = bk;
         choice[2 * k + 1] = bg;
       }
+    }
+    // the near field of tier 0 with one right-hand side and targets =
+    // sources: the per-target kernel against the pair-symmetric one
+    if (rc == EIFMM_OK && ops->o.tier == 0 && R == 1 && t.same && t.exclude_self && ws.gsym) {
+      float tn[2] = {1e30f, 1e30f};
+      for (int v = 0; v < 2 && rc == EIFMM_OK; ++v) {
+        ws.p2p_sym = v;
+        float ms[3];
+        for (int rep = 0; rep < 4 && rc == EIFMM_OK; ++rep) {  // the first is a warm-up
+          cudaEventRecord(e0, s);
+          rc = launch_p2p32(&t, (int)ops->o.kern, ws.sig32, R, ws.fnear, s, false, ws.gsym);
+          cudaEventRecord(e1, s);
+          cudaEventSynchronize(e1);
+          if (rep > 0) cudaEventElapsedTime(&ms[rep - 1], e0, e1);
+        }
+        // the median of the three
+        tn[v] = ms[0] + ms[1] + ms[2] - std::min(ms[0], std::min(ms[1], ms[2])) -
+                std::max(ms[0], std::max(ms[1], ms[2]));
+      }
+      ws.p2p_sym = tn[1] < tn[0] * 0.98f ? 1 : 0;  // the pair-symmetric kernel must win by 2%
+      if (choice) choice[0] = ws.p2p_sym;
     }
     if (rc == EIFMM_OK && cudaStreamSynchronize(s) != cudaSuccess) {
       rc = EIFMM_ECUDA;

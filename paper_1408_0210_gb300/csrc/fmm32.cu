@@ -638,6 +638,193 @@ k_p2p32x(const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff, c
   }
 }
 
+// ------------------------------------- P2M and L2P of 1/r, one RHS ------
+// Steps 1 and 7 for K = 1/r with one right-hand side, with the distances
+// computed two at a time (sub/mul/fma.rn.f32x2) over pairs of interpolation
+// points: one warp per leaf, PT_WARPS leaves per CTA, the level's points
+// x_l^{I_0} (= y_l^{J_0}) staged once per CTA as SoA pairs
+//   s_xy[q] = (x_2q, x_2q+1 | y_2q, y_2q+1),  s_z[q] = (z_2q, z_2q+1),
+// with a far-away pad (and a zero coefficient) past d.  No CTA barrier after
+// the staging: each warp owns its leaf.
+constexpr int PT_WARPS = 8;
+constexpr int PT_MAXQ = 128;  // pairs: dp <= 256
+
+__device__ __forceinline__ void pt_stage_x(const float* __restrict__ X, int d, int nq, ulonglong2* s_xy,
+                                           uint64_t* s_z) {
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    const int a = 2 * q, b = 2 * q + 1;
+    const float x0 = a < d ? X[3 * a] : NF_FAR, y0 = a < d ? X[3 * a + 1] : NF_FAR, z0 = a < d ? X[3 * a + 2] : NF_FAR;
+    const float x1 = b < d ? X[3 * b] : NF_FAR, y1 = b < d ? X[3 * b + 1] : NF_FAR, z1 = b < d ? X[3 * b + 2] : NF_FAR;
+    s_xy[q] = make_ulonglong2(pk2(x0, x1), pk2(y0, y1));
+    s_z[q] = pk2(z0, z1);
+  }
+}
+
+// (1/r_lo, 1/r_hi) of a packed r^2, with a Newton step when ACC
+template <bool ACC>
+__device__ __forceinline__ uint64_t pt_rsqrt2(uint64_t r2) {
+  float rl, rh;
+  up2(r2, rl, rh);
+  float yl = rsqrt_approx(rl), yh = rsqrt_approx(rh);
+  if (ACC) {
+    yl = yl * fmaf(-0.5f * rl, yl * yl, 1.5f);
+    yh = yh * fmaf(-0.5f * rh, yh * yh, 1.5f);
+  }
+  return pk2(yl, yh);
+}
+
+__device__ __forceinline__ uint64_t pt_r2(uint64_t ax, uint64_t ay, uint64_t az, uint64_t bx, uint64_t by,
+                                          uint64_t bz) {
+  uint64_t dx, dy, dz, r2;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(ax), "l"(bx));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(ay), "l"(by));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(az), "l"(bz));
+  asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(r2) : "l"(dx));
+  asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(r2) : "l"(dy));
+  asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(r2) : "l"(dz));
+  return r2;
+}
+
+__device__ __forceinline__ void pt_fma2(uint64_t& acc, uint64_t a, uint64_t b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+
+// Step 1: W_m = sum_j sigma_j / |x_m - y_j|.  Lane owns the coefficient
+// pairs q = lane + 32 i (at most PT_MAXQ / 32 of them, in registers); the
+// leaf's points pass through shared memory 32 at a time, each as two
+// broadcast 16-byte words (x, x | y, y) and (z, z | sigma, sigma).
+template <bool ACC>
+__global__ void __launch_bounds__(32 * PT_WARPS, 4)
+k_p2m32x(const int32_t* __restrict__ off, int64_t nleaf, const float* __restrict__ lx,
+         const float* __restrict__ ly, const float* __restrict__ lz, const float* __restrict__ sig,
+         const float* __restrict__ X, int d, int dp, float* __restrict__ W) {
+  constexpr int NI = PT_MAXQ / 32;
+  __shared__ ulonglong2 s_xy[PT_MAXQ];
+  __shared__ uint64_t s_z[PT_MAXQ];
+  __shared__ ulonglong2 s_pt[PT_WARPS][32][2];
+  const int nq = (d + 1) >> 1, nqi = (nq + 31) >> 5;
+  pt_stage_x(X, d, nq, s_xy, s_z);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t b = (int64_t)blockIdx.x * PT_WARPS + w;
+  if (b >= nleaf) return;
+  uint64_t ax[NI], ay[NI], az[NI], acc[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int q = lane + 32 * i;
+    acc[i] = 0;
+    if (q < nq) {
+      const ulonglong2 e = s_xy[q];
+      ax[i] = e.x;
+      ay[i] = e.y;
+      az[i] = s_z[q];
+    } else {
+      ax[i] = ay[i] = az[i] = pk2(NF_FAR, NF_FAR);
+    }
+  }
+  const int beg = off[b], end = off[b + 1];
+  for (int j0 = beg; j0 < end; j0 += 32) {
+    const int j = j0 + lane;
+    __syncwarp();
+    if (j < end) {
+      const float px = lx[j], py = ly[j], pz = lz[j], s = sig[j];
+      s_pt[w][lane][0] = make_ulonglong2(pk2(px, px), pk2(py, py));
+      s_pt[w][lane][1] = make_ulonglong2(pk2(pz, pz), pk2(s, s));
+    }
+    __syncwarp();
+    const int cnt = min(32, end - j0);
+    // two points per step: their distances and 1/r are independent, only
+    // the accumulation is sequential (in point order)
+    int t = 0;
+    for (; t + 1 < cnt; t += 2) {
+      const ulonglong2 p0 = s_pt[w][t][0], p1 = s_pt[w][t][1];
+      const ulonglong2 o0 = s_pt[w][t + 1][0], o1 = s_pt[w][t + 1][1];
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+        if (i < nqi) {  // warp-uniform; lanes past nq work on the far pad
+          const uint64_t kp = pt_rsqrt2<ACC>(pt_r2(ax[i], ay[i], az[i], p0.x, p0.y, p1.x));
+          const uint64_t ko = pt_rsqrt2<ACC>(pt_r2(ax[i], ay[i], az[i], o0.x, o0.y, o1.x));
+          pt_fma2(acc[i], kp, p1.y);
+          pt_fma2(acc[i], ko, o1.y);
+        }
+    }
+    if (t < cnt) {
+      const ulonglong2 p0 = s_pt[w][t][0], p1 = s_pt[w][t][1];
+#pragma unroll
+      for (int i = 0; i < NI; ++i)
+        if (i < nqi) pt_fma2(acc[i], pt_rsqrt2<ACC>(pt_r2(ax[i], ay[i], az[i], p0.x, p0.y, p1.x)), p1.y);
+    }
+  }
+  float* row = W + b * dp;
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int q = lane + 32 * i;
+    if (2 * q < dp) {
+      float lo, hi;
+      up2(acc[i], lo, hi);
+      if (2 * q >= d) lo = 0.f;
+      if (2 * q + 1 >= d) hi = 0.f;
+      *reinterpret_cast<float2*>(row + 2 * q) = make_float2(lo, hi);
+    }
+  }
+}
+
+// Step 7 (the far field alone): f_F(x_i) = sum_l lhat_l / |x_i - x_l|.  The
+// warp stages the leaf's coefficient pairs beside the z pairs,
+// s_zl[q] = (z_2q, z_2q+1 | lhat_2q, lhat_2q+1); lanes = (point, slice):
+// 32 points per pass while that many remain, then the rest with
+// S = 32 / rest slices of the pairs, added by shuffles.
+template <bool ACC>
+__global__ void __launch_bounds__(32 * PT_WARPS)
+k_l2p32x(const int32_t* __restrict__ leaves, int64_t nl, const int32_t* __restrict__ off,
+         const float* __restrict__ lx, const float* __restrict__ ly, const float* __restrict__ lz,
+         const float* __restrict__ X, int d, int dp, const float* __restrict__ lh, double* __restrict__ ffar) {
+  __shared__ ulonglong2 s_xy[PT_MAXQ];
+  __shared__ uint64_t s_z[PT_MAXQ];
+  __shared__ ulonglong2 s_zl[PT_WARPS][PT_MAXQ];
+  const int nq = (d + 1) >> 1;
+  pt_stage_x(X, d, nq, s_xy, s_z);
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * PT_WARPS + w;
+  if (i >= nl) return;
+  const int b = leaves[i];
+  const float* lrow = lh + (int64_t)b * dp;
+  for (int q = lane; q < nq; q += 32) {
+    const float2 c = *reinterpret_cast<const float2*>(lrow + 2 * q);
+    s_zl[w][q] = make_ulonglong2(s_z[q], pk2(c.x, 2 * q + 1 < d ? c.y : 0.f));
+  }
+  __syncwarp();
+  const int beg = off[b], end = off[b + 1];
+  for (int t0 = beg; t0 < end; t0 += 32) {
+    const int P = min(32, end - t0), S = 32 / P;
+    const int ti = lane % P, si = lane / P;
+    const int p = t0 + ti;
+    float s = 0.f;
+    if (si < S) {
+      const float px = lx[p], py = ly[p], pz = lz[p];
+      const uint64_t PX = pk2(px, px), PY = pk2(py, py), PZ = pk2(pz, pz);
+      const int L = (nq + S - 1) / S;
+      const int qb = min(nq, si * L), qe = min(nq, qb + L);
+      uint64_t acc = 0;
+#pragma unroll 4
+      for (int q = qb; q < qe; ++q) {
+        const ulonglong2 e = s_xy[q], f = s_zl[w][q];
+        pt_fma2(acc, pt_rsqrt2<ACC>(pt_r2(e.x, e.y, f.x, PX, PY, PZ)), f.y);
+      }
+      float lo, hi;
+      up2(acc, lo, hi);
+      s = lo + hi;
+    }
+    // slices si = 1..S-1 of point ti sit at lanes ti + P si
+    for (int k = 1; k < S; ++k) {
+      const float o = __shfl_sync(0xffffffffu, s, min(31, lane + P * k));
+      if (lane < P) s += o;
+    }
+    if (lane < P) ffar[p] = (double)s;
+  }
+}
+
 // --------------------------------------------------- operator images ----
 // K^delta (kdT[slot][l][m'] FP64) -> two planes in the swizzled image used
 // by the tensor-core M2L: byte offset of row n, 16-byte unit j inside the
@@ -1314,7 +1501,8 @@ static void p2p_launch(const Tree* t, int kern, const float* sig32, int R, doubl
 // (read at every evaluate).  It is not the default: it measured slower than
 // the per-target kernel (588 against 423 us at 1M points).
 static bool use_p2p_sym(const Tree* t, int R, bool accurate, const float* gsym) {
-  return gsym && !accurate && R == 1 && t->same && t->exclude_self && t->opt[EIFMM_OPT_P2P_PAIR_SYMMETRIC];
+  return gsym && !accurate && R == 1 && t->same && t->exclude_self &&
+         (t->opt[EIFMM_OPT_P2P_PAIR_SYMMETRIC] || t->ws.p2p_sym == 1);
 }
 
 eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R, double* fnear,
@@ -1499,7 +1687,17 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
 #define EIFMM_P2M(K, RC_, A)                                                                   \
   k_p2m32<K, RC_, A><<<nb, TPB, 0, s>>>(kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32, S.n, R, vl.X32, \
                                         vl.d, vl.dp, ws.W32[kap])
-    EIFMM_POINT_DISPATCH(EIFMM_P2M);
+    if (kern == EIFMM_KERNEL_INV_R && R == 1 && vl.dp <= 2 * PT_MAXQ) {
+      const unsigned g = (unsigned)((nboxes(kap) + PT_WARPS - 1) / PT_WARPS);
+      if (acc)
+        k_p2m32x<true><<<g, 32 * PT_WARPS, 0, s>>>(S.leaf_off, nboxes(kap), S.lx, S.ly, S.lz, ws.sig32, vl.X32,
+                                                   vl.d, vl.dp, ws.W32[kap]);
+      else
+        k_p2m32x<false><<<g, 32 * PT_WARPS, 0, s>>>(S.leaf_off, nboxes(kap), S.lx, S.ly, S.lz, ws.sig32, vl.X32,
+                                                    vl.d, vl.dp, ws.W32[kap]);
+    } else {
+      EIFMM_POINT_DISPATCH(EIFMM_P2M);
+    }
 #undef EIFMM_P2M
     EIFMM_CHECK_LAUNCH();
   }
@@ -1514,7 +1712,8 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     x.ncol = nboxes(k) * R;
     x.A = a.m2m32; x.B = ws.W32[k + 1]; x.G = nullptr; x.C = ws.W32[k];
     x.P8 = (float*)ws.tmp;  // 8 x nboxes(k) x R x dp floats fit in the scratch
-    EIFMM_TRY(launch_xfer_gemm(x, s));
+    if (!(R == 1 && xfer_blas(true, a, c, nboxes(k), ws.W32[k + 1], nullptr, ws.W32[k], s)))
+      EIFMM_TRY(launch_xfer_gemm(x, s));
   }
   record(ws, 2, s);
   // step 3: What = Delta W is folded into the M2L operator (K^delta Delta,
@@ -1592,7 +1791,8 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     x.ncol = nboxes(k - 1) * R;
     x.A = v.l2l32; x.B = ws.l32[k - 1]; x.G = ws.g32[k]; x.C = ws.l32[k];
     x.P8 = nullptr;
-    EIFMM_TRY(launch_xfer_gemm(x, s));
+    if (!(R == 1 && xfer_blas(false, v, pv, nboxes(k - 1), ws.l32[k - 1], ws.g32[k], ws.l32[k], s)))
+      EIFMM_TRY(launch_xfer_gemm(x, s));
   }
   record(ws, 5, s);
   // step 6: lhat = Delta^t l (B z = l, then Gamma^t lhat = z)
@@ -1611,6 +1811,17 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   auto l2p = [&](double* fout) -> eifmm_status {
     if (T.n_nonempty == 0) return EIFMM_OK;
     const unsigned nl = (unsigned)T.n_nonempty;
+    if (!fout && !p2p_sym && kern == EIFMM_KERNEL_INV_R && R == 1 && vl.dp <= 2 * PT_MAXQ) {
+      const unsigned g = (unsigned)((T.n_nonempty + PT_WARPS - 1) / PT_WARPS);
+      if (acc)
+        k_l2p32x<true><<<g, 32 * PT_WARPS, 0, s>>>(T.nonempty, T.n_nonempty, T.leaf_off, T.lx, T.ly, T.lz,
+                                                   vl.X32, vl.d, vl.dp, ws.lh32, ws.ffar);
+      else
+        k_l2p32x<false><<<g, 32 * PT_WARPS, 0, s>>>(T.nonempty, T.n_nonempty, T.leaf_off, T.lx, T.ly, T.lz,
+                                                    vl.X32, vl.d, vl.dp, ws.lh32, ws.ffar);
+      EIFMM_CHECK_LAUNCH();
+      return EIFMM_OK;
+    }
     const int rct = R == 1 ? 1 : RC;
     const size_t sm = (size_t)vl.d * sizeof(float4) + (size_t)((rct > 1 ? rct * vl.d : 0) + rct * TPB) * sizeof(float);
 #define EIFMM_L2P(K, RC_, A)                                                                     \

@@ -68,6 +68,8 @@ struct LevelOps {
   double* l2l = nullptr;   // [8][m' < d][q' < d_{k-1}]: K_L2L^i row-major
   float* m2m32 = nullptr;
   float* l2l32 = nullptr;
+  float* m2m_cb = nullptr;  // [K_M2M^0 .. K_M2M^7] col-major dp x 8 dp_child, zero-padded (library GEMM)
+  float* l2l_cb = nullptr;  // [K_L2L^0; ..; K_L2L^7] col-major 8 dp x dp_parent, zero-padded
   // Delta and Delta^t as tiled triangular solves (solve.cuh): tiles [0]
   // Gamma, [1] B^t reversed, [2] B, [3] Gamma^t reversed; pivots [0] of
   // Gamma, [1] of Gamma^t reversed (FP64: the pivots, FP32: reciprocals)
@@ -166,6 +168,7 @@ struct Workspace {
   // offset-group count (groups << shift, or >> -shift)
   int m2l_kind[kMaxLevel + 1] = {};
   int m2l_gshift[kMaxLevel + 1] = {};
+  int p2p_sym = 0;  // near-field kernel chosen by eifmm_autotune: 1 pair-symmetric
   size_t m2l_part_cap = 0;  // floats in m2l_part (levels below the leaves)
   float* m2l_part_leaf = nullptr;  // partial sums of the leaf level
   size_t m2l_part_leaf_cap = 0;
@@ -233,6 +236,10 @@ eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R,
 enum PlaneFmt { kPlaneBF16 = 0, kPlaneTF32 = 1, kPlaneF16 = 2 };
 eifmm_status build_kd_image(Ops* ops, int fmt, cudaStream_t s);
 eifmm_status build_kd32(Ops* ops, cudaStream_t s);
+// M2M / L2L of one right-hand side as library GEMMs (xfer_blas.cu)
+eifmm_status build_xfer_blas(Ops* ops, cudaStream_t s);
+bool xfer_blas(bool m2m, const LevelOps& out, const LevelOps& in, int64_t n_par, const float* B, const float* G,
+               float* C, cudaStream_t s);
 // M2L compression (sarcmp.cu): eps <= 0 removes it.
 eifmm_status compress_ops(Ops* ops, double eps, cudaStream_t s);
 void free_compression(LevelOps& v);

@@ -1020,12 +1020,16 @@ k_m2l_t256s(const __grid_constant__ CUtensorMap tW0, const __grid_constant__ CUt
 
 // The split tiles of the stream-K M2L: tile fix_t[i] is the sum, in CTA
 // order, of the partial slots fix_slot[fix_b[i] .. fix_b[i + 1]) (none: a
-// tile without active offsets, g = 0).  One block per split tile, thread n
-// = tile row n.
+// tile without active offsets, g = 0).  Block (i, y) takes rows 32 y .. 32 y
+// + 31 of split tile i: warp w rows 32 y + 4 w .. + 3, lane j the 16-byte
+// word j of each row, so that every read of a partial row and every write of
+// g is one coalesced 512-byte access, with the four rows' reads in flight
+// together.
+constexpr int kSkFixRowsPerWarp = 4;
 __global__ void __launch_bounds__(256)
 k_sk_fixup(M2LTcArgs a, SkPlan sk, const int* __restrict__ fix_t, const int* __restrict__ fix_b,
            const int* __restrict__ fix_slot) {
-  const int i = blockIdx.x, n = threadIdx.x;
+  const int i = blockIdx.x, w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t = fix_t[i];
   const int h = a.h, R = a.R, bxr = a.bx * R;
   const int ntx = (h * R + bxr - 1) / bxr, nty = (h + a.by - 1) / a.by;
@@ -1034,23 +1038,35 @@ k_sk_fixup(M2LTcArgs a, SkPlan sk, const int* __restrict__ fix_t, const int* __r
   const int tx = tile % ntx;
   tile /= ntx;
   const int ty = tile % nty, tz = tile / nty;
-  const int xr = tx * bxr + n % bxr;
-  const int yy = ty * a.by + (n / bxr) % a.by;
-  const int zz = tz * a.bz + n / (bxr * a.by);
-  if (!(xr < h * R && yy < h && zz < h)) return;
-  const int x = xr / R, r = xr % R;
-  const int64_t row = morton_encode(2 * x + (oct & 1), 2 * yy + ((oct >> 1) & 1), 2 * zz + ((oct >> 2) & 1), a.level) * R + r;
-  float4* out = reinterpret_cast<float4*>(a.g + row * a.dp);
-  for (int j = 0; j < 32; ++j) {
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int k = fix_b[i]; k < fix_b[i + 1]; ++k) {
-      const float4 p = reinterpret_cast<const float4*>(sk.part + ((size_t)fix_slot[k] * kT2Rows + n) * 128)[j];
-      v.x += p.x;
-      v.y += p.y;
-      v.z += p.z;
-      v.w += p.w;
+  const int kb = fix_b[i], ke = fix_b[i + 1];
+  const int n0 = 32 * (int)blockIdx.y + kSkFixRowsPerWarp * w;
+  float4 v[kSkFixRowsPerWarp];
+#pragma unroll
+  for (int u = 0; u < kSkFixRowsPerWarp; ++u) v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int k = kb; k < ke; ++k) {
+    const float4* __restrict__ src = reinterpret_cast<const float4*>(sk.part + ((size_t)fix_slot[k] * kT2Rows + n0) * 128);
+    float4 p[kSkFixRowsPerWarp];
+#pragma unroll
+    for (int u = 0; u < kSkFixRowsPerWarp; ++u) p[u] = src[u * 32 + lane];
+#pragma unroll
+    for (int u = 0; u < kSkFixRowsPerWarp; ++u) {
+      v[u].x += p[u].x;
+      v[u].y += p[u].y;
+      v[u].z += p[u].z;
+      v[u].w += p[u].w;
     }
-    out[j] = v;
+  }
+#pragma unroll
+  for (int u = 0; u < kSkFixRowsPerWarp; ++u) {
+    const int n = n0 + u;
+    const int xr = tx * bxr + n % bxr;
+    const int yy = ty * a.by + (n / bxr) % a.by;
+    const int zz = tz * a.bz + n / (bxr * a.by);
+    if (!(xr < h * R && yy < h && zz < h)) continue;
+    const int x = xr / R, r = xr % R;
+    const int64_t row =
+        morton_encode(2 * x + (oct & 1), 2 * yy + ((oct >> 1) & 1), 2 * zz + ((oct >> 2) & 1), a.level) * R + r;
+    reinterpret_cast<float4*>(a.g + row * a.dp)[lane] = v[u];
   }
 }
 
@@ -1677,7 +1693,8 @@ eifmm_status launch_m2l_t256s(const M2LTcArgs& a0, const void* map0, const void*
   k_m2l_t256s<false><<<(unsigned)p.nctas, kT2Threads, sm, s>>>(m0, m1, a, sk);
   EIFMM_CHECK_LAUNCH();
   if (p.nfix > 0) {
-    k_sk_fixup<<<(unsigned)p.nfix, 256, 0, s>>>(a, sk, p.fix_t, p.fix_b, p.fix_slot);
+    static_assert(kT2Rows == 32 * 8, "fix-up grid: 8 row groups of 32 rows");
+    k_sk_fixup<<<dim3((unsigned)p.nfix, kT2Rows / 32), 256, 0, s>>>(a, sk, p.fix_t, p.fix_b, p.fix_slot);
     EIFMM_CHECK_LAUNCH();
   }
   return EIFMM_OK;

@@ -257,6 +257,7 @@ eifmm_status assemble_ops(Ops* ops, cudaStream_t s) {
           lists[c * kListLen + n++] = (dx + 3) + 7 * (dy + 3) + 49 * (dz + 3);
         }
   }
+  EIFMM_TRY(build_xfer_blas(ops, s));
   EIFMM_TRY(dalloc(&ops->d_slot_lists, lists.size()));
   EIFMM_CUDA(cudaMemcpyAsync(ops->d_slot_lists, lists.data(), lists.size() * sizeof(int),
                              cudaMemcpyHostToDevice, s));
@@ -270,7 +271,7 @@ void free_ops(Ops* ops) {
     LevelOps& v = ops->lv[k];
     dfree(v.X); dfree(v.Y); dfree(v.G_rm); dfree(v.B_rm);
     dfree(v.m2mT); dfree(v.l2lT); dfree(v.kdT); dfree(v.m2mT32); dfree(v.l2lT32);
-    dfree(v.m2m); dfree(v.l2l); dfree(v.m2m32); dfree(v.l2l32);
+    dfree(v.m2m); dfree(v.l2l); dfree(v.m2m32); dfree(v.l2l32); dfree(v.m2m_cb); dfree(v.l2l_cb);
     for (int o = 0; o < 4; ++o) { dfree(v.dt64[o]); dfree(v.dt32[o]); }
     for (int o = 0; o < 2; ++o) { dfree(v.piv64[o]); dfree(v.piv32[o]); }
     dfree(v.X32);

@@ -5,16 +5,19 @@
 //   Delta v   : Gamma z = v (lower, forward), B^t w = z (upper, backward)
 //   Delta^t v : B z = v (lower, forward),     Gamma^t w = z (upper, backward)
 //
-// Both solves of one application run in one kernel.  A warp owns 32 vectors,
-// one per lane, kept transposed in shared memory ([entry][lane], row stride
-// 33 so both the transposing copy and the lane-wise access are free of bank
-// conflicts).  Each solve walks 32-row blocks (blocked left-looking
-// substitution): the block's 32 entries of the lane's vector sit in
-// registers, every earlier block contributes a dense 32 x 32 tile product
-// (32 FMAs per lane for each solved entry read back from shared memory), and
-// the diagonal 32 x 32 block is solved in registers.  The tile entries are
-// warp-uniform broadcast loads, so there is no synchronisation inside a
-// solve: the cost is the d^2/2 FMAs per vector and solve.
+// Both solves of one application run in one kernel.  A warp owns 16 vectors,
+// two lanes per vector, kept transposed in shared memory ([entry][vector],
+// row stride 17 so both the transposing copy and the lane-wise access are
+// free of bank conflicts).  Each solve walks 32-row blocks (blocked
+// left-looking substitution): lane half h holds rows 16h .. 16h+15 of the
+// block in registers, every earlier block contributes a dense 32 x 32 tile
+// product (16 FMAs per lane for each solved entry read back from shared
+// memory), and the diagonal 32 x 32 block is solved in registers, each
+// solved entry passed to the other half by a shuffle.  The tile entries are
+// broadcast loads, so there is no synchronisation inside a solve: the cost
+// is the d^2/2 FMAs per vector and solve, spread over twice as many warps as
+// with one lane per vector (a single wave of CTAs then holds 16 warps per SM
+// instead of 8, and the latency of the shared loads is hidden).
 //
 // The backward (upper) solve is run as a forward solve in reversed entry
 // order: with p(a) = dpad-1-a, U w = z becomes L' w' = z' with
@@ -28,8 +31,11 @@
 namespace eifmm {
 
 constexpr int kDeltaTile = 32;
-constexpr int kDeltaLd = 33;       // shared row stride (floats or doubles)
-constexpr int kDeltaMaxWarps = 4;  // warps per CTA
+constexpr int kDeltaLpv = 2;                    // lanes per vector
+constexpr int kDeltaVpw = 32 / kDeltaLpv;       // vectors per warp
+constexpr int kDeltaRl = kDeltaTile / kDeltaLpv;  // rows of a block per lane
+constexpr int kDeltaLd = kDeltaVpw + 1;         // shared row stride (floats or doubles)
+constexpr int kDeltaMaxWarps = 8;               // warps per CTA
 
 // Tiles of one solve: tile (J, K), K <= J, at (J(J+1)/2 + K) * 1024, entry
 // [k][i] = L'[32J + i][32K + k]; the diagonal tiles are zero above the
@@ -59,13 +65,14 @@ __device__ __forceinline__ int64_t plane_row(int64_t v, int grid_level, int R) {
   return ((((int64_t)cls * h + (c[2] >> 1)) * h + (c[1] >> 1)) * h + (c[0] >> 1)) * R + r;
 }
 
-// acc[i] -= col[i] * z for the 32 rows of one tile column (16-byte loads of
-// a warp-uniform address: shared memory when SH, else global through L1).
+// acc[i] -= col[i] * z for the lane's rows of one tile column (16-byte
+// loads of a half-warp-uniform address: shared memory when SH, else global
+// through L1).
 template <bool SH>
-__device__ __forceinline__ void tile_col_update(float (&acc)[kDeltaTile], const float* __restrict__ col,
+__device__ __forceinline__ void tile_col_update(float (&acc)[kDeltaRl], const float* __restrict__ col,
                                                 float z) {
 #pragma unroll
-  for (int q = 0; q < kDeltaTile / 4; ++q) {
+  for (int q = 0; q < kDeltaRl / 4; ++q) {
     const float4 m = SH ? reinterpret_cast<const float4*>(col)[q] : __ldg(reinterpret_cast<const float4*>(col) + q);
     acc[4 * q + 0] -= m.x * z;
     acc[4 * q + 1] -= m.y * z;
@@ -74,10 +81,10 @@ __device__ __forceinline__ void tile_col_update(float (&acc)[kDeltaTile], const 
   }
 }
 template <bool SH>
-__device__ __forceinline__ void tile_col_update(double (&acc)[kDeltaTile], const double* __restrict__ col,
+__device__ __forceinline__ void tile_col_update(double (&acc)[kDeltaRl], const double* __restrict__ col,
                                                 double z) {
 #pragma unroll
-  for (int q = 0; q < kDeltaTile / 2; ++q) {
+  for (int q = 0; q < kDeltaRl / 2; ++q) {
     const double2 m =
         SH ? reinterpret_cast<const double2*>(col)[q] : __ldg(reinterpret_cast<const double2*>(col) + q);
     acc[2 * q + 0] -= m.x * z;
@@ -93,22 +100,27 @@ __device__ __forceinline__ T tile_ld(const T* p) {
 __device__ __forceinline__ float apply_pivot(float v, float rp) { return v * rp; }
 __device__ __forceinline__ double apply_pivot(double v, double p) { return v / p; }
 
-// One forward solve L' x = v over the warp's 32 vectors held in sz (physical
-// entry e of lane l at sz[e * 33 + l]); REV maps logical entry a to physical
-// dpad-1-a.  The solution overwrites sz.
+// One forward solve L' x = v over the warp's kDeltaVpw vectors held in sz
+// (physical entry e of vector c at sz[e * kDeltaLd + c]); lane = c + kDeltaVpw h
+// works on rows kDeltaRl h .. of every block.  REV maps logical entry a to
+// physical dpad-1-a.  The solution overwrites sz.
 template <typename T, bool DIAG, bool REV, bool SH>
 __device__ __forceinline__ void tiled_solve(T* __restrict__ sz, int nb, const T* __restrict__ tiles,
                                             const T* __restrict__ piv, int lane) {
-  constexpr int TL = kDeltaTile;
+  constexpr int TL = kDeltaTile, RL = kDeltaRl;
+  const int c = lane % kDeltaVpw, h = lane / kDeltaVpw;
   for (int J = 0; J < nb; ++J) {
     const int pj = REV ? nb - 1 - J : J;
-    T acc[TL];
+    T acc[RL];
 #pragma unroll
-    for (int i = 0; i < TL; ++i) acc[i] = sz[(pj * TL + (REV ? TL - 1 - i : i)) * kDeltaLd + lane];
+    for (int i = 0; i < RL; ++i) {
+      const int row = h * RL + i;
+      acc[i] = sz[(pj * TL + (REV ? TL - 1 - row : row)) * kDeltaLd + c];
+    }
     const T* tJ = tiles + (int64_t)(J * (J + 1) / 2) * TL * TL;
     for (int K = 0; K < J; ++K) {
-      const T* tk = tJ + (int64_t)K * TL * TL;
-      const T* zK = sz + (REV ? (nb - 1 - K) * TL + TL - 1 : K * TL) * kDeltaLd + lane;
+      const T* tk = tJ + (int64_t)K * TL * TL + h * RL;
+      const T* zK = sz + (REV ? (nb - 1 - K) * TL + TL - 1 : K * TL) * kDeltaLd + c;
 #pragma unroll
       for (int k = 0; k < TL; ++k) {
         const T zk = zK[(REV ? -k : k) * kDeltaLd];
@@ -118,13 +130,20 @@ __device__ __forceinline__ void tiled_solve(T* __restrict__ sz, int nb, const T*
     const T* td = tJ + (int64_t)J * TL * TL;
 #pragma unroll
     for (int k = 0; k < TL; ++k) {
-      const T zk = DIAG ? apply_pivot(acc[k], __ldg(piv + J * TL + k)) : acc[k];
-      acc[k] = zk;
+      const int owner = k / RL;  // the half that holds entry k
+      T mine = acc[k % RL];
+      if (DIAG && h == owner) mine = apply_pivot(mine, __ldg(piv + J * TL + k));
+      const T zk = kDeltaLpv == 1 ? mine : __shfl_sync(0xffffffffu, mine, c + owner * kDeltaVpw);
+      if (h == owner) acc[k % RL] = zk;
 #pragma unroll
-      for (int i = k + 1; i < TL; ++i) acc[i] -= tile_ld<SH>(td + k * TL + i) * zk;
+      for (int i = 0; i < RL; ++i)
+        if (h * RL + i > k) acc[i] -= tile_ld<SH>(td + k * TL + h * RL + i) * zk;
     }
 #pragma unroll
-    for (int i = 0; i < TL; ++i) sz[(pj * TL + (REV ? TL - 1 - i : i)) * kDeltaLd + lane] = acc[i];
+    for (int i = 0; i < RL; ++i) {
+      const int row = h * RL + i;
+      sz[(pj * TL + (REV ? TL - 1 - row : row)) * kDeltaLd + c] = acc[i];
+    }
   }
 }
 
@@ -170,17 +189,24 @@ k_delta(const __grid_constant__ DeltaBatch b) {
   const int64_t tile_elems = (int64_t)nb * (nb + 1) / 2 * kDeltaTile * kDeltaTile;
   T* s_tiles = reinterpret_cast<T*>(s_raw);
   T* sz = s_tiles + (SH ? tile_elems : 0) + (int64_t)w * dpad * kDeltaLd;
-  const int64_t v0 = ((int64_t)(blockIdx.x - L.block0) * (blockDim.x >> 5) + w) * 32;
+  const int64_t v0 = ((int64_t)(blockIdx.x - L.block0) * (blockDim.x >> 5) + w) * kDeltaVpw;
   const int64_t nvec = L.nvec;
   const bool live = v0 < nvec;
-  const Ti* in = (const Ti*)L.in;
+  const Ti* __restrict__ in = (const Ti*)L.in;
   if (live) {
-    // transposing load: row v0+vv -> column vv
-    for (int vv = 0; vv < 32; ++vv) {
-      const int64_t v = v0 + vv;
-      const Ti* row = in + v * L.ldi;
-      for (int j = lane; j < dpad; j += 32)
-        sz[j * kDeltaLd + vv] = (v < nvec && j < d) ? (T)row[j] : (T)0;
+    // transposing load: row v0+vv -> column vv (four rows' loads in flight
+    // before their shared stores)
+    for (int vv0 = 0; vv0 < kDeltaVpw; vv0 += 4) {
+      for (int j = lane; j < dpad; j += 32) {
+        T x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int64_t v = v0 + vv0 + u;
+          x[u] = (v < nvec && j < d) ? (T)__ldg(in + v * L.ldi + j) : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) sz[j * kDeltaLd + vv0 + u] = x[u];
+      }
     }
   }
   const T* t1 = (const T*)L.t1;
@@ -204,7 +230,7 @@ k_delta(const __grid_constant__ DeltaBatch b) {
   __syncwarp();
   To* out = (To*)L.out;
   const int ldo = L.ldo;
-  for (int vv = 0; vv < 32; ++vv) {
+  for (int vv = 0; vv < kDeltaVpw; ++vv) {
     const int64_t v = v0 + vv;
     if (v >= nvec) break;
     if (PLANES == 0) {
@@ -263,10 +289,13 @@ DeltaLevel delta_level(int d, const DeltaOps<T>& op, bool transpose, const void*
 
 template <auto KFN>
 eifmm_status delta_launch(const DeltaBatch& b, int blocks, int warps, size_t sm, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
+  constexpr int kDev = 64;
+  static bool attr[kDev] = {};  // the attribute is per device
+  int dev = 0;
+  EIFMM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kDev || !attr[dev]) {
     EIFMM_CUDA(cudaFuncSetAttribute(KFN, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    attr = true;
+    if (dev >= 0 && dev < kDev) attr[dev] = true;
   }
   KFN<<<(unsigned)blocks, 32 * warps, sm, s>>>(b);
   EIFMM_CHECK_LAUNCH();
@@ -293,7 +322,7 @@ eifmm_status launch_delta_batch(DeltaBatch& b, bool transpose, cudaStream_t s) {
   int blocks = 0;
   for (int i = 0; i < b.nlev; ++i) {
     b.lv[i].block0 = blocks;
-    const int64_t nw = (b.lv[i].nvec + 31) / 32;
+    const int64_t nw = (b.lv[i].nvec + kDeltaVpw - 1) / kDeltaVpw;
     blocks += (int)((nw + warps - 1) / warps);
   }
   if (blocks == 0) return EIFMM_OK;

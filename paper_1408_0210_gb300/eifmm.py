@@ -240,6 +240,7 @@ class Tree:
         self.n_src = n_src
         self.n_tgt = n_tgt
         self.depth = depth
+        self.p2p_pair_symmetric = None  # set by eifmm_autotune
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
@@ -366,10 +367,13 @@ M2L_VARIANTS = {0: "rule", 1: "transposed", 2: "128-row", 3: "transposed stream-
 
 def eifmm_autotune(tree: Tree, ops: Ops, n_rhs: int = 1, prec="mixed", stream=None) -> dict:
     """Time the M2L variants per level on this tree and keep the fastest;
-    returns {level: (variant, group shift)}."""
+    returns {level: (variant, group shift)}.  The near-field kernel chosen by
+    the same timing is left in tree.p2p_pair_symmetric (True when the
+    pair-symmetric near field was kept)."""
     ch = (C.c_int * 22)()
     _check(lib().eifmm_autotune(tree.handle, ops.handle, int(n_rhs), _prec(prec), _stream(stream),
                                 C.cast(ch, C.c_void_p)))
+    tree.p2p_pair_symmetric = bool(ch[0])
     return {k: (ch[2 * k], ch[2 * k + 1]) for k in range(2, tree.depth + 1)}
 
 

@@ -198,6 +198,7 @@ def test_autotune_keeps_the_result(E, orc):
     assert rel2(f1.cpu().numpy()[idx], f_exact) <= 1e-4
     # the FP64 path has no tensor-core M2L: nothing to tune
     assert all(v == (0, 0) for v in E.eifmm_autotune(tree, ops, 1, "fp64").values())
+    assert tree.p2p_pair_symmetric in (True, False)
 
 
 @pytest.mark.parametrize("eps,tol", [(1e-5, 1e-5), (1e-6, 1e-6), (1e-7, 1e-7)])
