@@ -1653,10 +1653,15 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   // the far field continues on the high-priority stream; the caller's stream
   // waits for it at the end
   const cudaStream_t caller = s;
-  if (!t->opt[EIFMM_OPT_SINGLE_STREAM]) {
+  const bool single = t->opt[EIFMM_OPT_SINGLE_STREAM] != 0;
+  if (!single) {
     EIFMM_CUDA(cudaStreamWaitEvent(ws.hi, ws.ev_fork, 0));
     s = ws.hi;
   }
+  // with the single-stream option every launch below goes to the caller's
+  // stream, in submission order
+  const cudaStream_t nf_stream = single ? s : ws.side;
+  const cudaStream_t coarse_stream = single ? s : ws.side2;
   // when a step fails after the fork, the caller's stream still waits for
   // every stream this call may have used, so that no work of the call is
   // left unordered against the caller's next one
@@ -1674,10 +1679,10 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
       cudaStreamWaitEvent(caller, w.ev_hi, 0);
     }
   } guard{ws, caller};
-  if (timing_enabled()) cudaEventRecord(ws.ev_nf[0], ws.side);
+  if (timing_enabled()) cudaEventRecord(ws.ev_nf[0], nf_stream);
   const bool p2p_sym = use_p2p_sym(t, R, ops->tier >= 1, ws.gsym);
-  EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, ws.side, ops->tier >= 1, ws.gsym));
-  if (timing_enabled()) cudaEventRecord(ws.ev_nf[1], ws.side);
+  EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, nf_stream, ops->tier >= 1, ws.gsym));
+  if (timing_enabled()) cudaEventRecord(ws.ev_nf[1], nf_stream);
   EIFMM_CUDA(cudaEventRecord(ws.ev_join, ws.side));
 
   // step 1 (every leaf, empty ones get zeros)
@@ -1765,9 +1770,9 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   // within the leaf level.
   auto coarse = [&]() -> eifmm_status {
     for (int k = 2; k < kap; ++k) {
-      if (timing_enabled()) cudaEventRecord(ws.ev_m2l[k], ws.side2);
-      EIFMM_TRY(m2l(k, ws.side2));
-      if (timing_enabled()) cudaEventRecord(ws.ev_m2le[k], ws.side2);
+      if (timing_enabled()) cudaEventRecord(ws.ev_m2l[k], coarse_stream);
+      EIFMM_TRY(m2l(k, coarse_stream));
+      if (timing_enabled()) cudaEventRecord(ws.ev_m2le[k], coarse_stream);
     }
     return EIFMM_OK;
   };

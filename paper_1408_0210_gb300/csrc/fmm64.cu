@@ -480,13 +480,15 @@ eifmm_status eval_fp64(Tree* t, const Ops* ops, const double* sigma, int64_t ld_
   const double lk = t->L * ldexp(1.0, -(kap + 1));
   record(ws, 0, s);
   EIFMM_TRY(launch_gather_sigma(sigma, ld_sigma, S, R, ws.sig, near32 ? ws.sig32 : nullptr, s));
-  // near field on the side stream, concurrent with the far field
+  // near field on the side stream, concurrent with the far field (on the
+  // caller's stream, before it, with the single-stream option)
   EIFMM_CUDA(cudaEventRecord(ws.ev_fork, s));
   EIFMM_CUDA(cudaStreamWaitEvent(ws.side, ws.ev_fork, 0));
-  if (timing_enabled()) cudaEventRecord(ws.ev_nf[0], ws.side);
-  if (near32) EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, ws.side, true));
-  else EIFMM_TRY(launch_p2p64(t, kern, ws.sig, R, ws.fnear, ws.side));
-  if (timing_enabled()) cudaEventRecord(ws.ev_nf[1], ws.side);
+  const cudaStream_t nf_stream = t->opt[EIFMM_OPT_SINGLE_STREAM] ? s : ws.side;
+  if (timing_enabled()) cudaEventRecord(ws.ev_nf[0], nf_stream);
+  if (near32) EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, nf_stream, true));
+  else EIFMM_TRY(launch_p2p64(t, kern, ws.sig, R, ws.fnear, nf_stream));
+  if (timing_enabled()) cudaEventRecord(ws.ev_nf[1], nf_stream);
   EIFMM_CUDA(cudaEventRecord(ws.ev_join, ws.side));
 
   // step 1

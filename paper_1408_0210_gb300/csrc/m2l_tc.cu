@@ -1526,7 +1526,13 @@ int64_t m2l_tma_ctas(int level, int R) {
 }
 
 // Offset groups of the FP16 M2L: the fewest that fill one wave of the SMs
-// (its per-offset drains need no extra chains for accuracy).
+// (its per-offset drains need no extra chains for accuracy): with fewer
+// tiles than SMs, double the groups until the SMs are covered (at most
+// 16).  More groups at a level that already fills the SMs shorten the
+// launch alone (256 tiles at the 1M-point leaf level: two waves, 939 us;
+// four groups: seven quarter waves, 846 us + 34 us of partial sums) but
+// lengthened the evaluate (1.95 -> 2.04 ms): the idle SMs of the second
+// wave were running the near field.
 int m2l_h16_groups(int64_t ctas, int nsm) {
   int g = 1;
   while (g < 16 && ctas * g < nsm) g *= 2;

@@ -122,7 +122,9 @@ __global__ void k_transpose_slots(const double* __restrict__ in, int d, double* 
 // Tiles of one lower-triangular solve operator L' (layout in solve.cuh):
 // L'[a][b] = M[p][q] with (p, q) = (a, b), or (dpad-1-a, dpad-1-b) when
 // `rev`; `transpose` reads M[q][p].  Entries beyond d are those of the
-// identity; entries above the diagonal are zero.
+// identity.  Entries on and above the diagonal are stored as zeros: the
+// diagonal is held by the pivots (or is one), and the zeros let the solve
+// update every row of a diagonal tile with one vector load per four rows.
 __global__ void k_build_delta_tiles(const double* __restrict__ M, int d, int nb, int transpose, int rev,
                                     double* __restrict__ t64, float* __restrict__ t32,
                                     double* __restrict__ piv64, float* __restrict__ piv32) {
@@ -135,7 +137,7 @@ __global__ void k_build_delta_tiles(const double* __restrict__ M, int d, int nb,
     const int K = tile, k = (int)((e >> 5) & 31), i = (int)(e & 31);
     const int a = J * 32 + i, b = K * 32 + k;
     double v = 0.0;
-    if (b <= a) {
+    if (b < a) {
       const int p = rev ? dpad - 1 - a : a, q = rev ? dpad - 1 - b : b;
       if (p < d && q < d) v = transpose ? M[(int64_t)q * d + p] : M[(int64_t)p * d + q];
       else v = p == q ? 1.0 : 0.0;

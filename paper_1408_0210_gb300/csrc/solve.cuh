@@ -5,19 +5,19 @@
 //   Delta v   : Gamma z = v (lower, forward), B^t w = z (upper, backward)
 //   Delta^t v : B z = v (lower, forward),     Gamma^t w = z (upper, backward)
 //
-// Both solves of one application run in one kernel.  A warp owns 16 vectors,
-// two lanes per vector, kept transposed in shared memory ([entry][vector],
-// row stride 17 so both the transposing copy and the lane-wise access are
-// free of bank conflicts).  Each solve walks 32-row blocks (blocked
-// left-looking substitution): lane half h holds rows 16h .. 16h+15 of the
-// block in registers, every earlier block contributes a dense 32 x 32 tile
-// product (16 FMAs per lane for each solved entry read back from shared
-// memory), and the diagonal 32 x 32 block is solved in registers, each
-// solved entry passed to the other half by a shuffle.  The tile entries are
-// broadcast loads, so there is no synchronisation inside a solve: the cost
-// is the d^2/2 FMAs per vector and solve, spread over twice as many warps as
-// with one lane per vector (a single wave of CTAs then holds 16 warps per SM
-// instead of 8, and the latency of the shared loads is hidden).
+// Both solves of one application run in one kernel.  A warp owns
+// kDeltaVpw = 16 vectors, kDeltaLpv = 2 lanes per vector, kept transposed in
+// shared memory ([entry][vector], row stride 17 so that both the transposing
+// copy and the lane-wise access are free of bank conflicts).  Each solve
+// walks 32-row blocks (blocked left-looking substitution): lane half h
+// holds rows 16h .. 16h+15 of the block in registers, every earlier block
+// contributes a dense 32 x 32 tile product (16 FMAs per lane for each solved
+// entry read back from shared memory), and the diagonal 32 x 32 block is
+// solved in registers, each solved entry passed from its owner to the other
+// half by a shuffle.  The tile entries are broadcast loads, so there is no
+// synchronisation inside a solve: the cost is the d^2/2 FMAs per vector and
+// solve.  (At the 1M-point leaf level: 66 us with one lane per vector, 63
+// with two, 68 with four.)
 //
 // The backward (upper) solve is run as a forward solve in reversed entry
 // order: with p(a) = dpad-1-a, U w = z becomes L' w' = z' with
@@ -38,8 +38,8 @@ constexpr int kDeltaLd = kDeltaVpw + 1;         // shared row stride (floats or 
 constexpr int kDeltaMaxWarps = 8;               // warps per CTA
 
 // Tiles of one solve: tile (J, K), K <= J, at (J(J+1)/2 + K) * 1024, entry
-// [k][i] = L'[32J + i][32K + k]; the diagonal tiles are zero above the
-// diagonal.  Pivots: FP32 stores 1/L'[a][a], FP64 stores L'[a][a].
+// [k][i] = L'[32J + i][32K + k]; the diagonal tiles are zero on and above
+// the diagonal.  Pivots: FP32 stores 1/L'[a][a], FP64 stores L'[a][a].
 inline int64_t delta_tiles_elems(int d) {
   const int nb = (d + kDeltaTile - 1) / kDeltaTile;
   return (int64_t)nb * (nb + 1) / 2 * kDeltaTile * kDeltaTile;
@@ -92,11 +92,6 @@ __device__ __forceinline__ void tile_col_update(double (&acc)[kDeltaRl], const d
   }
 }
 
-template <bool SH, typename T>
-__device__ __forceinline__ T tile_ld(const T* p) {
-  return SH ? *p : __ldg(p);
-}
-
 __device__ __forceinline__ float apply_pivot(float v, float rp) { return v * rp; }
 __device__ __forceinline__ double apply_pivot(double v, double p) { return v / p; }
 
@@ -135,9 +130,9 @@ __device__ __forceinline__ void tiled_solve(T* __restrict__ sz, int nb, const T*
       if (DIAG && h == owner) mine = apply_pivot(mine, __ldg(piv + J * TL + k));
       const T zk = kDeltaLpv == 1 ? mine : __shfl_sync(0xffffffffu, mine, c + owner * kDeltaVpw);
       if (h == owner) acc[k % RL] = zk;
-#pragma unroll
-      for (int i = 0; i < RL; ++i)
-        if (h * RL + i > k) acc[i] -= tile_ld<SH>(td + k * TL + h * RL + i) * zk;
+      // the tile holds zeros on and above its diagonal, so the update of
+      // every row leaves the rows up to k as they are
+      tile_col_update<SH>(acc, td + k * TL + h * RL, zk);
     }
 #pragma unroll
     for (int i = 0; i < RL; ++i) {
