@@ -262,8 +262,14 @@ void eifmm_tree_destroy(eifmm_tree* tree);
  *     and 4;
  *   M2L_STREAM_K: 1 runs the leaf-level transposed M2L as one CTA per SM
  *     over equal shares of the (tile, offset) work, split tiles added by a
- *     fix-up kernel, instead of one CTA per tile (measured slower at 2^20
- *     points: 384 against 369 us).
+ *     fix-up kernel, instead of one CTA per tile (at 2^20 points the launch
+ *     is 2% shorter, but the evaluate slower: it holds every SM, so the
+ *     near field cannot run beside it);
+ *   NEAR_FIELD_LATE: 1 starts the mixed path's near field when the M2L
+ *     starts (after the plane split of step 3) instead of with the far
+ *     field, so that steps 1-3 run alone (at 2^20 points steps 1-3 take
+ *     0.15 instead of 0.23 ms, but the near field then ends after the far
+ *     field: 1.087 against 1.043 ms per evaluate).
  * The option holds for later evaluations of this tree.  Errors: EINVAL
  * (null tree, unknown option, value other than 0 or 1). */
 typedef enum {
@@ -271,7 +277,8 @@ typedef enum {
   EIFMM_OPT_P2P_PAIR_SYMMETRIC = 1,
   EIFMM_OPT_SINGLE_STREAM = 2,
   EIFMM_OPT_M2L_FP64 = 3,
-  EIFMM_OPT_M2L_STREAM_K = 4
+  EIFMM_OPT_M2L_STREAM_K = 4,
+  EIFMM_OPT_NEAR_FIELD_LATE = 5
 } eifmm_option;
 eifmm_status eifmm_tree_set_option(eifmm_tree* tree, eifmm_option opt, int value);
 

@@ -1679,11 +1679,18 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
       cudaStreamWaitEvent(caller, w.ev_hi, 0);
     }
   } guard{ws, caller};
-  if (timing_enabled()) cudaEventRecord(ws.ev_nf[0], nf_stream);
   const bool p2p_sym = use_p2p_sym(t, R, ops->tier >= 1, ws.gsym);
-  EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, nf_stream, ops->tier >= 1, ws.gsym));
-  if (timing_enabled()) cudaEventRecord(ws.ev_nf[1], nf_stream);
-  EIFMM_CUDA(cudaEventRecord(ws.ev_join, ws.side));
+  auto near_field = [&]() -> eifmm_status {
+    if (timing_enabled()) cudaEventRecord(ws.ev_nf[0], nf_stream);
+    EIFMM_TRY(launch_p2p32(t, kern, ws.sig32, R, ws.fnear, nf_stream, ops->tier >= 1, ws.gsym));
+    if (timing_enabled()) cudaEventRecord(ws.ev_nf[1], nf_stream);
+    EIFMM_CUDA(cudaEventRecord(ws.ev_join, ws.side));
+    return EIFMM_OK;
+  };
+  // by default the near field starts with the far field; with the option
+  // NEAR_FIELD_LATE it starts with the M2L (step 4 below)
+  const bool nf_late = !single && t->opt[EIFMM_OPT_NEAR_FIELD_LATE];
+  if (!nf_late) EIFMM_TRY(near_field());
 
   // step 1 (every leaf, empty ones get zeros)
   const LevelOps& vl = ops->lv[kap];
@@ -1757,9 +1764,11 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   // step 4: the levels are independent.  The coarse levels run on a second
   // stream while the leaf level runs here, so their small grids fill the
   // SMs the leaf level leaves free; each side has its own partial sums.
-  if (kap > 2) {
-    EIFMM_CUDA(cudaEventRecord(ws.ev_fork2, s));
-    EIFMM_CUDA(cudaStreamWaitEvent(ws.side2, ws.ev_fork2, 0));
+  EIFMM_CUDA(cudaEventRecord(ws.ev_fork2, s));
+  if (kap > 2) EIFMM_CUDA(cudaStreamWaitEvent(ws.side2, ws.ev_fork2, 0));
+  if (nf_late) {
+    EIFMM_CUDA(cudaStreamWaitEvent(ws.side, ws.ev_fork2, 0));
+    EIFMM_TRY(near_field());
   }
   auto m2l = [&](int k, cudaStream_t st) {
     return simt ? launch_m2l_simt(t, ops, k, R, st)

@@ -205,7 +205,7 @@ struct Workspace {
   float step_ms[20] = {};
 };
 
-constexpr int kNumOptions = 5;  // eifmm_option
+constexpr int kNumOptions = 6;  // eifmm_option
 
 struct Tree {
   int depth = 0;

@@ -30,7 +30,7 @@ EXPORTS = [
     "eifmm_wait_selftest",
 ]
 OPTIONS = {"m2l_128row": 0, "p2p_pair_symmetric": 1, "single_stream": 2, "m2l_fp64": 3,
-           "m2l_stream_k": 4}
+           "m2l_stream_k": 4, "near_field_late": 5}
 
 
 class EifmmError(RuntimeError):
