@@ -429,8 +429,8 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
 // per non-empty target leaf.  The sources of the 27 neighbour leaves are
 // staged in shared memory in chunks of NF_SRC, in the frame of the target
 // leaf, as SoA pairs:
-//   pair q: ulonglong2 [2q] = (x_2q, x_2q+1 | y_2q, y_2q+1),
-//           ulonglong2 [2q + 1] = (z_2q, z_2q+1 | sigma_2q, sigma_2q+1),
+//   pair q: float4 [2q] = (x_2q, x_2q+1 | y_2q, y_2q+1),
+//           float4 [2q + 1] = (z_2q, z_2q+1 | sigma_2q, sigma_2q+1),
 // the 26 other leaves first, then the leaf itself from the next even
 // position; a pad source (far away, sigma = 0, an exact zero) fills an odd
 // end.  Threads = (target t, slice s), thread = t + P s: P targets of the
@@ -438,7 +438,7 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
 // the passes take 128 targets while that many remain, else 32 while more
 // than 32 remain, then the rest, so that the lanes stay busy.  Per pair of
 // sources the distance is 3 packed differences and 3 packed multiply-adds
-// (sub/mul/fma.rn.f32x2, operands straight from the shared loads); 1/r is
+// (add/mul/fma.rn.f32x2, operands straight from the shared loads); 1/r is
 // the approximate reciprocal square root on each half, with a Newton step
 // and Kahan sums when ACC.  Each half keeps its own FP32 sum over the slice
 // (at most 256 pairs) before a compensated flush.  Only the pairs of the leaf
@@ -450,30 +450,25 @@ constexpr int NF_THREADS = 128;
 constexpr int NF_SRC = 1024;               // sources per chunk
 constexpr int NF_MAXS = 32;                // slices per pass
 constexpr float NF_FAR = 1.0e4f;
-constexpr size_t NF_SMEM = NF_SRC * sizeof(ulonglong2);  // NF_SRC / 2 pairs of 32 bytes
+constexpr size_t NF_SMEM = NF_SRC * sizeof(float4);  // NF_SRC / 2 pairs of 32 bytes
 
-__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void up2(uint64_t v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
+// Packed FP32 pairs are float2 values handled by the sm_100 builtins
+// __fadd2_rn / __fmul2_rn / __ffma2_rn (the f32x2 add, mul, fma): the halves
+// stay ordinary registers, so no moves split or join 64-bit values.  A
+// difference a - b is formed as a + (-b) (the same IEEE result), with -b
+// negated once outside the loops.
 
-// r2 of the staged pair e[0..1] against the target (X, Y, Z) (packed), and
-// the pair's sigma.
-__device__ __forceinline__ void nf_r2(const ulonglong2* e, uint64_t X, uint64_t Y, uint64_t Z, uint64_t& r2,
-                                      uint64_t& sg) {
-  const ulonglong2 v0 = e[0], v1 = e[1];
-  sg = v1.y;
-  uint64_t dx, dy, dz;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(v0.x), "l"(X));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(v0.y), "l"(Y));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(v1.x), "l"(Z));
-  asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(r2) : "l"(dx));
-  asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(r2) : "l"(dy));
-  asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(r2) : "l"(dz));
+// r2 of the staged pair e[0..1] against the target, given negated as
+// (NX, NX), (NY, NY), (NZ, NZ); and the pair's sigma.
+__device__ __forceinline__ float2 nf_r2(const float4* e, float2 NX, float2 NY, float2 NZ, float2& sg) {
+  const float4 v0 = e[0], v1 = e[1];
+  sg = make_float2(v1.z, v1.w);
+  const float2 dx = __fadd2_rn(make_float2(v0.x, v0.y), NX);
+  const float2 dy = __fadd2_rn(make_float2(v0.z, v0.w), NY);
+  const float2 dz = __fadd2_rn(make_float2(v1.x, v1.y), NZ);
+  float2 r2 = __fmul2_rn(dx, dx);
+  r2 = __ffma2_rn(dy, dy, r2);
+  return __ffma2_rn(dz, dz, r2);
 }
 
 // sum (+)= sigma / r for one half.
@@ -491,21 +486,18 @@ __device__ __forceinline__ void nf_term(float r2, float sg, float& sa, float& ca
 // Pairs [qa, qe) of the staged list; SELF: pair qs, half hs is the target
 // itself.
 template <bool ACC, bool SELF>
-__device__ __forceinline__ void nf_span(const ulonglong2* s_pair, int qa, int qe, int qs, int hs, uint64_t X,
-                                        uint64_t Y, uint64_t Z, float& sl, float& sh, float& cl, float& ch) {
+__device__ __forceinline__ void nf_span(const float4* s_pair, int qa, int qe, int qs, int hs, float2 NX,
+                                        float2 NY, float2 NZ, float& sl, float& sh, float& cl, float& ch) {
 #pragma unroll 8
   for (int q = qa; q < qe; ++q) {
-    uint64_t r2, sg;
-    nf_r2(s_pair + 2 * q, X, Y, Z, r2, sg);
-    float rl, rh, gl, gh;
-    up2(r2, rl, rh);
-    up2(sg, gl, gh);
+    float2 sg;
+    float2 r2 = nf_r2(s_pair + 2 * q, NX, NY, NZ, sg);
     if (SELF && q == qs) {  // the self pair: sigma 0 at distance 1
-      if (hs) rh = 1.f, gh = 0.f;
-      else rl = 1.f, gl = 0.f;
+      if (hs) r2.y = 1.f, sg.y = 0.f;
+      else r2.x = 1.f, sg.x = 0.f;
     }
-    nf_term<ACC>(rl, gl, sl, cl);
-    nf_term<ACC>(rh, gh, sh, ch);
+    nf_term<ACC>(r2.x, sg.x, sl, cl);
+    nf_term<ACC>(r2.y, sg.y, sh, ch);
   }
 }
 
@@ -515,7 +507,7 @@ k_p2p32x(const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff, c
          const float* __restrict__ tly, const float* __restrict__ tlz, const int32_t* __restrict__ soff,
          const float* __restrict__ slx, const float* __restrict__ sly, const float* __restrict__ slz,
          const float* __restrict__ sig, int depth, float two_l, int exclude_self, double* __restrict__ fnear) {
-  extern __shared__ __align__(16) ulonglong2 s_pair[];  // [NF_SRC]: NF_SRC / 2 pairs
+  extern __shared__ __align__(16) float4 s_pair[];  // [NF_SRC]: NF_SRC / 2 pairs
   __shared__ double s_red[NF_THREADS];
   __shared__ int s_pos[28];  // logical start of each segment, then the end
   __shared__ int s_len[27];
@@ -571,7 +563,7 @@ k_p2p32x(const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff, c
     const bool act = si < S;
     const int p = t0 + (act ? ti : 0);
     const float x0 = tlx[p], x1 = tly[p], x2 = tlz[p];
-    const uint64_t X = pk2(x0, x0), Y = pk2(x1, x1), Z = pk2(x2, x2);
+    const float2 NX = make_float2(-x0, -x0), NY = make_float2(-x1, -x1), NZ = make_float2(-x2, -x2);
     const int js = exclude_self ? n_other + (p - beg) : -1;  // logical position of the self pair
     float th0 = 0.f, tc0 = 0.f, th1 = 0.f, tc1 = 0.f;      // tier 0: FP32 Kahan totals per half
     double td = 0.0;                                       // ACC: FP64 total
@@ -616,8 +608,9 @@ k_p2p32x(const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff, c
         const int qs = js - c0 >= 0 && js - c0 < cn ? (js - c0) >> 1 : -1, hs = (js - c0) & 1;
         const int qm = qs < 0 ? qe : max(qb, min(qe, qown));
         float sl = 0.f, sh = 0.f, cl = 0.f, ch = 0.f;
-        nf_span<ACC, false>(s_pair, qb, qm, -1, 0, X, Y, Z, sl, sh, cl, ch);
-        nf_span<ACC, true>(s_pair, qm, qe, qs, hs, X, Y, Z, sl, sh, cl, ch);
+        const float4* sp4 = reinterpret_cast<const float4*>(s_pair);
+        nf_span<ACC, false>(sp4, qb, qm, -1, 0, NX, NY, NZ, sl, sh, cl, ch);
+        nf_span<ACC, true>(sp4, qm, qe, qs, hs, NX, NY, NZ, sl, sh, cl, ch);
         if (ACC) {
           td += ((double)sl - (double)cl) + ((double)sh - (double)ch);
         } else {
@@ -640,7 +633,7 @@ k_p2p32x(const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff, c
 
 // ------------------------------------- P2M and L2P of 1/r, one RHS ------
 // Steps 1 and 7 for K = 1/r with one right-hand side, with the distances
-// computed two at a time (sub/mul/fma.rn.f32x2) over pairs of interpolation
+// computed two at a time (the packed f32x2 builtins) over pairs of interpolation
 // points: one warp per leaf, PT_WARPS leaves per CTA, the level's points
 // x_l^{I_0} (= y_l^{J_0}) staged once per CTA as SoA pairs
 //   s_xy[q] = (x_2q, x_2q+1 | y_2q, y_2q+1),  s_z[q] = (z_2q, z_2q+1),
@@ -649,77 +642,69 @@ k_p2p32x(const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff, c
 constexpr int PT_WARPS = 8;
 constexpr int PT_MAXQ = 128;  // pairs: dp <= 256
 
-__device__ __forceinline__ void pt_stage_x(const float* __restrict__ X, int d, int nq, ulonglong2* s_xy,
-                                           uint64_t* s_z) {
+__device__ __forceinline__ void pt_stage_x(const float* __restrict__ X, int d, int nq, float4* s_xy,
+                                           float2* s_z) {
   for (int q = threadIdx.x; q < nq; q += blockDim.x) {
     const int a = 2 * q, b = 2 * q + 1;
     const float x0 = a < d ? X[3 * a] : NF_FAR, y0 = a < d ? X[3 * a + 1] : NF_FAR, z0 = a < d ? X[3 * a + 2] : NF_FAR;
     const float x1 = b < d ? X[3 * b] : NF_FAR, y1 = b < d ? X[3 * b + 1] : NF_FAR, z1 = b < d ? X[3 * b + 2] : NF_FAR;
-    s_xy[q] = make_ulonglong2(pk2(x0, x1), pk2(y0, y1));
-    s_z[q] = pk2(z0, z1);
+    s_xy[q] = make_float4(x0, x1, y0, y1);
+    s_z[q] = make_float2(z0, z1);
   }
 }
 
 // (1/r_lo, 1/r_hi) of a packed r^2, with a Newton step when ACC
 template <bool ACC>
-__device__ __forceinline__ uint64_t pt_rsqrt2(uint64_t r2) {
-  float rl, rh;
-  up2(r2, rl, rh);
-  float yl = rsqrt_approx(rl), yh = rsqrt_approx(rh);
+__device__ __forceinline__ float2 pt_rsqrt2(float2 r2) {
+  float yl = rsqrt_approx(r2.x), yh = rsqrt_approx(r2.y);
   if (ACC) {
-    yl = yl * fmaf(-0.5f * rl, yl * yl, 1.5f);
-    yh = yh * fmaf(-0.5f * rh, yh * yh, 1.5f);
+    yl = yl * fmaf(-0.5f * r2.x, yl * yl, 1.5f);
+    yh = yh * fmaf(-0.5f * r2.y, yh * yh, 1.5f);
   }
-  return pk2(yl, yh);
+  return make_float2(yl, yh);
 }
 
-__device__ __forceinline__ uint64_t pt_r2(uint64_t ax, uint64_t ay, uint64_t az, uint64_t bx, uint64_t by,
-                                          uint64_t bz) {
-  uint64_t dx, dy, dz, r2;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dx) : "l"(ax), "l"(bx));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dy) : "l"(ay), "l"(by));
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(dz) : "l"(az), "l"(bz));
-  asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(r2) : "l"(dx));
-  asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(r2) : "l"(dy));
-  asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(r2) : "l"(dz));
-  return r2;
-}
-
-__device__ __forceinline__ void pt_fma2(uint64_t& acc, uint64_t a, uint64_t b) {
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+// |a - b|^2 of two packed points, b given negated
+__device__ __forceinline__ float2 pt_r2(float2 ax, float2 ay, float2 az, float2 nbx, float2 nby, float2 nbz) {
+  const float2 dx = __fadd2_rn(ax, nbx);
+  const float2 dy = __fadd2_rn(ay, nby);
+  const float2 dz = __fadd2_rn(az, nbz);
+  float2 r2 = __fmul2_rn(dx, dx);
+  r2 = __ffma2_rn(dy, dy, r2);
+  return __ffma2_rn(dz, dz, r2);
 }
 
 // Step 1: W_m = sum_j sigma_j / |x_m - y_j|.  Lane owns the coefficient
 // pairs q = lane + 32 i (at most PT_MAXQ / 32 of them, in registers); the
 // leaf's points pass through shared memory 32 at a time, each as two
-// broadcast 16-byte words (x, x | y, y) and (z, z | sigma, sigma).
+// broadcast 16-byte words (-x, -x | -y, -y) and (-z, -z | sigma, sigma).
 template <bool ACC>
 __global__ void __launch_bounds__(32 * PT_WARPS, 4)
 k_p2m32x(const int32_t* __restrict__ off, int64_t nleaf, const float* __restrict__ lx,
          const float* __restrict__ ly, const float* __restrict__ lz, const float* __restrict__ sig,
          const float* __restrict__ X, int d, int dp, float* __restrict__ W) {
   constexpr int NI = PT_MAXQ / 32;
-  __shared__ ulonglong2 s_xy[PT_MAXQ];
-  __shared__ uint64_t s_z[PT_MAXQ];
-  __shared__ ulonglong2 s_pt[PT_WARPS][32][2];
+  __shared__ float4 s_xy[PT_MAXQ];
+  __shared__ float2 s_z[PT_MAXQ];
+  __shared__ float4 s_pt[PT_WARPS][32][2];
   const int nq = (d + 1) >> 1, nqi = (nq + 31) >> 5;
   pt_stage_x(X, d, nq, s_xy, s_z);
   __syncthreads();
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t b = (int64_t)blockIdx.x * PT_WARPS + w;
   if (b >= nleaf) return;
-  uint64_t ax[NI], ay[NI], az[NI], acc[NI];
+  float2 ax[NI], ay[NI], az[NI], acc[NI];
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     const int q = lane + 32 * i;
-    acc[i] = 0;
+    acc[i] = make_float2(0.f, 0.f);
     if (q < nq) {
-      const ulonglong2 e = s_xy[q];
-      ax[i] = e.x;
-      ay[i] = e.y;
+      const float4 e = s_xy[q];
+      ax[i] = make_float2(e.x, e.y);
+      ay[i] = make_float2(e.z, e.w);
       az[i] = s_z[q];
     } else {
-      ax[i] = ay[i] = az[i] = pk2(NF_FAR, NF_FAR);
+      ax[i] = ay[i] = az[i] = make_float2(NF_FAR, NF_FAR);
     }
   }
   const int beg = off[b], end = off[b + 1];
@@ -727,9 +712,9 @@ k_p2m32x(const int32_t* __restrict__ off, int64_t nleaf, const float* __restrict
     const int j = j0 + lane;
     __syncwarp();
     if (j < end) {
-      const float px = lx[j], py = ly[j], pz = lz[j], s = sig[j];
-      s_pt[w][lane][0] = make_ulonglong2(pk2(px, px), pk2(py, py));
-      s_pt[w][lane][1] = make_ulonglong2(pk2(pz, pz), pk2(s, s));
+      const float px = -lx[j], py = -ly[j], pz = -lz[j], s = sig[j];
+      s_pt[w][lane][0] = make_float4(px, px, py, py);
+      s_pt[w][lane][1] = make_float4(pz, pz, s, s);
     }
     __syncwarp();
     const int cnt = min(32, end - j0);
@@ -737,22 +722,27 @@ k_p2m32x(const int32_t* __restrict__ off, int64_t nleaf, const float* __restrict
     // the accumulation is sequential (in point order)
     int t = 0;
     for (; t + 1 < cnt; t += 2) {
-      const ulonglong2 p0 = s_pt[w][t][0], p1 = s_pt[w][t][1];
-      const ulonglong2 o0 = s_pt[w][t + 1][0], o1 = s_pt[w][t + 1][1];
+      const float4 p0 = s_pt[w][t][0], p1 = s_pt[w][t][1];
+      const float4 o0 = s_pt[w][t + 1][0], o1 = s_pt[w][t + 1][1];
 #pragma unroll
       for (int i = 0; i < NI; ++i)
         if (i < nqi) {  // warp-uniform; lanes past nq work on the far pad
-          const uint64_t kp = pt_rsqrt2<ACC>(pt_r2(ax[i], ay[i], az[i], p0.x, p0.y, p1.x));
-          const uint64_t ko = pt_rsqrt2<ACC>(pt_r2(ax[i], ay[i], az[i], o0.x, o0.y, o1.x));
-          pt_fma2(acc[i], kp, p1.y);
-          pt_fma2(acc[i], ko, o1.y);
+          const float2 kp = pt_rsqrt2<ACC>(pt_r2(ax[i], ay[i], az[i], make_float2(p0.x, p0.y),
+                                                 make_float2(p0.z, p0.w), make_float2(p1.x, p1.y)));
+          const float2 ko = pt_rsqrt2<ACC>(pt_r2(ax[i], ay[i], az[i], make_float2(o0.x, o0.y),
+                                                 make_float2(o0.z, o0.w), make_float2(o1.x, o1.y)));
+          acc[i] = __ffma2_rn(kp, make_float2(p1.z, p1.w), acc[i]);
+          acc[i] = __ffma2_rn(ko, make_float2(o1.z, o1.w), acc[i]);
         }
     }
     if (t < cnt) {
-      const ulonglong2 p0 = s_pt[w][t][0], p1 = s_pt[w][t][1];
+      const float4 p0 = s_pt[w][t][0], p1 = s_pt[w][t][1];
 #pragma unroll
       for (int i = 0; i < NI; ++i)
-        if (i < nqi) pt_fma2(acc[i], pt_rsqrt2<ACC>(pt_r2(ax[i], ay[i], az[i], p0.x, p0.y, p1.x)), p1.y);
+        if (i < nqi)
+          acc[i] = __ffma2_rn(pt_rsqrt2<ACC>(pt_r2(ax[i], ay[i], az[i], make_float2(p0.x, p0.y),
+                                                   make_float2(p0.z, p0.w), make_float2(p1.x, p1.y))),
+                              make_float2(p1.z, p1.w), acc[i]);
     }
   }
   float* row = W + b * dp;
@@ -760,8 +750,7 @@ k_p2m32x(const int32_t* __restrict__ off, int64_t nleaf, const float* __restrict
   for (int i = 0; i < NI; ++i) {
     const int q = lane + 32 * i;
     if (2 * q < dp) {
-      float lo, hi;
-      up2(acc[i], lo, hi);
+      float lo = acc[i].x, hi = acc[i].y;
       if (2 * q >= d) lo = 0.f;
       if (2 * q + 1 >= d) hi = 0.f;
       *reinterpret_cast<float2*>(row + 2 * q) = make_float2(lo, hi);
@@ -779,9 +768,9 @@ __global__ void __launch_bounds__(32 * PT_WARPS)
 k_l2p32x(const int32_t* __restrict__ leaves, int64_t nl, const int32_t* __restrict__ off,
          const float* __restrict__ lx, const float* __restrict__ ly, const float* __restrict__ lz,
          const float* __restrict__ X, int d, int dp, const float* __restrict__ lh, double* __restrict__ ffar) {
-  __shared__ ulonglong2 s_xy[PT_MAXQ];
-  __shared__ uint64_t s_z[PT_MAXQ];
-  __shared__ ulonglong2 s_zl[PT_WARPS][PT_MAXQ];
+  __shared__ float4 s_xy[PT_MAXQ];
+  __shared__ float2 s_z[PT_MAXQ];
+  __shared__ float4 s_zl[PT_WARPS][PT_MAXQ];
   const int nq = (d + 1) >> 1;
   pt_stage_x(X, d, nq, s_xy, s_z);
   __syncthreads();
@@ -792,7 +781,8 @@ k_l2p32x(const int32_t* __restrict__ leaves, int64_t nl, const int32_t* __restri
   const float* lrow = lh + (int64_t)b * dp;
   for (int q = lane; q < nq; q += 32) {
     const float2 c = *reinterpret_cast<const float2*>(lrow + 2 * q);
-    s_zl[w][q] = make_ulonglong2(s_z[q], pk2(c.x, 2 * q + 1 < d ? c.y : 0.f));
+    const float2 z = s_z[q];
+    s_zl[w][q] = make_float4(z.x, z.y, c.x, 2 * q + 1 < d ? c.y : 0.f);
   }
   __syncwarp();
   const int beg = off[b], end = off[b + 1];
@@ -802,19 +792,19 @@ k_l2p32x(const int32_t* __restrict__ leaves, int64_t nl, const int32_t* __restri
     const int p = t0 + ti;
     float s = 0.f;
     if (si < S) {
-      const float px = lx[p], py = ly[p], pz = lz[p];
-      const uint64_t PX = pk2(px, px), PY = pk2(py, py), PZ = pk2(pz, pz);
+      const float px = -lx[p], py = -ly[p], pz = -lz[p];
+      const float2 PX = make_float2(px, px), PY = make_float2(py, py), PZ = make_float2(pz, pz);
       const int L = (nq + S - 1) / S;
       const int qb = min(nq, si * L), qe = min(nq, qb + L);
-      uint64_t acc = 0;
+      float2 acc = make_float2(0.f, 0.f);
 #pragma unroll 4
       for (int q = qb; q < qe; ++q) {
-        const ulonglong2 e = s_xy[q], f = s_zl[w][q];
-        pt_fma2(acc, pt_rsqrt2<ACC>(pt_r2(e.x, e.y, f.x, PX, PY, PZ)), f.y);
+        const float4 e = s_xy[q], f = s_zl[w][q];
+        const float2 k = pt_rsqrt2<ACC>(
+            pt_r2(make_float2(e.x, e.y), make_float2(e.z, e.w), make_float2(f.x, f.y), PX, PY, PZ));
+        acc = __ffma2_rn(k, make_float2(f.z, f.w), acc);
       }
-      float lo, hi;
-      up2(acc, lo, hi);
-      s = lo + hi;
+      s = acc.x + acc.y;
     }
     // slices si = 1..S-1 of point ti sit at lanes ti + P si
     for (int k = 1; k < S; ++k) {
