@@ -67,6 +67,9 @@ void free_workspace(Workspace* ws) {
   dfree(ws->m2l_part_leaf);
   ws->m2l_part_leaf = nullptr;
   ws->m2l_part_leaf_cap = 0;
+  dfree(ws->part64);
+  ws->part64 = nullptr;
+  ws->part64_cap = 0;
   for (int k = 0; k <= kMaxLevel; ++k) ws->m2l_kind[k] = ws->m2l_gshift[k] = 0;
   ws->p2p_sym = 0;
   free_sk_plan(&ws->sk);
@@ -158,6 +161,18 @@ eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec) {
       else EIFMM_TRY(dalloc(&ws.l[k], n));
     }
     EIFMM_TRY(dalloc(&ws.lh, ((size_t)1 << (3 * kap)) * R * ops->lv[kap].d));
+    // partial sums of the offset groups of the coarse levels' M2L
+    int dev = 0;
+    EIFMM_CUDA(cudaGetDevice(&dev));
+    EIFMM_CUDA(cudaDeviceGetAttribute(&ws.nsm, cudaDevAttrMultiProcessorCount, dev));
+    size_t need = 0;
+    for (int k = 2; k <= kap; ++k) {
+      const int d = ops->lv[k].d;
+      const int G = std::max(m2l64_groups(m2l64_blocks(k, R), ws.nsm), m2l64_groups(m2l_df_blocks(k, d, R), ws.nsm));
+      if (G > 1) need = std::max(need, (size_t)G * ((size_t)1 << (3 * k)) * R * d);
+    }
+    if (need) EIFMM_TRY(dalloc(&ws.part64, need));
+    ws.part64_cap = need;
   } else {
     EIFMM_TRY(alloc_mixed_workspace(t, ops, R));
   }

@@ -501,6 +501,8 @@ __device__ __forceinline__ void nf_span(const float4* s_pair, int qa, int qe, in
   }
 }
 
+// (Capping it at 40 registers for 12 CTAs per SM instead of 10 made the
+// evaluate slower: 1.053 against 1.045 ms at 2^20 points.)
 template <bool ACC>
 __global__ void __launch_bounds__(NF_THREADS)
 k_p2p32x(const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff, const float* __restrict__ tlx,

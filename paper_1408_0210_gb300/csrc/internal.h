@@ -174,6 +174,9 @@ struct Workspace {
   size_t m2l_part_leaf_cap = 0;
   alignas(64) unsigned char tmap2[kMaxLevel + 1][2][128] = {};
   float* m2l_part = nullptr;    // partial M2L sums of the split offset lists
+  double* part64 = nullptr;     // the same for the FP64 far field (FP64 and FP32-pair M2L)
+  size_t part64_cap = 0;        // doubles in part64
+  int nsm = 0;                  // SMs of the workspace's device
   uint32_t* wmax = nullptr;     // [kMaxLevel + 1] bits of max |W| per level (FP16 planes)
   SkPlanDev sk;                 // stream-K plan of the leaf level (tier 0), when it pays
   int* err = nullptr;           // device error word of bounded waits
@@ -250,6 +253,15 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma,
 eifmm_status ensure_workspace(Tree* t, const Ops* ops, int R, int prec);
 // Step 4 of level k with the compressed operators (sarcmp.cu) on the FP64
 // far field; pair: FP32-pair arithmetic, else FP64.
+// FP64 far-field M2L (fmm64.cu): offset groups split the offset list of a
+// level with few blocks; `part` (part_cap doubles) holds their partial sums.
+int m2l64_groups(int64_t blocks, int nsm);
+int64_t m2l_df_blocks(int level, int d, int R);
+int64_t m2l64_blocks(int level, int R);
+eifmm_status launch_m2l_df(int level, int d, int R, const double* kdT, const int* slot_lists, const double* W,
+                           double* g, double* part, size_t part_cap, int nsm, cudaStream_t s);
+eifmm_status launch_m2l64(int level, int d, int R, const double* kdT, const int* slot_lists, const double* W,
+                          double* g, double* part, size_t part_cap, int nsm, cudaStream_t s);
 eifmm_status m2l_compressed(Workspace& ws, const Ops* ops, int k, int R, bool pair, cudaStream_t s);
 void free_workspace(Workspace* ws);
 bool timing_enabled();

@@ -311,10 +311,6 @@ eifmm_status compress_ops(Ops* ops, double eps, cudaStream_t s) {
 // the FP64 far field: What = Delta W into Wh[k], w~ = What U into tmp,
 // g~ = sum C^delta w~ into Wh[k] (FP32-pair arithmetic or FP64, as the
 // uncompressed M2L of the same path), g = g~ U^t.
-eifmm_status launch_m2l_df(int level, int d, int R, const double* kdT, const int* slot_lists, const double* W,
-                           double* g, cudaStream_t s);
-eifmm_status launch_m2l64(int level, int d, int R, const double* kdT, const int* slot_lists, const double* W,
-                          double* g, cudaStream_t s);
 
 eifmm_status m2l_compressed(Workspace& ws, const Ops* ops, int k, int R, bool pair, cudaStream_t s) {
   const LevelOps& v = ops->lv[k];
@@ -326,8 +322,10 @@ eifmm_status m2l_compressed(Workspace& ws, const Ops* ops, int k, int R, bool pa
   EIFMM_TRY((launch_delta_batch<double, double, double, 0>(b, false, s)));
   double* wt = (double*)ws.tmp;  // rows x r
   EIFMM_TRY(gemm64(false, rows, r, d, ws.Wh[k], d, v.U, r, wt, r, s));
-  if (pair) EIFMM_TRY(launch_m2l_df(k, r, R, v.Ct, ops->d_slot_lists, wt, ws.Wh[k], s));
-  else EIFMM_TRY(launch_m2l64(k, r, R, v.Ct, ops->d_slot_lists, wt, ws.Wh[k], s));
+  if (pair)
+    EIFMM_TRY(launch_m2l_df(k, r, R, v.Ct, ops->d_slot_lists, wt, ws.Wh[k], ws.part64, ws.part64_cap, ws.nsm, s));
+  else
+    EIFMM_TRY(launch_m2l64(k, r, R, v.Ct, ops->d_slot_lists, wt, ws.Wh[k], ws.part64, ws.part64_cap, ws.nsm, s));
   EIFMM_TRY(gemm64(true, rows, d, r, ws.Wh[k], r, v.U, r, ws.g[k], d, s));
   return EIFMM_OK;
 }
