@@ -574,20 +574,28 @@ k_p2p32x(const int32_t* __restrict__ leaves, const int32_t* __restrict__ toff, c
       const int np = (cn + 1) >> 1;
       if (staged_c0 != c0) {
         __syncthreads();
-        for (int sg = w; sg < 27; sg += NF_THREADS / 32) {
-          const int pb = s_pos[sg];
-          const int lo = max(pb, c0), hi = min(pb + s_len[sg], c0 + cn);
-          const float sx = s_sh[sg][0], sy = s_sh[sg][1], sz = s_sh[sg][2];
-          const int sb = s_beg[sg] - pb;
-          for (int pos = lo + lane; pos < hi; pos += 32) {
-            const int sj = sb + pos;
-            const int lp = pos - c0;
-            float* e = reinterpret_cast<float*>(&s_pair[2 * (lp >> 1)]) + (lp & 1);
-            e[0] = slx[sj] + sx;
-            e[2] = sly[sj] + sy;
-            e[4] = slz[sj] + sz;
-            e[6] = sig[sj];
+        // thread tid stages logical positions c0 + tid, c0 + tid + 128, ...
+        // of the chunk; the segment of a position is the last one starting
+        // at or before it (a binary search over the 26 starts), so the
+        // global loads of all of a thread's sources are independent and in
+        // flight together
+#pragma unroll 4
+        for (int lp = tid; lp < cn; lp += NF_THREADS) {
+          const int pos = c0 + lp;
+          int sg = 26;
+          if (pos < n_other) {
+            if (pos >= n_real_other) continue;  // the pad before the leaf itself
+            sg = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1)
+              if (sg + step < 26 && s_pos[sg + step] <= pos) sg += step;
           }
+          const int sj = s_beg[sg] + (pos - s_pos[sg]);
+          float* e = reinterpret_cast<float*>(&s_pair[2 * (lp >> 1)]) + (lp & 1);
+          e[0] = slx[sj] + s_sh[sg][0];
+          e[2] = sly[sj] + s_sh[sg][1];
+          e[4] = slz[sj] + s_sh[sg][2];
+          e[6] = sig[sj];
         }
         // pads at an odd end of the other leaves and of the chunk
         if (tid < 2) {
