@@ -1427,6 +1427,10 @@ static int current_device() {
 
 eifmm_status launch_m2l_tma(const M2LTcArgs& a0, const void* map0, const void* map1, bool tf32,
                             cudaStream_t s) {
+  if (tf32) {  // the TF32 planes of an earlier tier are no longer built
+    set_error("tensor-core M2L: TF32 operand planes are not built (BF16 and FP16 only)");
+    return EIFMM_EUNSUPPORTED;
+  }
   M2LTcArgs a = a0;
   a.stages = m2l_tc_stages(a.dp);
   a.chains = a.dp <= 128 ? 4 : (a.dp <= 256 ? 2 : 1);
@@ -1449,17 +1453,13 @@ eifmm_status launch_m2l_tma(const M2LTcArgs& a0, const void* map0, const void* m
   static bool attr[kMaxDevices][2] = {};
   const int dev = current_device();
   if (dev >= kMaxDevices || !attr[dev][tf32]) {
-    if (tf32)
-      EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    else
-      EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     if (dev < kMaxDevices) attr[dev][tf32] = true;
   }
   const unsigned grid = (unsigned)(tiles * 8 * a.groups);
   const CUtensorMap& m0 = *(const CUtensorMap*)map0;
   const CUtensorMap& m1 = *(const CUtensorMap*)map1;
-  if (tf32) k_m2l_tma<true><<<grid, 192, sm, s>>>(m0, m1, a);
-  else k_m2l_tma<false><<<grid, 192, sm, s>>>(m0, m1, a);
+  k_m2l_tma<false><<<grid, 192, sm, s>>>(m0, m1, a);
   EIFMM_CHECK_LAUNCH();
   if (a.groups > 1) {
     const int64_t n4 = a.rows * (int64_t)a.dp / 4;
@@ -1473,6 +1473,10 @@ eifmm_status launch_m2l_tma(const M2LTcArgs& a0, const void* map0, const void* m
 size_t m2l_t256_smem_bytes() { return (size_t)kT2Stages * (2 * 16384 + 2 * kT2Rows * 128) + 1024 + 128 + 8 * kT2Rows; }
 
 eifmm_status launch_m2l_t256(const M2LTcArgs& a0, const void* map0, const void* map1, bool tf32, cudaStream_t s) {
+  if (tf32) {  // the TF32 planes of an earlier tier are no longer built
+    set_error("tensor-core M2L: TF32 operand planes are not built (BF16 and FP16 only)");
+    return EIFMM_EUNSUPPORTED;
+  }
   M2LTcArgs a = a0;
   if (a.dp != 128 || !m2l_t256_block(a.R, &a.bx, &a.by, &a.bz)) {
     set_error("transposed M2L: needs dp = 128 and a tile shape for R");
@@ -1493,17 +1497,13 @@ eifmm_status launch_m2l_t256(const M2LTcArgs& a0, const void* map0, const void* 
   static bool attr[kMaxDevices][2] = {};
   const int dev = current_device();
   if (dev >= kMaxDevices || !attr[dev][tf32]) {
-    if (tf32)
-      EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_t256<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    else
-      EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_t256<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_t256<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     if (dev < kMaxDevices) attr[dev][tf32] = true;
   }
   const unsigned grid = (unsigned)(tiles * 8 * a.groups);
   const CUtensorMap& m0 = *(const CUtensorMap*)map0;
   const CUtensorMap& m1 = *(const CUtensorMap*)map1;
-  if (tf32) k_m2l_t256<true><<<grid, kT2Threads, sm, s>>>(m0, m1, a);
-  else k_m2l_t256<false><<<grid, kT2Threads, sm, s>>>(m0, m1, a);
+  k_m2l_t256<false><<<grid, kT2Threads, sm, s>>>(m0, m1, a);
   EIFMM_CHECK_LAUNCH();
   if (a.groups > 1) {
     const int64_t n4 = a.rows * (int64_t)a.dp / 4;
@@ -1714,6 +1714,10 @@ int64_t m2l_t256_ctas(int level, int R) {
 }
 
 eifmm_status launch_m2l_tc(const M2LTcArgs& a0, bool tf32, cudaStream_t s) {
+  if (tf32) {  // the TF32 planes of an earlier tier are no longer built
+    set_error("tensor-core M2L: TF32 operand planes are not built (BF16 and FP16 only)");
+    return EIFMM_EUNSUPPORTED;
+  }
   M2LTcArgs a = a0;
   a.stages = m2l_tc_stages(a.dp);
   a.chains = a.dp <= 128 ? 4 : (a.dp <= 256 ? 2 : 1);
@@ -1722,10 +1726,7 @@ eifmm_status launch_m2l_tc(const M2LTcArgs& a0, bool tf32, cudaStream_t s) {
   static bool attr[kMaxDevices][2] = {};
   const int dev = current_device();
   if (dev >= kMaxDevices || !attr[dev][tf32]) {
-    if (tf32)
-      EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    else
-      EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    EIFMM_CUDA(cudaFuncSetAttribute(k_m2l_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
     if (dev < kMaxDevices) attr[dev][tf32] = true;
   }
   const int64_t tiles = (a.nbox / 8 * a.R + kRows - 1) / kRows;
@@ -1737,8 +1738,7 @@ eifmm_status launch_m2l_tc(const M2LTcArgs& a0, bool tf32, cudaStream_t s) {
     a.part_stride = 0;
   }
   const unsigned grid = (unsigned)(tiles * 8 * a.groups);
-  if (tf32) k_m2l_tc<true><<<grid, 160, sm, s>>>(a);
-  else k_m2l_tc<false><<<grid, 160, sm, s>>>(a);
+  k_m2l_tc<false><<<grid, 160, sm, s>>>(a);
   EIFMM_CHECK_LAUNCH();
   if (a.groups > 1) {
     const int64_t n4 = a.rows * (int64_t)a.dp / 4;

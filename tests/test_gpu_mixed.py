@@ -1,10 +1,11 @@
 """GPU parity of the mixed-precision EIFMM (FP32 SIMT steps, tcgen05 M2L with
-split BF16/TF32 operands, compensated FP32 near field) against the CPU checker.
+split BF16 or scaled FP16 operands, compensated FP32 near field) against the
+CPU checker.
 
 Tolerances come from the arithmetic of each tier (and the precision study
-recorded with the design): BF16 hi+lo planes keep ~16 bits per product, TF32
-hi+lo ~21 bits, FP32 steps ~24 bits, amplified by the conditioning of the EIM
-basis (up to ~30x in M2L).  The end-to-end requirement is the method's:
+recorded with the design): BF16 hi+lo planes keep ~16 bits per product,
+scaled FP16 hi+lo ~22 bits, FP32 steps ~24 bits, amplified by the
+conditioning of the EIM basis (up to ~30x in M2L).  The end-to-end requirement is the method's:
 rel-L2 against the exact sum within the EIM tolerance eps.
 """
 import numpy as np
