@@ -222,7 +222,7 @@ WORKLOADS = {
 }
 
 
-def run_workloads(names, stream, flush, dist):
+def run_workloads(names, stream, flush, dist, profile_steps=0):
     import math
 
     import torch
@@ -239,6 +239,14 @@ def run_workloads(names, stream, flush, dist):
         for _ in range(warmup):
             fn()
         torch.cuda.synchronize()
+        if profile_steps > 0:  # for ncu --profile-from-start off: no timing
+            torch.cuda.profiler.start()
+            for _ in range(profile_steps):
+                with torch.cuda.stream(st):
+                    fn()
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
+            return float("nan"), 0
         launches0 = E.eifmm_kernel_launches()
         e0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         e1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -350,6 +358,9 @@ def main():
                     help="name=0|1: eifmm_tree_set_option on the workload's tree (for comparisons)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the built-in M2L and near-field rules (with --tree-option, to compare kernels)")
+    ap.add_argument("--profile-workload-steps", type=int, default=0,
+                    help="run this many evaluations of each --workloads entry between "
+                         "cudaProfilerStart/Stop instead of timing them")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run this many evaluations of the first variant between "
                          "cudaProfilerStart/Stop (for ncu --profile-from-start off) and exit")
@@ -496,7 +507,7 @@ def main():
             if headline is None and err <= eps and (name, eps) in (("mixed", 1e-4), ("fp64", 1e-4)):
                 headline = (name, eps)
         names = [w for w in args.workloads.split(",") if w]
-        workloads = run_workloads(names, stream, flush, dist) if names else {}
+        workloads = run_workloads(names, stream, flush, dist, args.profile_workload_steps) if names else {}
     clocks = clk.summary()
 
     if headline is None:  # no 1e-4 variant met its tolerance: the first one that ran

@@ -1724,7 +1724,7 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     x.ncol = nboxes(k) * R;
     x.A = a.m2m32; x.B = ws.W32[k + 1]; x.G = nullptr; x.C = ws.W32[k];
     x.P8 = (float*)ws.tmp;  // 8 x nboxes(k) x R x dp floats fit in the scratch
-    if (!(R == 1 && xfer_blas(true, a, c, nboxes(k), ws.W32[k + 1], nullptr, ws.W32[k], s)))
+    if (!xfer_blas(true, a, c, nboxes(k), R, ws.W32[k + 1], nullptr, ws.W32[k], s))
       EIFMM_TRY(launch_xfer_gemm(x, s));
   }
   record(ws, 2, s);
@@ -1805,7 +1805,7 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     x.ncol = nboxes(k - 1) * R;
     x.A = v.l2l32; x.B = ws.l32[k - 1]; x.G = ws.g32[k]; x.C = ws.l32[k];
     x.P8 = nullptr;
-    if (!(R == 1 && xfer_blas(false, v, pv, nboxes(k - 1), ws.l32[k - 1], ws.g32[k], ws.l32[k], s)))
+    if (!xfer_blas(false, v, pv, nboxes(k - 1), R, ws.l32[k - 1], ws.g32[k], ws.l32[k], s))
       EIFMM_TRY(launch_xfer_gemm(x, s));
   }
   record(ws, 5, s);

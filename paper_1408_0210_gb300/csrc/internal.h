@@ -239,10 +239,11 @@ eifmm_status launch_p2p32(const Tree* t, int kern, const float* sig32, int R,
 enum PlaneFmt { kPlaneBF16 = 0, kPlaneTF32 = 1, kPlaneF16 = 2 };
 eifmm_status build_kd_image(Ops* ops, int fmt, cudaStream_t s);
 eifmm_status build_kd32(Ops* ops, cudaStream_t s);
-// M2M / L2L of one right-hand side as library GEMMs (xfer_blas.cu)
+// M2M / L2L as library GEMMs (xfer_blas.cu): one per level with one right-hand
+// side, 8 strided-batched ones per level with several
 eifmm_status build_xfer_blas(Ops* ops, cudaStream_t s);
-bool xfer_blas(bool m2m, const LevelOps& out, const LevelOps& in, int64_t n_par, const float* B, const float* G,
-               float* C, cudaStream_t s);
+bool xfer_blas(bool m2m, const LevelOps& out, const LevelOps& in, int64_t n_par, int R, const float* B,
+               const float* G, float* C, cudaStream_t s);
 // M2L compression (sarcmp.cu): eps <= 0 removes it.
 eifmm_status compress_ops(Ops* ops, double eps, cudaStream_t s);
 void free_compression(LevelOps& v);

@@ -11,7 +11,8 @@
 //             + [K_L2L^0; ...; K_L2L^7] (8 dp_k x dp_p) x l_parent (dp_p x n_par)
 // with the operators zero-padded to dp (so the padding columns stay zero).
 // These are plain GEMMs, so a library GEMM serves them; any failure of the
-// library leaves the SIMT kernel of transfer.cuh to do the step.
+// library leaves the SIMT kernel of transfer.cuh to do the step.  With
+// several right-hand sides each level is 8 strided-batched GEMMs (below).
 #include <cublas_v2.h>
 
 #include <mutex>
@@ -86,9 +87,58 @@ eifmm_status build_xfer_blas(Ops* ops, cudaStream_t s) {
   return EIFMM_OK;
 }
 
+// Several right-hand sides (rows [box R + r][dp]): the rows of one octant i
+// and one column r are a matrix with a constant leading dimension, so each
+// level is 8 strided-batched GEMMs (one per octant, batched over r):
+//   M2M: W_parent[:, P R + r] (+)= K_M2M^i W_child[:, (8P + i) R + r]
+//   L2L: l_child[:, (8P + i) R + r] = g_child[...] + K_L2L^i l_parent[:, P R + r]
+// (column-major, as above).  Below kBatchedMinParents parents the SIMT
+// kernel is left the level: 8 library calls cost more there.
+constexpr int64_t kBatchedMinParents = 512;
+bool g_batched_failed[kMaxDev] = {};
+
+bool xfer_blas_rhs(bool m2m, const LevelOps& out, const LevelOps& in, int64_t n_par, int R, const float* B,
+                   const float* G, float* C, cudaStream_t s) {
+  const float* A = m2m ? out.m2m_cb : out.l2l_cb;
+  if (!A || n_par < kBatchedMinParents || n_par > 2147483647LL || R < 2) return false;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev || g_batched_failed[dev]) return false;
+  std::lock_guard<std::mutex> lk(g_mu);
+  cublasHandle_t h = handle_here();
+  if (!h || cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return false;
+  const float one = 1.f, zero = 0.f;
+  const int dk = out.dp, dc = in.dp;
+  const int n = (int)n_par;
+  if (!m2m &&
+      cudaMemcpyAsync(C, G, (size_t)n_par * 8 * R * dk * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return false;
+  for (int i = 0; i < 8; ++i) {
+    cublasStatus_t st;
+    if (m2m) {
+      st = cublasGemmStridedBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_N, dk, n, dc, &one, A + (size_t)i * dc * dk,
+                                      CUDA_R_32F, dk, 0, B + (size_t)dc * i * R, CUDA_R_32F, 8 * R * dc, dc,
+                                      i == 0 ? &zero : &one, C, CUDA_R_32F, R * dk, dk, R,
+                                      CUBLAS_COMPUTE_32F_EMULATED_16BFX9, CUBLAS_GEMM_DEFAULT);
+    } else {
+      st = cublasGemmStridedBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_N, dk, n, dc, &one, A + (size_t)i * dk, CUDA_R_32F,
+                                      8 * dk, 0, B, CUDA_R_32F, R * dc, dc, &one, C + (size_t)dk * i * R,
+                                      CUDA_R_32F, 8 * R * dk, dk, R, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+                                      CUBLAS_GEMM_DEFAULT);
+    }
+    if (st != CUBLAS_STATUS_SUCCESS) {
+      // the SIMT kernel then writes the whole level afresh (it stores, it
+      // does not add), whatever the octants before this one left there
+      g_batched_failed[dev] = true;
+      return false;
+    }
+  }
+  return true;
+}
+
 // true when the library took the step; false: the caller runs its own kernel
-bool xfer_blas(bool m2m, const LevelOps& out, const LevelOps& in, int64_t n_par, const float* B, const float* G,
-               float* C, cudaStream_t s) {
+bool xfer_blas(bool m2m, const LevelOps& out, const LevelOps& in, int64_t n_par, int R, const float* B,
+               const float* G, float* C, cudaStream_t s) {
+  if (R > 1) return xfer_blas_rhs(m2m, out, in, n_par, R, B, G, C, s);
   const float* A = m2m ? out.m2m_cb : out.l2l_cb;
   if (!A || n_par <= 0 || n_par > 2147483647LL) return false;
   std::lock_guard<std::mutex> lk(g_mu);

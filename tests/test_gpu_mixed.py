@@ -316,6 +316,32 @@ def test_many_rhs_64(E, orc, prec, tol):
     assert max(errs) <= tol
 
 
+def test_many_rhs_transfers_at_depth4(E, orc):
+    """Several sigma columns on a depth-4 tree: M2M into level 3 and L2L into
+    level 4 have 512 parents, so they run as strided-batched library GEMMs
+    over the columns (one right-hand side runs one GEMM per level).  Each
+    column against the CPU EIFMM, and against evaluating that column alone
+    (the same method and precision through the other GEMM shape and other
+    M2L tile shapes: the two agree to the tier's own error, about 4e-6)."""
+    n, depth, eps, R = 40000, 4, 1e-4, 4
+    x = wl.uniform_cube(n, 17)
+    s = wl.sigma_uniform(n, R, 18)
+    lv = orc.build_levels("inv_r", 1.0, depth, eps)
+    f2 = orc.eifmm("inv_r", 1.0, [0, 0, 0], depth, lv, x, x, s)
+    ops = E.eifmm_ops_build("inv_r", 1.0, depth, eps)
+    assert ops.plan() == 0
+    tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
+    sd = torch.from_numpy(np.asfortranarray(s)).to("cuda").T.contiguous().T
+    f = torch.zeros(R, n, dtype=torch.float64, device="cuda").T
+    E.eifmm_evaluate(tree, ops, sd, f, "mixed")
+    fg = f.cpu().numpy()
+    for r in range(R):
+        f1 = torch.zeros(n, dtype=torch.float64, device="cuda")
+        E.eifmm_evaluate(tree, ops, dev(s[:, r]), f1, "mixed")
+        assert rel2(fg[:, r], f2[:, r]) <= 2e-5, r
+        assert rel2(fg[:, r], f1.cpu().numpy()) <= 1e-5, r
+
+
 @pytest.mark.parametrize("kern,eps", [("exp_r2", 1e-6), ("cos20r_r", 1e-4), ("sqrt_r2p1", 1e-5)])
 def test_other_inhomogeneous_kernels(E, orc, kern, eps):
     """The kernels of the paper's inhomogeneous experiments (Section 5.4) on
