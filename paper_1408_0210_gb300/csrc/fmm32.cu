@@ -674,6 +674,14 @@ __device__ __forceinline__ float2 pt_rsqrt2(float2 r2) {
   return make_float2(yl, yh);
 }
 
+// acc (+)= k sigma on each half with scalar FMAs: the two rsqrt results stay
+// in registers of their own (joining them into a pair for one packed FMA
+// measured slower in the near field)
+__device__ __forceinline__ void pt_fma_halves(float2& acc, float2 k, float2 sg) {
+  acc.x = fmaf(k.x, sg.x, acc.x);
+  acc.y = fmaf(k.y, sg.y, acc.y);
+}
+
 // |a - b|^2 of two packed points, b given negated
 __device__ __forceinline__ float2 pt_r2(float2 ax, float2 ay, float2 az, float2 nbx, float2 nby, float2 nbz) {
   const float2 dx = __fadd2_rn(ax, nbx);
@@ -741,8 +749,8 @@ k_p2m32x(const int32_t* __restrict__ off, int64_t nleaf, const float* __restrict
                                                  make_float2(p0.z, p0.w), make_float2(p1.x, p1.y)));
           const float2 ko = pt_rsqrt2<ACC>(pt_r2(ax[i], ay[i], az[i], make_float2(o0.x, o0.y),
                                                  make_float2(o0.z, o0.w), make_float2(o1.x, o1.y)));
-          acc[i] = __ffma2_rn(kp, make_float2(p1.z, p1.w), acc[i]);
-          acc[i] = __ffma2_rn(ko, make_float2(o1.z, o1.w), acc[i]);
+          pt_fma_halves(acc[i], kp, make_float2(p1.z, p1.w));
+          pt_fma_halves(acc[i], ko, make_float2(o1.z, o1.w));
         }
     }
     if (t < cnt) {
@@ -750,9 +758,10 @@ k_p2m32x(const int32_t* __restrict__ off, int64_t nleaf, const float* __restrict
 #pragma unroll
       for (int i = 0; i < NI; ++i)
         if (i < nqi)
-          acc[i] = __ffma2_rn(pt_rsqrt2<ACC>(pt_r2(ax[i], ay[i], az[i], make_float2(p0.x, p0.y),
-                                                   make_float2(p0.z, p0.w), make_float2(p1.x, p1.y))),
-                              make_float2(p1.z, p1.w), acc[i]);
+          pt_fma_halves(acc[i],
+                        pt_rsqrt2<ACC>(pt_r2(ax[i], ay[i], az[i], make_float2(p0.x, p0.y),
+                                             make_float2(p0.z, p0.w), make_float2(p1.x, p1.y))),
+                        make_float2(p1.z, p1.w));
     }
   }
   float* row = W + b * dp;
@@ -812,7 +821,7 @@ k_l2p32x(const int32_t* __restrict__ leaves, int64_t nl, const int32_t* __restri
         const float4 e = s_xy[q], f = s_zl[w][q];
         const float2 k = pt_rsqrt2<ACC>(
             pt_r2(make_float2(e.x, e.y), make_float2(e.z, e.w), make_float2(f.x, f.y), PX, PY, PZ));
-        acc = __ffma2_rn(k, make_float2(f.z, f.w), acc);
+        pt_fma_halves(acc, k, make_float2(f.z, f.w));
       }
       s = acc.x + acc.y;
     }
