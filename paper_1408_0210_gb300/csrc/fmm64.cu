@@ -207,11 +207,16 @@ k_m2l_df(int level, int d, int R, const double* __restrict__ kdT, const int* __r
   // (the padding of the last row tile) skips the sums
   const int tm = (tid >> 4) * 4, tb = (tid & 15) * 4;
   const bool rows_live = m0 + (tid >> 5) * 8 < d;
-  float ah[4][4], al[4][4];  // running sums of boxes tb.. x rows tm..
+  // running sums (hi, lo) of boxes tb.. x rows tm..; rows 2jp, 2jp + 1 side
+  // by side in a float2, the pair arithmetic done two rows at a time by the
+  // f32x2 builtins (the same IEEE operations as one row at a time: a - b is
+  // fma(b, -1, a), and -p is formed as (-w) t)
+  float2 ah[4][2], al[4][2];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) ah[i][j] = al[i][j] = 0.f;
+    for (int j = 0; j < 2; ++j) ah[i][j] = al[i][j] = make_float2(0.f, 0.f);
+  const float2 m1 = make_float2(-1.f, -1.f);
   const int* lst = slot_lists + oct * kListLen;
   const int lb = tid >> 2, lq = (tid & 3) * 4;   // staging: box lb, terms lq..lq+3
   const int ll = tid >> 4, lm = (tid & 15) * 4;  // staging: term ll, rows lm..lm+3
@@ -256,22 +261,27 @@ k_m2l_df(int level, int d, int R, const double* __restrict__ kdT, const int* __r
         const float4 th = *reinterpret_cast<const float4*>(&sTh[u][tm]);
         const float4 tl = *reinterpret_cast<const float4*>(&sTl[u][tm]);
         const float whv[4] = {wh.x, wh.y, wh.z, wh.w}, wlv[4] = {wl.x, wl.y, wl.z, wl.w};
-        const float thv[4] = {th.x, th.y, th.z, th.w}, tlv[4] = {tl.x, tl.y, tl.z, tl.w};
+        const float2 T[2] = {make_float2(th.x, th.y), make_float2(th.z, th.w)};
+        const float2 TL[2] = {make_float2(tl.x, tl.y), make_float2(tl.z, tl.w)};
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i) {
+          const float2 Wp = make_float2(whv[i], whv[i]), Wn = make_float2(-whv[i], -whv[i]);
+          const float2 WL = make_float2(wlv[i], wlv[i]);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
+          for (int j = 0; j < 2; ++j) {
             // explicit roundings: no contraction may merge the product into
             // the two-sum
-            const float p = __fmul_rn(whv[i], thv[j]);
-            const float e = fmaf(whv[i], thv[j], -p);
-            const float c = fmaf(whv[i], tlv[j], __fmul_rn(wlv[i], thv[j]));
-            const float sum = __fadd_rn(ah[i][j], p);
-            const float bb = __fsub_rn(sum, ah[i][j]);
-            const float err = __fadd_rn(__fsub_rn(ah[i][j], __fsub_rn(sum, bb)), __fsub_rn(p, bb));
-            al[i][j] += err + (e + c);
+            const float2 pn = __fmul2_rn(Wn, T[j]);                           // -p, p = wh th
+            const float2 e = __ffma2_rn(Wp, T[j], pn);                        // wh th - p
+            const float2 c = __ffma2_rn(Wp, TL[j], __fmul2_rn(WL, T[j]));      // wh tl + wl th
+            const float2 sum = __ffma2_rn(pn, m1, ah[i][j]);                  // ah + p
+            const float2 bb = __ffma2_rn(ah[i][j], m1, sum);                  // sum - ah
+            const float2 t2 = __ffma2_rn(__ffma2_rn(bb, m1, sum), m1, ah[i][j]);  // ah - (sum - bb)
+            const float2 err = __ffma2_rn(__fadd2_rn(pn, bb), m1, t2);        // t2 + (p - bb)
+            al[i][j] = __fadd2_rn(al[i][j], __fadd2_rn(err, __fadd2_rn(e, c)));
             ah[i][j] = sum;
           }
+        }
       }
       __syncthreads();
     }
@@ -283,7 +293,9 @@ k_m2l_df(int level, int d, int R, const double* __restrict__ kdT, const int* __r
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int mp = m0 + tm + j;
-      if (mp < d) g[(I * R + r) * d + mp] = (double)ah[i][j] + (double)al[i][j];
+      const float h2 = (j & 1) ? ah[i][j >> 1].y : ah[i][j >> 1].x;
+      const float l2 = (j & 1) ? al[i][j >> 1].y : al[i][j >> 1].x;
+      if (mp < d) g[(I * R + r) * d + mp] = (double)h2 + (double)l2;
     }
   }
 }
