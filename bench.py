@@ -298,7 +298,8 @@ def run_workloads(names, stream, flush, dist, profile_steps=0):
                 if prec == "mixed" and ops.plan() <= 1:
                     E.eifmm_autotune(tree, ops, R, prec, stream)
                 ms, launches = timed(lambda: E.eifmm_evaluate(tree, ops, sd, f, prec, stream), steps, warmup)
-                idx = wl.sample_targets(n, 512 if R == 1 else 128, 55)
+                # the 16M-point workload is checked on 4096 random targets
+                idx = wl.sample_targets(n, 4096 if name == "c5" else (512 if R == 1 else 128), 55)
                 ff = f if R > 1 else f[:, None]
                 r.update({"n_targets": n, "n_rhs": R, "eps": eps, "path": prec,
                           "tier": ops.plan() if prec == "mixed" else None,
