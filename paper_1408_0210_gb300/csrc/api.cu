@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <atomic>
 #include <mutex>
 #include <set>
@@ -860,10 +861,10 @@ extern "C" eifmm_status eifmm_evaluate_host(eifmm_tree* tree, const eifmm_ops* o
 // The batch is recorded once into a CUDA graph (after one direct pass that
 // sizes every workspace) and replayed by a single cudaGraphLaunch while the
 // same trees, operators, precision and array pointers are passed again.  The
-// problems run on kBranches parallel branches (problem p on branch p mod
-// kBranches), each tree on its own workspace and streams and the operators
-// only read, so the many small launches of uneven problems overlap instead
-// of following one another.
+// problems run on kBranches parallel branches (balanced by an estimated
+// cost, below), each tree on its own workspace and streams and the
+// operators only read, so the many small launches of uneven problems
+// overlap instead of following one another.
 constexpr int kBranches = 8;
 namespace {
 struct BatchGraph {
@@ -944,16 +945,43 @@ extern "C" eifmm_status eifmm_evaluate_batched(eifmm_tree* const* trees, const d
     }
     g_batch.dev = dev;
   }
-  // every problem on its branch; the branches fork from and join into s
+  // every problem on a branch: largest estimated cost first, each to the
+  // branch with the least cost so far (longest-processing-time order), so
+  // that the few deep problems of an uneven batch do not share a branch.
+  // Cost: the leaf-level M2L (boxes x d^2) plus the near field (points x
+  // 27 leaves' points).
+  const int K = n_problems < kBranches ? (n_problems > 0 ? n_problems : 1) : kBranches;
+  std::vector<int> order(n_problems), branch(n_problems, 0);
+  {
+    std::vector<double> cost(n_problems);
+    for (int p = 0; p < n_problems; ++p) {
+      const Tree& t = trees[p]->t;
+      const double boxes = std::ldexp(1.0, 3 * t.depth);
+      const double dl = t.depth <= ops->o.depth ? ops->o.lv[t.depth].d : 1.0;
+      const double per_leaf = (double)t.src.n / boxes;
+      cost[p] = boxes * dl * dl + (double)t.tgt.n * 27.0 * per_leaf;
+      order[p] = p;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    double load[kBranches] = {};
+    for (int p : order) {
+      int b = 0;
+      for (int c = 1; c < K; ++c)
+        if (load[c] < load[b]) b = c;
+      branch[p] = b;
+      load[b] += cost[p];
+    }
+  }
+  // the branches fork from and join into s
   auto run_all = [&]() -> eifmm_status {
-    const int K = n_problems < kBranches ? (n_problems > 0 ? n_problems : 1) : kBranches;
     EIFMM_CUDA(cudaEventRecord(g_batch.fork, s));
     for (int b = 0; b < K; ++b) EIFMM_CUDA(cudaStreamWaitEvent(g_batch.br[b], g_batch.fork, 0));
     eifmm_status rc = EIFMM_OK;
-    for (int p = 0; p < n_problems && rc == EIFMM_OK; ++p) {
+    for (int i = 0; i < n_problems && rc == EIFMM_OK; ++i) {
+      const int p = order[i];
       if (trees[p]->t.tgt.n == 0) continue;
       rc = evaluate_impl(trees[p], ops, sigma[p], trees[p]->t.src.n, 1, f[p], trees[p]->t.tgt.n, (int)prec,
-                         g_batch.br[p % K]);
+                         g_batch.br[branch[p]]);
     }
     for (int b = 0; b < K; ++b) {  // joined also after a failure
       cudaEventRecord(g_batch.join[b], g_batch.br[b]);
