@@ -179,7 +179,11 @@ __device__ __forceinline__ void df_split(double x, float& h, float& l) {
   l = (float)(x - (double)h);
 }
 
-__global__ void __launch_bounds__(DF_THREADS, 2)
+// Three CTAs per SM (80 registers; small spills outside the inner loop):
+// the leaf level at 2^20 points, eps 1e-6, took 131 ms with two (128
+// registers), 122 ms with three, 125 ms with four (64 registers, spills)
+// and 182 ms with one.
+__global__ void __launch_bounds__(DF_THREADS, 3)
 k_m2l_df(int level, int d, int R, const double* __restrict__ kdT, const int* __restrict__ slot_lists,
          const double* __restrict__ W, double* __restrict__ g, int groups, int64_t part_stride) {
   __shared__ __align__(16) float sWh[DF_L][DF_BOX], sWl[DF_L][DF_BOX];  // [l][box]
