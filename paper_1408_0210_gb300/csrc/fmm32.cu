@@ -439,9 +439,10 @@ k_p2p32(int kern_rt, const int32_t* __restrict__ leaves, const int32_t* __restri
 // than 32 remain, then the rest, so that the lanes stay busy.  Per pair of
 // sources the distance is 3 packed differences and 3 packed multiply-adds
 // (add/mul/fma.rn.f32x2, operands straight from the shared loads); 1/r is
-// the approximate reciprocal square root on each half, with a Newton step
-// and Kahan sums when ACC.  Each half keeps its own FP32 sum over the slice
-// (at most 256 pairs) before a compensated flush.  Only the pairs of the leaf
+// the approximate reciprocal square root on each half.  Each half keeps its
+// own FP32 sum over the slice (at most 256 pairs) before a compensated
+// flush; when ACC, 1/r gets one Newton step and the sum is compensated
+// (Kahan) every NF_KBLOCK pairs.  Only the pairs of the leaf
 // itself test for the self pair, whose sigma is replaced by 0 (and its zero
 // distance by 1).  The slices of a target are added in FP64 in a fixed
 // order.  Staging costs about as much as the arithmetic of one target per
@@ -451,6 +452,7 @@ constexpr int NF_SRC = 1024;               // sources per chunk
 constexpr int NF_MAXS = 32;                // slices per pass
 constexpr float NF_FAR = 1.0e4f;
 constexpr size_t NF_SMEM = NF_SRC * sizeof(float4);  // NF_SRC / 2 pairs of 32 bytes
+constexpr int NF_KBLOCK = 8;               // pairs per plain FP32 block when ACC
 
 // Packed FP32 pairs are float2 values handled by the sm_100 builtins
 // __fadd2_rn / __fmul2_rn / __ffma2_rn (the f32x2 add, mul, fma): the halves
@@ -485,11 +487,39 @@ __device__ __forceinline__ void nf_term(float r2, float sg, float& sa, float& ca
 
 // Pairs [qa, qe) of the staged list; SELF: pair qs, half hs is the target
 // itself.
+// 1/r with one Newton step (ACC)
+__device__ __forceinline__ float nf_rsqrt_newton(float r2) {
+  const float y = rsqrt_approx(r2);
+  return y * fmaf(-0.5f * r2, y * y, 1.5f);
+}
+
 template <bool ACC, bool SELF>
 __device__ __forceinline__ void nf_span(const float4* s_pair, int qa, int qe, int qs, int hs, float2 NX,
                                         float2 NY, float2 NZ, float& sl, float& sh, float& cl, float& ch) {
+  int q = qa;
+  if (ACC) {
+    // blocks of NF_KBLOCK pairs summed in plain FP32, each block added to
+    // the compensated total: the Kahan step once per block instead of once
+    // per term
+    for (; q + NF_KBLOCK <= qe; q += NF_KBLOCK) {
+      float pl = 0.f, ph = 0.f;
+#pragma unroll
+      for (int u = 0; u < NF_KBLOCK; ++u) {
+        float2 sg;
+        float2 r2 = nf_r2(s_pair + 2 * (q + u), NX, NY, NZ, sg);
+        if (SELF && q + u == qs) {  // the self pair: sigma 0 at distance 1
+          if (hs) r2.y = 1.f, sg.y = 0.f;
+          else r2.x = 1.f, sg.x = 0.f;
+        }
+        pl = fmaf(sg.x, nf_rsqrt_newton(r2.x), pl);
+        ph = fmaf(sg.y, nf_rsqrt_newton(r2.y), ph);
+      }
+      kahan_add(sl, cl, pl);
+      kahan_add(sh, ch, ph);
+    }
+  }
 #pragma unroll 8
-  for (int q = qa; q < qe; ++q) {
+  for (; q < qe; ++q) {
     float2 sg;
     float2 r2 = nf_r2(s_pair + 2 * q, NX, NY, NZ, sg);
     if (SELF && q == qs) {  // the self pair: sigma 0 at distance 1
