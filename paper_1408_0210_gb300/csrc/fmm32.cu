@@ -293,10 +293,36 @@ __device__ __forceinline__ void p2p_span(int kern, const float4* __restrict__ sr
         else sa[rr] = fmaf(sg, kv, sa[rr]);
       }
     };
+    // ACC: 8 terms at a time summed in plain FP32, each block added to the
+    // compensated sum (a Kahan step per block instead of per term)
+    auto block8 = [&](int jb8) {
+      float bp[RCT];
+#pragma unroll
+      for (int rr = 0; rr < RCT; ++rr) bp[rr] = 0.f;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = jb8 + u;
+        float4 y;
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(y.x), "=f"(y.y), "=f"(y.z), "=f"(y.w)
+                     : "r"(sbase + 16u * (uint32_t)j));
+        float kv = kern_pt<KERN, ACC>(kern, x0 - y.x, x1 - y.y, x2 - y.z);
+        if (SELF && j == js) kv = 0.f;
+#pragma unroll
+        for (int rr = 0; rr < RCT; ++rr) bp[rr] = fmaf(RCT == 1 ? y.w : ssig[rr * P2P_SRC + j], kv, bp[rr]);
+      }
+#pragma unroll
+      for (int rr = 0; rr < RCT; ++rr) kahan_add(sa[rr], ca[rr], bp[rr]);
+    };
     int j = j0;
     for (; j + 16 <= j1; j += 16) {
+      if (ACC) {
+        block8(j);
+        block8(j + 8);
+      } else {
 #pragma unroll
-      for (int u = 0; u < 16; ++u) term(j + u);
+        for (int u = 0; u < 16; ++u) term(j + u);
+      }
     }
     for (; j < j1; ++j) term(j);
 #pragma unroll
