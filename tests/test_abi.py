@@ -127,3 +127,16 @@ def test_binding_rejects_bad_tensors_before_any_launch(E):
     with pytest.raises(ValueError, match="CUDA"):
         E.check_int32_out(torch.zeros(10, dtype=torch.int32), 10, dev, "perm")
     assert E.eifmm_kernel_launches() == n0
+
+
+def test_tree_options_match_the_header(E):
+    """The binding's option names and numbers are the header's
+    EIFMM_OPT_* enumerators, and the entry point rejects a null tree, an
+    unknown option and a value other than 0 or 1 before any device work."""
+    txt = open(os.path.join(ROOT, "include", "eifmm.h")).read()
+    enum = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"EIFMM_OPT_([A-Z0-9_]+)\s*=\s*(\d+)", txt)}
+    assert enum == E.OPTIONS
+    L = E.lib()
+    for opt in range(len(enum) + 2):
+        assert L.eifmm_tree_set_option(None, opt, 1) == 1
+    assert "unknown option" in L.eifmm_last_error().decode()
