@@ -756,7 +756,8 @@ template <bool ACC>
 __global__ void __launch_bounds__(32 * PT_WARPS, 4)
 k_p2m32x(const int32_t* __restrict__ off, int64_t nleaf, const float* __restrict__ lx,
          const float* __restrict__ ly, const float* __restrict__ lz, const float* __restrict__ sig,
-         const float* __restrict__ X, int d, int dp, float* __restrict__ W) {
+         const float* __restrict__ X, int d, int dp, float* __restrict__ W,
+         __nv_bfloat16* __restrict__ planes, int grid_level) {
   constexpr int NI = PT_MAXQ / 32;
   __shared__ float4 s_xy[PT_MAXQ];
   __shared__ float2 s_z[PT_MAXQ];
@@ -821,6 +822,9 @@ k_p2m32x(const int32_t* __restrict__ off, int64_t nleaf, const float* __restrict
     }
   }
   float* row = W + b * dp;
+  // step 3's BF16 hi/lo planes of the leaf level too, when given (the same
+  // split as k_planes, at the plane row of the box)
+  const int64_t prow = planes ? plane_row(b, grid_level, 1) * dp : 0;
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     const int q = lane + 32 * i;
@@ -829,6 +833,13 @@ k_p2m32x(const int32_t* __restrict__ off, int64_t nleaf, const float* __restrict
       if (2 * q >= d) lo = 0.f;
       if (2 * q + 1 >= d) hi = 0.f;
       *reinterpret_cast<float2*>(row + 2 * q) = make_float2(lo, hi);
+      if (planes) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        const float2 fh = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(lo - fh.x, hi - fh.y);
+        *reinterpret_cast<__nv_bfloat162*>(planes + prow + 2 * q) = h;
+        *reinterpret_cast<__nv_bfloat162*>(planes + nleaf * dp + prow + 2 * q) = l;
+      }
     }
   }
 }
@@ -1712,7 +1723,8 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   const PointSet& S = t->src;
   const PointSet& T = t->tgt;
   record(ws, 0, s);
-  EIFMM_TRY(launch_gather_sigma(sigma, ld_sigma, S, R, ws.sig, ws.sig32, s));
+  // the FP32 tiers read only the FP32 copy of the sorted sigma
+  EIFMM_TRY(launch_gather_sigma(sigma, ld_sigma, S, R, nullptr, ws.sig32, s));
   EIFMM_CUDA(cudaEventRecord(ws.ev_fork, s));
   EIFMM_CUDA(cudaStreamWaitEvent(ws.side, ws.ev_fork, 0));
   // the far field continues on the high-priority stream; the caller's stream
@@ -1759,19 +1771,24 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
 
   // step 1 (every leaf, empty ones get zeros)
   const LevelOps& vl = ops->lv[kap];
+  const bool p2m_x = kern == EIFMM_KERNEL_INV_R && R == 1 && vl.dp <= 2 * PT_MAXQ;
+  // tier 0: the packed P2M also writes the leaf level's BF16 planes (step 3)
+  const bool leaf_planes_in_p2m = p2m_x && ops->tier == 0 && ws.wa[kap] != nullptr;
   {
     const unsigned nb = (unsigned)nboxes(kap);
 #define EIFMM_P2M(K, RC_, A)                                                                   \
   k_p2m32<K, RC_, A><<<nb, TPB, 0, s>>>(kern, S.leaf_off, S.lx, S.ly, S.lz, ws.sig32, S.n, R, vl.X32, \
                                         vl.d, vl.dp, ws.W32[kap])
-    if (kern == EIFMM_KERNEL_INV_R && R == 1 && vl.dp <= 2 * PT_MAXQ) {
+    if (p2m_x) {
       const unsigned g = (unsigned)((nboxes(kap) + PT_WARPS - 1) / PT_WARPS);
+      __nv_bfloat16* lp = leaf_planes_in_p2m ? (__nv_bfloat16*)ws.wa[kap] : nullptr;
+      const int gl = ws.wa_grid[kap] ? kap : -1;
       if (acc)
         k_p2m32x<true><<<g, 32 * PT_WARPS, 0, s>>>(S.leaf_off, nboxes(kap), S.lx, S.ly, S.lz, ws.sig32, vl.X32,
-                                                   vl.d, vl.dp, ws.W32[kap]);
+                                                   vl.d, vl.dp, ws.W32[kap], lp, gl);
       else
         k_p2m32x<false><<<g, 32 * PT_WARPS, 0, s>>>(S.leaf_off, nboxes(kap), S.lx, S.ly, S.lz, ws.sig32, vl.X32,
-                                                    vl.d, vl.dp, ws.W32[kap]);
+                                                    vl.d, vl.dp, ws.W32[kap], lp, gl);
     } else {
       EIFMM_POINT_DISPATCH(EIFMM_P2M);
     }
@@ -1803,6 +1820,7 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     mb.lo = 2;
     mb.hi = kap;
     for (int k = 2; k <= kap; ++k) {
+      if (k == kap && leaf_planes_in_p2m) continue;  // written by the P2M
       const LevelOps& v = ops->lv[k];
       PlaneLevel& L = b.lv[b.nlev++];
       L.in = ws.W32[k]; L.out = ws.wa[k];
@@ -1812,8 +1830,10 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
       mb.w[k] = ws.W32[k];
       mb.n[k] = L.rows * v.dp;
     }
-    const unsigned g = grid_for(b.nq, 256, 152 * 16);
-    if (ops->tier == 1) {
+    const unsigned g = grid_for(b.nq > 0 ? b.nq : 1, 256, 152 * 16);
+    if (b.nq == 0) {
+      // nothing left to split
+    } else if (ops->tier == 1) {
       // the FP16 planes need the largest |W| of every level first
       EIFMM_CUDA(cudaMemsetAsync(ws.wmax, 0, (kMaxLevel + 1) * sizeof(uint32_t), s));
       k_absmax<<<152 * 4, 256, 0, s>>>(mb, ws.wmax);

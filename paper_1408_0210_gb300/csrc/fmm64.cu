@@ -34,7 +34,7 @@ __global__ void k_gather_sigma(const double* __restrict__ sigma, int64_t ld,
   const int64_t i = perm[p];
   for (int r = 0; r < R; ++r) {
     const double v = sigma[i + r * ld];
-    s64[p + r * n] = v;
+    if (s64) s64[p + r * n] = v;
     if (s32) s32[p + r * n] = (float)v;
   }
 }
