@@ -329,8 +329,10 @@ eifmm_status eifmm_tree_sort_static(const double* xyz, int64_t n,
  * levels deeper than the tree are not used) and have the tree's L.  The
  * tree owns the workspace; the first call for a given (ops, n_rhs) allocates
  * it and later calls allocate nothing.  Calls that share a tree must not
- * overlap.  Errors: EINVAL (null, n_rhs < 1 or > 256, ld < n, ops depth
- * below the tree's, L mismatch), ENOMEM, ECUDA. */
+ * overlap.  sigma must be finite: the mixed path's library GEMMs (M2M,
+ * L2L) do not carry infinities or NaNs through, so a non-finite sigma gives
+ * an unspecified f.  Errors: EINVAL (null, n_rhs < 1 or > 256, ld < n, ops
+ * depth below the tree's, L mismatch), ENOMEM, ECUDA. */
 eifmm_status eifmm_evaluate(eifmm_tree* tree, const eifmm_ops* ops,
                             const double* sigma, int64_t ld_sigma, int n_rhs,
                             double* f, int64_t ld_f, eifmm_precision prec,
@@ -367,11 +369,13 @@ eifmm_status eifmm_evaluate_host(eifmm_tree* tree, const eifmm_ops* ops,
  * many-query setting, Section 1; same kernel and L; each tree's depth at
  * most the operators'): problem p evaluates trees[p] with DEVICE sigma[p]
  * and f[p] (one RHS each, ld = n).  The problems run on 8 parallel branches
- * (problem p on branch p mod 8) that fork from and join into `stream`, so
- * the launches of small, uneven problems overlap.  The first call evaluates
- * them directly and records them into a CUDA graph; a later call with the
- * same trees, arrays, operators,
- * precision, tier and stream replays that graph with one launch.  The
+ * that fork from and join into `stream`, so the launches of small, uneven
+ * problems overlap; largest estimated cost first, each problem goes to the
+ * branch with the least estimated cost so far (cost: the leaf level's M2L,
+ * boxes x d^2, plus the near field, targets x 27 x sources per leaf).
+ * The first call evaluates them directly and records them into a CUDA
+ * graph; a later call with the same trees, arrays, operators, precision,
+ * tier and stream replays that graph with one launch.  The
  * library keeps one such graph per process (a call with other arguments
  * records a new one; destroying one of its trees or its operators drops
  * it).  The legacy default stream (NULL) is never captured: every call on it

@@ -62,6 +62,10 @@ cublasHandle_t handle_here() {
       g_failed[dev] = true;
       return nullptr;
     }
+    // the operands are finite (sigma is required finite), so the emulation
+    // needs no scan of its inputs for infinities and NaNs nor the patch
+    // passes that follow one; a library without the switch keeps its default
+    cublasSetEmulationSpecialValuesSupport(g_handle[dev], CUDA_EMULATION_SPECIAL_VALUES_SUPPORT_NONE);
   }
   return g_handle[dev];
 }
