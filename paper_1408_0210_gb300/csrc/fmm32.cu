@@ -757,7 +757,8 @@ __global__ void __launch_bounds__(32 * PT_WARPS, 4)
 k_p2m32x(const int32_t* __restrict__ off, int64_t nleaf, const float* __restrict__ lx,
          const float* __restrict__ ly, const float* __restrict__ lz, const float* __restrict__ sig,
          const float* __restrict__ X, int d, int dp, float* __restrict__ W,
-         __nv_bfloat16* __restrict__ planes, int grid_level) {
+         __nv_bfloat16* __restrict__ planes, int grid_level, const double* __restrict__ sig64,
+         const int32_t* __restrict__ perm) {
   constexpr int NI = PT_MAXQ / 32;
   __shared__ float4 s_xy[PT_MAXQ];
   __shared__ float2 s_z[PT_MAXQ];
@@ -787,7 +788,10 @@ k_p2m32x(const int32_t* __restrict__ off, int64_t nleaf, const float* __restrict
     const int j = j0 + lane;
     __syncwarp();
     if (j < end) {
-      const float px = -lx[j], py = -ly[j], pz = -lz[j], s = sig[j];
+      // sigma in sorted order, or (sig64) read through the permutation from
+      // the caller's FP64 array and rounded as the gather rounds it
+      const float s = sig64 ? (float)sig64[perm[j]] : sig[j];
+      const float px = -lx[j], py = -ly[j], pz = -lz[j];
       s_pt[w][lane][0] = make_float4(px, px, py, py);
       s_pt[w][lane][1] = make_float4(pz, pz, s, s);
     }
@@ -1723,8 +1727,12 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   const PointSet& S = t->src;
   const PointSet& T = t->tgt;
   record(ws, 0, s);
-  // the FP32 tiers read only the FP32 copy of the sorted sigma
-  EIFMM_TRY(launch_gather_sigma(sigma, ld_sigma, S, R, nullptr, ws.sig32, s));
+  const LevelOps& vl = ops->lv[kap];
+  const bool p2m_x = kern == EIFMM_KERNEL_INV_R && R == 1 && vl.dp <= 2 * PT_MAXQ;
+  // the FP32 tiers read only the FP32 copy of the sorted sigma.  The packed
+  // P2M reads sigma through the permutation itself, so there only the near
+  // field waits for the copy (it is made on the near field's stream)
+  if (!p2m_x) EIFMM_TRY(launch_gather_sigma(sigma, ld_sigma, S, R, nullptr, ws.sig32, s));
   EIFMM_CUDA(cudaEventRecord(ws.ev_fork, s));
   EIFMM_CUDA(cudaStreamWaitEvent(ws.side, ws.ev_fork, 0));
   // the far field continues on the high-priority stream; the caller's stream
@@ -1756,6 +1764,7 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
       cudaStreamWaitEvent(caller, w.ev_hi, 0);
     }
   } guard{ws, caller};
+  if (p2m_x) EIFMM_TRY(launch_gather_sigma(sigma, ld_sigma, S, R, nullptr, ws.sig32, nf_stream));
   const bool p2p_sym = use_p2p_sym(t, R, ops->tier >= 1, ws.gsym);
   auto near_field = [&]() -> eifmm_status {
     if (timing_enabled()) cudaEventRecord(ws.ev_nf[0], nf_stream);
@@ -1770,8 +1779,6 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
   if (!nf_late) EIFMM_TRY(near_field());
 
   // step 1 (every leaf, empty ones get zeros)
-  const LevelOps& vl = ops->lv[kap];
-  const bool p2m_x = kern == EIFMM_KERNEL_INV_R && R == 1 && vl.dp <= 2 * PT_MAXQ;
   // tier 0: the packed P2M also writes the leaf level's BF16 planes (step 3)
   const bool leaf_planes_in_p2m = p2m_x && ops->tier == 0 && ws.wa[kap] != nullptr;
   {
@@ -1785,10 +1792,10 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
       const int gl = ws.wa_grid[kap] ? kap : -1;
       if (acc)
         k_p2m32x<true><<<g, 32 * PT_WARPS, 0, s>>>(S.leaf_off, nboxes(kap), S.lx, S.ly, S.lz, ws.sig32, vl.X32,
-                                                   vl.d, vl.dp, ws.W32[kap], lp, gl);
+                                                   vl.d, vl.dp, ws.W32[kap], lp, gl, sigma, S.perm);
       else
         k_p2m32x<false><<<g, 32 * PT_WARPS, 0, s>>>(S.leaf_off, nboxes(kap), S.lx, S.ly, S.lz, ws.sig32, vl.X32,
-                                                    vl.d, vl.dp, ws.W32[kap], lp, gl);
+                                                    vl.d, vl.dp, ws.W32[kap], lp, gl, sigma, S.perm);
     } else {
       EIFMM_POINT_DISPATCH(EIFMM_P2M);
     }
