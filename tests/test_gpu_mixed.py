@@ -444,21 +444,26 @@ def test_stream_layout_does_not_change_the_result(E):
     and the coarse M2L levels on a second stream: every sum has a fixed
     order, so the result is bitwise the same as with everything on the
     caller's stream (option single_stream), with the near field started at
-    the M2L (option near_field_late) and across repeated calls."""
+    the M2L (option near_field_late) and across repeated calls.  Two sigma
+    vectors alternate, so a stream that read the previous call's sorted
+    sigma would show."""
     n, depth = 200000, 4
     x = wl.uniform_cube(n, 91)
-    s = wl.sigma_uniform(n, 1, 92)
+    s = wl.sigma_uniform(n, 2, 92)
     ops = E.eifmm_ops_build("inv_r", 1.0, depth, 1e-4)
     tree = E.eifmm_tree_build(dev(x), None, (0, 0, 0), 1.0, depth, True)
-    out = []
+    out = {0: [], 1: []}
     for single, late in ((False, False), (True, False), (False, True), (False, False)):
         tree.set_option("single_stream", single)
         tree.set_option("near_field_late", late)
-        f = torch.zeros(n, dtype=torch.float64, device="cuda")
-        E.eifmm_evaluate(tree, ops, dev(s[:, 0]), f, "mixed")
-        torch.cuda.synchronize()
-        out.append(f)
-    assert all(torch.equal(out[0], o) for o in out[1:])
+        for c in (0, 1):
+            f = torch.zeros(n, dtype=torch.float64, device="cuda")
+            E.eifmm_evaluate(tree, ops, dev(s[:, c]), f, "mixed")
+            out[c].append(f)
+    torch.cuda.synchronize()
+    for c in (0, 1):
+        assert all(torch.equal(out[c][0], o) for o in out[c][1:])
+    assert not torch.equal(out[0][0], out[1][0])
 
 
 def test_tier3_pair_arithmetic_m2l(E):
