@@ -71,6 +71,8 @@ void free_workspace(Workspace* ws) {
   dfree(ws->part64);
   ws->part64 = nullptr;
   ws->part64_cap = 0;
+  dfree(ws->blas_ws);
+  ws->blas_ws = nullptr;
   for (int k = 0; k <= kMaxLevel; ++k) ws->m2l_kind[k] = ws->m2l_gshift[k] = 0;
   ws->p2p_sym = 0;
   free_sk_plan(&ws->sk);

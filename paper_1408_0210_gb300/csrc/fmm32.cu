@@ -1338,6 +1338,7 @@ eifmm_status alloc_mixed_workspace(Tree* t, const Ops* ops, int R) {
     }
   }
   EIFMM_TRY(dalloc(&ws.lh32, (size_t)nboxes(kap) * R * ops->lv[kap].dp));
+  if (!ws.blas_ws) EIFMM_TRY(dmalloc(&ws.blas_ws, kXferBlasWorkspace));
   {
     int dev = 0, nsm = 148;
     cudaGetDevice(&dev);
@@ -1813,7 +1814,7 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     x.ncol = nboxes(k) * R;
     x.A = a.m2m32; x.B = ws.W32[k + 1]; x.G = nullptr; x.C = ws.W32[k];
     x.P8 = (float*)ws.tmp;  // 8 x nboxes(k) x R x dp floats fit in the scratch
-    if (!xfer_blas(true, a, c, nboxes(k), R, ws.W32[k + 1], nullptr, ws.W32[k], s))
+    if (!xfer_blas(true, a, c, nboxes(k), R, ws.W32[k + 1], nullptr, ws.W32[k], ws.blas_ws, s))
       EIFMM_TRY(launch_xfer_gemm(x, s));
   }
   record(ws, 2, s);
@@ -1897,7 +1898,7 @@ eifmm_status eval_mixed(Tree* t, const Ops* ops, const double* sigma, int64_t ld
     x.ncol = nboxes(k - 1) * R;
     x.A = v.l2l32; x.B = ws.l32[k - 1]; x.G = ws.g32[k]; x.C = ws.l32[k];
     x.P8 = nullptr;
-    if (!xfer_blas(false, v, pv, nboxes(k - 1), R, ws.l32[k - 1], ws.g32[k], ws.l32[k], s))
+    if (!xfer_blas(false, v, pv, nboxes(k - 1), R, ws.l32[k - 1], ws.g32[k], ws.l32[k], ws.blas_ws, s))
       EIFMM_TRY(launch_xfer_gemm(x, s));
   }
   record(ws, 5, s);

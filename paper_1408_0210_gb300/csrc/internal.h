@@ -182,6 +182,7 @@ struct Workspace {
   int* err = nullptr;           // device error word of bounded waits
   int* err_host = nullptr;      // pinned copy, read at the next call
   void* tmp = nullptr;          // intermediate of the two Delta sweeps
+  void* blas_ws = nullptr;      // the library GEMMs' workspace of this tree (kXferBlasWorkspace bytes)
   double* sig = nullptr;        // sorted sigma, n_src x R (col-major, ld n_src)
   float* sig32 = nullptr;
   double* fnear = nullptr;      // n_tgt x R, sorted order
@@ -242,8 +243,12 @@ eifmm_status build_kd32(Ops* ops, cudaStream_t s);
 // M2M / L2L as library GEMMs (xfer_blas.cu): one per level with one right-hand
 // side, 8 strided-batched ones per level with several
 eifmm_status build_xfer_blas(Ops* ops, cudaStream_t s);
+// wsp: the calling tree's workspace for the library (kXferBlasWorkspace
+// bytes), so that the GEMMs of trees evaluated on concurrent streams never
+// share one; null: the per-device one
+constexpr size_t kXferBlasWorkspace = 32u << 20;
 bool xfer_blas(bool m2m, const LevelOps& out, const LevelOps& in, int64_t n_par, int R, const float* B,
-               const float* G, float* C, cudaStream_t s);
+               const float* G, float* C, void* wsp, cudaStream_t s);
 // M2L compression (sarcmp.cu): eps <= 0 removes it.
 eifmm_status compress_ops(Ops* ops, double eps, cudaStream_t s);
 void free_compression(LevelOps& v);

@@ -23,7 +23,7 @@ namespace eifmm {
 namespace {
 
 constexpr int kMaxDev = 64;
-constexpr size_t kBlasWorkspace = 32u << 20;  // set up front: no allocation inside a capture
+constexpr size_t kBlasWorkspace = kXferBlasWorkspace;  // set up front: no allocation inside a capture
 cublasHandle_t g_handle[kMaxDev] = {};
 void* g_ws[kMaxDev] = {};
 bool g_failed[kMaxDev] = {};
@@ -70,6 +70,16 @@ cublasHandle_t handle_here() {
   return g_handle[dev];
 }
 
+// the handle on stream s with the workspace wsp (else the device's own):
+// kernels of the library that run at the same time on different streams
+// must not share a workspace
+bool bind(cublasHandle_t h, void* wsp, cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return false;
+  return cublasSetStream(h, s) == CUBLAS_STATUS_SUCCESS &&
+         cublasSetWorkspace(h, wsp ? wsp : g_ws[dev], kBlasWorkspace) == CUBLAS_STATUS_SUCCESS;
+}
+
 }  // namespace
 
 eifmm_status build_xfer_blas(Ops* ops, cudaStream_t s) {
@@ -102,14 +112,14 @@ constexpr int64_t kBatchedMinParents = 512;
 bool g_batched_failed[kMaxDev] = {};
 
 bool xfer_blas_rhs(bool m2m, const LevelOps& out, const LevelOps& in, int64_t n_par, int R, const float* B,
-                   const float* G, float* C, cudaStream_t s) {
+                   const float* G, float* C, void* wsp, cudaStream_t s) {
   const float* A = m2m ? out.m2m_cb : out.l2l_cb;
   if (!A || n_par < kBatchedMinParents || n_par > 2147483647LL || R < 2) return false;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev || g_batched_failed[dev]) return false;
   std::lock_guard<std::mutex> lk(g_mu);
   cublasHandle_t h = handle_here();
-  if (!h || cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return false;
+  if (!h || !bind(h, wsp, s)) return false;
   const float one = 1.f, zero = 0.f;
   const int dk = out.dp, dc = in.dp;
   const int n = (int)n_par;
@@ -141,13 +151,13 @@ bool xfer_blas_rhs(bool m2m, const LevelOps& out, const LevelOps& in, int64_t n_
 
 // true when the library took the step; false: the caller runs its own kernel
 bool xfer_blas(bool m2m, const LevelOps& out, const LevelOps& in, int64_t n_par, int R, const float* B,
-               const float* G, float* C, cudaStream_t s) {
-  if (R > 1) return xfer_blas_rhs(m2m, out, in, n_par, R, B, G, C, s);
+               const float* G, float* C, void* wsp, cudaStream_t s) {
+  if (R > 1) return xfer_blas_rhs(m2m, out, in, n_par, R, B, G, C, wsp, s);
   const float* A = m2m ? out.m2m_cb : out.l2l_cb;
   if (!A || n_par <= 0 || n_par > 2147483647LL) return false;
   std::lock_guard<std::mutex> lk(g_mu);
   cublasHandle_t h = handle_here();
-  if (!h || cublasSetStream(h, s) != CUBLAS_STATUS_SUCCESS) return false;
+  if (!h || !bind(h, wsp, s)) return false;
   const float one = 1.f, zero = 0.f;
   cublasStatus_t st;
   if (m2m) {
