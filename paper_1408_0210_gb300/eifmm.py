@@ -313,7 +313,9 @@ def eifmm_tree_build(src_xyz, tgt_xyz=None, lo=(0.0, 0.0, 0.0), L: float = 1.0, 
 
 def eifmm_evaluate(tree: Tree, ops: Ops, sigma, f, prec="fp64", stream=None) -> None:
     """sigma (n_src, R) and f (n_tgt, R): CUDA float64 tensors, column-major
-    (use ``t.T.contiguous().T`` or allocate as ``torch.empty(R, n).T``)."""
+    (use ``t.T.contiguous().T`` or allocate as ``torch.empty(R, n).T``).
+    sigma must be finite: the mixed path's M2M/L2L library GEMMs do not carry
+    infinities or NaNs through."""
     import torch
     for name, t, n in (("sigma", sigma, tree.n_src), ("f", f, tree.n_tgt)):
         if not isinstance(t, torch.Tensor) or t.dtype != torch.float64 or not t.is_cuda:
