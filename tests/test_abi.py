@@ -140,3 +140,17 @@ def test_tree_options_match_the_header(E):
     for opt in range(len(enum) + 2):
         assert L.eifmm_tree_set_option(None, opt, 1) == 1
     assert "unknown option" in L.eifmm_last_error().decode()
+
+
+def test_binding_constants_match_the_header(E):
+    """The binding's kernel, precision and status numbers and the static
+    sort's point limit are the header's enumerators and define."""
+    txt = open(os.path.join(ROOT, "include", "eifmm.h")).read()
+    kern = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"EIFMM_KERNEL_([A-Z0-9_]+)\s*=\s*(\d+)", txt)}
+    assert kern == E.KERNELS
+    prec = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"EIFMM_PREC_([A-Z0-9_]+)\s*=\s*(\d+)", txt)}
+    assert prec == E.PREC
+    status = {int(m.group(2)): m.group(1) for m in re.finditer(r"EIFMM_(OK|E[A-Z]+)\s*=\s*(\d+)", txt)}
+    assert status == E.STATUS
+    lim = re.search(r"#define EIFMM_STATIC_SORT_MAX_POINTS (\d+)", txt)
+    assert int(lim.group(1)) == E.STATIC_SORT_MAX_POINTS
